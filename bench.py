@@ -1,0 +1,444 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 monopole + quadrupole tree-force hot path.
+
+One step = one qg_run over every sink group of the workload: device work-queue
+build, then the persistent force kernel (FP64 group centring, list staging,
+FP32 particle and cell loops, FP64 merges, outputs).  Inputs are resident in
+HBM before the timed region; the L2 is flushed (a 256 MiB device write)
+before every timed step and the flush is outside the per-step event pairs.
+
+Printed (rank 0, one JSON line): interactions/s (particle-particle +
+particle-cell), ms per step, the roofline of the force kernel (FP32 issue
+bound), the FP64 oracle as a CPU baseline, an end-to-end number through the
+C-ABI with host buffers, the clocks seen during the timed region, and the
+quadrupole-vs-monopole force time at equal 99th-percentile force error.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "interactions/s; force time/step quad vs mono-only at equal 99th-pct force error"
+UNIT = "interactions/s"
+FLUSH_BYTES = 256 << 20
+DESCR = {
+    "cube_1m": "2^20 equal-mass particles uniform in the unit cube, eps=1/(20 N^(1/3)), leaf<=8, "
+               "n_crit=256, quadrupole cells",
+    "sphere_4k": "4096 particles uniform in the unit sphere, eps=1e-2, leaf<=8, n_crit=64",
+    "plummer_4m": "2^22-particle Plummer sphere (a=1, r<=100), eps=1e-3, leaf<=8, n_crit=256",
+    "batched_512": "512 independent Plummer/Hernquist systems, N log-uniform in [1024, 65536], eps=1e-2, "
+                   "n_crit=64, one persistent launch",
+    "clumpy_16m": "2^24 particles in the unit cube, 70% in 2000 Plummer clumps + 30% uniform, eps=5e-5, "
+                  "n_crit=256",
+}
+# Algorithmic FP32 instructions per interaction (FMA = 1), see the design doc
+OPS_QUAD, OPS_MONO = 33, 13
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="cube_1m")
+    ap.add_argument("--theta", type=float, default=None)
+    ap.add_argument("--no-equal-error", action="store_true", help="skip the monopole equal-error search")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="qg_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = np.array([float(r[1]) for r in rows if r[1].replace(".", "").isdigit()])
+        smax = float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if len(sm) else None, "sm_max_mhz": smax,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ---------------------------------------------------------------- helpers
+
+def build_case(name, theta):
+    from paper_1812_07313_gb300 import tree as qtree
+    from paper_1812_07313_gb300 import workloads
+    wl = workloads.WORKLOADS[name]
+    ps = wl.particles()
+    t0 = time.perf_counter()
+    tr = qtree.Tree(ps.x, ps.m, ps.sys_off, wl.leaf_max, wl.n_crit)
+    t1 = time.perf_counter()
+    L = tr.walk(wl.theta if theta is None else theta)
+    t2 = time.perf_counter()
+    eps2 = None
+    eps2_all = float(ps.eps[0]) ** 2
+    if ps.nsys > 1 and len(set(ps.eps.tolist())) > 1:
+        eps2 = (ps.eps[tr.sink_sys] ** 2).astype(np.float32)
+        eps2_all = 0.0
+    return wl, ps, tr, L, eps2_all, eps2, {"construct_s": t1 - t0, "traverse_s": t2 - t1}
+
+
+def load_ctx(ctx, tr, L, eps2_all, eps2):
+    ctx.qg_set_sinks(tr.x, tr.group_off, eps2_all, eps2)
+    ctx.qg_set_sources(tr.x, tr.m, L.plist_off, L.plist_idx)
+    ctx.qg_set_cells(tr.cell_com, tr.cell_m, tr.cell_q, L.clist_off, L.clist_idx)
+
+
+def timed_steps(torch, ctx, stream, flush, steps):
+    """Per step: L2 flush (untimed), then events around qg_run; the force
+    kernel's own time comes from the events inside the step's graph."""
+    step_ms, force_ms = [], []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.add_(1)
+            e0.record(stream)
+            ctx.qg_run(stream.cuda_stream)
+            e1.record(stream)
+        _, f = ctx.qg_last_timing()  # synchronises the stream
+        step_ms.append(e0.elapsed_time(e1))
+        force_ms.append(f)
+    return np.array(step_ms), np.array(force_ms)
+
+
+def oracle_sample(tr, L, eps2_all, eps2, seconds, seed=0):
+    """Groups in seeded random order until the oracle has about `seconds` of work."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    order = rng.permutation(tr.ngroups)
+    ni = np.diff(tr.group_off)
+    work = ni * (np.diff(L.plist_off) + np.diff(L.clist_off))
+    # calibrate the oracle's rate on a few groups first
+    probe = order[:8]
+    t0 = time.perf_counter()
+    oracle.expansion_forces(tr.group_off, tr.x, tr.x, tr.m, L.plist_off, L.plist_idx, tr.cell_com, tr.cell_m,
+                            tr.cell_q, L.clist_off, L.clist_idx, eps2_all=eps2_all,
+                            sink_eps2=None if eps2 is None else eps2.astype(np.float64), groups=probe)
+    rate = max(work[probe].sum(), 1) / max(time.perf_counter() - t0, 1e-6)
+    target = rate * seconds
+    k = int(np.searchsorted(np.cumsum(work[order]), target)) + 1
+    return order[:max(k, 1)], work
+
+
+def run_oracle(tr, L, eps2_all, eps2, groups):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.expansion_forces(tr.group_off, tr.x, tr.x, tr.m, L.plist_off, L.plist_idx, tr.cell_com, tr.cell_m,
+                            tr.cell_q, L.clist_off, L.clist_idx, eps2_all=eps2_all,
+                            sink_eps2=None if eps2 is None else eps2.astype(np.float64), groups=groups)
+    return time.perf_counter() - t0
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    """The FP64 oracle as it stands, single-threaded on the host, on bounded
+    samples of the same workload (rank 0 only)."""
+    if rank != 0:
+        return
+    wl, ps, tr, L, eps2_all, eps2, _ = build_case(args.workload, args.theta)
+    per_step = max(1.0, 150.0 / max(args.steps + args.warmup, 1))
+    total_int, total_t = 0, 0.0
+    for s in range(args.warmup + args.steps):
+        groups, work = oracle_sample(tr, L, eps2_all, eps2, per_step, seed=1000 + s)
+        dt = run_oracle(tr, L, eps2_all, eps2, groups)
+        if s >= args.warmup:
+            total_int += int(work[groups].sum())
+            total_t += dt
+    value = total_int / total_t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / max(args.steps, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "%s: %s" % (args.workload, DESCR.get(args.workload, "")),
+                      "theta": L.theta, "sample": "seeded random groups, ~%.0f s of oracle work per step" % per_step},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "%d steps of seeded random group samples, %d interactions in total"
+                                      % (args.steps, total_int)},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------- our arm
+
+def equal_error(torch, qgrav, tr, L_quad, eps2_all, eps2, a_quad, wl_name, theta_q, rank, flush, stream, steps):
+    """theta_mono with p99 (Eq. 9, vs FP64 direct summation on 4096 seeded
+    sinks) no larger than the quadrupole's at theta_q; then time monopole-only
+    steps at that theta."""
+    rng = np.random.default_rng(12345)
+    ns = min(4096, tr.n)
+    sample = np.sort(rng.choice(tr.n, ns, replace=False))
+    dev = torch.device("cuda")
+    xs = torch.as_tensor(tr.x[sample]).to(dev)
+    a_d = torch.empty((ns, 3), dtype=torch.float64, device=dev)
+    p_d = torch.empty(ns, dtype=torch.float64, device=dev)
+    # systems are independent: direct sums per system
+    sys_of = tr.sink_sys[sample]
+    a_dir = np.empty((ns, 3))
+    for s in np.unique(sys_of):
+        sel = np.nonzero(sys_of == s)[0]
+        b, e = tr.sys_off[s], tr.sys_off[s + 1]
+        qgrav.qg_direct_dev(xs[sel].contiguous(), torch.as_tensor(tr.x[b:e]).to(dev),
+                            torch.as_tensor(tr.m[b:e]).to(dev), eps2_all, a_d[:len(sel)], p_d[:len(sel)])
+        a_dir[sel] = a_d[:len(sel)].cpu().numpy()
+
+    def p99(a):
+        e = np.linalg.norm(a[sample] - a_dir, axis=1) / np.linalg.norm(a_dir, axis=1)
+        return float(np.percentile(e, 99))
+
+    target = p99(a_quad)
+    ctx = qgrav.Context(torch.cuda.current_device(), qgrav.Options(expansion=qgrav.QG_MONO))
+    cache = {}
+
+    def mono_at(th):
+        th = round(th, 4)
+        if th not in cache:
+            L = tr.walk(th)
+            load_ctx(ctx, tr, L, eps2_all, eps2)
+            ctx.qg_run()
+            a, _ = ctx.qg_get_forces()
+            cache[th] = (p99(a), L)
+        return cache[th]
+
+    lo, hi = 0.2, theta_q
+    if mono_at(lo)[0] > target:
+        th_m = lo
+    else:
+        for _ in range(7):
+            mid = 0.5 * (lo + hi)
+            if mono_at(mid)[0] <= target:
+                lo = mid
+            else:
+                hi = mid
+        th_m = lo
+    p_m, L_m = mono_at(th_m)
+    load_ctx(ctx, tr, L_m, eps2_all, eps2)
+    for _ in range(3):
+        ctx.qg_run(stream.cuda_stream)
+    torch.cuda.synchronize()
+    ms, force = timed_steps(torch, ctx, stream, flush, steps)
+    st = ctx.qg_get_stats()
+    ctx.close()
+    return {"theta_quad": theta_q, "p99_quad": target, "theta_mono": th_m, "p99_mono": p_m,
+            "mono_ms_per_step": float(ms.mean()), "mono_interactions": int(st["i_pp"] + st["i_pc"]),
+            "error_sample": "FP64 GPU direct summation on %d seeded sinks" % ns}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1812_07313_gb300 import qgrav
+
+    torch.cuda.set_device(local_rank)
+    qgrav.lib()
+    wl, ps, tr, L, eps2_all, eps2, host_times = build_case(args.workload, args.theta)
+    theta = L.theta
+    dev = torch.cuda.current_device()
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    ctx = qgrav.Context(dev)
+    load_ctx(ctx, tr, L, eps2_all, eps2)
+    st = ctx.qg_get_stats()
+    i_pp, i_pc = int(st["i_pp"]), int(st["i_pc"])
+    inter = i_pp + i_pc
+    stream = torch.cuda.Stream()
+    flush = torch.zeros(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 0)):
+        ctx.qg_run(stream.cuda_stream)
+    torch.cuda.synchronize()
+    a_quad, _ = ctx.qg_get_forces()
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    t_wall0 = time.perf_counter()
+    step_ms, force_ms = timed_steps(torch, ctx, stream, flush, args.steps)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * args.steps * inter / (total_ms * 1e-3)
+
+    # roofline of the force kernel: FP32 issue bound (lane instructions, FMA = 1)
+    alg = OPS_QUAD * i_pc + OPS_MONO * i_pp
+    f_mean = float(force_ms.mean()) * 1e-3
+    achieved = alg / f_mean / 1e12
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
+    peak_max = n_sm * 128 * 2070e6 / 1e12
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                tj = json.load(f)
+            if tj.get("workload") == args.workload and tj.get("kernel_hash") == _kernel_hash():
+                traffic = tj.get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
+                "traffic": traffic,
+                "peak_basis": "FP32 lane-instructions/s = %d SMs x 128 x median SM clock %.0f MHz under load "
+                              "(at the 2070 MHz maximum: %.1f Tinst/s, frac %.3f)"
+                              % (n_sm, sm_mhz, peak_max, achieved / peak_max),
+                "kernel": "force_kernel<float,R=4,quad>", "force_kernel_ms": float(force_ms.mean())}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "%s: %s" % (args.workload, DESCR.get(args.workload, "")),
+                      "theta": theta, "expansion": "quad", "precision": "fp32, fp64 centring and merges",
+                      "interactions": {"i_pp": i_pp, "i_pc": i_pc}, "groups": tr.ngroups,
+                      "l2": "flushed before every timed step (256 MiB device write, outside the step events)",
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "host_tree_s": host_times},
+           "roofline": roofline, "gpu_launches": 3 * args.steps, "clocks": clocks,
+           "wall_s_timed_loop": t_wall}
+
+    if rank == 0 and not args.no_equal_error and eps2 is None:
+        out["equal_error"] = equal_error(torch, qgrav, tr, L, eps2_all, eps2, a_quad, args.workload, theta,
+                                         rank, flush, stream, max(5, args.steps // 2))
+        out["equal_error"]["quad_ms_per_step"] = total_ms / args.steps
+        out["gpu_launches"] += 3 * max(5, args.steps // 2)
+
+    # end to end through the C-ABI with host buffers (pinned), every step
+    out["e2e"] = e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        groups, work = oracle_sample(tr, L, eps2_all, eps2, args.cpu_seconds)
+        dt = run_oracle(tr, L, eps2_all, eps2, groups)
+        out["cpu_baseline"] = {"value": float(work[groups].sum() / dt), "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": "%d of %d groups in seeded random order, %d interactions, %.1f s"
+                                         % (len(groups), tr.ngroups, int(work[groups].sum()), dt)}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world, steps=3):
+    tdt = {np.dtype("float64"): torch.float64, np.dtype("int64"): torch.int64,
+           np.dtype("int32"): torch.int32, np.dtype("float32"): torch.float32}
+
+    def pin(a):
+        """A page-locked host copy of a (numpy view of a pinned torch tensor)."""
+        t = torch.empty(a.shape, dtype=tdt[a.dtype], pin_memory=True)
+        v = t.numpy()
+        v[...] = a
+        return v
+    x, m, goff = pin(tr.x), pin(tr.m), pin(tr.group_off)
+    po, pi, co, ci = pin(L.plist_off), pin(L.plist_idx), pin(L.clist_off), pin(L.clist_idx)
+    com, cm, cq = pin(tr.cell_com), pin(tr.cell_m), pin(tr.cell_q)
+    e = None if eps2 is None else pin(eps2)
+    a_out, p_out = pin(np.empty((tr.n, 3))), pin(np.empty(tr.n))
+    h2d = sum(v.nbytes for v in (x, goff, x, m, po, pi, com, cm, cq, co, ci)) + (0 if e is None else e.nbytes)
+    d2h = a_out.nbytes + p_out.nbytes
+    ctx = qgrav.Context(torch.cuda.current_device())
+
+    def step():
+        ctx.qg_set_sinks(x, goff, eps2_all, e)
+        ctx.qg_set_sources(x, m, po, pi)
+        ctx.qg_set_cells(com, cm, cq, co, ci)
+        ctx.qg_run()
+        ctx.qg_get_forces(a_out, p_out)
+
+    step()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = (time.perf_counter() - t0) / steps
+    ctx.close()
+    return {"value": world * inter / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": dt * 1e3, "api": "qg_set_sinks/qg_set_sources/qg_set_cells (host, pinned) + qg_run + "
+                                            "qg_get_forces, wall clock"}
+
+
+def _kernel_hash():
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("qg_force.cuh", "qg_force_f32.cu", "qg_api.cu"):
+        with open(os.path.join(ROOT, "paper_1812_07313_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

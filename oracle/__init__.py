@@ -71,6 +71,45 @@ def _load():
     return _lib
 
 
+class use_library:
+    """Context manager: route every oracle call through another build of the
+    oracle source (the mutation tests plant mistakes in copies of it)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        _load()
+        self._saved = _lib
+        lib = ctypes.CDLL(self.path)
+        for name in ("qgo_cell_moments", "qgo_expansion_forces", "qgo_direct_forces"):
+            getattr(lib, name).argtypes = getattr(self._saved, name).argtypes
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+        return False
+
+
+def compile_variant(src_text, out_path):
+    """Compile a (possibly modified) copy of the oracle source to out_path."""
+    c = out_path + ".c"
+    with open(c, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-fno-fast-math", c, "-o", out_path, "-lm"])
+    return out_path
+
+
+def source_text():
+    with open(_SRC) as f:
+        return f.read()
+
+
 def _ptr(a, typ):
     if a is None:
         return ctypes.cast(None, typ)

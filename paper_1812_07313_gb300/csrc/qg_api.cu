@@ -1,0 +1,756 @@
+// qg_api.cu -- the qg_* C-ABI (include/qgrav.h): context, input upload and
+// packing, argument validation, the device work queue and the CUDA graph
+// that one qg_run replays.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qg_internal.h"
+#include "qgrav.h"
+
+namespace {
+
+constexpr int kBuckets = 128;  // cost classes of the work queue (4 per octave)
+
+// ------------------------------------------------------------------ kernels
+
+// sources: [ns][3] + [ns] -> double4_32a (x, y, z, m)
+__global__ void pack_src_kernel(int64_t ns, const double *__restrict__ x, const double *__restrict__ m,
+                                double4_32a *__restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = make_double4_32a(x[3 * i], x[3 * i + 1], x[3 * i + 2], m[i]);
+}
+
+// cells: com [nc][3], m [nc], q [nc][6] -> double4_32a (x, y, z, m), float4 x 2 (Q),
+// and a dense FP64 copy of Q for the all-FP64 kernel.
+__global__ void pack_cells_kernel(int64_t nc, const double *__restrict__ com, const double *__restrict__ m,
+                                  const double *__restrict__ q, double4_32a *__restrict__ xm,
+                                  float4 *__restrict__ qf, double *__restrict__ q64) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc; i += (int64_t)gridDim.x * blockDim.x) {
+    xm[i] = make_double4_32a(com[3 * i], com[3 * i + 1], com[3 * i + 2], m[i]);
+    const double *qi = q + 6 * i;
+    qf[2 * i] = make_float4((float)qi[0], (float)qi[1], (float)qi[2], (float)qi[3]);
+    qf[2 * i + 1] = make_float4((float)qi[4], (float)qi[5], 0.f, 0.f);
+    if (q64 != q)
+      for (int c = 0; c < 6; c++) q64[6 * i + c] = qi[c];
+  }
+}
+
+// Index check of a device list: sets *bad when an entry is outside [0, n).
+__global__ void check_index_kernel(int64_t cnt, const int32_t *__restrict__ idx, int64_t n, int *bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = idx[i];
+    if (v < 0 || (int64_t)v >= n) atomicOr(bad, 1);
+  }
+}
+
+__device__ __forceinline__ int cost_bucket(double cost) {
+  if (!(cost > 1.0)) return 0;
+  const int b = (int)(4.0 * log2(cost));
+  return b < kBuckets ? b : kBuckets - 1;
+}
+
+// Work queue, pass 1: cost class of every group and a histogram of classes.
+// cost = n_i * (13 n_p + c_cell n_c) FP32 ops + staging of the list entries.
+__global__ void queue_hist_kernel(int64_t G, const int64_t *__restrict__ goff, const int64_t *__restrict__ poff,
+                                  const int64_t *__restrict__ coff, double cell_ops, unsigned char *bucket,
+                                  int *hist) {
+  __shared__ int h[kBuckets];
+  for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
+    const double ni = (double)(goff[g + 1] - goff[g]);
+    const double np = (double)(poff[g + 1] - poff[g]);
+    const double nc = (double)(coff[g + 1] - coff[g]);
+    const double cost = ni * (13.0 * np + cell_ops * nc) + 64.0 * (np + nc) + 256.0;
+    const int b = cost_bucket(cost);
+    bucket[g] = (unsigned char)b;
+    atomicAdd(&h[b], 1);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kBuckets; b += blockDim.x)
+    if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+// Work queue, pass 2: groups scattered in descending cost class.
+__global__ void queue_scatter_kernel(int64_t G, const unsigned char *__restrict__ bucket,
+                                     const int *__restrict__ hist, int *cursor, int32_t *queue) {
+  __shared__ int start[kBuckets];
+  for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) {
+    int s = 0;
+    for (int c = b + 1; c < kBuckets; c++) s += hist[c];
+    start[b] = s;
+  }
+  __syncthreads();
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
+    const int b = bucket[g];
+    const int pos = start[b] + atomicAdd(&cursor[b], 1);
+    queue[pos] = (int32_t)g;
+  }
+}
+
+// ------------------------------------------------------------------ buffers
+
+template <typename T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t cap = 0;  // elements
+  cudaError_t reserve(size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e == cudaSuccess) cap = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+}  // namespace
+
+struct qg_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t last_stream = nullptr;
+  qg_options opt{};
+  std::string err;
+
+  // sinks
+  int64_t n = 0, G = -1;
+  bool sinks_ok = false;
+  bool eps_positive = true;  // every sink's eps^2 > 0
+  bool has_eps2 = false;
+  double eps2_all = 0.0;
+  DevBuf<double> sink_x;
+  DevBuf<float> sink_eps2;
+  DevBuf<int64_t> goff;
+  std::vector<int64_t> h_goff;
+  // sources
+  int64_t ns = 0, G_src = -1, np_list = 0;
+  bool src_ok = false;
+  DevBuf<double4_32a> src;
+  DevBuf<double> stage_x, stage_m, stage_q;  // device staging of host inputs
+  DevBuf<int64_t> poff;
+  DevBuf<int32_t> pidx;
+  std::vector<int64_t> h_poff;
+  // cells
+  int64_t nc = 0, G_cell = -1, nc_list = 0;
+  bool cells_ok = false;
+  DevBuf<double4_32a> cell_xm;
+  DevBuf<float4> cell_q;
+  DevBuf<double> cell_q64;
+  DevBuf<int64_t> coff;
+  DevBuf<int32_t> cidx;
+  std::vector<int64_t> h_coff;
+  // outputs and queue
+  DevBuf<double> a, phi;
+  DevBuf<int> scratch;  // hist[kBuckets], cursor[kBuckets], head, bad
+  DevBuf<unsigned char> bucket;
+  DevBuf<int32_t> queue;
+  bool ran = false;  // outputs hold the result of a qg_run for the current sinks
+  // graph, and events recorded inside it (step start, force start/end)
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool graph_valid = false;
+  qg_stats stats{};
+  // chosen launch
+  const void *kernel = nullptr;
+  int R = 4, nthreads = 128, tile = 256, flush = 128, grid = 0;
+  size_t smem = 0;
+};
+
+namespace {
+
+qg_status fail(qg_ctx *c, qg_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define QG_CUDA(ctx, call)                                                                       \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? QG_ERR_NOMEM : QG_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+cudaStream_t pick_stream(qg_ctx *c, void *s) { return s ? (cudaStream_t)s : c->stream; }
+
+void invalidate(qg_ctx *c) {
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  c->exec = nullptr;
+  c->graph_valid = false;
+}
+
+bool valid_options(const qg_options &o, std::string &why) {
+  if (o.precision < QG_FP32_CENTRED || o.precision > QG_FP64) { why = "precision"; return false; }
+  if (o.expansion != QG_QUAD && o.expansion != QG_MONO) { why = "expansion"; return false; }
+  if (o.tile_j && (o.tile_j < 32 || o.tile_j > 1024 || o.tile_j % 32)) { why = "tile_j"; return false; }
+  if (o.warps_per_group && o.warps_per_group != 2 && o.warps_per_group != 4 && o.warps_per_group != 8) {
+    why = "warps_per_group";
+    return false;
+  }
+  if (o.sinks_per_thread && o.sinks_per_thread != 2 && o.sinks_per_thread != 4 && o.sinks_per_thread != 8) {
+    why = "sinks_per_thread";
+    return false;
+  }
+  if (o.flush_j < 0) { why = "flush_j"; return false; }
+  return true;
+}
+
+// Offsets of length G+1: off[0] = 0, non-decreasing, off[G] = total.
+bool valid_offsets(const int64_t *off, int64_t G, int64_t total) {
+  if (off[0] != 0 || off[G] != total) return false;
+  for (int64_t g = 0; g < G; g++)
+    if (off[g + 1] < off[g]) return false;
+  return true;
+}
+
+bool valid_offsets_any_total(const int64_t *off, int64_t G) {
+  if (off[0] != 0) return false;
+  for (int64_t g = 0; g < G; g++)
+    if (off[g + 1] < off[g]) return false;
+  return true;
+}
+
+int grid_for(int64_t n, int block) {
+  int64_t b = (n + block - 1) / block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 4096));
+}
+
+// Stats that depend on every input.
+void update_counts(qg_ctx *c) {
+  c->stats.n_sinks = c->n;
+  c->stats.n_groups = c->G < 0 ? 0 : c->G;
+  c->stats.n_sources = c->ns;
+  c->stats.n_cells = c->nc;
+  c->stats.n_plist = c->np_list;
+  c->stats.n_clist = c->nc_list;
+  int64_t ipp = 0, ipc = 0;
+  if (c->sinks_ok && (int64_t)c->h_goff.size() == c->G + 1) {
+    for (int64_t g = 0; g < c->G; g++) {
+      const int64_t ni = c->h_goff[g + 1] - c->h_goff[g];
+      if (c->src_ok && c->G_src == c->G) ipp += ni * (c->h_poff[g + 1] - c->h_poff[g]);
+      if (c->cells_ok && c->G_cell == c->G) ipc += ni * (c->h_coff[g + 1] - c->h_coff[g]);
+    }
+  }
+  c->stats.i_pp = ipp;
+  c->stats.i_pc = ipc;
+}
+
+qg_status choose_kernel(qg_ctx *c) {
+  const qg_options &o = c->opt;
+  const bool fp64 = o.precision == QG_FP64;
+  const bool quad = o.expansion == QG_QUAD;
+  const bool guard = !c->eps_positive;
+  int R = o.sinks_per_thread ? o.sinks_per_thread : 4;
+  if (fp64) R = 2;
+  int warps = o.warps_per_group ? o.warps_per_group : 4;
+  if (R >= 8 && warps > 4) warps = 4;
+  const int nt = 32 * warps;
+  const void *k = fp64 ? qg::force_kernel_f64(R, quad, guard)
+                       : qg::force_kernel_f32(R, quad, guard, o.precision == QG_FP32_CENTRED);
+  if (!k) return fail(c, QG_ERR_ARG, "no kernel for precision %d, R %d", o.precision, R);
+  const int tile = o.tile_j ? o.tile_j : 256;
+  const size_t smem = qg::force_smem_bytes(fp64, R, nt, tile);
+  QG_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  QG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, smem));
+  if (per_sm < 1) return fail(c, QG_ERR_ARG, "force kernel does not fit on an SM (smem %zu)", smem);
+  c->kernel = k;
+  c->R = R;
+  c->nthreads = nt;
+  c->tile = tile;
+  c->flush = o.flush_j ? o.flush_j : 128;
+  c->smem = smem;
+  c->grid = per_sm * c->num_sms;
+  c->stats.block = nt;
+  c->stats.sinks_per_thread = R;
+  c->stats.tile_j = tile;
+  return QG_OK;
+}
+
+// Record the queue build and the persistent force launch on stream s.
+qg_status record_step(qg_ctx *c, cudaStream_t s) {
+  const int64_t G = c->G;
+  int *hist = c->scratch.p, *cursor = hist + kBuckets, *head = cursor + kBuckets;
+  QG_CUDA(c, cudaEventRecord(c->ev[0], s));
+  QG_CUDA(c, cudaMemsetAsync(hist, 0, (2 * kBuckets + 2) * sizeof(int), s));
+  const double cell_ops = c->opt.expansion == QG_QUAD ? 33.0 : 13.0;
+  queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->goff.p, c->poff.p, c->coff.p, cell_ops,
+                                                      c->bucket.p, hist);
+  QG_CUDA(c, cudaGetLastError());
+  queue_scatter_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->bucket.p, hist, cursor, c->queue.p);
+  QG_CUDA(c, cudaGetLastError());
+  qg::ForceParams p{};
+  p.sink_x = c->sink_x.p;
+  p.sink_eps2 = c->has_eps2 ? c->sink_eps2.p : nullptr;
+  p.eps2_all = c->eps2_all;
+  p.group_off = c->goff.p;
+  p.src = c->src.p;
+  p.plist_off = c->poff.p;
+  p.plist_idx = c->pidx.p;
+  p.cell_xm = c->cell_xm.p;
+  p.cell_q = c->cell_q.p;
+  p.cell_q64 = c->cell_q64.p;
+  p.clist_off = c->coff.p;
+  p.clist_idx = c->cidx.p;
+  p.queue = c->queue.p;
+  p.nitems = (int32_t)G;
+  p.head = head;
+  p.a = c->a.p;
+  p.phi = c->phi.p;
+  p.tile = c->tile;
+  p.flush_j = c->flush;
+  const int grid = (int)std::min<int64_t>(c->grid, std::max<int64_t>(G, 1));
+  c->stats.grid = grid;
+  void *args[] = {&p};
+  QG_CUDA(c, cudaEventRecord(c->ev[1], s));
+  QG_CUDA(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(c->nthreads), args, c->smem, s));
+  QG_CUDA(c, cudaEventRecord(c->ev[2], s));
+  return QG_OK;
+}
+
+qg_status ensure_graph(qg_ctx *c) {
+  if (c->graph_valid) return QG_OK;
+  invalidate(c);
+  qg_status st = choose_kernel(c);
+  if (st != QG_OK) return st;
+  const int64_t G = c->G;
+  {
+    cudaError_t e;
+    if ((e = c->scratch.reserve(2 * kBuckets + 2)) != cudaSuccess ||
+        (e = c->bucket.reserve(G)) != cudaSuccess || (e = c->queue.reserve(G)) != cudaSuccess ||
+        (e = c->a.reserve(3 * std::max<int64_t>(c->n, 1))) != cudaSuccess ||
+        (e = c->phi.reserve(std::max<int64_t>(c->n, 1))) != cudaSuccess)
+      return fail(c, QG_ERR_NOMEM, "device allocation: %s", cudaGetErrorString(e));
+  }
+  cudaStream_t cap;
+  QG_CUDA(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaStreamDestroy(cap);
+    return fail(c, QG_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+  }
+  st = record_step(c, cap);
+  e = cudaStreamEndCapture(cap, &graph);
+  cudaStreamDestroy(cap);
+  if (st != QG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(c, QG_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&c->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    c->exec = nullptr;
+    return fail(c, QG_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  c->graph_valid = true;
+  return QG_OK;
+}
+
+template <typename T>
+qg_status upload(qg_ctx *c, DevBuf<T> &buf, const T *h, size_t count, cudaStream_t s) {
+  cudaError_t e = buf.reserve(count);
+  if (e != cudaSuccess) return fail(c, QG_ERR_NOMEM, "device allocation of %zu bytes", count * sizeof(T));
+  if (count) QG_CUDA(c, cudaMemcpyAsync(buf.p, h, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  return QG_OK;
+}
+
+template <typename T>
+qg_status copy_d2d(qg_ctx *c, DevBuf<T> &buf, const T *d, size_t count, cudaStream_t s) {
+  cudaError_t e = buf.reserve(count);
+  if (e != cudaSuccess) return fail(c, QG_ERR_NOMEM, "device allocation of %zu bytes", count * sizeof(T));
+  if (count) QG_CUDA(c, cudaMemcpyAsync(buf.p, d, count * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  return QG_OK;
+}
+
+qg_status check_indices_dev(qg_ctx *c, const int32_t *idx, int64_t cnt, int64_t n, cudaStream_t s,
+                            const char *what) {
+  if (cnt == 0) return QG_OK;
+  cudaError_t e = c->scratch.reserve(2 * kBuckets + 2);
+  if (e != cudaSuccess) return fail(c, QG_ERR_NOMEM, "scratch allocation");
+  int *bad = c->scratch.p + 2 * kBuckets + 1;
+  QG_CUDA(c, cudaMemsetAsync(bad, 0, sizeof(int), s));
+  check_index_kernel<<<grid_for(cnt, 256), 256, 0, s>>>(cnt, idx, n, bad);
+  QG_CUDA(c, cudaGetLastError());
+  int h = 0;
+  QG_CUDA(c, cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  QG_CUDA(c, cudaStreamSynchronize(s));
+  if (h) return fail(c, QG_ERR_ARG, "%s: list entry outside [0, %lld)", what, (long long)n);
+  return QG_OK;
+}
+
+qg_status check_lists_host(qg_ctx *c, int64_t G, const int64_t *off, const int32_t *idx, int64_t n,
+                           const char *what) {
+  if (!valid_offsets_any_total(off, G)) return fail(c, QG_ERR_ARG, "%s: bad list offsets", what);
+  const int64_t cnt = off[G];
+  if (cnt > 0 && !idx) return fail(c, QG_ERR_ARG, "%s: list_idx is NULL", what);
+  for (int64_t i = 0; i < cnt; i++)
+    if (idx[i] < 0 || (int64_t)idx[i] >= n) return fail(c, QG_ERR_ARG, "%s: list entry %lld = %d outside [0, %lld)",
+                                                        what, (long long)i, idx[i], (long long)n);
+  return QG_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+
+extern "C" {
+
+qg_status qg_create(qg_ctx **out, int device, const qg_options *opt) {
+  if (!out) return QG_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return QG_ERR_ARG;
+  qg_ctx *c = new (std::nothrow) qg_ctx;
+  if (!c) return QG_ERR_NOMEM;
+  c->device = device;
+  if (opt) {
+    std::string why;
+    if (!valid_options(*opt, why)) {
+      delete c;
+      return QG_ERR_ARG;
+    }
+    c->opt = *opt;
+  }
+  DeviceGuard dg(device);
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return QG_ERR_CUDA;
+  }
+  c->last_stream = c->stream;
+  for (auto &e : c->ev) {
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      qg_destroy(c);
+      return QG_ERR_CUDA;
+    }
+  }
+  *out = c;
+  return QG_OK;
+}
+
+void qg_destroy(qg_ctx *c) {
+  if (!c) return;
+  DeviceGuard dg(c->device);
+  if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  invalidate(c);
+  c->sink_x.release(); c->sink_eps2.release(); c->goff.release();
+  c->src.release(); c->stage_x.release(); c->stage_m.release(); c->stage_q.release();
+  c->poff.release(); c->pidx.release();
+  c->cell_xm.release(); c->cell_q.release(); c->cell_q64.release(); c->coff.release(); c->cidx.release();
+  c->a.release(); c->phi.release(); c->scratch.release(); c->bucket.release(); c->queue.release();
+  for (auto &e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+qg_status qg_set_options(qg_ctx *c, const qg_options *opt) {
+  if (!c || !opt) return QG_ERR_ARG;
+  std::string why;
+  if (!valid_options(*opt, why)) return fail(c, QG_ERR_ARG, "bad option: %s", why.c_str());
+  c->opt = *opt;
+  invalidate(c);
+  return QG_OK;
+}
+
+static qg_status set_sinks_common(qg_ctx *c, int64_t n, const double *x, const float *eps2, double eps2_all,
+                                  int64_t ngroups, const int64_t *group_off, bool dev, cudaStream_t s) {
+  // inputs must not change under a step that is still running
+  if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+  c->sinks_ok = false;
+  invalidate(c);
+  if (n < 0 || ngroups < 0 || ngroups >= INT32_MAX || !group_off || (n > 0 && !x))
+    return fail(c, QG_ERR_ARG, "qg_set_sinks: bad sizes or NULL pointer");
+  if (!std::isfinite(eps2_all) || eps2_all < 0) return fail(c, QG_ERR_ARG, "qg_set_sinks: eps2_all must be >= 0");
+  DeviceGuard dg(c->device);
+  std::vector<int64_t> h(ngroups + 1);
+  if (dev) {
+    QG_CUDA(c, cudaMemcpyAsync(h.data(), group_off, (ngroups + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    QG_CUDA(c, cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(h.data(), group_off, (ngroups + 1) * sizeof(int64_t));
+  }
+  if (!valid_offsets(h.data(), ngroups, n)) return fail(c, QG_ERR_ARG, "qg_set_sinks: bad group offsets");
+  bool pos = eps2_all > 0;
+  if (eps2) {
+    if (dev) {
+      // device eps^2: positivity is decided conservatively (guarded kernel)
+      pos = false;
+    } else {
+      pos = true;
+      for (int64_t i = 0; i < n; i++) {
+        if (!(eps2[i] >= 0.f) || !std::isfinite(eps2[i]))
+          return fail(c, QG_ERR_ARG, "qg_set_sinks: eps2[%lld] invalid", (long long)i);
+        if (!(eps2[i] > 0.f)) pos = false;
+      }
+    }
+  }
+  qg_status st;
+  if (dev) {
+    if ((st = copy_d2d(c, c->sink_x, x, 3 * n, s)) != QG_OK) return st;
+    if (eps2 && (st = copy_d2d(c, c->sink_eps2, eps2, n, s)) != QG_OK) return st;
+    if ((st = copy_d2d(c, c->goff, group_off, ngroups + 1, s)) != QG_OK) return st;
+  } else {
+    if ((st = upload(c, c->sink_x, x, 3 * n, s)) != QG_OK) return st;
+    if (eps2 && (st = upload(c, c->sink_eps2, eps2, n, s)) != QG_OK) return st;
+    if ((st = upload(c, c->goff, group_off, ngroups + 1, s)) != QG_OK) return st;
+  }
+  QG_CUDA(c, cudaStreamSynchronize(s));
+  c->n = n;
+  c->G = ngroups;
+  c->has_eps2 = eps2 != nullptr;
+  c->eps2_all = eps2_all;
+  c->eps_positive = pos;
+  c->h_goff.swap(h);
+  c->sinks_ok = true;
+  c->ran = false;
+  update_counts(c);
+  return QG_OK;
+}
+
+qg_status qg_set_sinks(qg_ctx *c, int64_t n, const double *x, const float *eps2, double eps2_all,
+                       int64_t ngroups, const int64_t *group_off) {
+  if (!c) return QG_ERR_ARG;
+  return set_sinks_common(c, n, x, eps2, eps2_all, ngroups, group_off, false, c->stream);
+}
+
+qg_status qg_set_sinks_dev(qg_ctx *c, int64_t n, const double *x, const float *eps2, double eps2_all,
+                           int64_t ngroups, const int64_t *group_off, void *stream) {
+  if (!c) return QG_ERR_ARG;
+  return set_sinks_common(c, n, x, eps2, eps2_all, ngroups, group_off, true, pick_stream(c, stream));
+}
+
+static qg_status set_sources_common(qg_ctx *c, int64_t ns, const double *x, const double *m,
+                                    const int64_t *list_off, const int32_t *list_idx, int64_t n_list_dev,
+                                    bool dev, cudaStream_t s) {
+  // inputs must not change under a step that is still running
+  if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+  c->src_ok = false;
+  invalidate(c);
+  if (c->G < 0 || !c->sinks_ok) return fail(c, QG_ERR_STATE, "qg_set_sources: set the sinks first");
+  if (ns < 0 || ns >= INT32_MAX || !list_off || (ns > 0 && (!x || !m)))
+    return fail(c, QG_ERR_ARG, "qg_set_sources: bad sizes or NULL pointer");
+  const int64_t G = c->G;
+  DeviceGuard dg(c->device);
+  std::vector<int64_t> h(G + 1);
+  qg_status st;
+  if (dev) {
+    QG_CUDA(c, cudaMemcpyAsync(h.data(), list_off, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    QG_CUDA(c, cudaStreamSynchronize(s));
+    if (!valid_offsets(h.data(), G, n_list_dev)) return fail(c, QG_ERR_ARG, "qg_set_sources: bad list offsets");
+    if (n_list_dev > 0 && !list_idx) return fail(c, QG_ERR_ARG, "qg_set_sources: list_idx is NULL");
+    if ((st = check_indices_dev(c, list_idx, n_list_dev, ns, s, "qg_set_sources")) != QG_OK) return st;
+  } else {
+    std::memcpy(h.data(), list_off, (G + 1) * sizeof(int64_t));
+    if ((st = check_lists_host(c, G, h.data(), list_idx, ns, "qg_set_sources")) != QG_OK) return st;
+  }
+  const int64_t cnt = h[G];
+  if (dev) {
+    if ((st = copy_d2d(c, c->poff, list_off, G + 1, s)) != QG_OK) return st;
+    if ((st = copy_d2d(c, c->pidx, list_idx, cnt, s)) != QG_OK) return st;
+    cudaError_t e = c->src.reserve(ns);
+    if (e != cudaSuccess) return fail(c, QG_ERR_NOMEM, "source allocation");
+    if (ns) pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, x, m, c->src.p);
+  } else {
+    if ((st = upload(c, c->poff, list_off, G + 1, s)) != QG_OK) return st;
+    if ((st = upload(c, c->pidx, list_idx, cnt, s)) != QG_OK) return st;
+    if ((st = upload(c, c->stage_x, x, 3 * ns, s)) != QG_OK) return st;
+    if ((st = upload(c, c->stage_m, m, ns, s)) != QG_OK) return st;
+    cudaError_t e = c->src.reserve(ns);
+    if (e != cudaSuccess) return fail(c, QG_ERR_NOMEM, "source allocation");
+    if (ns) pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, c->stage_x.p, c->stage_m.p, c->src.p);
+  }
+  QG_CUDA(c, cudaGetLastError());
+  QG_CUDA(c, cudaStreamSynchronize(s));
+  c->ns = ns;
+  c->G_src = G;
+  c->np_list = cnt;
+  c->h_poff.swap(h);
+  c->src_ok = true;
+  update_counts(c);
+  return QG_OK;
+}
+
+qg_status qg_set_sources(qg_ctx *c, int64_t ns, const double *x, const double *m, const int64_t *list_off,
+                         const int32_t *list_idx) {
+  if (!c) return QG_ERR_ARG;
+  return set_sources_common(c, ns, x, m, list_off, list_idx, 0, false, c->stream);
+}
+
+qg_status qg_set_sources_dev(qg_ctx *c, int64_t ns, const double *x, const double *m, const int64_t *list_off,
+                             const int32_t *list_idx, int64_t n_list, void *stream) {
+  if (!c) return QG_ERR_ARG;
+  return set_sources_common(c, ns, x, m, list_off, list_idx, n_list, true, pick_stream(c, stream));
+}
+
+static qg_status set_cells_common(qg_ctx *c, int64_t nc, const double *com, const double *m, const double *q,
+                                  const int64_t *list_off, const int32_t *list_idx, int64_t n_list_dev, bool dev,
+                                  cudaStream_t s) {
+  // inputs must not change under a step that is still running
+  if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+  c->cells_ok = false;
+  invalidate(c);
+  if (c->G < 0 || !c->sinks_ok) return fail(c, QG_ERR_STATE, "qg_set_cells: set the sinks first");
+  if (nc < 0 || nc >= INT32_MAX || !list_off || (nc > 0 && (!com || !m || !q)))
+    return fail(c, QG_ERR_ARG, "qg_set_cells: bad sizes or NULL pointer");
+  const int64_t G = c->G;
+  DeviceGuard dg(c->device);
+  std::vector<int64_t> h(G + 1);
+  qg_status st;
+  if (dev) {
+    QG_CUDA(c, cudaMemcpyAsync(h.data(), list_off, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    QG_CUDA(c, cudaStreamSynchronize(s));
+    if (!valid_offsets(h.data(), G, n_list_dev)) return fail(c, QG_ERR_ARG, "qg_set_cells: bad list offsets");
+    if (n_list_dev > 0 && !list_idx) return fail(c, QG_ERR_ARG, "qg_set_cells: list_idx is NULL");
+    if ((st = check_indices_dev(c, list_idx, n_list_dev, nc, s, "qg_set_cells")) != QG_OK) return st;
+  } else {
+    std::memcpy(h.data(), list_off, (G + 1) * sizeof(int64_t));
+    if ((st = check_lists_host(c, G, h.data(), list_idx, nc, "qg_set_cells")) != QG_OK) return st;
+  }
+  const int64_t cnt = h[G];
+  if (c->cell_xm.reserve(nc) != cudaSuccess || c->cell_q.reserve(2 * nc) != cudaSuccess ||
+      c->cell_q64.reserve(6 * nc) != cudaSuccess)
+    return fail(c, QG_ERR_NOMEM, "cell allocation");
+  if (dev) {
+    if ((st = copy_d2d(c, c->coff, list_off, G + 1, s)) != QG_OK) return st;
+    if ((st = copy_d2d(c, c->cidx, list_idx, cnt, s)) != QG_OK) return st;
+    if (nc)
+      pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, com, m, q, c->cell_xm.p, c->cell_q.p, c->cell_q64.p);
+  } else {
+    if ((st = upload(c, c->coff, list_off, G + 1, s)) != QG_OK) return st;
+    if ((st = upload(c, c->cidx, list_idx, cnt, s)) != QG_OK) return st;
+    if ((st = upload(c, c->stage_x, com, 3 * nc, s)) != QG_OK) return st;
+    if ((st = upload(c, c->stage_m, m, nc, s)) != QG_OK) return st;
+    // Q goes straight into the FP64 copy, which the packer then reads
+    if ((st = upload(c, c->cell_q64, q, 6 * nc, s)) != QG_OK) return st;
+    if (nc)
+      pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, c->stage_x.p, c->stage_m.p, c->cell_q64.p,
+                                                           c->cell_xm.p, c->cell_q.p, c->cell_q64.p);
+  }
+  QG_CUDA(c, cudaGetLastError());
+  QG_CUDA(c, cudaStreamSynchronize(s));
+  c->nc = nc;
+  c->G_cell = G;
+  c->nc_list = cnt;
+  c->h_coff.swap(h);
+  c->cells_ok = true;
+  update_counts(c);
+  return QG_OK;
+}
+
+qg_status qg_set_cells(qg_ctx *c, int64_t nc, const double *com, const double *m, const double *q,
+                       const int64_t *list_off, const int32_t *list_idx) {
+  if (!c) return QG_ERR_ARG;
+  return set_cells_common(c, nc, com, m, q, list_off, list_idx, 0, false, c->stream);
+}
+
+qg_status qg_set_cells_dev(qg_ctx *c, int64_t nc, const double *com, const double *m, const double *q,
+                           const int64_t *list_off, const int32_t *list_idx, int64_t n_list, void *stream) {
+  if (!c) return QG_ERR_ARG;
+  return set_cells_common(c, nc, com, m, q, list_off, list_idx, n_list, true, pick_stream(c, stream));
+}
+
+qg_status qg_run(qg_ctx *c, void *stream) {
+  if (!c) return QG_ERR_ARG;
+  if (!c->sinks_ok || !c->src_ok || !c->cells_ok)
+    return fail(c, QG_ERR_STATE, "qg_run: sinks, sources and cells must all be set");
+  if (c->G_src != c->G || c->G_cell != c->G)
+    return fail(c, QG_ERR_STATE, "qg_run: lists were set for %lld / %lld groups, sinks have %lld",
+                (long long)c->G_src, (long long)c->G_cell, (long long)c->G);
+  DeviceGuard dg(c->device);
+  cudaStream_t s = pick_stream(c, stream);
+  c->last_stream = s;
+  if (c->G == 0) {
+    c->ran = true;
+    return QG_OK;
+  }
+  qg_status st = ensure_graph(c);
+  if (st != QG_OK) return st;
+  QG_CUDA(c, cudaGraphLaunch(c->exec, s));
+  c->ran = true;
+  return QG_OK;
+}
+
+qg_status qg_get_forces(qg_ctx *c, double *a, double *phi) {
+  if (!c) return QG_ERR_ARG;
+  if (!c->ran) return fail(c, QG_ERR_STATE, "qg_get_forces: nothing has been run for these sinks");
+  DeviceGuard dg(c->device);
+  cudaStream_t s = c->last_stream;
+  if (c->n == 0) {
+    QG_CUDA(c, cudaStreamSynchronize(s));
+    return QG_OK;
+  }
+  if (a) QG_CUDA(c, cudaMemcpyAsync(a, c->a.p, 3 * c->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (phi) QG_CUDA(c, cudaMemcpyAsync(phi, c->phi.p, c->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  QG_CUDA(c, cudaStreamSynchronize(s));
+  return QG_OK;
+}
+
+qg_status qg_get_forces_dev(qg_ctx *c, double *a, double *phi, void *stream) {
+  if (!c) return QG_ERR_ARG;
+  if (!c->ran) return fail(c, QG_ERR_STATE, "qg_get_forces_dev: nothing has been run for these sinks");
+  if (c->n == 0) return QG_OK;
+  DeviceGuard dg(c->device);
+  cudaStream_t s = pick_stream(c, stream);
+  if (a) QG_CUDA(c, cudaMemcpyAsync(a, c->a.p, 3 * c->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (phi) QG_CUDA(c, cudaMemcpyAsync(phi, c->phi.p, c->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  return QG_OK;
+}
+
+qg_status qg_get_stats(const qg_ctx *c, qg_stats *out) {
+  if (!c || !out) return QG_ERR_ARG;
+  *out = c->stats;
+  return QG_OK;
+}
+
+qg_status qg_last_timing(qg_ctx *c, float *step_ms, float *force_ms) {
+  if (!c) return QG_ERR_ARG;
+  if (!c->ran || !c->graph_valid) return fail(c, QG_ERR_STATE, "qg_last_timing: no timed run");
+  DeviceGuard dg(c->device);
+  QG_CUDA(c, cudaStreamSynchronize(c->last_stream));
+  if (step_ms) QG_CUDA(c, cudaEventElapsedTime(step_ms, c->ev[0], c->ev[2]));
+  if (force_ms) QG_CUDA(c, cudaEventElapsedTime(force_ms, c->ev[1], c->ev[2]));
+  return QG_OK;
+}
+
+const char *qg_last_error(const qg_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -1,0 +1,312 @@
+// qg_force.cuh -- the persistent group-force kernel (monopole particles +
+// quadrupole cells, Kodama & Ishiyama arXiv:1812.07313, Eqs. 1, 4-8).
+//
+// One CTA evaluates one sink group at a time, taking group ids from a
+// device work queue (ordered by descending cost) with an atomic counter.
+// Inside the CTA:
+//   1. c_g = centre of the bounding box of the group's sinks (FP64).
+//   2. sink offsets x_i - c_g are formed in FP64, cast to Real, kept in
+//      shared memory; each thread holds R sinks in registers.
+//   3. the group's list is staged tile by tile into shared memory:
+//      particles (x_j - c_g, m) and cells (x_j - c_g, m, Q) gathered through
+//      the CSR index list, centred in FP64, cast to Real.
+//   4. the threads form S sink slots x K list streams (S = ceil(n_i / R),
+//      K = blockDim / S); stream k walks entries k, k+K, ... of each tile,
+//      so every staged entry is read from shared memory once per thread and
+//      used for R sinks.
+//   5. Real partial sums are folded into FP64 accumulators (shared memory)
+//      after at most flush_j entries per thread; at the end the K streams of
+//      each sink are merged in FP64 in a fixed order (deterministic).
+//
+// Real = float is the production path; Real = double is the all-FP64
+// comparison kernel (same structure, no casts).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qg_internal.h"
+
+namespace qg {
+
+template <typename Real> struct RT;
+template <> struct RT<float> {
+  using v4 = float4;
+  using v2 = float2;
+  static __device__ __forceinline__ v4 make4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+  static __device__ __forceinline__ v2 make2(float a, float b) { return make_float2(a, b); }
+  static __device__ __forceinline__ float cvt(double x) { return __double2float_rn(x); }
+  // SFU approximate reciprocal square root (MUFU.RSQ)
+  static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
+};
+template <> struct RT<double> {
+  using v4 = double4_16a;  // shared memory only guarantees 16-byte alignment
+  using v2 = double2;
+  static __device__ __forceinline__ v4 make4(double a, double b, double c, double d) { return make_double4_16a(a, b, c, d); }
+  static __device__ __forceinline__ v2 make2(double a, double b) { return make_double2(a, b); }
+  static __device__ __forceinline__ double cvt(double x) { return x; }
+  static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / sqrt(x); }
+};
+
+// One source particle on one sink: Eq. 4 and its gradient.  13 Real ops + 1 rsqrt.
+template <typename Real, bool GUARD>
+__device__ __forceinline__ void mono_pair(Real dx, Real dy, Real dz, Real m, Real e2,
+                                          Real &ax, Real &ay, Real &az, Real &pot) {
+  const Real r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, e2)));
+  Real ri = RT<Real>::rsqrt(r2);
+  if (GUARD) ri = r2 > Real(0) ? ri : Real(0);
+  const Real pm = m * ri;            // phi_mono = m / rhat
+  pot += pm;
+  const Real c = pm * (ri * ri);     // m / rhat^3
+  ax = fma(c, dx, ax);
+  ay = fma(c, dy, ay);
+  az = fma(c, dz, az);
+}
+
+// One cell on one sink: Eqs. 1, 4-5 and -grad of Eq. 1.  33 Real ops + 1 rsqrt.
+// q = (q00, q01, q02, q11), qq = (q12, q22).
+template <typename Real, bool GUARD>
+__device__ __forceinline__ void quad_pair(Real dx, Real dy, Real dz, Real m,
+                                          Real q00, Real q01, Real q02, Real q11, Real q12, Real q22,
+                                          Real e2, Real &ax, Real &ay, Real &az, Real &pot) {
+  const Real r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, e2)));
+  Real ri = RT<Real>::rsqrt(r2);
+  if (GUARD) ri = r2 > Real(0) ? ri : Real(0);
+  const Real ri2 = ri * ri;
+  const Real pm = m * ri;                                  // phi_mono
+  const Real qx = fma(q00, dx, fma(q01, dy, q02 * dz));    // (Q r)_x
+  const Real qy = fma(q01, dx, fma(q11, dy, q12 * dz));    // (Q r)_y
+  const Real qz = fma(q02, dx, fma(q12, dy, q22 * dz));    // (Q r)_z
+  const Real rqr = fma(dx, qx, fma(dy, qy, dz * qz));      // r.Q.r
+  const Real ri5 = ri2 * ri2 * ri;
+  const Real u = rqr * ri5;                                // 2 phi_quad
+  pot += pm;
+  pot = fma(Real(0.5), u, pot);                            // + phi_quad
+  const Real c = fma(Real(2.5), u, pm) * ri2;              // (phi_mono + 5 phi_quad) / rhat^2
+  ax = fma(c, dx, ax);
+  ax = fma(-ri5, qx, ax);
+  ay = fma(c, dy, ay);
+  ay = fma(-ri5, qy, ay);
+  az = fma(c, dz, az);
+  az = fma(-ri5, qz, az);
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Largest block a variant is launched with: R = 8 keeps 8 sinks x 4 sums in
+// registers and is limited to 128 threads so that it does not spill.
+template <int R> struct MaxThreads { static constexpr int value = R >= 8 ? 128 : 256; };
+
+template <typename Real, int R, bool QUAD, bool GUARD, bool CENTRED>
+__global__ void __launch_bounds__(MaxThreads<R>::value) force_kernel(const ForceParams p) {
+  using V4 = typename RT<Real>::v4;
+  using V2 = typename RT<Real>::v2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  __shared__ float s_box[8][6];
+  __shared__ double s_c[3];
+
+  const int NT = blockDim.x;
+  const int tid = threadIdx.x;
+  const int T = p.tile;
+  V4 *sink_s = reinterpret_cast<V4 *>(smem_raw);
+  V4 *tA = sink_s + R * NT;
+  V4 *tB = tA + T;
+  V2 *tC = reinterpret_cast<V2 *>(tB + T);
+  double *acc64 = reinterpret_cast<double *>(tC + T);
+
+  for (;;) {
+    __syncthreads();  // the previous group is finished with shared memory
+    if (tid == 0) s_item = atomicAdd(p.head, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= p.nitems) break;
+    const int g = p.queue[item];
+    const int64_t s0 = p.group_off[g];
+    const int ni = (int)(p.group_off[g + 1] - s0);
+    if (ni <= 0) continue;
+
+    // ---- 1. group centre: bounding box of the sinks ----------------------
+    double cx = 0.0, cy = 0.0, cz = 0.0;
+    if (CENTRED) {
+      const double x0 = p.sink_x[3 * s0], y0 = p.sink_x[3 * s0 + 1], z0 = p.sink_x[3 * s0 + 2];
+      float mn0 = 0.f, mn1 = 0.f, mn2 = 0.f, mx0 = 0.f, mx1 = 0.f, mx2 = 0.f;
+      for (int i = tid; i < ni; i += NT) {
+        const double *xi = p.sink_x + 3 * (s0 + i);
+        const float o0 = __double2float_rn(xi[0] - x0);
+        const float o1 = __double2float_rn(xi[1] - y0);
+        const float o2 = __double2float_rn(xi[2] - z0);
+        mn0 = fminf(mn0, o0); mn1 = fminf(mn1, o1); mn2 = fminf(mn2, o2);
+        mx0 = fmaxf(mx0, o0); mx1 = fmaxf(mx1, o1); mx2 = fmaxf(mx2, o2);
+      }
+      mn0 = warp_min(mn0); mn1 = warp_min(mn1); mn2 = warp_min(mn2);
+      mx0 = warp_max(mx0); mx1 = warp_max(mx1); mx2 = warp_max(mx2);
+      const int w = tid >> 5;
+      if ((tid & 31) == 0) {
+        s_box[w][0] = mn0; s_box[w][1] = mn1; s_box[w][2] = mn2;
+        s_box[w][3] = mx0; s_box[w][4] = mx1; s_box[w][5] = mx2;
+      }
+      __syncthreads();
+      if (tid < 3) {
+        float lo = s_box[0][tid], hi = s_box[0][tid + 3];
+        for (int v = 1; v < (NT >> 5); v++) {
+          lo = fminf(lo, s_box[v][tid]);
+          hi = fmaxf(hi, s_box[v][tid + 3]);
+        }
+        const double base = tid == 0 ? x0 : (tid == 1 ? y0 : z0);
+        s_c[tid] = base + 0.5 * ((double)lo + (double)hi);
+      }
+      __syncthreads();
+      cx = s_c[0]; cy = s_c[1]; cz = s_c[2];
+    }
+
+    const int64_t p0 = p.plist_off[g], p1 = p.plist_off[g + 1];
+    const int64_t c0 = p.clist_off[g], c1 = p.clist_off[g + 1];
+
+    // ---- sink chunks of at most R * NT sinks --------------------------------
+    for (int sb = 0; sb < ni; sb += R * NT) {
+      const int nch = min(ni - sb, R * NT);
+      __syncthreads();  // previous chunk's readers of sink_s / acc64 are done
+      for (int i = tid; i < nch; i += NT) {
+        const int64_t si = s0 + sb + i;
+        const double *xi = p.sink_x + 3 * si;
+        const double e2 = p.sink_eps2 ? (double)p.sink_eps2[si] : p.eps2_all;
+        sink_s[i] = RT<Real>::make4(RT<Real>::cvt(xi[0] - cx), RT<Real>::cvt(xi[1] - cy),
+                                    RT<Real>::cvt(xi[2] - cz), RT<Real>::cvt(e2));
+      }
+#pragma unroll
+      for (int v = 0; v < 4 * R; v++) acc64[tid * 4 * R + v] = 0.0;
+      __syncthreads();
+
+      const int S = (nch + R - 1) / R;  // sink slots
+      const int K = NT / S;             // list streams
+      const int s = tid % S;
+      const int k = tid / S;
+      const bool active = k < K;
+
+      Real sx[R], sy[R], sz[R], se[R];
+      Real ax[R], ay[R], az[R], pt[R];
+#pragma unroll
+      for (int r = 0; r < R; r++) {
+        const int i = s + S * r;
+        const V4 v = sink_s[i < nch ? i : 0];
+        sx[r] = v.x; sy[r] = v.y; sz[r] = v.z; se[r] = v.w;
+        ax[r] = ay[r] = az[r] = pt[r] = Real(0);
+      }
+      int nproc = 0;
+
+      auto fold = [&]() {
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          double *a = acc64 + tid * 4 * R + 4 * r;
+          a[0] += (double)ax[r]; a[1] += (double)ay[r]; a[2] += (double)az[r]; a[3] += (double)pt[r];
+          ax[r] = ay[r] = az[r] = pt[r] = Real(0);
+        }
+        nproc = 0;
+      };
+
+      // ---- 3-4. particle part of the list (monopole, Eq. 4) ----------------
+      for (int64_t base = p0; base < p1; base += T) {
+        const int cnt = (int)min((int64_t)T, p1 - base);
+        __syncthreads();
+        for (int t = tid; t < cnt; t += NT) {
+          const int j = p.plist_idx[base + t];
+          const double4_32a v = p.src[j];
+          tA[t] = RT<Real>::make4(RT<Real>::cvt(v.x - cx), RT<Real>::cvt(v.y - cy),
+                                  RT<Real>::cvt(v.z - cz), RT<Real>::cvt(v.w));
+        }
+        __syncthreads();
+        if (active) {
+#pragma unroll 2
+          for (int jj = k; jj < cnt; jj += K) {
+            const V4 A = tA[jj];
+#pragma unroll
+            for (int r = 0; r < R; r++)
+              mono_pair<Real, GUARD>(A.x - sx[r], A.y - sy[r], A.z - sz[r], A.w, se[r],
+                                     ax[r], ay[r], az[r], pt[r]);
+          }
+          nproc += (cnt - k + K - 1) / K;
+          if (nproc >= p.flush_j) fold();
+        }
+      }
+
+      // ---- 3-4. cell part of the list (Eq. 1 / Eq. 8, or monopole) --------
+      for (int64_t base = c0; base < c1; base += T) {
+        const int cnt = (int)min((int64_t)T, c1 - base);
+        __syncthreads();
+        for (int t = tid; t < cnt; t += NT) {
+          const int j = p.clist_idx[base + t];
+          const double4_32a v = p.cell_xm[j];
+          tA[t] = RT<Real>::make4(RT<Real>::cvt(v.x - cx), RT<Real>::cvt(v.y - cy),
+                                  RT<Real>::cvt(v.z - cz), RT<Real>::cvt(v.w));
+          if (QUAD) {
+            if (sizeof(Real) == 4) {
+              const float4 q0 = p.cell_q[2 * j], q1 = p.cell_q[2 * j + 1];
+              tB[t] = RT<Real>::make4(q0.x, q0.y, q0.z, q0.w);
+              tC[t] = RT<Real>::make2(q1.x, q1.y);
+            } else {
+              const double *q = p.cell_q64 + 6 * (int64_t)j;
+              tB[t] = RT<Real>::make4((Real)q[0], (Real)q[1], (Real)q[2], (Real)q[3]);
+              tC[t] = RT<Real>::make2((Real)q[4], (Real)q[5]);
+            }
+          }
+        }
+        __syncthreads();
+        if (active) {
+          if (QUAD) {
+#pragma unroll 2
+            for (int jj = k; jj < cnt; jj += K) {
+              const V4 A = tA[jj];
+              const V4 B = tB[jj];
+              const V2 C = tC[jj];
+#pragma unroll
+              for (int r = 0; r < R; r++)
+                quad_pair<Real, GUARD>(A.x - sx[r], A.y - sy[r], A.z - sz[r], A.w,
+                                       B.x, B.y, B.z, B.w, C.x, C.y, se[r],
+                                       ax[r], ay[r], az[r], pt[r]);
+            }
+          } else {
+#pragma unroll 2
+            for (int jj = k; jj < cnt; jj += K) {
+              const V4 A = tA[jj];
+#pragma unroll
+              for (int r = 0; r < R; r++)
+                mono_pair<Real, GUARD>(A.x - sx[r], A.y - sy[r], A.z - sz[r], A.w, se[r],
+                                       ax[r], ay[r], az[r], pt[r]);
+            }
+          }
+          nproc += (cnt - k + K - 1) / K;
+          if (nproc >= p.flush_j) fold();
+        }
+      }
+
+      // ---- 5. FP64 merge of the K streams, fixed order ----------------------
+      if (active) fold();
+      __syncthreads();
+      for (int i = tid; i < nch; i += NT) {
+        const int si = i % S, ri = i / S;
+        double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+        for (int kk = 0; kk < K; kk++) {
+          const double *a = acc64 + (kk * S + si) * 4 * R + 4 * ri;
+          m0 += a[0]; m1 += a[1]; m2 += a[2]; m3 += a[3];
+        }
+        const int64_t o = s0 + sb + i;
+        p.a[3 * o] = m0;
+        p.a[3 * o + 1] = m1;
+        p.a[3 * o + 2] = m2;
+        p.phi[o] = -m3;  // physical potential, Eq. 1
+      }
+    }
+  }
+}
+
+}  // namespace qg

@@ -1,0 +1,30 @@
+// FP32 instantiations of the group-force kernel (mixed precision: FP64
+// centring and merging, FP32 pairwise arithmetic).
+#include "qg_force.cuh"
+
+namespace qg {
+
+template <int R>
+static const void *pick_f32(bool quad, bool guard, bool centred) {
+  if (centred) {
+    if (quad) return guard ? (const void *)force_kernel<float, R, true, true, true>
+                           : (const void *)force_kernel<float, R, true, false, true>;
+    return guard ? (const void *)force_kernel<float, R, false, true, true>
+                 : (const void *)force_kernel<float, R, false, false, true>;
+  }
+  if (quad) return guard ? (const void *)force_kernel<float, R, true, true, false>
+                         : (const void *)force_kernel<float, R, true, false, false>;
+  return guard ? (const void *)force_kernel<float, R, false, true, false>
+               : (const void *)force_kernel<float, R, false, false, false>;
+}
+
+const void *force_kernel_f32(int R, bool quad, bool guard, bool centred) {
+  switch (R) {
+    case 2: return pick_f32<2>(quad, guard, centred);
+    case 4: return pick_f32<4>(quad, guard, centred);
+    case 8: return pick_f32<8>(quad, guard, centred);
+    default: return nullptr;
+  }
+}
+
+}  // namespace qg

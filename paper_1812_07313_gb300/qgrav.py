@@ -1,0 +1,265 @@
+"""Python binding of the ``qg_*`` C-ABI (``include/qgrav.h``).
+
+Argument marshalling only: every step of the force evaluation runs in the
+CUDA library ``_build/libqgrav.so``.  There is no Python or CPU fallback: if
+the library cannot be built or loaded, importing a function raises.
+
+Host inputs are numpy arrays; device inputs are torch CUDA tensors (their
+storage is passed by pointer to the ``*_dev`` entry points).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _native
+
+QG_OK, QG_ERR_ARG, QG_ERR_CUDA, QG_ERR_NOMEM, QG_ERR_STATE, QG_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+QG_FP32_CENTRED, QG_FP32_RAW, QG_FP64 = 0, 1, 2
+QG_QUAD, QG_MONO = 0, 1
+
+_STATUS = {0: "QG_OK", -1: "QG_ERR_ARG", -2: "QG_ERR_CUDA", -3: "QG_ERR_NOMEM", -4: "QG_ERR_STATE",
+           -5: "QG_ERR_TIMEOUT"}
+
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+
+# every symbol include/qgrav.h declares, with its argument types
+SIGNATURES = {
+    "qg_create": ([_P(_vp), _int, _vp], _int),
+    "qg_destroy": ([_vp], None),
+    "qg_set_options": ([_vp, _vp], _int),
+    "qg_set_sinks": ([_vp, _i64, _vp, _vp, _dbl, _i64, _vp], _int),
+    "qg_set_sources": ([_vp, _i64, _vp, _vp, _vp, _vp], _int),
+    "qg_set_cells": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp], _int),
+    "qg_set_sinks_dev": ([_vp, _i64, _vp, _vp, _dbl, _i64, _vp, _vp], _int),
+    "qg_set_sources_dev": ([_vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp], _int),
+    "qg_set_cells_dev": ([_vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp], _int),
+    "qg_run": ([_vp, _vp], _int),
+    "qg_get_forces": ([_vp, _vp, _vp], _int),
+    "qg_get_forces_dev": ([_vp, _vp, _vp, _vp], _int),
+    "qg_get_stats": ([_vp, _vp], _int),
+    "qg_last_error": ([_vp], ctypes.c_char_p),
+    "qg_last_timing": ([_vp, _vp, _vp], _int),
+    "qg_direct_dev": ([_int, _i64, _vp, _dbl, _i64, _vp, _vp, _vp, _vp, _vp], _int),
+}
+
+
+class qg_options(ctypes.Structure):
+    _fields_ = [("precision", _int), ("expansion", _int), ("tile_j", _int),
+                ("warps_per_group", _int), ("sinks_per_thread", _int), ("flush_j", _int)]
+
+
+class qg_stats(ctypes.Structure):
+    _fields_ = [("n_sinks", _i64), ("n_groups", _i64), ("n_sources", _i64), ("n_cells", _i64),
+                ("n_plist", _i64), ("n_clist", _i64), ("i_pp", _i64), ("i_pc", _i64),
+                ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("sinks_per_thread", ctypes.c_int32), ("tile_j", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib(build: bool = True):
+    """Load (building first if needed) the CUDA library and bind every symbol."""
+    global _lib
+    if _lib is None:
+        path = _native.build_cuda() if build else _native.CUDA_LIB
+        L = _native.load(path)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+class QGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+def _host(a, dtype, shape=None):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a
+
+
+def _hp(a):
+    return None if a is None else a.ctypes.data
+
+
+def _dp(t):
+    return None if t is None else t.data_ptr()
+
+
+def _check_dev(t, dtype_name):
+    if t is None:
+        return
+    if not (hasattr(t, "is_cuda") and t.is_cuda):
+        raise TypeError("device entry points take CUDA tensors")
+    if str(t.dtype) != "torch." + dtype_name:
+        raise TypeError("expected torch.%s, got %s" % (dtype_name, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+
+
+@dataclass
+class Options:
+    precision: int = QG_FP32_CENTRED
+    expansion: int = QG_QUAD
+    tile_j: int = 0
+    warps_per_group: int = 0
+    sinks_per_thread: int = 0
+    flush_j: int = 0
+
+    def c(self):
+        return qg_options(self.precision, self.expansion, self.tile_j, self.warps_per_group,
+                          self.sinks_per_thread, self.flush_j)
+
+
+class Context:
+    """One ``qg_ctx``: inputs resident on one GPU, one force evaluation per run()."""
+
+    def __init__(self, device: int = 0, options: Options | None = None):
+        self._L = lib()
+        self._h = _vp()
+        o = (options or Options()).c()
+        st = self._L.qg_create(ctypes.byref(self._h), int(device), ctypes.addressof(o))
+        if st != QG_OK:
+            raise QGError(st, "qg_create(device=%d) failed" % device)
+        self.device = device
+        self.n = 0
+        self.G = -1
+
+    def _ok(self, st, what):
+        if st != QG_OK:
+            raise QGError(st, "%s: %s" % (what, self._L.qg_last_error(self._h).decode()))
+
+    def close(self):
+        if self._h:
+            self._L.qg_destroy(self._h)
+            self._h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, options: Options):
+        o = options.c()
+        self._ok(self._L.qg_set_options(self._h, ctypes.addressof(o)), "qg_set_options")
+
+    # ---- host inputs ------------------------------------------------------
+    def qg_set_sinks(self, x, group_off, eps2_all=0.0, eps2=None):
+        x = _host(x, np.float64, (-1, 3))
+        g = _host(group_off, np.int64)
+        e = None if eps2 is None else _host(eps2, np.float32)
+        if g.ndim != 1 or len(g) < 1 or (e is not None and len(e) != len(x)):
+            raise ValueError("qg_set_sinks: group_off must have ngroups+1 entries, eps2 one per sink")
+        self._ok(self._L.qg_set_sinks(self._h, len(x), _hp(x), _hp(e), float(eps2_all), len(g) - 1, _hp(g)),
+                 "qg_set_sinks")
+        self.n = len(x)
+        self.G = len(g) - 1
+
+    def _check_list(self, off, idx, what):
+        if len(off) != self.G + 1:
+            raise ValueError("%s: list_off has %d entries, the sinks have %d groups" % (what, len(off), self.G))
+        if off[-1] != len(idx):
+            raise ValueError("%s: list_off[-1] = %d but list_idx has %d entries" % (what, off[-1], len(idx)))
+
+    def qg_set_sources(self, x, m, list_off, list_idx):
+        x = _host(x, np.float64, (-1, 3))
+        m = _host(m, np.float64)
+        o = _host(list_off, np.int64)
+        i = _host(list_idx, np.int32)
+        self._check_list(o, i, "qg_set_sources")
+        if len(x) != len(m):
+            raise ValueError("qg_set_sources: x and m differ in length")
+        self._ok(self._L.qg_set_sources(self._h, len(m), _hp(x), _hp(m), _hp(o), _hp(i)), "qg_set_sources")
+
+    def qg_set_cells(self, com, m, q, list_off, list_idx):
+        com = _host(com, np.float64, (-1, 3))
+        m = _host(m, np.float64)
+        q = _host(q, np.float64, (-1, 6))
+        o = _host(list_off, np.int64)
+        i = _host(list_idx, np.int32)
+        self._check_list(o, i, "qg_set_cells")
+        if not (len(com) == len(m) == len(q)):
+            raise ValueError("qg_set_cells: com, m and q differ in length")
+        self._ok(self._L.qg_set_cells(self._h, len(m), _hp(com), _hp(m), _hp(q), _hp(o), _hp(i)),
+                 "qg_set_cells")
+
+    # ---- device inputs (torch CUDA tensors) --------------------------------
+    def qg_set_sinks_dev(self, x, group_off, eps2_all=0.0, eps2=None, stream=None):
+        _check_dev(x, "float64"), _check_dev(group_off, "int64"), _check_dev(eps2, "float32")
+        self._ok(self._L.qg_set_sinks_dev(self._h, x.numel() // 3, _dp(x), _dp(eps2), float(eps2_all),
+                                          group_off.numel() - 1, _dp(group_off), stream),
+                 "qg_set_sinks_dev")
+        self.n = x.numel() // 3
+        self.G = group_off.numel() - 1
+
+    def qg_set_sources_dev(self, x, m, list_off, list_idx, stream=None):
+        _check_dev(x, "float64"), _check_dev(m, "float64"), _check_dev(list_off, "int64")
+        _check_dev(list_idx, "int32")
+        if list_off.numel() != self.G + 1:
+            raise ValueError("qg_set_sources_dev: list_off must have ngroups+1 entries")
+        self._ok(self._L.qg_set_sources_dev(self._h, m.numel(), _dp(x), _dp(m), _dp(list_off), _dp(list_idx),
+                                            list_idx.numel(), stream), "qg_set_sources_dev")
+
+    def qg_set_cells_dev(self, com, m, q, list_off, list_idx, stream=None):
+        for t, d in ((com, "float64"), (m, "float64"), (q, "float64"), (list_off, "int64"), (list_idx, "int32")):
+            _check_dev(t, d)
+        if list_off.numel() != self.G + 1:
+            raise ValueError("qg_set_cells_dev: list_off must have ngroups+1 entries")
+        self._ok(self._L.qg_set_cells_dev(self._h, m.numel(), _dp(com), _dp(m), _dp(q), _dp(list_off),
+                                          _dp(list_idx), list_idx.numel(), stream), "qg_set_cells_dev")
+
+    # ---- run and results ---------------------------------------------------
+    def qg_run(self, stream=None):
+        """stream: a raw cudaStream_t (int), e.g. torch.cuda.current_stream().cuda_stream."""
+        self._ok(self._L.qg_run(self._h, stream), "qg_run")
+
+    def qg_get_forces(self, a=None, phi=None):
+        if a is None:
+            a = np.empty((self.n, 3))
+        if phi is None:
+            phi = np.empty(self.n)
+        assert a.flags.c_contiguous and a.dtype == np.float64 and a.size == 3 * self.n
+        assert phi.flags.c_contiguous and phi.dtype == np.float64 and phi.size == self.n
+        self._ok(self._L.qg_get_forces(self._h, _hp(a), _hp(phi)), "qg_get_forces")
+        return a, phi
+
+    def qg_get_forces_dev(self, a, phi, stream=None):
+        _check_dev(a, "float64"), _check_dev(phi, "float64")
+        self._ok(self._L.qg_get_forces_dev(self._h, _dp(a), _dp(phi), stream), "qg_get_forces_dev")
+
+    def qg_last_timing(self):
+        """(step_ms, force_ms) of the last run, from events inside its graph."""
+        st, fo = ctypes.c_float(), ctypes.c_float()
+        self._ok(self._L.qg_last_timing(self._h, ctypes.addressof(st), ctypes.addressof(fo)), "qg_last_timing")
+        return st.value, fo.value
+
+    def qg_get_stats(self) -> dict:
+        s = qg_stats()
+        self._ok(self._L.qg_get_stats(self._h, ctypes.addressof(s)), "qg_get_stats")
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def qg_direct_dev(sink_x, src_x, src_m, eps2, a, phi, device=0, stream=None):
+    """FP64 direct summation on the GPU (torch CUDA tensors in and out)."""
+    for t, d in ((sink_x, "float64"), (src_x, "float64"), (src_m, "float64"), (a, "float64"),
+                 (phi, "float64")):
+        _check_dev(t, d)
+    st = lib().qg_direct_dev(int(device), sink_x.numel() // 3, _dp(sink_x), float(eps2), src_m.numel(),
+                             _dp(src_x), _dp(src_m), _dp(a), _dp(phi), stream)
+    if st != QG_OK:
+        raise QGError(st, "qg_direct_dev failed")

@@ -1,0 +1,264 @@
+"""CUDA path (through the qg_* C-ABI) against the FP64 oracle, element by element
+on the same seeded inputs and lists."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_07313_gb300 import qgrav, workloads
+from tests.parity_util import Case, assert_parity, rel_err, summary, TOL_FP64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    qgrav.lib()  # a GPU machine without the library is a failure, not a skip
+
+
+@pytest.fixture(scope="module")
+def sphere4k():
+    return Case.workload("sphere_4k")
+
+
+def test_sphere_4k_quad_all_sinks(sphere4k):
+    """4096 particles in a sphere, theta = 0.5, n_crit = 64: every sink."""
+    a, phi, st = sphere4k.gpu()
+    a_ref, phi_ref = sphere4k.oracle()
+    assert st["i_pc"] > 0 and st["i_pp"] > 0
+    assert_parity(a, phi, a_ref, phi_ref, label="sphere_4k quad")
+
+
+def test_sphere_4k_mono(sphere4k):
+    a, phi, _ = sphere4k.gpu(qgrav.Options(expansion=qgrav.QG_MONO))
+    a_ref, phi_ref = sphere4k.oracle(use_quad=False)
+    assert_parity(a, phi, a_ref, phi_ref, label="sphere_4k mono")
+
+
+def test_sphere_4k_fp64_kernel(sphere4k):
+    for exp, uq in ((qgrav.QG_QUAD, True), (qgrav.QG_MONO, False)):
+        a, phi, _ = sphere4k.gpu(qgrav.Options(precision=qgrav.QG_FP64, expansion=exp))
+        a_ref, phi_ref = sphere4k.oracle(use_quad=uq)
+        assert_parity(a, phi, a_ref, phi_ref, med=TOL_FP64, p99=TOL_FP64, label="sphere_4k fp64")
+
+
+@pytest.mark.parametrize("R,warps,tile,flush", [
+    (2, 2, 32, 16), (2, 8, 96, 0), (4, 2, 64, 40), (4, 4, 256, 0), (4, 8, 1024, 1000),
+    (8, 2, 128, 0), (8, 4, 512, 8)])
+def test_launch_shapes_and_ragged_tiles(sphere4k, R, warps, tile, flush):
+    """Every supported launch shape, tiles that leave ragged tails, and FP64
+    folds from every entry to never."""
+    o = qgrav.Options(tile_j=tile, warps_per_group=warps, sinks_per_thread=R, flush_j=flush)
+    a, phi, st = sphere4k.gpu(o)
+    assert st["sinks_per_thread"] == R and st["tile_j"] == tile
+    a_ref, phi_ref = sphere4k.oracle()
+    assert_parity(a, phi, a_ref, phi_ref, label="shape %s" % ((R, warps, tile, flush),))
+
+
+def test_deterministic_and_repeatable(sphere4k):
+    ctx = qgrav.Context(0)
+    a1, p1, _ = sphere4k.gpu(ctx=ctx)
+    ctx.qg_run()
+    a2, p2 = ctx.qg_get_forces()
+    ctx.close()
+    assert np.array_equal(a1, a2) and np.array_equal(p1, p2)
+
+
+def test_device_pointer_entry_points_match_host(sphere4k):
+    import torch
+    t, L = sphere4k.tree, sphere4k.lists
+    a_h, phi_h, _ = sphere4k.gpu()
+    d = lambda x, dt: torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dt)
+    ctx = qgrav.Context(0)
+    ctx.qg_set_sinks_dev(d(t.x, torch.float64), d(t.group_off, torch.int64), sphere4k.eps2_all)
+    ctx.qg_set_sources_dev(d(t.x, torch.float64), d(t.m, torch.float64), d(L.plist_off, torch.int64),
+                           d(L.plist_idx, torch.int32))
+    ctx.qg_set_cells_dev(d(t.cell_com, torch.float64), d(t.cell_m, torch.float64), d(t.cell_q, torch.float64),
+                         d(L.clist_off, torch.int64), d(L.clist_idx, torch.int32))
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx.qg_run(stream)
+    a = torch.empty((t.n, 3), dtype=torch.float64, device="cuda")
+    phi = torch.empty(t.n, dtype=torch.float64, device="cuda")
+    ctx.qg_get_forces_dev(a, phi, stream)
+    torch.cuda.synchronize()
+    ctx.close()
+    assert np.array_equal(a.cpu().numpy(), a_h) and np.array_equal(phi.cpu().numpy(), phi_h)
+
+
+def test_gpu_direct_sum_matches_oracle():
+    import torch
+    ps = workloads.small_set("plummer", 3000, 4, 0.01)
+    sinks = ps.x[::7]
+    a_ref, phi_ref = oracle.direct_forces(sinks, ps.x, ps.m, eps2_all=1e-4)
+    d = lambda x: torch.as_tensor(np.ascontiguousarray(x)).cuda()
+    a = torch.empty((len(sinks), 3), dtype=torch.float64, device="cuda")
+    phi = torch.empty(len(sinks), dtype=torch.float64, device="cuda")
+    qgrav.qg_direct_dev(d(sinks), d(ps.x), d(ps.m), 1e-4, a, phi)
+    assert np.max(rel_err(a.cpu().numpy(), a_ref)) < 1e-12
+    assert np.max(rel_err(phi.cpu().numpy(), phi_ref)) < 1e-12
+
+
+# ------------------------------------------------------------------ edge cases
+
+def _explicit(sink_x, group_off, src_x, src_m, plist_off, plist_idx, com, cm, cq, clist_off, clist_idx,
+              eps2_all, eps2=None, options=None):
+    ctx = qgrav.Context(0, options)
+    ctx.qg_set_sinks(sink_x, group_off, eps2_all, eps2)
+    ctx.qg_set_sources(src_x, src_m, plist_off, plist_idx)
+    ctx.qg_set_cells(com, cm, cq, clist_off, clist_idx)
+    ctx.qg_run()
+    a, phi = ctx.qg_get_forces()
+    ctx.close()
+    e = None if eps2 is None else np.asarray(eps2, dtype=np.float64)
+    a_ref, phi_ref = oracle.expansion_forces(group_off, sink_x, src_x, src_m, plist_off, plist_idx, com, cm, cq,
+                                             clist_off, clist_idx, eps2_all=eps2_all, sink_eps2=e,
+                                             use_quad=(options is None or options.expansion == qgrav.QG_QUAD))
+    return a, phi, a_ref, phi_ref
+
+
+def _random_cells(rng, nc, centre, spread):
+    com = centre + rng.uniform(-spread, spread, (nc, 3))
+    cm = rng.uniform(0.5, 2.0, nc)
+    q = np.empty((nc, 6))
+    for c in range(nc):
+        xs = rng.uniform(-0.3, 0.3, (5, 3))
+        _, _, q[c] = oracle.cell_moments(xs, rng.uniform(0.1, 1, 5))
+    return com, cm, q
+
+
+def test_empty_lists_single_sinks_and_empty_groups():
+    """Groups with no list entries get zero force; one-sink groups; a group
+    with no sinks at all; lists of every length 0..70 (ragged tails)."""
+    rng = np.random.default_rng(1)
+    G = 72
+    sizes = rng.integers(0, 4, G)
+    sizes[5] = 0
+    sizes[6] = 1
+    group_off = np.concatenate([[0], np.cumsum(sizes)])
+    n = int(group_off[-1])
+    sink_x = rng.uniform(-1, 1, (n, 3))
+    src_x = rng.uniform(-5, 5, (300, 3))
+    src_m = rng.uniform(0.1, 1, 300)
+    com, cm, cq = _random_cells(rng, 90, np.array([10.0, 0, 0]), 3.0)
+    plen = np.arange(G) % 71
+    clen = (np.arange(G) * 7) % 67
+    plen[3] = 0
+    clen[3] = 0
+    plist_off = np.concatenate([[0], np.cumsum(plen)])
+    clist_off = np.concatenate([[0], np.cumsum(clen)])
+    plist_idx = rng.integers(0, 300, plist_off[-1]).astype(np.int32)
+    clist_idx = rng.integers(0, 90, clist_off[-1]).astype(np.int32)
+    a, phi, a_ref, phi_ref = _explicit(sink_x, group_off, src_x, src_m, plist_off, plist_idx, com, cm, cq,
+                                       clist_off, clist_idx, 1e-3, options=qgrav.Options(tile_j=32))
+    empty = np.arange(group_off[3], group_off[4])
+    assert np.all(a[empty] == 0.0) and np.all(phi[empty] == 0.0)
+    live = np.setdiff1d(np.arange(n), empty)
+    assert_parity(a[live], phi[live], a_ref[live], phi_ref[live], label="edges")
+
+
+def test_group_larger_than_one_cta_pass():
+    """A group of 1500 sinks is evaluated in several sink chunks of one CTA."""
+    ps = workloads.small_set("cube", 6000, 8, 2e-3)
+    case = Case(ps, 0.5, leaf_max=8, n_crit=1500)
+    assert np.diff(case.tree.group_off).max() > 512
+    for R in (2, 4):
+        a, phi, _ = case.gpu(qgrav.Options(sinks_per_thread=R))
+        a_ref, phi_ref = case.oracle()
+        assert_parity(a, phi, a_ref, phi_ref, label="big groups R=%d" % R)
+
+
+def test_zero_softening_skips_coincident_pairs():
+    """eps = 0: the self pair of every sink has rhat = 0 and is skipped by both."""
+    ps = workloads.small_set("sphere", 2000, 12, 0.0)
+    case = Case(ps, 0.5)
+    assert case.eps2_all == 0.0
+    a, phi, _ = case.gpu()
+    a_ref, phi_ref = case.oracle()
+    assert np.all(np.isfinite(a))
+    assert_parity(a, phi, a_ref, phi_ref, med=3e-6, p99=3e-5, label="eps=0")
+
+
+def test_per_sink_softening():
+    rng = np.random.default_rng(3)
+    ps = workloads.small_set("plummer", 3000, 13, 0.02)
+    case = Case(ps, 0.6)
+    case.eps2 = rng.uniform(1e-4, 4e-3, case.tree.n).astype(np.float32)
+    a, phi, _ = case.gpu()
+    a_ref, phi_ref = case.oracle()
+    assert_parity(a, phi, a_ref, phi_ref, label="per-sink eps")
+
+
+def test_far_from_origin_needs_centring():
+    """Systems thousands of units from the origin: the centred FP32 path holds
+    the tolerance; casting absolute coordinates (QG_FP32_RAW) cannot."""
+    ps = workloads.batched_systems(nsys=4, seed=21, n_lo=1500, n_hi=3000, spacing=4096.0)
+    case = Case(ps, 0.5)
+    a_ref, phi_ref = case.oracle()
+    a, phi, _ = case.gpu()
+    assert_parity(a, phi, a_ref, phi_ref, label="far, centred")
+    a_raw, phi_raw, _ = case.gpu(qgrav.Options(precision=qgrav.QG_FP32_RAW))
+    assert np.median(rel_err(a_raw, a_ref)) > 1e-3
+
+
+def test_invalid_lists_are_rejected_before_any_kernel_reads_them():
+    import torch
+    case = Case(workloads.small_set("sphere", 500, 2, 0.01), 0.5)
+    t, L = case.tree, case.lists
+    ctx = qgrav.Context(0)
+    ctx.qg_set_sinks(t.x, t.group_off, case.eps2_all)
+    bad = L.plist_idx.copy()
+    bad[len(bad) // 2] = t.n + 5
+    with pytest.raises(qgrav.QGError) as e:
+        ctx.qg_set_sources(t.x, t.m, L.plist_off, bad)
+    assert e.value.status == qgrav.QG_ERR_ARG
+    with pytest.raises(qgrav.QGError) as e:
+        ctx.qg_set_sources_dev(torch.as_tensor(t.x).cuda(), torch.as_tensor(t.m).cuda(),
+                               torch.as_tensor(L.plist_off).cuda(), torch.as_tensor(bad).cuda())
+    assert e.value.status == qgrav.QG_ERR_ARG
+    with pytest.raises(qgrav.QGError) as e:
+        ctx.qg_run()
+    assert e.value.status == qgrav.QG_ERR_STATE
+    ctx.qg_set_sources(t.x, t.m, L.plist_off, L.plist_idx)
+    ctx.qg_set_cells(t.cell_com, t.cell_m, t.cell_q, L.clist_off, L.clist_idx)
+    ctx.qg_run()
+    a, phi = ctx.qg_get_forces()
+    # lists set for another group count are refused by the binding
+    with pytest.raises(ValueError):
+        ctx.qg_set_cells(t.cell_com, t.cell_m, t.cell_q, L.clist_off[:-1], L.clist_idx)
+    # and offsets that do not start at 0 by the library
+    off = L.clist_off.copy()
+    off[0] = 1
+    with pytest.raises(qgrav.QGError) as e:
+        ctx.qg_set_cells(t.cell_com, t.cell_m, t.cell_q, off, np.zeros(off[-1], dtype=np.int32))
+    assert e.value.status == qgrav.QG_ERR_ARG
+    ctx.close()
+    assert np.all(np.isfinite(a))
+
+
+# ------------------------------------------------------------------ full sizes, sampled
+
+@pytest.mark.parametrize("name,theta,k", [
+    ("cube_1m", 0.5, 160), ("cube_1m", 0.3, 60), ("plummer_4m", 0.5, 120),
+    ("batched_512", 0.5, 160), ("clumpy_16m", 0.5, 100)])
+def test_full_size_sampled(name, theta, k):
+    """Full workloads in the launch configuration the benchmark times; the
+    oracle evaluates a seeded sample of groups (plus the largest group and
+    the one with the longest list)."""
+    case = Case.workload(name, theta)
+    a, phi, st = case.gpu()
+    groups = case.sample_groups(k, seed=hash(name) % 1000)
+    a_ref, phi_ref = case.oracle(groups=groups)
+    s = case.sinks_of(groups)
+    assert_parity(a[s], phi[s], a_ref[s], phi_ref[s], label="%s theta=%.2f" % (name, theta))
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(phi))
+
+
+def test_plummer_4m_fp64_kernel_sampled():
+    case = Case.workload("plummer_4m", 0.6)
+    a, phi, _ = case.gpu(qgrav.Options(precision=qgrav.QG_FP64))
+    groups = case.sample_groups(40, seed=5)
+    a_ref, phi_ref = case.oracle(groups=groups)
+    s = case.sinks_of(groups)
+    assert_parity(a[s], phi[s], a_ref[s], phi_ref[s], med=TOL_FP64, p99=TOL_FP64, label="plummer fp64")
