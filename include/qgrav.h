@@ -47,8 +47,8 @@
  * place but marks the context not runnable until the failing input is set
  * again successfully; qg_last_error() returns a message for the last error.
  * Out-of-range offsets or indices are rejected (QG_ERR_ARG) before any
- * kernel reads them: on the host for host arrays, by a checking kernel for
- * device arrays.  qg_run is asynchronous: a CUDA error from it surfaces as
+ * force kernel reads them: offsets on the host, list indices by a checking
+ * kernel on the device copy.  qg_run is asynchronous: a CUDA error from it surfaces as
  * QG_ERR_CUDA from qg_run or from the next synchronising call.
  *
  * Threading.  A context is used by one host thread at a time.
@@ -86,7 +86,7 @@ typedef struct {
   int sinks_per_thread; /* sinks held in registers per thread;
                            0 = default; supported: 2, 4, 8                  */
   int flush_j;          /* FP32 partials are folded into FP64 after at most
-                           this many list entries per thread; 0 = 128       */
+                           this many list entries per thread; 0 = 256       */
 } qg_options;
 
 typedef struct {
@@ -96,6 +96,8 @@ typedef struct {
   int32_t grid, block;        /* launch shape of the force kernel            */
   int32_t sinks_per_thread;   /* the kernel variant chosen                   */
   int32_t tile_j;
+  int32_t warps_per_group;
+  int32_t flush_j;
 } qg_stats;
 
 /* Create a context on CUDA device `device`.  opt may be NULL (defaults). */
@@ -151,6 +153,18 @@ qg_status qg_set_cells_dev(qg_ctx *ctx, int64_t nc, const double *com, const dou
  * `cuda_stream` (NULL = the context's stream).
  */
 qg_status qg_run(qg_ctx *ctx, void *cuda_stream);
+
+/*
+ * Autotuner: times every supported launch shape (sinks_per_thread x
+ * warps_per_group x tile_j) of the current precision / expansion on the
+ * inputs currently set, `reps` timed runs each after one warm-up run (the
+ * force kernel's device time, CUDA events), and keeps the fastest as the
+ * context's options.  The sink grouping itself (n_crit) is an input and is
+ * not tuned here.  best (may be NULL) receives the chosen options,
+ * best_ms the chosen shape's mean force-kernel time.  Synchronous; the
+ * outputs afterwards hold a valid result of the chosen shape.
+ */
+qg_status qg_autotune(qg_ctx *ctx, void *cuda_stream, int reps, qg_options *best, float *best_ms);
 
 /* Copy a [n][3] and phi [n] (either may be NULL) to the host; synchronises. */
 qg_status qg_get_forces(qg_ctx *ctx, double *a, double *phi);

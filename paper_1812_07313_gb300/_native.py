@@ -27,6 +27,9 @@ TREE_LIB = os.path.join(BUILD, "libqg_tree.so")
 CUDA_LIB = os.path.join(BUILD, "libqgrav.so")
 
 CUDA_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Per-source extra flags: the FP32 force kernels flush single-precision
+# denormals (one SFU instruction per reciprocal square root, no fix-up path).
+CUDA_FLAGS = {"qg_force_f32.cu": ["-ftz=true"]}
 
 _lock = threading.Lock()
 
@@ -79,7 +82,8 @@ def build_cuda(force=False, verbose=False, extra_flags=()):
                 o = os.path.join(BUILD, os.path.basename(s) + ".o")
                 objs.append(o)
                 cmd = [nvcc] + CUDA_ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                                            "-I" + INCLUDE, "-I" + CSRC, "-c", s, "-o", o] + list(extra_flags)
+                                            "-I" + INCLUDE, "-I" + CSRC, "-c", s, "-o", o] + list(extra_flags) \
+                    + CUDA_FLAGS.get(os.path.basename(s), [])
                 if verbose:
                     print(" ".join(cmd))
                 procs.append((cmd, subprocess.Popen(cmd)))

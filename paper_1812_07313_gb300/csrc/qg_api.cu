@@ -293,12 +293,14 @@ qg_status choose_kernel(qg_ctx *c) {
   c->R = R;
   c->nthreads = nt;
   c->tile = tile;
-  c->flush = o.flush_j ? o.flush_j : 128;
+  c->flush = o.flush_j ? o.flush_j : 256;
   c->smem = smem;
   c->grid = per_sm * c->num_sms;
   c->stats.block = nt;
   c->stats.sinks_per_thread = R;
   c->stats.tile_j = tile;
+  c->stats.warps_per_group = warps;
+  c->stats.flush_j = c->flush;
   return QG_OK;
 }
 
@@ -306,7 +308,7 @@ qg_status choose_kernel(qg_ctx *c) {
 qg_status record_step(qg_ctx *c, cudaStream_t s) {
   const int64_t G = c->G;
   int *hist = c->scratch.p, *cursor = hist + kBuckets, *head = cursor + kBuckets;
-  QG_CUDA(c, cudaEventRecord(c->ev[0], s));
+  QG_CUDA(c, cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
   QG_CUDA(c, cudaMemsetAsync(hist, 0, (2 * kBuckets + 2) * sizeof(int), s));
   const double cell_ops = c->opt.expansion == QG_QUAD ? 33.0 : 13.0;
   queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->goff.p, c->poff.p, c->coff.p, cell_ops,
@@ -337,9 +339,9 @@ qg_status record_step(qg_ctx *c, cudaStream_t s) {
   const int grid = (int)std::min<int64_t>(c->grid, std::max<int64_t>(G, 1));
   c->stats.grid = grid;
   void *args[] = {&p};
-  QG_CUDA(c, cudaEventRecord(c->ev[1], s));
+  QG_CUDA(c, cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
   QG_CUDA(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(c->nthreads), args, c->smem, s));
-  QG_CUDA(c, cudaEventRecord(c->ev[2], s));
+  QG_CUDA(c, cudaEventRecordWithFlags(c->ev[2], s, cudaEventRecordExternal));
   return QG_OK;
 }
 
@@ -412,17 +414,6 @@ qg_status check_indices_dev(qg_ctx *c, const int32_t *idx, int64_t cnt, int64_t 
   QG_CUDA(c, cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   QG_CUDA(c, cudaStreamSynchronize(s));
   if (h) return fail(c, QG_ERR_ARG, "%s: list entry outside [0, %lld)", what, (long long)n);
-  return QG_OK;
-}
-
-qg_status check_lists_host(qg_ctx *c, int64_t G, const int64_t *off, const int32_t *idx, int64_t n,
-                           const char *what) {
-  if (!valid_offsets_any_total(off, G)) return fail(c, QG_ERR_ARG, "%s: bad list offsets", what);
-  const int64_t cnt = off[G];
-  if (cnt > 0 && !idx) return fail(c, QG_ERR_ARG, "%s: list_idx is NULL", what);
-  for (int64_t i = 0; i < cnt; i++)
-    if (idx[i] < 0 || (int64_t)idx[i] >= n) return fail(c, QG_ERR_ARG, "%s: list entry %lld = %d outside [0, %lld)",
-                                                        what, (long long)i, idx[i], (long long)n);
   return QG_OK;
 }
 
@@ -580,7 +571,8 @@ static qg_status set_sources_common(qg_ctx *c, int64_t ns, const double *x, cons
     if ((st = check_indices_dev(c, list_idx, n_list_dev, ns, s, "qg_set_sources")) != QG_OK) return st;
   } else {
     std::memcpy(h.data(), list_off, (G + 1) * sizeof(int64_t));
-    if ((st = check_lists_host(c, G, h.data(), list_idx, ns, "qg_set_sources")) != QG_OK) return st;
+    if (!valid_offsets_any_total(h.data(), G)) return fail(c, QG_ERR_ARG, "qg_set_sources: bad list offsets");
+    if (h[G] > 0 && !list_idx) return fail(c, QG_ERR_ARG, "qg_set_sources: list_idx is NULL");
   }
   const int64_t cnt = h[G];
   if (dev) {
@@ -592,6 +584,8 @@ static qg_status set_sources_common(qg_ctx *c, int64_t ns, const double *x, cons
   } else {
     if ((st = upload(c, c->poff, list_off, G + 1, s)) != QG_OK) return st;
     if ((st = upload(c, c->pidx, list_idx, cnt, s)) != QG_OK) return st;
+    // indices are checked on the device, after the copy, before any kernel uses them
+    if ((st = check_indices_dev(c, c->pidx.p, cnt, ns, s, "qg_set_sources")) != QG_OK) return st;
     if ((st = upload(c, c->stage_x, x, 3 * ns, s)) != QG_OK) return st;
     if ((st = upload(c, c->stage_m, m, ns, s)) != QG_OK) return st;
     cudaError_t e = c->src.reserve(ns);
@@ -643,7 +637,8 @@ static qg_status set_cells_common(qg_ctx *c, int64_t nc, const double *com, cons
     if ((st = check_indices_dev(c, list_idx, n_list_dev, nc, s, "qg_set_cells")) != QG_OK) return st;
   } else {
     std::memcpy(h.data(), list_off, (G + 1) * sizeof(int64_t));
-    if ((st = check_lists_host(c, G, h.data(), list_idx, nc, "qg_set_cells")) != QG_OK) return st;
+    if (!valid_offsets_any_total(h.data(), G)) return fail(c, QG_ERR_ARG, "qg_set_cells: bad list offsets");
+    if (h[G] > 0 && !list_idx) return fail(c, QG_ERR_ARG, "qg_set_cells: list_idx is NULL");
   }
   const int64_t cnt = h[G];
   if (c->cell_xm.reserve(nc) != cudaSuccess || c->cell_q.reserve(2 * nc) != cudaSuccess ||
@@ -657,6 +652,7 @@ static qg_status set_cells_common(qg_ctx *c, int64_t nc, const double *com, cons
   } else {
     if ((st = upload(c, c->coff, list_off, G + 1, s)) != QG_OK) return st;
     if ((st = upload(c, c->cidx, list_idx, cnt, s)) != QG_OK) return st;
+    if ((st = check_indices_dev(c, c->cidx.p, cnt, nc, s, "qg_set_cells")) != QG_OK) return st;
     if ((st = upload(c, c->stage_x, com, 3 * nc, s)) != QG_OK) return st;
     if ((st = upload(c, c->stage_m, m, nc, s)) != QG_OK) return st;
     // Q goes straight into the FP64 copy, which the packer then reads
@@ -738,6 +734,67 @@ qg_status qg_get_forces_dev(qg_ctx *c, double *a, double *phi, void *stream) {
 qg_status qg_get_stats(const qg_ctx *c, qg_stats *out) {
   if (!c || !out) return QG_ERR_ARG;
   *out = c->stats;
+  return QG_OK;
+}
+
+qg_status qg_autotune(qg_ctx *c, void *stream, int reps, qg_options *best, float *best_ms) {
+  if (!c || reps < 1) return c ? fail(c, QG_ERR_ARG, "qg_autotune: reps must be >= 1") : QG_ERR_ARG;
+  if (!c->sinks_ok || !c->src_ok || !c->cells_ok || c->G_src != c->G || c->G_cell != c->G)
+    return fail(c, QG_ERR_STATE, "qg_autotune: sinks, sources and cells must all be set");
+  DeviceGuard dg(c->device);
+  cudaStream_t s = pick_stream(c, stream);
+  const qg_options base = c->opt;
+  qg_options chosen = base;
+  float chosen_ms = 0.f;
+  bool have = false;
+  if (c->G > 0) {
+    const int Rs[3] = {2, 4, 8}, Ws[3] = {2, 4, 8}, Ts[3] = {128, 256, 512};
+    for (int ri = 0; ri < 3; ri++)
+      for (int wi = 0; wi < 3; wi++)
+        for (int ti = 0; ti < 3; ti++) {
+          qg_options o = base;
+          o.sinks_per_thread = Rs[ri];
+          o.warps_per_group = Ws[wi];
+          o.tile_j = Ts[ti];
+          if (base.precision == QG_FP64 && Rs[ri] != 2) continue;
+          if (Rs[ri] >= 8 && Ws[wi] > 4) continue;
+          c->opt = o;
+          invalidate(c);
+          qg_status st = ensure_graph(c);
+          if (st != QG_OK) {
+            if (st == QG_ERR_ARG) continue;  // shape does not fit this device: skip it
+            c->opt = base;
+            invalidate(c);
+            return st;
+          }
+          float tot = 0.f;
+          for (int k = 0; k <= reps; k++) {
+            QG_CUDA(c, cudaGraphLaunch(c->exec, s));
+            QG_CUDA(c, cudaStreamSynchronize(s));
+            float ms = 0.f;
+            QG_CUDA(c, cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]));
+            if (k > 0) tot += ms;
+          }
+          const float mean = tot / reps;
+          if (!have || mean < chosen_ms) {
+            have = true;
+            chosen = o;
+            chosen_ms = mean;
+          }
+        }
+  }
+  c->opt = chosen;
+  invalidate(c);
+  if (c->G > 0) {
+    qg_status st = ensure_graph(c);
+    if (st != QG_OK) return st;
+    QG_CUDA(c, cudaGraphLaunch(c->exec, s));
+    QG_CUDA(c, cudaStreamSynchronize(s));
+  }
+  c->last_stream = s;
+  c->ran = true;
+  if (best) *best = chosen;
+  if (best_ms) *best_ms = chosen_ms;
   return QG_OK;
 }
 

@@ -102,12 +102,17 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
-// Largest block a variant is launched with: R = 8 keeps 8 sinks x 4 sums in
-// registers and is limited to 128 threads so that it does not spill.
-template <int R> struct MaxThreads { static constexpr int value = R >= 8 ? 128 : 256; };
+// Launch bounds per variant: the largest block it is launched with and the
+// CTAs per SM the register budget must allow.  R <= 4 is held to 64
+// registers (8 CTAs of 128 threads per SM); R = 8 keeps 8 sinks x 4 sums in
+// registers and is limited to 128 threads.
+template <int R> struct Bounds {
+  static constexpr int threads = R >= 8 ? 128 : 256;
+  static constexpr int min_blocks = R >= 8 ? 2 : 4;
+};
 
 template <typename Real, int R, bool QUAD, bool GUARD, bool CENTRED>
-__global__ void __launch_bounds__(MaxThreads<R>::value) force_kernel(const ForceParams p) {
+__global__ void __launch_bounds__(Bounds<R>::threads, Bounds<R>::min_blocks) force_kernel(const ForceParams p) {
   using V4 = typename RT<Real>::v4;
   using V2 = typename RT<Real>::v2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -118,11 +123,14 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) force_kernel(const Force
   const int NT = blockDim.x;
   const int tid = threadIdx.x;
   const int T = p.tile;
+  // acc64 [4R][NT] (value-major, so that a warp's accesses are consecutive);
+  // sink_s aliases it: the sink offsets are read into registers before the
+  // accumulators are zeroed.
+  double *acc64 = reinterpret_cast<double *>(smem_raw);
   V4 *sink_s = reinterpret_cast<V4 *>(smem_raw);
-  V4 *tA = sink_s + R * NT;
+  V4 *tA = reinterpret_cast<V4 *>(acc64 + 4 * R * NT);
   V4 *tB = tA + T;
   V2 *tC = reinterpret_cast<V2 *>(tB + T);
-  double *acc64 = reinterpret_cast<double *>(tC + T);
 
   for (;;) {
     __syncthreads();  // the previous group is finished with shared memory
@@ -183,8 +191,6 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) force_kernel(const Force
         sink_s[i] = RT<Real>::make4(RT<Real>::cvt(xi[0] - cx), RT<Real>::cvt(xi[1] - cy),
                                     RT<Real>::cvt(xi[2] - cz), RT<Real>::cvt(e2));
       }
-#pragma unroll
-      for (int v = 0; v < 4 * R; v++) acc64[tid * 4 * R + v] = 0.0;
       __syncthreads();
 
       const int S = (nch + R - 1) / R;  // sink slots
@@ -202,13 +208,19 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) force_kernel(const Force
         sx[r] = v.x; sy[r] = v.y; sz[r] = v.z; se[r] = v.w;
         ax[r] = ay[r] = az[r] = pt[r] = Real(0);
       }
+      __syncthreads();  // every thread holds its sinks: sink_s becomes acc64
+#pragma unroll
+      for (int v = 0; v < 4 * R; v++) acc64[v * NT + tid] = 0.0;
       int nproc = 0;
 
       auto fold = [&]() {
 #pragma unroll
         for (int r = 0; r < R; r++) {
-          double *a = acc64 + tid * 4 * R + 4 * r;
-          a[0] += (double)ax[r]; a[1] += (double)ay[r]; a[2] += (double)az[r]; a[3] += (double)pt[r];
+          double *a = acc64 + 4 * r * NT + tid;
+          a[0] += (double)ax[r];
+          a[NT] += (double)ay[r];
+          a[2 * NT] += (double)az[r];
+          a[3 * NT] += (double)pt[r];
           ax[r] = ay[r] = az[r] = pt[r] = Real(0);
         }
         nproc = 0;
@@ -296,8 +308,8 @@ __global__ void __launch_bounds__(MaxThreads<R>::value) force_kernel(const Force
         const int si = i % S, ri = i / S;
         double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
         for (int kk = 0; kk < K; kk++) {
-          const double *a = acc64 + (kk * S + si) * 4 * R + 4 * ri;
-          m0 += a[0]; m1 += a[1]; m2 += a[2]; m3 += a[3];
+          const double *a = acc64 + 4 * ri * NT + kk * S + si;
+          m0 += a[0]; m1 += a[NT]; m2 += a[2 * NT]; m3 += a[3 * NT];
         }
         const int64_t o = s0 + sb + i;
         p.a[3 * o] = m0;

@@ -40,9 +40,11 @@ struct ForceParams {
 // Dynamic shared memory of one force CTA.
 inline size_t force_smem_bytes(bool fp64, int R, int nthreads, int tile) {
   const size_t r4 = fp64 ? 32 : 16, r2 = fp64 ? 16 : 8;
-  return (size_t)R * nthreads * r4          // sink offsets + eps^2
-         + (size_t)tile * (2 * r4 + r2)     // staged tile: A, B (float4/double4_32a), C (2-vector)
-         + (size_t)nthreads * 4 * R * 8;    // FP64 accumulators
+  // FP64 accumulators [4R][nthreads]; the sink offsets (R * nthreads
+  // 4-vectors of Real, never larger) alias them
+  (void)r4;
+  return (size_t)nthreads * 4 * R * 8
+         + (size_t)tile * (2 * (fp64 ? 32 : 16) + r2);  // staged tile: A, B (4-vectors), C (2-vector)
 }
 
 // Kernel registry (one function per translation unit that instantiates it).

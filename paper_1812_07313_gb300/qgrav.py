@@ -46,6 +46,7 @@ SIGNATURES = {
     "qg_get_stats": ([_vp, _vp], _int),
     "qg_last_error": ([_vp], ctypes.c_char_p),
     "qg_last_timing": ([_vp, _vp, _vp], _int),
+    "qg_autotune": ([_vp, _vp, _int, _vp, _vp], _int),
     "qg_direct_dev": ([_int, _i64, _vp, _dbl, _i64, _vp, _vp, _vp, _vp, _vp], _int),
 }
 
@@ -59,7 +60,8 @@ class qg_stats(ctypes.Structure):
     _fields_ = [("n_sinks", _i64), ("n_groups", _i64), ("n_sources", _i64), ("n_cells", _i64),
                 ("n_plist", _i64), ("n_clist", _i64), ("i_pp", _i64), ("i_pc", _i64),
                 ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("sinks_per_thread", ctypes.c_int32), ("tile_j", ctypes.c_int32)]
+                ("sinks_per_thread", ctypes.c_int32), ("tile_j", ctypes.c_int32),
+                ("warps_per_group", ctypes.c_int32), ("flush_j", ctypes.c_int32)]
 
 
 _lib = None
@@ -241,6 +243,15 @@ class Context:
     def qg_get_forces_dev(self, a, phi, stream=None):
         _check_dev(a, "float64"), _check_dev(phi, "float64")
         self._ok(self._L.qg_get_forces_dev(self._h, _dp(a), _dp(phi), stream), "qg_get_forces_dev")
+
+    def qg_autotune(self, stream=None, reps=3):
+        """Time every launch shape on the current inputs, keep the fastest.
+        Returns (Options chosen, mean force-kernel ms)."""
+        o = qg_options()
+        ms = ctypes.c_float()
+        self._ok(self._L.qg_autotune(self._h, stream, int(reps), ctypes.addressof(o), ctypes.addressof(ms)),
+                 "qg_autotune")
+        return Options(o.precision, o.expansion, o.tile_j, o.warps_per_group, o.sinks_per_thread, o.flush_j), ms.value
 
     def qg_last_timing(self):
         """(step_ms, force_ms) of the last run, from events inside its graph."""

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_1812_07313_gb300 import qgrav, workloads
-from tests.parity_util import Case, assert_parity, rel_err, summary, TOL_FP64
+from tests.parity_util import Case, assert_parity, rel_err, summary, TOL_FP64, TOL_MEDIAN
 
 pytestmark = pytest.mark.gpu
 
@@ -55,6 +55,26 @@ def test_launch_shapes_and_ragged_tiles(sphere4k, R, warps, tile, flush):
     assert st["sinks_per_thread"] == R and st["tile_j"] == tile
     a_ref, phi_ref = sphere4k.oracle()
     assert_parity(a, phi, a_ref, phi_ref, label="shape %s" % ((R, warps, tile, flush),))
+
+
+def test_autotuner_picks_a_supported_shape_and_keeps_parity(sphere4k):
+    t, L = sphere4k.tree, sphere4k.lists
+    ctx = qgrav.Context(0)
+    ctx.qg_set_sinks(t.x, t.group_off, sphere4k.eps2_all)
+    ctx.qg_set_sources(t.x, t.m, L.plist_off, L.plist_idx)
+    ctx.qg_set_cells(t.cell_com, t.cell_m, t.cell_q, L.clist_off, L.clist_idx)
+    best, ms = ctx.qg_autotune(reps=2)
+    assert best.sinks_per_thread in (2, 4, 8) and best.warps_per_group in (2, 4, 8)
+    assert best.tile_j in (128, 256, 512) and ms > 0
+    st = ctx.qg_get_stats()
+    assert st["sinks_per_thread"] == best.sinks_per_thread and st["tile_j"] == best.tile_j
+    a0, p0 = ctx.qg_get_forces()
+    ctx.qg_run()
+    a, phi = ctx.qg_get_forces()
+    ctx.close()
+    assert np.array_equal(a, a0) and np.array_equal(phi, p0)
+    a_ref, phi_ref = sphere4k.oracle()
+    assert_parity(a, phi, a_ref, phi_ref, label="autotuned %s" % best)
 
 
 def test_deterministic_and_repeatable(sphere4k):
@@ -152,7 +172,10 @@ def test_empty_lists_single_sinks_and_empty_groups():
     clist_idx = rng.integers(0, 90, clist_off[-1]).astype(np.int32)
     a, phi, a_ref, phi_ref = _explicit(sink_x, group_off, src_x, src_m, plist_off, plist_idx, com, cm, cq,
                                        clist_off, clist_idx, 1e-3, options=qgrav.Options(tile_j=32))
-    empty = np.arange(group_off[3], group_off[4])
+    no_list = np.nonzero((plen == 0) & (clen == 0))[0]
+    assert 3 in no_list
+    empty = np.concatenate([np.arange(group_off[g], group_off[g + 1]) for g in no_list])
+    assert len(empty) > 0
     assert np.all(a[empty] == 0.0) and np.all(phi[empty] == 0.0)
     live = np.setdiff1d(np.arange(n), empty)
     assert_parity(a[live], phi[live], a_ref[live], phi_ref[live], label="edges")
@@ -199,7 +222,9 @@ def test_far_from_origin_needs_centring():
     a, phi, _ = case.gpu()
     assert_parity(a, phi, a_ref, phi_ref, label="far, centred")
     a_raw, phi_raw, _ = case.gpu(qgrav.Options(precision=qgrav.QG_FP32_RAW))
-    assert np.median(rel_err(a_raw, a_ref)) > 1e-3
+    e_raw, e_c = np.median(rel_err(a_raw, a_ref)), np.median(rel_err(a, a_ref))
+    print("far: median |da|/|a| raw %.2e centred %.2e" % (e_raw, e_c))
+    assert e_raw > 100 * TOL_MEDIAN and e_raw > 100 * e_c
 
 
 def test_invalid_lists_are_rejected_before_any_kernel_reads_them():
