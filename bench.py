@@ -39,6 +39,8 @@ DESCR = {
     "plummer_4m": "2^22-particle Plummer sphere (a=1, r<=100), eps=1e-3, leaf<=8, n_crit=256",
     "batched_512": "512 independent Plummer/Hernquist systems, N log-uniform in [1024, 65536], eps=1e-2, "
                    "n_crit=64, one persistent launch",
+    "batched_64": "64 independent Plummer/Hernquist systems, N log-uniform in [1024, 65536], eps=1e-2, "
+                  "n_crit=64 (the profiling-size case of batched_512)",
     "clumpy_16m": "2^24 particles in the unit cube, 70% in 2000 Plummer clumps + 30% uniform, eps=5e-5, "
                   "n_crit=256",
 }
@@ -57,6 +59,8 @@ def parse():
     ap.add_argument("--no-equal-error", action="store_true", help="skip the monopole equal-error search")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--launch", default=None,
+                    help="R,W,T: fixed sinks/thread, warps/CTA, tile instead of the autotuner (profiling)")
     return ap.parse_args()
 
 
@@ -297,16 +301,23 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     flush = torch.zeros(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     t_tune = time.perf_counter()
-    best, best_ms = ctx.qg_autotune(stream.cuda_stream, reps=3)
+    if args.launch:
+        R, W, T = (int(v) for v in args.launch.split(","))
+        ctx.set_options(qgrav.Options(sinks_per_thread=R, warps_per_group=W, tile_j=T))
+    else:
+        ctx.qg_autotune(stream.cuda_stream, reps=3)
     t_tune = time.perf_counter() - t_tune
     st = ctx.qg_get_stats()
     launch = {"sinks_per_thread": st["sinks_per_thread"], "warps_per_group": st["warps_per_group"],
               "tile_j": st["tile_j"], "flush_j": st["flush_j"], "grid": st["grid"], "block": st["block"],
-              "autotune_s": t_tune}
+              "autotune_s": t_tune, "autotuned": not args.launch}
     for _ in range(max(args.warmup, 0)):
         ctx.qg_run(stream.cuda_stream)
     torch.cuda.synchronize()
     a_quad, _ = ctx.qg_get_forces()
+    st = ctx.qg_get_stats()
+    launch.update({"sinks_per_thread": st["sinks_per_thread"], "warps_per_group": st["warps_per_group"],
+                   "tile_j": st["tile_j"], "grid": st["grid"], "block": st["block"]})
 
     if world > 1:
         dist.barrier()

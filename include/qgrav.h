@@ -195,6 +195,17 @@ qg_status qg_direct_dev(int device, int64_t nsink, const double *sink_x, double 
                         int64_t nsrc, const double *src_x, const double *src_m,
                         double *a, double *phi, void *cuda_stream);
 
+/*
+ * Self-test of the rounding the FP32 kernels apply to FP64-centred offsets:
+ * double -> float, nearest with ties to even, done with integer operations
+ * (IEEE 754 binary64 -> binary32).  Magnitudes below the smallest normal
+ * float give a signed zero.  qg_round_f32_host runs it on the CPU (host
+ * arrays); qg_round_f32_dev runs it on the GPU (device arrays) and writes
+ * the hardware conversion of the same inputs to out_hw for comparison.
+ */
+qg_status qg_round_f32_host(int64_t n, const double *in, float *out);
+qg_status qg_round_f32_dev(int64_t n, const double *in, float *out, float *out_hw, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,20 +22,34 @@ constexpr int kBuckets = 128;  // cost classes of the work queue (4 per octave)
 
 // ------------------------------------------------------------------ kernels
 
-// sources: [ns][3] + [ns] -> double4_32a (x, y, z, m)
+// sources: [ns][3] + [ns] -> PosMass (x, y, z, float m); the FP64 masses
+// stay in their own array (m is that array).
 __global__ void pack_src_kernel(int64_t ns, const double *__restrict__ x, const double *__restrict__ m,
-                                double4_32a *__restrict__ out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = make_double4_32a(x[3 * i], x[3 * i + 1], x[3 * i + 2], m[i]);
+                                qg::PosMass *__restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x) {
+    qg::PosMass v;
+    v.x = x[3 * i];
+    v.y = x[3 * i + 1];
+    v.z = x[3 * i + 2];
+    v.m = (float)m[i];
+    v.pad = 0.f;
+    out[i] = v;
+  }
 }
 
-// cells: com [nc][3], m [nc], q [nc][6] -> double4_32a (x, y, z, m), float4 x 2 (Q),
-// and a dense FP64 copy of Q for the all-FP64 kernel.
+// cells: com [nc][3], m [nc], q [nc][6] -> PosMass, float4 x 2 (Q), and a
+// dense FP64 copy of Q for the all-FP64 kernel (skipped when q already is it).
 __global__ void pack_cells_kernel(int64_t nc, const double *__restrict__ com, const double *__restrict__ m,
-                                  const double *__restrict__ q, double4_32a *__restrict__ xm,
-                                  float4 *__restrict__ qf, double *__restrict__ q64) {
+                                  const double *q, qg::PosMass *__restrict__ pm,
+                                  float4 *__restrict__ qf, double *q64) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc; i += (int64_t)gridDim.x * blockDim.x) {
-    xm[i] = make_double4_32a(com[3 * i], com[3 * i + 1], com[3 * i + 2], m[i]);
+    qg::PosMass v;
+    v.x = com[3 * i];
+    v.y = com[3 * i + 1];
+    v.z = com[3 * i + 2];
+    v.m = (float)m[i];
+    v.pad = 0.f;
+    pm[i] = v;
     const double *qi = q + 6 * i;
     qf[2 * i] = make_float4((float)qi[0], (float)qi[1], (float)qi[2], (float)qi[3]);
     qf[2 * i + 1] = make_float4((float)qi[4], (float)qi[5], 0.f, 0.f);
@@ -143,15 +157,17 @@ struct qg_ctx {
   // sources
   int64_t ns = 0, G_src = -1, np_list = 0;
   bool src_ok = false;
-  DevBuf<double4_32a> src;
-  DevBuf<double> stage_x, stage_m, stage_q;  // device staging of host inputs
+  DevBuf<qg::PosMass> src;
+  DevBuf<double> src_m64;
+  DevBuf<double> stage_x;  // device staging of host positions
   DevBuf<int64_t> poff;
   DevBuf<int32_t> pidx;
   std::vector<int64_t> h_poff;
   // cells
   int64_t nc = 0, G_cell = -1, nc_list = 0;
   bool cells_ok = false;
-  DevBuf<double4_32a> cell_xm;
+  DevBuf<qg::PosMass> cell_pm;
+  DevBuf<double> cell_m64;
   DevBuf<float4> cell_q;
   DevBuf<double> cell_q64;
   DevBuf<int64_t> coff;
@@ -322,9 +338,11 @@ qg_status record_step(qg_ctx *c, cudaStream_t s) {
   p.eps2_all = c->eps2_all;
   p.group_off = c->goff.p;
   p.src = c->src.p;
+  p.src_m64 = c->src_m64.p;
   p.plist_off = c->poff.p;
   p.plist_idx = c->pidx.p;
-  p.cell_xm = c->cell_xm.p;
+  p.cell_pm = c->cell_pm.p;
+  p.cell_m64 = c->cell_m64.p;
   p.cell_q = c->cell_q.p;
   p.cell_q64 = c->cell_q64.p;
   p.clist_off = c->coff.p;
@@ -463,9 +481,9 @@ void qg_destroy(qg_ctx *c) {
   if (c->stream) cudaStreamSynchronize(c->stream);
   invalidate(c);
   c->sink_x.release(); c->sink_eps2.release(); c->goff.release();
-  c->src.release(); c->stage_x.release(); c->stage_m.release(); c->stage_q.release();
+  c->src.release(); c->src_m64.release(); c->stage_x.release();
   c->poff.release(); c->pidx.release();
-  c->cell_xm.release(); c->cell_q.release(); c->cell_q64.release(); c->coff.release(); c->cidx.release();
+  c->cell_pm.release(); c->cell_m64.release(); c->cell_q.release(); c->cell_q64.release(); c->coff.release(); c->cidx.release();
   c->a.release(); c->phi.release(); c->scratch.release(); c->bucket.release(); c->queue.release();
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
@@ -578,19 +596,20 @@ static qg_status set_sources_common(qg_ctx *c, int64_t ns, const double *x, cons
   if (dev) {
     if ((st = copy_d2d(c, c->poff, list_off, G + 1, s)) != QG_OK) return st;
     if ((st = copy_d2d(c, c->pidx, list_idx, cnt, s)) != QG_OK) return st;
+    if ((st = copy_d2d(c, c->src_m64, m, ns, s)) != QG_OK) return st;
     cudaError_t e = c->src.reserve(ns);
     if (e != cudaSuccess) return fail(c, QG_ERR_NOMEM, "source allocation");
-    if (ns) pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, x, m, c->src.p);
+    if (ns) pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, x, c->src_m64.p, c->src.p);
   } else {
     if ((st = upload(c, c->poff, list_off, G + 1, s)) != QG_OK) return st;
     if ((st = upload(c, c->pidx, list_idx, cnt, s)) != QG_OK) return st;
     // indices are checked on the device, after the copy, before any kernel uses them
     if ((st = check_indices_dev(c, c->pidx.p, cnt, ns, s, "qg_set_sources")) != QG_OK) return st;
     if ((st = upload(c, c->stage_x, x, 3 * ns, s)) != QG_OK) return st;
-    if ((st = upload(c, c->stage_m, m, ns, s)) != QG_OK) return st;
+    if ((st = upload(c, c->src_m64, m, ns, s)) != QG_OK) return st;
     cudaError_t e = c->src.reserve(ns);
     if (e != cudaSuccess) return fail(c, QG_ERR_NOMEM, "source allocation");
-    if (ns) pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, c->stage_x.p, c->stage_m.p, c->src.p);
+    if (ns) pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, c->stage_x.p, c->src_m64.p, c->src.p);
   }
   QG_CUDA(c, cudaGetLastError());
   QG_CUDA(c, cudaStreamSynchronize(s));
@@ -641,25 +660,27 @@ static qg_status set_cells_common(qg_ctx *c, int64_t nc, const double *com, cons
     if (h[G] > 0 && !list_idx) return fail(c, QG_ERR_ARG, "qg_set_cells: list_idx is NULL");
   }
   const int64_t cnt = h[G];
-  if (c->cell_xm.reserve(nc) != cudaSuccess || c->cell_q.reserve(2 * nc) != cudaSuccess ||
+  if (c->cell_pm.reserve(nc) != cudaSuccess || c->cell_q.reserve(2 * nc) != cudaSuccess ||
       c->cell_q64.reserve(6 * nc) != cudaSuccess)
     return fail(c, QG_ERR_NOMEM, "cell allocation");
   if (dev) {
     if ((st = copy_d2d(c, c->coff, list_off, G + 1, s)) != QG_OK) return st;
     if ((st = copy_d2d(c, c->cidx, list_idx, cnt, s)) != QG_OK) return st;
+    if ((st = copy_d2d(c, c->cell_m64, m, nc, s)) != QG_OK) return st;
     if (nc)
-      pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, com, m, q, c->cell_xm.p, c->cell_q.p, c->cell_q64.p);
+      pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, com, c->cell_m64.p, q, c->cell_pm.p, c->cell_q.p,
+                                                           c->cell_q64.p);
   } else {
     if ((st = upload(c, c->coff, list_off, G + 1, s)) != QG_OK) return st;
     if ((st = upload(c, c->cidx, list_idx, cnt, s)) != QG_OK) return st;
     if ((st = check_indices_dev(c, c->cidx.p, cnt, nc, s, "qg_set_cells")) != QG_OK) return st;
     if ((st = upload(c, c->stage_x, com, 3 * nc, s)) != QG_OK) return st;
-    if ((st = upload(c, c->stage_m, m, nc, s)) != QG_OK) return st;
+    if ((st = upload(c, c->cell_m64, m, nc, s)) != QG_OK) return st;
     // Q goes straight into the FP64 copy, which the packer then reads
     if ((st = upload(c, c->cell_q64, q, 6 * nc, s)) != QG_OK) return st;
     if (nc)
-      pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, c->stage_x.p, c->stage_m.p, c->cell_q64.p,
-                                                           c->cell_xm.p, c->cell_q.p, c->cell_q64.p);
+      pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, c->stage_x.p, c->cell_m64.p, c->cell_q64.p,
+                                                           c->cell_pm.p, c->cell_q.p, c->cell_q64.p);
   }
   QG_CUDA(c, cudaGetLastError());
   QG_CUDA(c, cudaStreamSynchronize(s));

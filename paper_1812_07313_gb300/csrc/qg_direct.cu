@@ -5,9 +5,18 @@
 
 #include <cstdint>
 
+#include "qg_internal.h"
 #include "qgrav.h"
 
 namespace {
+
+__global__ void round_f32_kernel(int64_t n, const double *__restrict__ in, float *__restrict__ out,
+                                 float *__restrict__ out_hw) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    out[i] = qg::f64_to_f32_rn(in[i]);
+    out_hw[i] = __double2float_rn(in[i]);
+  }
+}
 
 constexpr int kThreads = 128;
 
@@ -71,4 +80,20 @@ extern "C" qg_status qg_direct_dev(int device, int64_t nsink, const double *sink
   }
   if (prev != device) cudaSetDevice(prev);
   return st;
+}
+
+extern "C" qg_status qg_round_f32_host(int64_t n, const double *in, float *out) {
+  if (n < 0 || (n > 0 && (!in || !out))) return QG_ERR_ARG;
+  for (int64_t i = 0; i < n; i++) out[i] = qg::f64_to_f32_rn(in[i]);
+  return QG_OK;
+}
+
+extern "C" qg_status qg_round_f32_dev(int64_t n, const double *in, float *out, float *out_hw, void *cuda_stream) {
+  if (n < 0 || (n > 0 && (!in || !out || !out_hw))) return QG_ERR_ARG;
+  if (n == 0) return QG_OK;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int64_t blocks = (n + 255) / 256;
+  round_f32_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(n, in, out, out_hw);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return QG_ERR_CUDA;
+  return QG_OK;
 }

@@ -35,7 +35,7 @@ template <> struct RT<float> {
   using v2 = float2;
   static __device__ __forceinline__ v4 make4(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
   static __device__ __forceinline__ v2 make2(float a, float b) { return make_float2(a, b); }
-  static __device__ __forceinline__ float cvt(double x) { return __double2float_rn(x); }
+  static __device__ __forceinline__ float cvt(double x) { return f64_to_f32_rn(x); }
   // SFU approximate reciprocal square root (MUFU.RSQ)
   static __device__ __forceinline__ float rsqrt(float x) { return rsqrtf(x); }
 };
@@ -150,9 +150,9 @@ __global__ void __launch_bounds__(Bounds<R>::threads, Bounds<R>::min_blocks) for
       float mn0 = 0.f, mn1 = 0.f, mn2 = 0.f, mx0 = 0.f, mx1 = 0.f, mx2 = 0.f;
       for (int i = tid; i < ni; i += NT) {
         const double *xi = p.sink_x + 3 * (s0 + i);
-        const float o0 = __double2float_rn(xi[0] - x0);
-        const float o1 = __double2float_rn(xi[1] - y0);
-        const float o2 = __double2float_rn(xi[2] - z0);
+        const float o0 = f64_to_f32_rn(xi[0] - x0);
+        const float o1 = f64_to_f32_rn(xi[1] - y0);
+        const float o2 = f64_to_f32_rn(xi[2] - z0);
         mn0 = fminf(mn0, o0); mn1 = fminf(mn1, o1); mn2 = fminf(mn2, o2);
         mx0 = fmaxf(mx0, o0); mx1 = fmaxf(mx1, o1); mx2 = fmaxf(mx2, o2);
       }
@@ -232,9 +232,10 @@ __global__ void __launch_bounds__(Bounds<R>::threads, Bounds<R>::min_blocks) for
         __syncthreads();
         for (int t = tid; t < cnt; t += NT) {
           const int j = p.plist_idx[base + t];
-          const double4_32a v = p.src[j];
+          const PosMass v = p.src[j];
+          const Real m = sizeof(Real) == 4 ? (Real)v.m : (Real)p.src_m64[j];
           tA[t] = RT<Real>::make4(RT<Real>::cvt(v.x - cx), RT<Real>::cvt(v.y - cy),
-                                  RT<Real>::cvt(v.z - cz), RT<Real>::cvt(v.w));
+                                  RT<Real>::cvt(v.z - cz), m);
         }
         __syncthreads();
         if (active) {
@@ -257,9 +258,10 @@ __global__ void __launch_bounds__(Bounds<R>::threads, Bounds<R>::min_blocks) for
         __syncthreads();
         for (int t = tid; t < cnt; t += NT) {
           const int j = p.clist_idx[base + t];
-          const double4_32a v = p.cell_xm[j];
+          const PosMass v = p.cell_pm[j];
+          const Real m = sizeof(Real) == 4 ? (Real)v.m : (Real)p.cell_m64[j];
           tA[t] = RT<Real>::make4(RT<Real>::cvt(v.x - cx), RT<Real>::cvt(v.y - cy),
-                                  RT<Real>::cvt(v.z - cz), RT<Real>::cvt(v.w));
+                                  RT<Real>::cvt(v.z - cz), m);
           if (QUAD) {
             if (sizeof(Real) == 4) {
               const float4 q0 = p.cell_q[2 * j], q1 = p.cell_q[2 * j + 1];

@@ -7,23 +7,67 @@
 
 namespace qg {
 
+// One gathered list entry's position (FP64, centred on the GPU) and its
+// mass as the FP32 kernels use it: one aligned 32-byte sector.
+struct __align__(32) PosMass {
+  double x, y, z;
+  float m;
+  float pad;
+};
+
+// Round a double to the nearest float, ties to even, with integer
+// operations only (IEEE 754 binary64 -> binary32: keep the sign, rebias the
+// exponent from 1023 to 127, keep the top 23 of the 52 fraction bits and
+// round on the 29 dropped ones).  Magnitudes below the smallest normal float
+// give a signed zero (the FP32 kernels flush denormals anyway); callers only
+// pass position offsets, far below the largest float.  On this GPU the
+// hardware double->float conversion issues on the narrow FP64 pipe, which
+// this keeps free for the FP64 centring itself.
+__host__ __device__ inline float f64_to_f32_rn(double x) {
+#ifdef __CUDA_ARCH__
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long b;
+  __builtin_memcpy(&b, &x, sizeof b);
+#endif
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  unsigned t = (hi << 3) | (lo >> 29);       // low 9 exponent bits | 23 fraction bits
+  t -= 384u << 23;                           // exponent - 896 (mod 512): 1023 -> 127 bias
+  const unsigned r = lo & 0x1fffffffu;       // the 29 dropped fraction bits
+  t += (r + (t & 1u) + 0x0fffffffu) >> 29;   // round half to even (a carry bumps the exponent)
+  t = ((hi & 0x7ff00000u) < (897u << 20)) ? 0u : t;  // below the smallest normal float
+  t |= hi & 0x80000000u;                     // sign
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(t);
+#else
+  float f;
+  __builtin_memcpy(&f, &t, sizeof f);
+  return f;
+#endif
+}
+
 // Device pointers and sizes one force launch reads.  Layouts:
 //   sink_x    [n][3] double           sink_eps2 [n] float or null
 //   group_off [G+1]                   queue     [nitems] group ids
-//   src       [ns] double4_32a (x, y, z, m)
-//   cell_xm   [nc] double4_32a (x, y, z, m)
+//   src       [ns] PosMass (x, y, z double; m float)   src_m64  [ns] double m
+//   cell_pm   [nc] PosMass (x, y, z double; m float)   cell_m64 [nc] double m
 //   cell_q    [nc][2] float4 ((q00, q01, q02, q11), (q12, q22, 0, 0))
 //   cell_q64  [nc][6] double (q00 q01 q02 q11 q12 q22)
+// The FP32 kernels read PosMass and cell_q (two 32-byte sectors per cell);
+// the all-FP64 kernel reads the positions of PosMass and the *_m64 / q64
+// arrays.
 //   a         [n][3] double           phi [n] double
 struct ForceParams {
   const double *sink_x;
   const float *sink_eps2;
   double eps2_all;
   const int64_t *group_off;
-  const double4_32a *src;
+  const PosMass *src;
+  const double *src_m64;
   const int64_t *plist_off;
   const int32_t *plist_idx;
-  const double4_32a *cell_xm;
+  const PosMass *cell_pm;
+  const double *cell_m64;
   const float4 *cell_q;
   const double *cell_q64;
   const int64_t *clist_off;

@@ -48,6 +48,8 @@ SIGNATURES = {
     "qg_last_timing": ([_vp, _vp, _vp], _int),
     "qg_autotune": ([_vp, _vp, _int, _vp, _vp], _int),
     "qg_direct_dev": ([_int, _i64, _vp, _dbl, _i64, _vp, _vp, _vp, _vp, _vp], _int),
+    "qg_round_f32_host": ([_i64, _vp, _vp], _int),
+    "qg_round_f32_dev": ([_i64, _vp, _vp, _vp, _vp], _int),
 }
 
 
@@ -274,3 +276,21 @@ def qg_direct_dev(sink_x, src_x, src_m, eps2, a, phi, device=0, stream=None):
                              _dp(src_x), _dp(src_m), _dp(a), _dp(phi), stream)
     if st != QG_OK:
         raise QGError(st, "qg_direct_dev failed")
+
+
+def qg_round_f32_host(x):
+    """The kernels' FP64 -> FP32 rounding routine, run on the CPU."""
+    x = _host(x, np.float64)
+    out = np.empty(x.shape, dtype=np.float32)
+    st = lib().qg_round_f32_host(x.size, _hp(x), _hp(out))
+    if st != QG_OK:
+        raise QGError(st, "qg_round_f32_host failed")
+    return out
+
+
+def qg_round_f32_dev(x, out, out_hw, stream=None):
+    """The same routine on the GPU next to the hardware conversion (CUDA tensors)."""
+    _check_dev(x, "float64"), _check_dev(out, "float32"), _check_dev(out_hw, "float32")
+    st = lib().qg_round_f32_dev(x.numel(), _dp(x), _dp(out), _dp(out_hw), stream)
+    if st != QG_OK:
+        raise QGError(st, "qg_round_f32_dev failed")

@@ -17,6 +17,8 @@ workloads this library is measured on:
   ``batched_512``   512 independent Plummer / Hernquist systems with N
                     log-uniform in [1024, 65536], eps = 1e-2, n_crit = 64,
                     theta = 0.5, each system placed far from the origin
+  ``batched_64``    the first 64 systems' distribution of batched_512 (a
+                    smaller case of the same kernel shape, for profiling)
   ``clumpy_16m``    2^24 particles in the unit cube: 70 % in 2000 Plummer clumps
                     (clump masses dN/dM ~ M^-1.9 on [1, 1000], scale radii
                     log-uniform in [1e-3, 1e-2], truncated at 10 scale radii,
@@ -200,6 +202,7 @@ _GENERATORS = {
     "cube_1m": _cube_1m,
     "plummer_4m": lambda: single_system("plummer_4m", plummer(1 << 22, 3), 1e-3),
     "batched_512": lambda: batched_systems(512, 4),
+    "batched_64": lambda: batched_systems(64, 4),
     "clumpy_16m": lambda: single_system("clumpy_16m", clumpy_field(1 << 24, 5), 5e-5),
 }
 
@@ -208,6 +211,7 @@ WORKLOADS = {
     "cube_1m": Workload("cube_1m", 8, 256, (0.3, 0.5, 0.7), 0.5),
     "plummer_4m": Workload("plummer_4m", 8, 256, (0.3, 0.4, 0.5, 0.6, 0.7, 0.8), 0.5),
     "batched_512": Workload("batched_512", 8, 64, (0.5,), 0.5),
+    "batched_64": Workload("batched_64", 8, 64, (0.5,), 0.5),
     "clumpy_16m": Workload("clumpy_16m", 8, 256, (0.5,), 0.5),
 }
 
