@@ -70,7 +70,8 @@ typedef enum {
   QG_ERR_CUDA = -2,    /* a CUDA call failed                               */
   QG_ERR_NOMEM = -3,   /* device or host allocation failed                 */
   QG_ERR_STATE = -4,   /* inputs missing or inconsistent (e.g. ngroups)    */
-  QG_ERR_TIMEOUT = -5  /* a bounded device-side wait gave up               */
+  QG_ERR_TIMEOUT = -5, /* a bounded device-side wait gave up               */
+  QG_ERR_SIZE = -6     /* a size beyond a fixed maximum (qg_forces_noalloc) */
 } qg_status;
 
 enum { QG_FP32_CENTRED = 0, QG_FP32_RAW = 1, QG_FP64 = 2 };
@@ -205,6 +206,44 @@ qg_status qg_direct_dev(int device, int64_t nsink, const double *sink_x, double 
  */
 qg_status qg_round_f32_host(int64_t n, const double *in, float *out);
 qg_status qg_round_f32_dev(int64_t n, const double *in, float *out, float *out_hw, void *cuda_stream);
+
+/*
+ * One force evaluation that allocates no memory, host or device.  The paper
+ * has no counterpart: this is an entry point for callers that cannot call
+ * cudaMalloc -- host codes whose device memory belongs to their own pool or
+ * arena, and time-stepping loops that may not allocate (cudaMalloc and
+ * cudaFree can block or synchronise the device) once they are running.
+ *
+ * Every input and output is a caller-owned device array on `device`, in the
+ * layouts of qg_set_sinks_dev / qg_set_sources_dev / qg_set_cells_dev;
+ * a [n][3] and phi [n] receive the result (FP32 pairwise arithmetic with FP64
+ * centring and merges, QG_QUAD or QG_MONO as `expansion`; a fixed launch
+ * shape).  The step's only scratch, its work queue, lives in one fixed
+ * device array inside this library, sized for ngroups <= QG_NOALLOC_MAX_GROUPS
+ * (about 5 MiB, held by every GPU that loads the library until the process
+ * exits); a larger ngroups returns QG_ERR_SIZE before any GPU work.  Offsets
+ * and list indices are checked on the GPU first (QG_ERR_ARG if invalid);
+ * n_plist / n_clist are the list lengths, and every array must be at least
+ * as long as the sizes say.
+ *
+ * All calls on a device share that scratch array and it keeps the last
+ * call's contents (each call clears what it needs zeroed): calls whose work
+ * overlaps on the GPU -- on different streams, or from racing host threads
+ * -- corrupt each other.  The first call on a device looks up the array's
+ * device address and caches it (make that first call before any stream
+ * capture).  The call waits for the argument check on `cuda_stream`, then
+ * launches the step and returns; a and phi are complete when the stream
+ * reaches that point.
+ */
+#define QG_NOALLOC_MAX_GROUPS (1 << 20)
+qg_status qg_forces_noalloc(int device, int64_t n, const double *sink_x, const float *sink_eps2,
+                            double eps2_all, int64_t ngroups, const int64_t *group_off,
+                            int64_t ns, const double *src_x, const double *src_m,
+                            const int64_t *plist_off, const int32_t *plist_idx, int64_t n_plist,
+                            int64_t nc, const double *cell_com, const double *cell_m,
+                            const double *cell_q, const int64_t *clist_off,
+                            const int32_t *clist_idx, int64_t n_clist, int expansion,
+                            double *a, double *phi, void *cuda_stream);
 
 #ifdef __cplusplus
 }

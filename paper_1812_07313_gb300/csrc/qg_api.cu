@@ -14,11 +14,14 @@
 #include <vector>
 
 #include "qg_internal.h"
+#include "qg_queue.cuh"
 #include "qgrav.h"
 
 namespace {
 
-constexpr int kBuckets = 128;  // cost classes of the work queue (4 per octave)
+using qg::kBuckets;
+using qg::queue_hist_kernel;
+using qg::queue_scatter_kernel;
 
 // ------------------------------------------------------------------ kernels
 
@@ -63,51 +66,6 @@ __global__ void check_index_kernel(int64_t cnt, const int32_t *__restrict__ idx,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t v = idx[i];
     if (v < 0 || (int64_t)v >= n) atomicOr(bad, 1);
-  }
-}
-
-__device__ __forceinline__ int cost_bucket(double cost) {
-  if (!(cost > 1.0)) return 0;
-  const int b = (int)(4.0 * log2(cost));
-  return b < kBuckets ? b : kBuckets - 1;
-}
-
-// Work queue, pass 1: cost class of every group and a histogram of classes.
-// cost = n_i * (13 n_p + c_cell n_c) FP32 ops + staging of the list entries.
-__global__ void queue_hist_kernel(int64_t G, const int64_t *__restrict__ goff, const int64_t *__restrict__ poff,
-                                  const int64_t *__restrict__ coff, double cell_ops, unsigned char *bucket,
-                                  int *hist) {
-  __shared__ int h[kBuckets];
-  for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) h[b] = 0;
-  __syncthreads();
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
-    const double ni = (double)(goff[g + 1] - goff[g]);
-    const double np = (double)(poff[g + 1] - poff[g]);
-    const double nc = (double)(coff[g + 1] - coff[g]);
-    const double cost = ni * (13.0 * np + cell_ops * nc) + 64.0 * (np + nc) + 256.0;
-    const int b = cost_bucket(cost);
-    bucket[g] = (unsigned char)b;
-    atomicAdd(&h[b], 1);
-  }
-  __syncthreads();
-  for (int b = threadIdx.x; b < kBuckets; b += blockDim.x)
-    if (h[b]) atomicAdd(&hist[b], h[b]);
-}
-
-// Work queue, pass 2: groups scattered in descending cost class.
-__global__ void queue_scatter_kernel(int64_t G, const unsigned char *__restrict__ bucket,
-                                     const int *__restrict__ hist, int *cursor, int32_t *queue) {
-  __shared__ int start[kBuckets];
-  for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) {
-    int s = 0;
-    for (int c = b + 1; c < kBuckets; c++) s += hist[c];
-    start[b] = s;
-  }
-  __syncthreads();
-  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
-    const int b = bucket[g];
-    const int pos = start[b] + atomicAdd(&cursor[b], 1);
-    queue[pos] = (int32_t)g;
   }
 }
 

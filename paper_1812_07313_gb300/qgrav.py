@@ -17,11 +17,13 @@ import numpy as np
 from . import _native
 
 QG_OK, QG_ERR_ARG, QG_ERR_CUDA, QG_ERR_NOMEM, QG_ERR_STATE, QG_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+QG_ERR_SIZE = -6
+QG_NOALLOC_MAX_GROUPS = 1 << 20
 QG_FP32_CENTRED, QG_FP32_RAW, QG_FP64 = 0, 1, 2
 QG_QUAD, QG_MONO = 0, 1
 
 _STATUS = {0: "QG_OK", -1: "QG_ERR_ARG", -2: "QG_ERR_CUDA", -3: "QG_ERR_NOMEM", -4: "QG_ERR_STATE",
-           -5: "QG_ERR_TIMEOUT"}
+           -5: "QG_ERR_TIMEOUT", -6: "QG_ERR_SIZE"}
 
 _P = ctypes.POINTER
 _vp = ctypes.c_void_p
@@ -50,6 +52,8 @@ SIGNATURES = {
     "qg_direct_dev": ([_int, _i64, _vp, _dbl, _i64, _vp, _vp, _vp, _vp, _vp], _int),
     "qg_round_f32_host": ([_i64, _vp, _vp], _int),
     "qg_round_f32_dev": ([_i64, _vp, _vp, _vp, _vp], _int),
+    "qg_forces_noalloc": ([_int, _i64, _vp, _vp, _dbl, _i64, _vp, _i64, _vp, _vp, _vp, _vp, _i64,
+                           _i64, _vp, _vp, _vp, _vp, _vp, _i64, _int, _vp, _vp, _vp], _int),
 }
 
 
@@ -294,3 +298,29 @@ def qg_round_f32_dev(x, out, out_hw, stream=None):
     st = lib().qg_round_f32_dev(x.numel(), _dp(x), _dp(out), _dp(out_hw), stream)
     if st != QG_OK:
         raise QGError(st, "qg_round_f32_dev failed")
+
+
+def qg_forces_noalloc(sink_x, group_off, src_x, src_m, plist_off, plist_idx, cell_com, cell_m, cell_q,
+                      clist_off, clist_idx, a, phi, eps2_all=0.0, eps2=None, expansion=QG_QUAD, device=0,
+                      stream=None):
+    """One force evaluation that allocates nothing (torch CUDA tensors in the
+    qg_set_*_dev layouts in, a and phi out); its work-queue scratch is a fixed
+    array inside the library, for at most QG_NOALLOC_MAX_GROUPS groups."""
+    for t, d in ((sink_x, "float64"), (group_off, "int64"), (src_x, "float64"), (src_m, "float64"),
+                 (plist_off, "int64"), (plist_idx, "int32"), (cell_com, "float64"), (cell_m, "float64"),
+                 (cell_q, "float64"), (clist_off, "int64"), (clist_idx, "int32"), (a, "float64"),
+                 (phi, "float64"), (eps2, "float32")):
+        _check_dev(t, d)
+    G = group_off.numel() - 1
+    if plist_off.numel() != G + 1 or clist_off.numel() != G + 1:
+        raise ValueError("qg_forces_noalloc: list offsets must have ngroups+1 entries")
+    n = sink_x.numel() // 3
+    if a.numel() != 3 * n or phi.numel() != n:
+        raise ValueError("qg_forces_noalloc: a must be [n,3] and phi [n]")
+    st = lib().qg_forces_noalloc(int(device), n, _dp(sink_x), _dp(eps2), float(eps2_all), G, _dp(group_off),
+                                 src_m.numel(), _dp(src_x), _dp(src_m), _dp(plist_off), _dp(plist_idx),
+                                 plist_idx.numel(), cell_m.numel(), _dp(cell_com), _dp(cell_m), _dp(cell_q),
+                                 _dp(clist_off), _dp(clist_idx), clist_idx.numel(), int(expansion), _dp(a),
+                                 _dp(phi), stream)
+    if st != QG_OK:
+        raise QGError(st, "qg_forces_noalloc failed")
