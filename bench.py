@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--workload", default="cube_1m")
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--no-equal-error", action="store_true", help="skip the monopole equal-error search")
+    ap.add_argument("--equal-error-thetas", default="0.5",
+                    help="quadrupole thetas of the equal-error comparison (comma separated)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--launch", default=None,
@@ -217,10 +219,11 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- our arm
 
-def equal_error(torch, qgrav, tr, L_quad, eps2_all, eps2, a_quad, wl_name, theta_q, rank, flush, stream, steps):
-    """theta_mono with p99 (Eq. 9, vs FP64 direct summation on 4096 seeded
-    sinks) no larger than the quadrupole's at theta_q; then time monopole-only
-    steps at that theta."""
+def equal_error(torch, qgrav, tr, eps2_all, thetas, flush, stream, steps):
+    """For each quadrupole theta: time quadrupole steps, measure their p99 of
+    Eq. 9 against FP64 GPU direct summation on 4096 seeded sinks, find by
+    bisection the largest monopole-only theta whose p99 is no larger, and time
+    monopole-only steps there (both launch shapes autotuned)."""
     rng = np.random.default_rng(12345)
     ns = min(4096, tr.n)
     sample = np.sort(rng.choice(tr.n, ns, replace=False))
@@ -242,43 +245,55 @@ def equal_error(torch, qgrav, tr, L_quad, eps2_all, eps2, a_quad, wl_name, theta
         e = np.linalg.norm(a[sample] - a_dir, axis=1) / np.linalg.norm(a_dir, axis=1)
         return float(np.percentile(e, 99))
 
-    target = p99(a_quad)
-    ctx = qgrav.Context(torch.cuda.current_device(), qgrav.Options(expansion=qgrav.QG_MONO))
-    cache = {}
+    def timed(ctx, L):
+        load_ctx(ctx, tr, L, eps2_all, None)
+        ctx.qg_autotune(stream.cuda_stream, reps=3)
+        for _ in range(3):
+            ctx.qg_run(stream.cuda_stream)
+        torch.cuda.synchronize()
+        ms, _ = timed_steps(torch, ctx, stream, flush, steps)
+        a, _ = ctx.qg_get_forces()
+        st = ctx.qg_get_stats()
+        return float(ms.mean()), a, int(st["i_pp"] + st["i_pc"])
 
-    def mono_at(th):
-        th = round(th, 4)
-        if th not in cache:
-            L = tr.walk(th)
-            load_ctx(ctx, tr, L, eps2_all, eps2)
-            ctx.qg_run()
-            a, _ = ctx.qg_get_forces()
-            cache[th] = (p99(a), L)
-        return cache[th]
+    rows = []
+    quad = qgrav.Context(torch.cuda.current_device())
+    mono = qgrav.Context(torch.cuda.current_device(), qgrav.Options(expansion=qgrav.QG_MONO))
+    for theta_q in thetas:
+        q_ms, a_q, q_int = timed(quad, tr.walk(theta_q))
+        target = p99(a_q)
+        cache = {}
 
-    lo, hi = 0.2, theta_q
-    if mono_at(lo)[0] > target:
-        th_m = lo
-    else:
-        for _ in range(7):
-            mid = 0.5 * (lo + hi)
-            if mono_at(mid)[0] <= target:
-                lo = mid
-            else:
-                hi = mid
-        th_m = lo
-    p_m, L_m = mono_at(th_m)
-    load_ctx(ctx, tr, L_m, eps2_all, eps2)
-    ctx.qg_autotune(stream.cuda_stream, reps=3)
-    for _ in range(3):
-        ctx.qg_run(stream.cuda_stream)
-    torch.cuda.synchronize()
-    ms, force = timed_steps(torch, ctx, stream, flush, steps)
-    st = ctx.qg_get_stats()
-    ctx.close()
-    return {"theta_quad": theta_q, "p99_quad": target, "theta_mono": th_m, "p99_mono": p_m,
-            "mono_ms_per_step": float(ms.mean()), "mono_interactions": int(st["i_pp"] + st["i_pc"]),
-            "error_sample": "FP64 GPU direct summation on %d seeded sinks" % ns}
+        def mono_at(th):
+            th = round(th, 4)
+            if th not in cache:
+                L = tr.walk(th)
+                load_ctx(mono, tr, L, eps2_all, None)
+                mono.qg_run()
+                a, _ = mono.qg_get_forces()
+                cache[th] = (p99(a), L)
+            return cache[th]
+
+        lo, hi = max(0.1, 0.5 * theta_q), theta_q
+        if mono_at(lo)[0] > target:
+            th_m = lo
+        else:
+            for _ in range(7):
+                mid = 0.5 * (lo + hi)
+                if mono_at(mid)[0] <= target:
+                    lo = mid
+                else:
+                    hi = mid
+            th_m = lo
+        p_m, L_m = mono_at(th_m)
+        m_ms, _, m_int = timed(mono, L_m)
+        rows.append({"theta_quad": theta_q, "p99_quad": target, "quad_ms_per_step": q_ms, "quad_interactions": q_int,
+                     "theta_mono": th_m, "p99_mono": p_m, "mono_ms_per_step": m_ms, "mono_interactions": m_int,
+                     "quad_over_mono_time": q_ms / m_ms})
+        cache.clear()
+    quad.close()
+    mono.close()
+    return {"error_sample": "FP64 GPU direct summation on %d seeded sinks" % ns, "rows": rows}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -345,16 +360,7 @@ def run_ours(args, rank, world, local_rank):
     sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
     peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
     peak_max = n_sm * 128 * 2070e6 / 1e12
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "force_kernel_traffic.json")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                tj = json.load(f)
-            if tj.get("workload") == args.workload and tj.get("kernel_hash") == _kernel_hash():
-                traffic = tj.get("bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    traffic = _recorded_traffic(args.workload, launch)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
                 "traffic": traffic,
                 "peak_basis": "FP32 lane-instructions/s = %d SMs x 128 x median SM clock %.0f MHz under load "
@@ -378,10 +384,10 @@ def run_ours(args, rank, world, local_rank):
            "wall_s_timed_loop": t_wall}
 
     if rank == 0 and not args.no_equal_error and eps2 is None:
-        out["equal_error"] = equal_error(torch, qgrav, tr, L, eps2_all, eps2, a_quad, args.workload, theta,
-                                         rank, flush, stream, max(5, args.steps // 2))
-        out["equal_error"]["quad_ms_per_step"] = total_ms / args.steps
-        out["gpu_launches"] += 3 * max(5, args.steps // 2)
+        thetas = [float(v) for v in args.equal_error_thetas.split(",")]
+        ee_steps = max(5, args.steps // 2)
+        out["equal_error"] = equal_error(torch, qgrav, tr, eps2_all, thetas, flush, stream, ee_steps)
+        out["gpu_launches"] += 2 * 3 * ee_steps * len(thetas)
 
     # end to end through the C-ABI with host buffers (pinned), every step
     out["e2e"] = e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world)
@@ -434,13 +440,39 @@ def e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world, steps=3):
                                             "qg_get_forces, wall clock"}
 
 
-def _kernel_hash():
+KERNEL_SOURCES = ("qg_force.cuh", "qg_force_f32.cu", "qg_internal.h", "qg_queue.cuh", "qg_api.cu")
+
+
+def kernel_hash():
+    """Hash of the sources the force step is built from: a recorded DRAM
+    traffic figure is used only while it matches."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("qg_force.cuh", "qg_force_f32.cu", "qg_api.cu"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1812_07313_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
+
+
+def _recorded_traffic(workload, launch):
+    """DRAM bytes (read + write) per force-kernel launch from the ncu summary in
+    profiles/, when it was taken on this workload, launch shape and source."""
+    path = os.path.join(ROOT, "profiles", "force_kernel_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    with open(path) as f:
+        for line in f:
+            if "=" in line and not line.lstrip().startswith("#"):
+                k, v = line.split("=", 1)
+                rec[k.strip()] = v.strip()
+    shape = "%d,%d,%d" % (launch["sinks_per_thread"], launch["warps_per_group"], launch["tile_j"])
+    if rec.get("workload") != workload or rec.get("kernel_hash") != kernel_hash() or rec.get("launch") != shape:
+        return None
+    try:
+        return float(rec["bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def main():
