@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--launch", default=None,
-                    help="R,W,T: fixed sinks/thread, warps/CTA, tile instead of the autotuner (profiling)")
+                    help="R,W,T[,x1|x2]: fixed sinks/thread, warps/CTA, tile (and scalar or paired FP32) "
+                         "instead of the autotuner (profiling)")
     return ap.parse_args()
 
 
@@ -317,8 +318,10 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.zeros(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     t_tune = time.perf_counter()
     if args.launch:
-        R, W, T = (int(v) for v in args.launch.split(","))
-        ctx.set_options(qgrav.Options(sinks_per_thread=R, warps_per_group=W, tile_j=T))
+        parts = args.launch.split(",")
+        R, W, T = (int(v) for v in parts[:3])
+        arith = {"x1": qgrav.QG_ARITH_SCALAR, "x2": qgrav.QG_ARITH_PAIRED}[parts[3]] if len(parts) > 3 else 0
+        ctx.set_options(qgrav.Options(sinks_per_thread=R, warps_per_group=W, tile_j=T, arith=arith))
     else:
         ctx.qg_autotune(stream.cuda_stream, reps=3)
     t_tune = time.perf_counter() - t_tune
@@ -332,7 +335,8 @@ def run_ours(args, rank, world, local_rank):
     a_quad, _ = ctx.qg_get_forces()
     st = ctx.qg_get_stats()
     launch.update({"sinks_per_thread": st["sinks_per_thread"], "warps_per_group": st["warps_per_group"],
-                   "tile_j": st["tile_j"], "grid": st["grid"], "block": st["block"]})
+                   "tile_j": st["tile_j"], "grid": st["grid"], "block": st["block"],
+                   "arith": "paired f32x2" if st["paired"] else "scalar f32"})
 
     if world > 1:
         dist.barrier()
@@ -366,8 +370,8 @@ def run_ours(args, rank, world, local_rank):
                 "peak_basis": "FP32 lane-instructions/s = %d SMs x 128 x median SM clock %.0f MHz under load "
                               "(at the 2070 MHz maximum: %.1f Tinst/s, frac %.3f)"
                               % (n_sm, sm_mhz, peak_max, achieved / peak_max),
-                "kernel": "force_kernel<float,R=%d,quad>, %d threads, tile %d" % (
-                    launch["sinks_per_thread"], launch["block"], launch["tile_j"]),
+                "kernel": "force_kernel<float,R=%d,quad,%s>, %d threads, tile %d" % (
+                    launch["sinks_per_thread"], launch["arith"], launch["block"], launch["tile_j"]),
                 "force_kernel_ms": float(force_ms.mean())}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -466,7 +470,8 @@ def _recorded_traffic(workload, launch):
             if "=" in line and not line.lstrip().startswith("#"):
                 k, v = line.split("=", 1)
                 rec[k.strip()] = v.strip()
-    shape = "%d,%d,%d" % (launch["sinks_per_thread"], launch["warps_per_group"], launch["tile_j"])
+    shape = "%d,%d,%d,%s" % (launch["sinks_per_thread"], launch["warps_per_group"], launch["tile_j"],
+                             "x2" if launch.get("arith", "").startswith("paired") else "x1")
     if rec.get("workload") != workload or rec.get("kernel_hash") != kernel_hash() or rec.get("launch") != shape:
         return None
     try:

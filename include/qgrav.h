@@ -76,6 +76,7 @@ typedef enum {
 
 enum { QG_FP32_CENTRED = 0, QG_FP32_RAW = 1, QG_FP64 = 2 };
 enum { QG_QUAD = 0, QG_MONO = 1 };
+enum { QG_ARITH_DEFAULT = 0, QG_ARITH_SCALAR = 1, QG_ARITH_PAIRED = 2 };
 
 typedef struct {
   int precision;        /* QG_FP32_CENTRED | QG_FP32_RAW | QG_FP64          */
@@ -88,6 +89,9 @@ typedef struct {
                            0 = default; supported: 2, 4, 8                  */
   int flush_j;          /* FP32 partials are folded into FP64 after at most
                            this many list entries per thread; 0 = 256       */
+  int arith;            /* QG_FP32_CENTRED only: QG_ARITH_SCALAR (the
+                           default, 0) or QG_ARITH_PAIRED (two sinks per
+                           float2 register, f32x2 FMA instructions)          */
 } qg_options;
 
 typedef struct {
@@ -99,6 +103,7 @@ typedef struct {
   int32_t tile_j;
   int32_t warps_per_group;
   int32_t flush_j;
+  int32_t paired;             /* 1 if the paired-FP32 form runs              */
 } qg_stats;
 
 /* Create a context on CUDA device `device`.  opt may be NULL (defaults). */
@@ -157,7 +162,8 @@ qg_status qg_run(qg_ctx *ctx, void *cuda_stream);
 
 /*
  * Autotuner: times every supported launch shape (sinks_per_thread x
- * warps_per_group x tile_j) of the current precision / expansion on the
+ * warps_per_group x tile_j, and scalar vs paired FP32 arithmetic for
+ * QG_FP32_CENTRED) of the current precision / expansion on the
  * inputs currently set, `reps` timed runs each after one warm-up run (the
  * force kernel's device time, CUDA events), and keeps the fastest as the
  * context's options.  The sink grouping itself (n_crit) is an input and is

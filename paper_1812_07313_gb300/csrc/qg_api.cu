@@ -201,6 +201,7 @@ bool valid_options(const qg_options &o, std::string &why) {
     return false;
   }
   if (o.flush_j < 0) { why = "flush_j"; return false; }
+  if (o.arith < QG_ARITH_DEFAULT || o.arith > QG_ARITH_PAIRED) { why = "arith"; return false; }
   return true;
 }
 
@@ -254,11 +255,13 @@ qg_status choose_kernel(qg_ctx *c) {
   int warps = o.warps_per_group ? o.warps_per_group : 4;
   if (R >= 8 && warps > 4) warps = 4;
   const int nt = 32 * warps;
+  const bool paired = o.precision == QG_FP32_CENTRED && o.arith == QG_ARITH_PAIRED;
   const void *k = fp64 ? qg::force_kernel_f64(R, quad, guard)
-                       : qg::force_kernel_f32(R, quad, guard, o.precision == QG_FP32_CENTRED);
+                  : paired ? qg::force_kernel_f32x2(R, quad, guard)
+                           : qg::force_kernel_f32(R, quad, guard, o.precision == QG_FP32_CENTRED);
   if (!k) return fail(c, QG_ERR_ARG, "no kernel for precision %d, R %d", o.precision, R);
   const int tile = o.tile_j ? o.tile_j : 256;
-  const size_t smem = qg::force_smem_bytes(fp64, R, nt, tile);
+  const size_t smem = qg::force_smem_bytes(fp64, paired, R, nt, tile);
   QG_CUDA(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   QG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, smem));
@@ -275,6 +278,7 @@ qg_status choose_kernel(qg_ctx *c) {
   c->stats.tile_j = tile;
   c->stats.warps_per_group = warps;
   c->stats.flush_j = c->flush;
+  c->stats.paired = paired ? 1 : 0;
   return QG_OK;
 }
 
@@ -312,6 +316,8 @@ qg_status record_step(qg_ctx *c, cudaStream_t s) {
   p.phi = c->phi.p;
   p.tile = c->tile;
   p.flush_j = c->flush;
+  p.zero = 0.0f;
+  p.one = 1.0f;
   const int grid = (int)std::min<int64_t>(c->grid, std::max<int64_t>(G, 1));
   c->stats.grid = grid;
   void *args[] = {&p};
@@ -728,6 +734,9 @@ qg_status qg_autotune(qg_ctx *c, void *stream, int reps, qg_options *best, float
   bool have = false;
   if (c->G > 0) {
     const int Rs[3] = {2, 4, 8}, Ws[3] = {2, 4, 8}, Ts[3] = {128, 256, 512};
+    const int As[2] = {QG_ARITH_PAIRED, QG_ARITH_SCALAR};
+    const int n_arith = base.precision == QG_FP32_CENTRED ? 2 : 1;
+    for (int ai = 0; ai < n_arith; ai++)
     for (int ri = 0; ri < 3; ri++)
       for (int wi = 0; wi < 3; wi++)
         for (int ti = 0; ti < 3; ti++) {
@@ -735,6 +744,7 @@ qg_status qg_autotune(qg_ctx *c, void *stream, int reps, qg_options *best, float
           o.sinks_per_thread = Rs[ri];
           o.warps_per_group = Ws[wi];
           o.tile_j = Ts[ti];
+          if (n_arith == 2) o.arith = As[ai];
           if (base.precision == QG_FP64 && Rs[ri] != 2) continue;
           if (Rs[ri] >= 8 && Ws[wi] > 4) continue;
           c->opt = o;

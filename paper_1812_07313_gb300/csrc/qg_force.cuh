@@ -91,6 +91,76 @@ __device__ __forceinline__ void quad_pair(Real dx, Real dy, Real dz, Real m,
   az = fma(-ri5, qz, az);
 }
 
+// Paired FP32 forms: two sinks per float2 and Blackwell's f32x2 instructions,
+// one instruction issue per two lanes of work.  On this GPU the paired FMA
+// runs at the full FP32 rate but the paired add and multiply at half of it,
+// so every add and multiply is written as an FMA (a*b = fma(a, b, 0),
+// a + b = fma(a, 1, b): the same single rounding).  Operands: j-entry values
+// broadcast to both halves, (nx, ny, nz) the two sinks' offsets negated, so
+// that every sign folds into the instructions.  13 and 33 paired FMAs per
+// two pairs, as in the scalar forms.  The 0 and 1 operands come from the
+// kernel's parameters (ForceParams::zero2, one2): as compile-time constants
+// the compiler would fold the FMA back into the half-rate add or multiply.
+struct Pair2 {
+  float2 zero, one;
+  __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) const { return __ffma2_rn(a, b, c); }
+  __device__ __forceinline__ float2 mul2(float2 a, float2 b) const { return __ffma2_rn(a, b, zero); }
+  __device__ __forceinline__ float2 add2(float2 a, float2 b) const { return __ffma2_rn(a, one, b); }
+};
+
+template <bool GUARD>
+__device__ __forceinline__ void mono_pair2(const Pair2 &P, float2 jx, float2 jy, float2 jz, float2 jm, float2 nx,
+                                           float2 ny, float2 nz, float2 e2, float2 &ax, float2 &ay, float2 &az,
+                                           float2 &pot) {
+  const float2 dx = P.add2(jx, nx), dy = P.add2(jy, ny), dz = P.add2(jz, nz);
+  const float2 r2 = P.fma2(dx, dx, P.fma2(dy, dy, P.fma2(dz, dz, e2)));
+  float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+  if (GUARD) {
+    ri.x = r2.x > 0.f ? ri.x : 0.f;
+    ri.y = r2.y > 0.f ? ri.y : 0.f;
+  }
+  const float2 pm = P.mul2(jm, ri);             // phi_mono
+  pot = P.add2(pot, pm);
+  const float2 c = P.mul2(pm, P.mul2(ri, ri));    // m / rhat^3
+  ax = P.fma2(c, dx, ax);
+  ay = P.fma2(c, dy, ay);
+  az = P.fma2(c, dz, az);
+}
+
+// nq00..nq22 = -(q00, q01, q02, q11, q12, q22): with Q negated, nQ r = -(Q r)
+// and r.nQ.r = -(r.Q.r), so a += c r + rhat^-5 nQ r needs no negation.
+template <bool GUARD>
+__device__ __forceinline__ void quad_pair2(const Pair2 &P, float2 jx, float2 jy, float2 jz, float2 jm,
+                                           float2 nq00, float2 nq01,
+                                           float2 nq02, float2 nq11, float2 nq12, float2 nq22, float2 nx,
+                                           float2 ny, float2 nz, float2 e2, float2 &ax, float2 &ay, float2 &az,
+                                           float2 &pot) {
+  const float2 dx = P.add2(jx, nx), dy = P.add2(jy, ny), dz = P.add2(jz, nz);
+  const float2 r2 = P.fma2(dx, dx, P.fma2(dy, dy, P.fma2(dz, dz, e2)));
+  float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+  if (GUARD) {
+    ri.x = r2.x > 0.f ? ri.x : 0.f;
+    ri.y = r2.y > 0.f ? ri.y : 0.f;
+  }
+  const float2 ri2 = P.mul2(ri, ri);
+  const float2 pm = P.mul2(jm, ri);                                     // phi_mono
+  const float2 qx = P.fma2(nq00, dx, P.fma2(nq01, dy, P.mul2(nq02, dz)));   // -(Q r)_x
+  const float2 qy = P.fma2(nq01, dx, P.fma2(nq11, dy, P.mul2(nq12, dz)));   // -(Q r)_y
+  const float2 qz = P.fma2(nq02, dx, P.fma2(nq12, dy, P.mul2(nq22, dz)));   // -(Q r)_z
+  const float2 rqr = P.fma2(dx, qx, P.fma2(dy, qy, P.mul2(dz, qz)));        // -(r.Q.r)
+  const float2 ri5 = P.mul2(P.mul2(ri2, ri2), ri);
+  const float2 u = P.mul2(rqr, ri5);                                    // -2 phi_quad
+  pot = P.add2(pot, pm);
+  pot = P.fma2(make_float2(-0.5f, -0.5f), u, pot);                      // + phi_quad
+  const float2 c = P.mul2(P.fma2(make_float2(-2.5f, -2.5f), u, pm), ri2); // (phi_mono + 5 phi_quad)/rhat^2
+  ax = P.fma2(c, dx, ax);
+  ax = P.fma2(ri5, qx, ax);
+  ay = P.fma2(c, dy, ay);
+  ay = P.fma2(ri5, qy, ay);
+  az = P.fma2(c, dz, az);
+  az = P.fma2(ri5, qz, az);
+}
+
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -103,16 +173,22 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 // Launch bounds per variant: the largest block it is launched with and the
-// CTAs per SM the register budget must allow.  R <= 4 is held to 64
-// registers (8 CTAs of 128 threads per SM); R = 8 keeps 8 sinks x 4 sums in
-// registers and is limited to 128 threads.
-template <int R> struct Bounds {
+// CTAs per SM the register budget must allow.  Scalar R <= 4 is held to 64
+// registers (8 CTAs of 128 threads per SM); the paired R = 4 form carries
+// twice the j-entry registers and gets up to 128; R = 8 keeps 8 sinks x 4 sums in
+// registers and is limited to 128 threads; the all-FP64 comparison form gets
+// up to 128 registers.
+template <typename Real, int R, bool PAIRED> struct Bounds {
   static constexpr int threads = R >= 8 ? 128 : 256;
-  static constexpr int min_blocks = R >= 8 ? 2 : 4;
+  static constexpr int min_blocks = (R >= 8 || sizeof(Real) == 8) ? 2 : (PAIRED && R >= 4 ? 2 : 4);
 };
 
-template <typename Real, int R, bool QUAD, bool GUARD, bool CENTRED>
-__global__ void __launch_bounds__(Bounds<R>::threads, Bounds<R>::min_blocks) force_kernel(const ForceParams p) {
+template <typename Real, int R, bool QUAD, bool GUARD, bool CENTRED, bool PAIRED>
+__global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real, R, PAIRED>::min_blocks)
+    force_kernel(const ForceParams p) {
+  static_assert(!PAIRED || (sizeof(Real) == 4 && R % 2 == 0), "paired arithmetic: FP32, even R");
+  constexpr int H = R / 2;  // sink pairs per thread (paired form)
+  const Pair2 P2{make_float2(p.zero, p.zero), make_float2(p.one, p.one)};
   using V4 = typename RT<Real>::v4;
   using V2 = typename RT<Real>::v2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -128,9 +204,17 @@ __global__ void __launch_bounds__(Bounds<R>::threads, Bounds<R>::min_blocks) for
   // accumulators are zeroed.
   double *acc64 = reinterpret_cast<double *>(smem_raw);
   V4 *sink_s = reinterpret_cast<V4 *>(smem_raw);
+  // Staged tile.  Scalar form: A (dx dy dz m), B (q00 q01 q02 q11), C (q12 q22).
+  // Paired form: every value twice, (dx dx dy dy) (dz dz m m) and the negated
+  // quadrupole (q00 q00 q01 q01) (q02 q02 q11 q11) (q12 q12 q22 q22).
   V4 *tA = reinterpret_cast<V4 *>(acc64 + 4 * R * NT);
   V4 *tB = tA + T;
   V2 *tC = reinterpret_cast<V2 *>(tB + T);
+  float4 *tP0 = reinterpret_cast<float4 *>(acc64 + 4 * R * NT);
+  float4 *tP1 = tP0 + T;
+  float4 *tQ0 = tP1 + T;
+  float4 *tQ1 = tQ0 + T;
+  float4 *tQ2 = tQ1 + T;
 
   for (;;) {
     __syncthreads();  // the previous group is finished with shared memory
@@ -201,6 +285,8 @@ __global__ void __launch_bounds__(Bounds<R>::threads, Bounds<R>::min_blocks) for
 
       Real sx[R], sy[R], sz[R], se[R];
       Real ax[R], ay[R], az[R], pt[R];
+      float2 nx2[H > 0 ? H : 1], ny2[H > 0 ? H : 1], nz2[H > 0 ? H : 1], e22[H > 0 ? H : 1];
+      float2 ax2[H > 0 ? H : 1], ay2[H > 0 ? H : 1], az2[H > 0 ? H : 1], pt2[H > 0 ? H : 1];
 #pragma unroll
       for (int r = 0; r < R; r++) {
         const int i = s + S * r;
@@ -208,20 +294,46 @@ __global__ void __launch_bounds__(Bounds<R>::threads, Bounds<R>::min_blocks) for
         sx[r] = v.x; sy[r] = v.y; sz[r] = v.z; se[r] = v.w;
         ax[r] = ay[r] = az[r] = pt[r] = Real(0);
       }
+      if constexpr (PAIRED) {
+#pragma unroll
+        for (int h = 0; h < H; h++) {
+          nx2[h] = make_float2(-sx[2 * h], -sx[2 * h + 1]);
+          ny2[h] = make_float2(-sy[2 * h], -sy[2 * h + 1]);
+          nz2[h] = make_float2(-sz[2 * h], -sz[2 * h + 1]);
+          e22[h] = make_float2(se[2 * h], se[2 * h + 1]);
+          ax2[h] = ay2[h] = az2[h] = pt2[h] = make_float2(0.f, 0.f);
+        }
+      }
       __syncthreads();  // every thread holds its sinks: sink_s becomes acc64
 #pragma unroll
       for (int v = 0; v < 4 * R; v++) acc64[v * NT + tid] = 0.0;
       int nproc = 0;
 
       auto fold = [&]() {
+        if constexpr (PAIRED) {
 #pragma unroll
-        for (int r = 0; r < R; r++) {
-          double *a = acc64 + 4 * r * NT + tid;
-          a[0] += (double)ax[r];
-          a[NT] += (double)ay[r];
-          a[2 * NT] += (double)az[r];
-          a[3 * NT] += (double)pt[r];
-          ax[r] = ay[r] = az[r] = pt[r] = Real(0);
+          for (int h = 0; h < H; h++) {
+            double *a = acc64 + 8 * h * NT + tid;  // sinks 2h and 2h + 1
+            a[0] += (double)ax2[h].x;
+            a[NT] += (double)ay2[h].x;
+            a[2 * NT] += (double)az2[h].x;
+            a[3 * NT] += (double)pt2[h].x;
+            a[4 * NT] += (double)ax2[h].y;
+            a[5 * NT] += (double)ay2[h].y;
+            a[6 * NT] += (double)az2[h].y;
+            a[7 * NT] += (double)pt2[h].y;
+            ax2[h] = ay2[h] = az2[h] = pt2[h] = make_float2(0.f, 0.f);
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; r++) {
+            double *a = acc64 + 4 * r * NT + tid;
+            a[0] += (double)ax[r];
+            a[NT] += (double)ay[r];
+            a[2 * NT] += (double)az[r];
+            a[3 * NT] += (double)pt[r];
+            ax[r] = ay[r] = az[r] = pt[r] = Real(0);
+          }
         }
         nproc = 0;
       };
@@ -229,23 +341,40 @@ __global__ void __launch_bounds__(Bounds<R>::threads, Bounds<R>::min_blocks) for
       // ---- 3-4. particle part of the list (monopole, Eq. 4) ----------------
       for (int64_t base = p0; base < p1; base += T) {
         const int cnt = (int)min((int64_t)T, p1 - base);
-        __syncthreads();
+        __syncthreads();  // the previous tile's readers are done
         for (int t = tid; t < cnt; t += NT) {
           const int j = p.plist_idx[base + t];
           const PosMass v = p.src[j];
           const Real m = sizeof(Real) == 4 ? (Real)v.m : (Real)p.src_m64[j];
-          tA[t] = RT<Real>::make4(RT<Real>::cvt(v.x - cx), RT<Real>::cvt(v.y - cy),
-                                  RT<Real>::cvt(v.z - cz), m);
+          const Real dx = RT<Real>::cvt(v.x - cx), dy = RT<Real>::cvt(v.y - cy), dz = RT<Real>::cvt(v.z - cz);
+          if constexpr (PAIRED) {
+            tP0[t] = make_float4(dx, dx, dy, dy);
+            tP1[t] = make_float4(dz, dz, m, m);
+          } else {
+            tA[t] = RT<Real>::make4(dx, dy, dz, m);
+          }
         }
         __syncthreads();
         if (active) {
+          if constexpr (PAIRED) {
 #pragma unroll 2
-          for (int jj = k; jj < cnt; jj += K) {
-            const V4 A = tA[jj];
+            for (int jj = k; jj < cnt; jj += K) {
+              const float4 P0 = tP0[jj], P1 = tP1[jj];
 #pragma unroll
-            for (int r = 0; r < R; r++)
-              mono_pair<Real, GUARD>(A.x - sx[r], A.y - sy[r], A.z - sz[r], A.w, se[r],
-                                     ax[r], ay[r], az[r], pt[r]);
+              for (int h = 0; h < H; h++)
+                mono_pair2<GUARD>(P2, make_float2(P0.x, P0.y), make_float2(P0.z, P0.w), make_float2(P1.x, P1.y),
+                                  make_float2(P1.z, P1.w), nx2[h], ny2[h], nz2[h], e22[h], ax2[h], ay2[h],
+                                  az2[h], pt2[h]);
+            }
+          } else {
+#pragma unroll 2
+            for (int jj = k; jj < cnt; jj += K) {
+              const V4 A = tA[jj];
+#pragma unroll
+              for (int r = 0; r < R; r++)
+                mono_pair<Real, GUARD>(A.x - sx[r], A.y - sy[r], A.z - sz[r], A.w, se[r],
+                                       ax[r], ay[r], az[r], pt[r]);
+            }
           }
           nproc += (cnt - k + K - 1) / K;
           if (nproc >= p.flush_j) fold();
@@ -255,28 +384,63 @@ __global__ void __launch_bounds__(Bounds<R>::threads, Bounds<R>::min_blocks) for
       // ---- 3-4. cell part of the list (Eq. 1 / Eq. 8, or monopole) --------
       for (int64_t base = c0; base < c1; base += T) {
         const int cnt = (int)min((int64_t)T, c1 - base);
-        __syncthreads();
+        __syncthreads();  // the previous tile's readers are done
         for (int t = tid; t < cnt; t += NT) {
           const int j = p.clist_idx[base + t];
           const PosMass v = p.cell_pm[j];
           const Real m = sizeof(Real) == 4 ? (Real)v.m : (Real)p.cell_m64[j];
-          tA[t] = RT<Real>::make4(RT<Real>::cvt(v.x - cx), RT<Real>::cvt(v.y - cy),
-                                  RT<Real>::cvt(v.z - cz), m);
-          if (QUAD) {
-            if (sizeof(Real) == 4) {
+          const Real dx = RT<Real>::cvt(v.x - cx), dy = RT<Real>::cvt(v.y - cy), dz = RT<Real>::cvt(v.z - cz);
+          if constexpr (PAIRED) {
+            tP0[t] = make_float4(dx, dx, dy, dy);
+            tP1[t] = make_float4(dz, dz, m, m);
+            if (QUAD) {
               const float4 q0 = p.cell_q[2 * j], q1 = p.cell_q[2 * j + 1];
-              tB[t] = RT<Real>::make4(q0.x, q0.y, q0.z, q0.w);
-              tC[t] = RT<Real>::make2(q1.x, q1.y);
-            } else {
-              const double *q = p.cell_q64 + 6 * (int64_t)j;
-              tB[t] = RT<Real>::make4((Real)q[0], (Real)q[1], (Real)q[2], (Real)q[3]);
-              tC[t] = RT<Real>::make2((Real)q[4], (Real)q[5]);
+              tQ0[t] = make_float4(-q0.x, -q0.x, -q0.y, -q0.y);
+              tQ1[t] = make_float4(-q0.z, -q0.z, -q0.w, -q0.w);
+              tQ2[t] = make_float4(-q1.x, -q1.x, -q1.y, -q1.y);
+            }
+          } else {
+            tA[t] = RT<Real>::make4(dx, dy, dz, m);
+            if (QUAD) {
+              if (sizeof(Real) == 4) {
+                const float4 q0 = p.cell_q[2 * j], q1 = p.cell_q[2 * j + 1];
+                tB[t] = RT<Real>::make4(q0.x, q0.y, q0.z, q0.w);
+                tC[t] = RT<Real>::make2(q1.x, q1.y);
+              } else {
+                const double *q = p.cell_q64 + 6 * (int64_t)j;
+                tB[t] = RT<Real>::make4((Real)q[0], (Real)q[1], (Real)q[2], (Real)q[3]);
+                tC[t] = RT<Real>::make2((Real)q[4], (Real)q[5]);
+              }
             }
           }
         }
         __syncthreads();
         if (active) {
-          if (QUAD) {
+          if constexpr (PAIRED) {
+            if (QUAD) {
+#pragma unroll 2
+              for (int jj = k; jj < cnt; jj += K) {
+                const float4 P0 = tP0[jj], P1 = tP1[jj], Q0 = tQ0[jj], Q1 = tQ1[jj], Q2 = tQ2[jj];
+#pragma unroll
+                for (int h = 0; h < H; h++)
+                  quad_pair2<GUARD>(P2, make_float2(P0.x, P0.y), make_float2(P0.z, P0.w), make_float2(P1.x, P1.y),
+                                    make_float2(P1.z, P1.w), make_float2(Q0.x, Q0.y), make_float2(Q0.z, Q0.w),
+                                    make_float2(Q1.x, Q1.y), make_float2(Q1.z, Q1.w), make_float2(Q2.x, Q2.y),
+                                    make_float2(Q2.z, Q2.w), nx2[h], ny2[h], nz2[h], e22[h], ax2[h], ay2[h],
+                                    az2[h], pt2[h]);
+              }
+            } else {
+#pragma unroll 2
+              for (int jj = k; jj < cnt; jj += K) {
+                const float4 P0 = tP0[jj], P1 = tP1[jj];
+#pragma unroll
+                for (int h = 0; h < H; h++)
+                  mono_pair2<GUARD>(P2, make_float2(P0.x, P0.y), make_float2(P0.z, P0.w), make_float2(P1.x, P1.y),
+                                    make_float2(P1.z, P1.w), nx2[h], ny2[h], nz2[h], e22[h], ax2[h], ay2[h],
+                                    az2[h], pt2[h]);
+              }
+            }
+          } else if (QUAD) {
 #pragma unroll 2
             for (int jj = k; jj < cnt; jj += K) {
               const V4 A = tA[jj];

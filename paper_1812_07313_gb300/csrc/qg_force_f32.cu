@@ -1,5 +1,5 @@
 // FP32 instantiations of the group-force kernel (mixed precision: FP64
-// centring and merging, FP32 pairwise arithmetic).
+// centring and merging, FP32 pairwise arithmetic), scalar FP32 form.
 #include "qg_force.cuh"
 
 namespace qg {
@@ -7,15 +7,15 @@ namespace qg {
 template <int R>
 static const void *pick_f32(bool quad, bool guard, bool centred) {
   if (centred) {
-    if (quad) return guard ? (const void *)force_kernel<float, R, true, true, true>
-                           : (const void *)force_kernel<float, R, true, false, true>;
-    return guard ? (const void *)force_kernel<float, R, false, true, true>
-                 : (const void *)force_kernel<float, R, false, false, true>;
+    if (quad) return guard ? (const void *)force_kernel<float, R, true, true, true, false>
+                           : (const void *)force_kernel<float, R, true, false, true, false>;
+    return guard ? (const void *)force_kernel<float, R, false, true, true, false>
+                 : (const void *)force_kernel<float, R, false, false, true, false>;
   }
-  if (quad) return guard ? (const void *)force_kernel<float, R, true, true, false>
-                         : (const void *)force_kernel<float, R, true, false, false>;
-  return guard ? (const void *)force_kernel<float, R, false, true, false>
-               : (const void *)force_kernel<float, R, false, false, false>;
+  if (quad) return guard ? (const void *)force_kernel<float, R, true, true, false, false>
+                         : (const void *)force_kernel<float, R, true, false, false, false>;
+  return guard ? (const void *)force_kernel<float, R, false, true, false, false>
+               : (const void *)force_kernel<float, R, false, false, false, false>;
 }
 
 const void *force_kernel_f32(int R, bool quad, bool guard, bool centred) {

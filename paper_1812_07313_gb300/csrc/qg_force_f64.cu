@@ -5,10 +5,10 @@ namespace qg {
 
 const void *force_kernel_f64(int R, bool quad, bool guard) {
   if (R != 2) return nullptr;
-  if (quad) return guard ? (const void *)force_kernel<double, 2, true, true, true>
-                         : (const void *)force_kernel<double, 2, true, false, true>;
-  return guard ? (const void *)force_kernel<double, 2, false, true, true>
-               : (const void *)force_kernel<double, 2, false, false, true>;
+  if (quad) return guard ? (const void *)force_kernel<double, 2, true, true, true, false>
+                         : (const void *)force_kernel<double, 2, true, false, true, false>;
+  return guard ? (const void *)force_kernel<double, 2, false, true, true, false>
+               : (const void *)force_kernel<double, 2, false, false, true, false>;
 }
 
 }  // namespace qg

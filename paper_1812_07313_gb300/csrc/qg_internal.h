@@ -79,21 +79,22 @@ struct ForceParams {
   double *phi;
   int32_t tile;     // list entries per shared-memory tile
   int32_t flush_j;  // entries per thread between FP32 -> FP64 folds
+  float zero, one;  // 0 and 1, as runtime values (see Pair2 in qg_force.cuh)
 };
 
-// Dynamic shared memory of one force CTA.
-inline size_t force_smem_bytes(bool fp64, int R, int nthreads, int tile) {
-  const size_t r4 = fp64 ? 32 : 16, r2 = fp64 ? 16 : 8;
-  // FP64 accumulators [4R][nthreads]; the sink offsets (R * nthreads
-  // 4-vectors of Real, never larger) alias them
-  (void)r4;
-  return (size_t)nthreads * 4 * R * 8
-         + (size_t)tile * (2 * (fp64 ? 32 : 16) + r2);  // staged tile: A, B (4-vectors), C (2-vector)
+// Dynamic shared memory of one force CTA: the FP64 accumulators [4R][nthreads]
+// (the sink offsets, R * nthreads 4-vectors of Real, never larger, alias
+// them) and one tile of staged list entries.
+inline size_t force_smem_bytes(bool fp64, bool paired, int R, int nthreads, int tile) {
+  const size_t per_entry = paired ? 5 * 16                   // (dx dx dy dy) (dz dz m m) + 3 for -Q
+                                  : (fp64 ? 2 * 32 + 16 : 2 * 16 + 8);  // A, B 4-vectors, C 2-vector
+  return (size_t)nthreads * 4 * R * 8 + (size_t)tile * per_entry;
 }
 
 // Kernel registry (one function per translation unit that instantiates it).
 // Returns nullptr for an unsupported combination.
 const void *force_kernel_f32(int R, bool quad, bool guard, bool centred);
+const void *force_kernel_f32x2(int R, bool quad, bool guard);
 const void *force_kernel_f64(int R, bool quad, bool guard);
 
 }  // namespace qg

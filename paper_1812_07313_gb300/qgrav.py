@@ -21,6 +21,7 @@ QG_ERR_SIZE = -6
 QG_NOALLOC_MAX_GROUPS = 1 << 20
 QG_FP32_CENTRED, QG_FP32_RAW, QG_FP64 = 0, 1, 2
 QG_QUAD, QG_MONO = 0, 1
+QG_ARITH_DEFAULT, QG_ARITH_SCALAR, QG_ARITH_PAIRED = 0, 1, 2
 
 _STATUS = {0: "QG_OK", -1: "QG_ERR_ARG", -2: "QG_ERR_CUDA", -3: "QG_ERR_NOMEM", -4: "QG_ERR_STATE",
            -5: "QG_ERR_TIMEOUT", -6: "QG_ERR_SIZE"}
@@ -59,7 +60,7 @@ SIGNATURES = {
 
 class qg_options(ctypes.Structure):
     _fields_ = [("precision", _int), ("expansion", _int), ("tile_j", _int),
-                ("warps_per_group", _int), ("sinks_per_thread", _int), ("flush_j", _int)]
+                ("warps_per_group", _int), ("sinks_per_thread", _int), ("flush_j", _int), ("arith", _int)]
 
 
 class qg_stats(ctypes.Structure):
@@ -67,7 +68,8 @@ class qg_stats(ctypes.Structure):
                 ("n_plist", _i64), ("n_clist", _i64), ("i_pp", _i64), ("i_pc", _i64),
                 ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("sinks_per_thread", ctypes.c_int32), ("tile_j", ctypes.c_int32),
-                ("warps_per_group", ctypes.c_int32), ("flush_j", ctypes.c_int32)]
+                ("warps_per_group", ctypes.c_int32), ("flush_j", ctypes.c_int32),
+                ("paired", ctypes.c_int32)]
 
 
 _lib = None
@@ -127,10 +129,11 @@ class Options:
     warps_per_group: int = 0
     sinks_per_thread: int = 0
     flush_j: int = 0
+    arith: int = QG_ARITH_DEFAULT
 
     def c(self):
         return qg_options(self.precision, self.expansion, self.tile_j, self.warps_per_group,
-                          self.sinks_per_thread, self.flush_j)
+                          self.sinks_per_thread, self.flush_j, self.arith)
 
 
 class Context:
@@ -257,7 +260,8 @@ class Context:
         ms = ctypes.c_float()
         self._ok(self._L.qg_autotune(self._h, stream, int(reps), ctypes.addressof(o), ctypes.addressof(ms)),
                  "qg_autotune")
-        return Options(o.precision, o.expansion, o.tile_j, o.warps_per_group, o.sinks_per_thread, o.flush_j), ms.value
+        return (Options(o.precision, o.expansion, o.tile_j, o.warps_per_group, o.sinks_per_thread, o.flush_j,
+                        o.arith), ms.value)
 
     def qg_last_timing(self):
         """(step_ms, force_ms) of the last run, from events inside its graph."""

@@ -44,17 +44,31 @@ def test_sphere_4k_fp64_kernel(sphere4k):
         assert_parity(a, phi, a_ref, phi_ref, med=TOL_FP64, p99=TOL_FP64, label="sphere_4k fp64")
 
 
+@pytest.mark.parametrize("arith", [qgrav.QG_ARITH_SCALAR, qgrav.QG_ARITH_PAIRED])
 @pytest.mark.parametrize("R,warps,tile,flush", [
     (2, 2, 32, 16), (2, 8, 96, 0), (4, 2, 64, 40), (4, 4, 256, 0), (4, 8, 1024, 1000),
     (8, 2, 128, 0), (8, 4, 512, 8)])
-def test_launch_shapes_and_ragged_tiles(sphere4k, R, warps, tile, flush):
-    """Every supported launch shape, tiles that leave ragged tails, and FP64
-    folds from every entry to never."""
-    o = qgrav.Options(tile_j=tile, warps_per_group=warps, sinks_per_thread=R, flush_j=flush)
+def test_launch_shapes_and_ragged_tiles(sphere4k, R, warps, tile, flush, arith):
+    """Every supported launch shape in both FP32 forms (scalar, and two sinks
+    per float2 with f32x2 instructions), tiles that leave ragged tails, and
+    FP64 folds from every entry to never."""
+    o = qgrav.Options(tile_j=tile, warps_per_group=warps, sinks_per_thread=R, flush_j=flush, arith=arith)
     a, phi, st = sphere4k.gpu(o)
     assert st["sinks_per_thread"] == R and st["tile_j"] == tile
+    assert st["paired"] == (1 if arith == qgrav.QG_ARITH_PAIRED else 0)
     a_ref, phi_ref = sphere4k.oracle()
-    assert_parity(a, phi, a_ref, phi_ref, label="shape %s" % ((R, warps, tile, flush),))
+    assert_parity(a, phi, a_ref, phi_ref, label="shape %s" % ((R, warps, tile, flush, arith),))
+
+
+@pytest.mark.parametrize("arith", [qgrav.QG_ARITH_SCALAR, qgrav.QG_ARITH_PAIRED])
+def test_mono_and_guard_in_both_forms(arith):
+    """Monopole-only cells and the zero-softening guard in both FP32 forms."""
+    ps = workloads.small_set("sphere", 1500, 14, 0.0)
+    case = Case(ps, 0.6)
+    for exp, uq in ((qgrav.QG_QUAD, True), (qgrav.QG_MONO, False)):
+        a, phi, _ = case.gpu(qgrav.Options(expansion=exp, arith=arith))
+        a_ref, phi_ref = case.oracle(use_quad=uq)
+        assert_parity(a, phi, a_ref, phi_ref, med=3e-6, p99=3e-5, label="eps=0 %s %s" % (exp, arith))
 
 
 def test_autotuner_picks_a_supported_shape_and_keeps_parity(sphere4k):
