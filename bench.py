@@ -61,6 +61,10 @@ def parse():
                     help="quadrupole thetas of the equal-error comparison (comma separated)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--batching-compare", action="store_true",
+                    help="also time one launch per system against the single batched launch (multi-system sets)")
+    ap.add_argument("--precision-compare", action="store_true",
+                    help="also time the all-FP64 and the uncentred FP32 kernels and report their differences")
     ap.add_argument("--launch", default=None,
                     help="R,W,T[,x1|x2]: fixed sinks/thread, warps/CTA, tile (and scalar or paired FP32) "
                          "instead of the autotuner (profiling)")
@@ -350,12 +354,8 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
-    total_ms = float(step_ms.sum())
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * args.steps * inter / (total_ms * 1e-3)
+    total_ms, value = aggregate_ranks(float(step_ms.sum()), args.steps, inter, world,
+                                      dist if world > 1 else None, "cuda")
 
     # roofline of the force kernel: FP32 issue bound (lane instructions, FMA = 1)
     alg = OPS_QUAD * i_pc + OPS_MONO * i_pp
@@ -393,6 +393,12 @@ def run_ours(args, rank, world, local_rank):
         out["equal_error"] = equal_error(torch, qgrav, tr, eps2_all, thetas, flush, stream, ee_steps)
         out["gpu_launches"] += 2 * 3 * ee_steps * len(thetas)
 
+    if rank == 0 and args.batching_compare and ps.nsys > 1:
+        out["batching"] = batching_compare(torch, qgrav, tr, L, eps2_all, eps2, stream, flush,
+                                           float(np.mean(step_ms)))
+    if rank == 0 and args.precision_compare:
+        out["precision"] = precision_compare(torch, qgrav, ctx, tr, L, eps2_all, eps2, stream, flush)
+
     # end to end through the C-ABI with host buffers (pinned), every step
     out["e2e"] = e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world)
 
@@ -405,6 +411,96 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
     if rank == 0:
         print(json.dumps(out))
+
+
+def aggregate_ranks(total_ms, steps, units_per_step, world, dist=None, device="cpu"):
+    """Whole-job throughput of replicas: every rank processed `units_per_step`
+    per step; the job took the slowest rank's time (max over ranks)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, world * steps * units_per_step / (total_ms * 1e-3)
+
+
+def batching_compare(torch, qgrav, tr, L, eps2_all, eps2, stream, flush, batched_ms, steps=5):
+    """The same step as one qg_run per system (each system its own context,
+    its own queue build and force launch, launched back to back on one
+    stream) against the single batched launch."""
+    sys_of_group = tr.sink_sys[tr.group_off[:-1]]
+    ctxs = []
+    for s in range(len(tr.sys_off) - 1):
+        b, e = int(tr.sys_off[s]), int(tr.sys_off[s + 1])
+        gsel = np.nonzero(sys_of_group == s)[0]
+        if len(gsel) == 0:
+            continue
+        g0, g1 = int(gsel[0]), int(gsel[-1]) + 1
+        nodes = np.nonzero(tr.cell_sys == s)[0]
+        n0, n1 = int(nodes[0]), int(nodes[-1]) + 1
+        goff = tr.group_off[g0:g1 + 1] - tr.group_off[g0]
+        po = L.plist_off[g0:g1 + 1] - L.plist_off[g0]
+        co = L.clist_off[g0:g1 + 1] - L.clist_off[g0]
+        pi = L.plist_idx[L.plist_off[g0]:L.plist_off[g1]] - b
+        ci = L.clist_idx[L.clist_off[g0]:L.clist_off[g1]] - n0
+        c = qgrav.Context(torch.cuda.current_device())
+        c.qg_set_sinks(tr.x[b:e], goff, eps2_all, None if eps2 is None else eps2[b:e])
+        c.qg_set_sources(tr.x[b:e], tr.m[b:e], po, pi)
+        c.qg_set_cells(tr.cell_com[n0:n1], tr.cell_m[n0:n1], tr.cell_q[n0:n1], co, ci)
+        ctxs.append(c)
+    # one launch shape for all systems: the batched step's autotuned shape would
+    # favour the batched side, so each system keeps the default shape
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for c in ctxs:
+        c.qg_run(stream.cuda_stream)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.add_(1)
+            e0.record(stream)
+            for c in ctxs:
+                c.qg_run(stream.cuda_stream)
+            e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    for c in ctxs:
+        c.close()
+    per_sys = float(np.mean(times))
+    return {"systems": len(ctxs), "batched_ms_per_step": batched_ms, "per_system_ms_per_step": per_sys,
+            "speedup": per_sys / batched_ms, "per_system_launches": 3 * len(ctxs),
+            "note": "per-system contexts at the default launch shape, graphs replayed back to back on one stream"}
+
+
+def precision_compare(torch, qgrav, ctx, tr, L, eps2_all, eps2, stream, flush, steps=3):
+    """All-FP64 kernel and uncentred FP32 kernel on the same lists: device time
+    per step and the relative differences |a - a_64| / |a_64| (and of phi)
+    against the all-FP64 GPU result over every sink."""
+    a32, p32 = ctx.qg_get_forces()
+    res = {}
+    for name, opt in (("fp64", qgrav.Options(precision=qgrav.QG_FP64, sinks_per_thread=2, warps_per_group=4,
+                                              tile_j=256)),
+                      ("fp32_raw", qgrav.Options(precision=qgrav.QG_FP32_RAW))):
+        c = qgrav.Context(torch.cuda.current_device(), opt)
+        load_ctx(c, tr, L, eps2_all, eps2)
+        c.qg_run(stream.cuda_stream)
+        torch.cuda.synchronize()
+        ms, _ = timed_steps(torch, c, stream, flush, steps)
+        a, p = c.qg_get_forces()
+        c.close()
+        res[name] = {"ms_per_step": float(ms.mean()), "a": a, "phi": p}
+    a64, p64 = res["fp64"]["a"], res["fp64"]["phi"]
+
+    def pct(x):
+        return {"p50": float(np.percentile(x, 50)), "p90": float(np.percentile(x, 90)),
+                "p99": float(np.percentile(x, 99)), "max": float(np.max(x))}
+
+    out = {"fp64_ms_per_step": res["fp64"]["ms_per_step"], "fp32_raw_ms_per_step": res["fp32_raw"]["ms_per_step"]}
+    for name, a, p in (("fp32_centred", a32, p32), ("fp32_raw", res["fp32_raw"]["a"], res["fp32_raw"]["phi"])):
+        out[name + "_vs_fp64"] = {"a": pct(np.linalg.norm(a - a64, axis=1) / np.linalg.norm(a64, axis=1)),
+                                  "phi": pct(np.abs(p - p64) / np.abs(p64))}
+    return out
 
 
 def e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world, steps=3):
