@@ -48,6 +48,29 @@ template <> struct RT<double> {
   static __device__ __forceinline__ double rsqrt(double x) { return 1.0 / sqrt(x); }
 };
 
+// Staging choices, fixed at compile time:
+//   QG_CVT_HW  centred offsets rounded to FP32 by the hardware conversion for
+//              the first QG_CVT_HW coordinates (it issues on the narrow FP64
+//              pipe), by integer operations for the rest (ALU pipe);
+//   QG_GATHER2 each thread keeps two list entries' gathers in flight before
+//              converting either.
+#ifndef QG_CVT_HW
+#define QG_CVT_HW 0
+#endif
+#ifndef QG_GATHER2
+#define QG_GATHER2 1
+#endif
+
+template <typename Real, int K>
+__device__ __forceinline__ Real cvt_off(double v) {
+  if constexpr (sizeof(Real) == 4) {
+    if constexpr (K < QG_CVT_HW) return __double2float_rn(v);
+    else return f64_to_f32_rn(v);
+  } else {
+    return v;
+  }
+}
+
 // One source particle on one sink: Eq. 4 and its gradient.  13 Real ops + 1 rsqrt.
 template <typename Real, bool GUARD>
 __device__ __forceinline__ void mono_pair(Real dx, Real dy, Real dz, Real m, Real e2,
@@ -342,16 +365,31 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
       for (int64_t base = p0; base < p1; base += T) {
         const int cnt = (int)min((int64_t)T, p1 - base);
         __syncthreads();  // the previous tile's readers are done
-        for (int t = tid; t < cnt; t += NT) {
-          const int j = p.plist_idx[base + t];
-          const PosMass v = p.src[j];
+        auto put_p = [&](int t, const PosMass &v, int j) {
           const Real m = sizeof(Real) == 4 ? (Real)v.m : (Real)p.src_m64[j];
-          const Real dx = RT<Real>::cvt(v.x - cx), dy = RT<Real>::cvt(v.y - cy), dz = RT<Real>::cvt(v.z - cz);
+          const Real dx = cvt_off<Real, 0>(v.x - cx), dy = cvt_off<Real, 1>(v.y - cy),
+                     dz = cvt_off<Real, 2>(v.z - cz);
           if constexpr (PAIRED) {
             tP0[t] = make_float4(dx, dx, dy, dy);
             tP1[t] = make_float4(dz, dz, m, m);
           } else {
             tA[t] = RT<Real>::make4(dx, dy, dz, m);
+          }
+        };
+        if constexpr (QG_GATHER2 != 0) {
+          for (int t = tid; t < cnt; t += 2 * NT) {
+            const int t1 = t + NT;
+            const int j0 = p.plist_idx[base + t];
+            const int j1 = t1 < cnt ? p.plist_idx[base + t1] : j0;
+            const PosMass v0 = p.src[j0];
+            const PosMass v1 = p.src[j1];
+            put_p(t, v0, j0);
+            if (t1 < cnt) put_p(t1, v1, j1);
+          }
+        } else {
+          for (int t = tid; t < cnt; t += NT) {
+            const int j = p.plist_idx[base + t];
+            put_p(t, p.src[j], j);
           }
         }
         __syncthreads();
@@ -385,16 +423,14 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
       for (int64_t base = c0; base < c1; base += T) {
         const int cnt = (int)min((int64_t)T, c1 - base);
         __syncthreads();  // the previous tile's readers are done
-        for (int t = tid; t < cnt; t += NT) {
-          const int j = p.clist_idx[base + t];
-          const PosMass v = p.cell_pm[j];
+        auto put_c = [&](int t, const PosMass &v, int j, float4 q0, float4 q1) {
           const Real m = sizeof(Real) == 4 ? (Real)v.m : (Real)p.cell_m64[j];
-          const Real dx = RT<Real>::cvt(v.x - cx), dy = RT<Real>::cvt(v.y - cy), dz = RT<Real>::cvt(v.z - cz);
+          const Real dx = cvt_off<Real, 0>(v.x - cx), dy = cvt_off<Real, 1>(v.y - cy),
+                     dz = cvt_off<Real, 2>(v.z - cz);
           if constexpr (PAIRED) {
             tP0[t] = make_float4(dx, dx, dy, dy);
             tP1[t] = make_float4(dz, dz, m, m);
             if (QUAD) {
-              const float4 q0 = p.cell_q[2 * j], q1 = p.cell_q[2 * j + 1];
               tQ0[t] = make_float4(-q0.x, -q0.x, -q0.y, -q0.y);
               tQ1[t] = make_float4(-q0.z, -q0.z, -q0.w, -q0.w);
               tQ2[t] = make_float4(-q1.x, -q1.x, -q1.y, -q1.y);
@@ -403,7 +439,6 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
             tA[t] = RT<Real>::make4(dx, dy, dz, m);
             if (QUAD) {
               if (sizeof(Real) == 4) {
-                const float4 q0 = p.cell_q[2 * j], q1 = p.cell_q[2 * j + 1];
                 tB[t] = RT<Real>::make4(q0.x, q0.y, q0.z, q0.w);
                 tC[t] = RT<Real>::make2(q1.x, q1.y);
               } else {
@@ -412,6 +447,27 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
                 tC[t] = RT<Real>::make2((Real)q[4], (Real)q[5]);
               }
             }
+          }
+        };
+        const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (QG_GATHER2 != 0) {
+          for (int t = tid; t < cnt; t += 2 * NT) {
+            const int t1 = t + NT;
+            const int j0 = p.clist_idx[base + t];
+            const int j1 = t1 < cnt ? p.clist_idx[base + t1] : j0;
+            const PosMass v0 = p.cell_pm[j0];
+            const PosMass v1 = p.cell_pm[j1];
+            const bool fq = QUAD && sizeof(Real) == 4;
+            const float4 a0 = fq ? p.cell_q[2 * j0] : zero4, b0 = fq ? p.cell_q[2 * j0 + 1] : zero4;
+            const float4 a1 = fq ? p.cell_q[2 * j1] : zero4, b1 = fq ? p.cell_q[2 * j1 + 1] : zero4;
+            put_c(t, v0, j0, a0, b0);
+            if (t1 < cnt) put_c(t1, v1, j1, a1, b1);
+          }
+        } else {
+          for (int t = tid; t < cnt; t += NT) {
+            const int j = p.clist_idx[base + t];
+            const bool fq = QUAD && sizeof(Real) == 4;
+            put_c(t, p.cell_pm[j], j, fq ? p.cell_q[2 * j] : zero4, fq ? p.cell_q[2 * j + 1] : zero4);
           }
         }
         __syncthreads();
