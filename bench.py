@@ -38,7 +38,7 @@ DESCR = {
     "sphere_4k": "4096 particles uniform in the unit sphere, eps=1e-2, leaf<=8, n_crit=64",
     "plummer_4m": "2^22-particle Plummer sphere (a=1, r<=100), eps=1e-3, leaf<=8, n_crit=256",
     "batched_512": "512 independent Plummer/Hernquist systems, N log-uniform in [1024, 65536], eps=1e-2, "
-                   "n_crit=64, one persistent launch",
+                   "theta=0.5, one persistent launch (n_crit 64 unless --group-sizes tunes it)",
     "batched_64": "64 independent Plummer/Hernquist systems, N log-uniform in [1024, 65536], eps=1e-2, "
                   "n_crit=64 (the profiling-size case of batched_512)",
     "clumpy_16m": "2^24 particles in the unit cube, 70% in 2000 Plummer clumps + 30% uniform, eps=5e-5, "
@@ -65,6 +65,8 @@ def parse():
                     help="also time one launch per system against the single batched launch (multi-system sets)")
     ap.add_argument("--precision-compare", action="store_true",
                     help="also time the all-FP64 and the uncentred FP32 kernels and report their differences")
+    ap.add_argument("--group-sizes", default=None,
+                    help="candidate n_crit values (comma separated): time the step for each and use the fastest")
     ap.add_argument("--launch", default=None,
                     help="R,W,T[,x1|x2]: fixed sinks/thread, warps/CTA, tile (and scalar or paired FP32) "
                          "instead of the autotuner (profiling)")
@@ -309,6 +311,19 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     qgrav.lib()
     wl, ps, tr, L, eps2_all, eps2, host_times = build_case(args.workload, args.theta)
+    group_size = {"n_crit": wl.n_crit, "tuned": False}
+    if args.group_sizes:
+        from paper_1812_07313_gb300 import tuning
+        cands = [int(v) for v in args.group_sizes.split(",")]
+        best, table, (tr, L) = tuning.tune_group_size(
+            ps.x, ps.m, ps.sys_off, wl.leaf_max, L.theta, cands, eps2_all=eps2_all,
+            eps2_of_system=None if eps2 is None else ps.eps ** 2, device=torch.cuda.current_device())
+        if eps2 is not None:
+            eps2 = (ps.eps[tr.sink_sys] ** 2).astype(np.float32)
+        group_size = {"n_crit": best.n_crit, "tuned": True,
+                      "candidates": [{"n_crit": r.n_crit, "groups": r.groups, "interactions": r.interactions,
+                                      "step_ms": r.step_ms, "force_ms": r.force_ms, "launch": r.launch}
+                                     for r in table]}
     theta = L.theta
     dev = torch.cuda.current_device()
     props = torch.cuda.get_device_properties(dev)
@@ -380,7 +395,7 @@ def run_ours(args, rank, world, local_rank):
            "config": {"workload": "%s: %s" % (args.workload, DESCR.get(args.workload, "")),
                       "theta": theta, "expansion": "quad", "precision": "fp32, fp64 centring and merges",
                       "interactions": {"i_pp": i_pp, "i_pc": i_pc}, "groups": tr.ngroups,
-                      "launch": launch,
+                      "group_size": group_size, "launch": launch,
                       "l2": "flushed before every timed step (256 MiB device write, outside the step events)",
                       "parallelism": "replicas" if world > 1 else "single GPU",
                       "host_tree_s": host_times},

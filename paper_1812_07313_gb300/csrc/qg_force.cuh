@@ -302,6 +302,9 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
 
       const int S = (nch + R - 1) / R;  // sink slots
       const int K = NT / S;             // list streams
+      // tiles hold a whole number of passes of the K streams, so that no
+      // tile ends in a partly filled pass (only the list's last tile may)
+      const int TK = T >= K ? (T / K) * K : T;
       const int s = tid % S;
       const int k = tid / S;
       const bool active = k < K;
@@ -361,9 +364,21 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
         nproc = 0;
       };
 
+      // The first two list indices this thread stages from the next tile are
+      // loaded one tile ahead (during the current tile's arithmetic), so the
+      // gather of a tile waits for one memory round trip instead of two.
+      int pf0 = -1, pf1 = -1;
+      auto prefetch = [&](const int32_t *idx, int64_t b, int64_t end) {
+        const int c = (int)min((int64_t)TK, end - b);
+        pf0 = tid < c ? __ldg(idx + b + tid) : -1;
+        pf1 = tid + NT < c ? __ldg(idx + b + tid + NT) : -1;
+      };
+      if (p0 < p1) prefetch(p.plist_idx, p0, p1);
+      else if (c0 < c1) prefetch(p.clist_idx, c0, c1);
+
       // ---- 3-4. particle part of the list (monopole, Eq. 4) ----------------
-      for (int64_t base = p0; base < p1; base += T) {
-        const int cnt = (int)min((int64_t)T, p1 - base);
+      for (int64_t base = p0; base < p1; base += TK) {
+        const int cnt = (int)min((int64_t)TK, p1 - base);
         __syncthreads();  // the previous tile's readers are done
         auto put_p = [&](int t, const PosMass &v, int j) {
           const Real m = sizeof(Real) == 4 ? (Real)v.m : (Real)p.src_m64[j];
@@ -379,8 +394,9 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
         if constexpr (QG_GATHER2 != 0) {
           for (int t = tid; t < cnt; t += 2 * NT) {
             const int t1 = t + NT;
-            const int j0 = p.plist_idx[base + t];
-            const int j1 = t1 < cnt ? p.plist_idx[base + t1] : j0;
+            const bool first = t == tid;
+            const int j0 = first ? pf0 : p.plist_idx[base + t];
+            const int j1 = t1 < cnt ? (first ? pf1 : p.plist_idx[base + t1]) : j0;
             const PosMass v0 = p.src[j0];
             const PosMass v1 = p.src[j1];
             put_p(t, v0, j0);
@@ -388,10 +404,12 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
           }
         } else {
           for (int t = tid; t < cnt; t += NT) {
-            const int j = p.plist_idx[base + t];
+            const int j = t == tid ? pf0 : (t == tid + NT ? pf1 : p.plist_idx[base + t]);
             put_p(t, p.src[j], j);
           }
         }
+        if (base + TK < p1) prefetch(p.plist_idx, base + TK, p1);
+        else if (c0 < c1) prefetch(p.clist_idx, c0, c1);
         __syncthreads();
         if (active) {
           if constexpr (PAIRED) {
@@ -420,8 +438,8 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
       }
 
       // ---- 3-4. cell part of the list (Eq. 1 / Eq. 8, or monopole) --------
-      for (int64_t base = c0; base < c1; base += T) {
-        const int cnt = (int)min((int64_t)T, c1 - base);
+      for (int64_t base = c0; base < c1; base += TK) {
+        const int cnt = (int)min((int64_t)TK, c1 - base);
         __syncthreads();  // the previous tile's readers are done
         auto put_c = [&](int t, const PosMass &v, int j, float4 q0, float4 q1) {
           const Real m = sizeof(Real) == 4 ? (Real)v.m : (Real)p.cell_m64[j];
@@ -453,8 +471,9 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
         if constexpr (QG_GATHER2 != 0) {
           for (int t = tid; t < cnt; t += 2 * NT) {
             const int t1 = t + NT;
-            const int j0 = p.clist_idx[base + t];
-            const int j1 = t1 < cnt ? p.clist_idx[base + t1] : j0;
+            const bool first = t == tid;
+            const int j0 = first ? pf0 : p.clist_idx[base + t];
+            const int j1 = t1 < cnt ? (first ? pf1 : p.clist_idx[base + t1]) : j0;
             const PosMass v0 = p.cell_pm[j0];
             const PosMass v1 = p.cell_pm[j1];
             const bool fq = QUAD && sizeof(Real) == 4;
@@ -465,11 +484,12 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
           }
         } else {
           for (int t = tid; t < cnt; t += NT) {
-            const int j = p.clist_idx[base + t];
+            const int j = t == tid ? pf0 : (t == tid + NT ? pf1 : p.clist_idx[base + t]);
             const bool fq = QUAD && sizeof(Real) == 4;
             put_c(t, p.cell_pm[j], j, fq ? p.cell_q[2 * j] : zero4, fq ? p.cell_q[2 * j + 1] : zero4);
           }
         }
+        if (base + TK < c1) prefetch(p.clist_idx, base + TK, c1);
         __syncthreads();
         if (active) {
           if constexpr (PAIRED) {

@@ -91,6 +91,27 @@ def test_autotuner_picks_a_supported_shape_and_keeps_parity(sphere4k):
     assert_parity(a, phi, a_ref, phi_ref, label="autotuned %s" % best)
 
 
+def test_group_size_tuning_picks_the_fastest_and_keeps_parity():
+    from paper_1812_07313_gb300 import tuning
+    ps = workloads.batched_systems(nsys=6, seed=13, n_lo=800, n_hi=4000)
+    best, table, (tr, L) = tuning.tune_group_size(ps.x, ps.m, ps.sys_off, 8, 0.5, [16, 64, 256],
+                                                  eps2_all=1e-4, steps=2)
+    assert [r.n_crit for r in table] == [16, 64, 256]
+    assert best.step_ms == min(r.step_ms for r in table)
+    assert np.diff(tr.group_off).max() <= best.n_crit
+    ctx = qgrav.Context(0)
+    ctx.qg_set_sinks(tr.x, tr.group_off, 1e-4)
+    ctx.qg_set_sources(tr.x, tr.m, L.plist_off, L.plist_idx)
+    ctx.qg_set_cells(tr.cell_com, tr.cell_m, tr.cell_q, L.clist_off, L.clist_idx)
+    ctx.qg_run()
+    a, phi = ctx.qg_get_forces()
+    ctx.close()
+    a_ref, phi_ref = oracle.expansion_forces(tr.group_off, tr.x, tr.x, tr.m, L.plist_off, L.plist_idx,
+                                             tr.cell_com, tr.cell_m, tr.cell_q, L.clist_off, L.clist_idx,
+                                             eps2_all=1e-4)
+    assert_parity(a, phi, a_ref, phi_ref, label="tuned n_crit %d" % best.n_crit)
+
+
 def test_deterministic_and_repeatable(sphere4k):
     ctx = qgrav.Context(0)
     a1, p1, _ = sphere4k.gpu(ctx=ctx)
