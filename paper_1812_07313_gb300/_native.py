@@ -29,7 +29,10 @@ CUDA_LIB = os.path.join(BUILD, "libqgrav.so")
 CUDA_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Per-source extra flags: the FP32 force kernels flush single-precision
 # denormals (one SFU instruction per reciprocal square root, no fix-up path).
-CUDA_FLAGS = {"qg_force_f32.cu": ["-ftz=true"]}
+CUDA_FLAGS = {"qg_force_f32.cu": ["-ftz=true"], "qg_force_f32x2.cu": ["-ftz=true"],
+              # the GPU tree reproduces the host builder bit for bit: no FMA
+              # contraction on either side
+              "qg_gtree.cu": ["-fmad=false", "-Xcompiler", "-ffp-contract=off"]}
 
 _lock = threading.Lock()
 
@@ -55,7 +58,7 @@ def build_tree(force=False, verbose=False):
         if force or _newer(TREE_LIB, deps):
             os.makedirs(BUILD, exist_ok=True)
             tmp = TREE_LIB + ".tmp%d" % os.getpid()
-            cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
+            cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                    "-I" + INCLUDE] + srcs + ["-o", tmp]
             if verbose:
                 print(" ".join(cmd))

@@ -1,0 +1,1143 @@
+// qg_gtree.cu -- oct-tree build, cell moments (Eq. 2), sink groups (Sec. 3.4)
+// and the group walk on the GPU (include/qg_gtree.h).
+//
+// Built with -fmad=false (and the host side with -ffp-contract=off, like the
+// host builder): every FP64 expression here is evaluated in the host
+// builder's order without fused multiply-adds, so keys, moments and opening
+// decisions are bit-for-bit the host's.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qg_gtree.h"
+#include "qgrav.h"
+
+namespace {
+
+constexpr int kMaxLevel = 21;   // 21 bits per axis -> 63-bit Morton keys
+constexpr int kStack = 160;     // walk stack: 1 + 7 per level is enough
+constexpr int kScanThreads = 256, kScanItems = 4, kScanTile = kScanThreads * kScanItems;
+constexpr int kSortThreads = 256, kSortItems = 8, kSortTile = kSortThreads * kSortItems;
+
+template <typename T>
+struct DBuf {
+  T *p = nullptr;
+  size_t cap = 0;
+  cudaError_t reserve(size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e == cudaSuccess) cap = n;
+    return e;
+  }
+  // grow keeping the first `keep` elements
+  cudaError_t grow(size_t n, size_t keep, cudaStream_t s) {
+    if (n <= cap && p) return cudaSuccess;
+    size_t c = std::max(n, cap * 2);
+    T *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, c * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (keep && p) e = cudaMemcpyAsync(q, p, keep * sizeof(T), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (p) cudaFree(p);
+    p = q;
+    cap = c;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+int blocks_for(int64_t n, int per_block) {
+  const int64_t b = (n + per_block - 1) / per_block;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 1 << 20));
+}
+
+// ------------------------------------------------------------------ scan
+// Exclusive prefix sum of int32 counts into int64 offsets; out may be
+// [n+1] long: out[n] receives the total when with_total.
+
+__global__ void scan_block_kernel(int64_t n, const int32_t *__restrict__ in, int64_t *__restrict__ out,
+                                  int64_t *__restrict__ sums) {
+  __shared__ int64_t s[kScanThreads];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t tot = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    v[k] = base + k < n ? (int64_t)in[base + k] : 0;
+    tot += v[k];
+  }
+  s[threadIdx.x] = tot;
+  __syncthreads();
+  for (int o = 1; o < kScanThreads; o <<= 1) {  // Hillis-Steele over the thread totals
+    const int64_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+    __syncthreads();
+    s[threadIdx.x] += t;
+    __syncthreads();
+  }
+  int64_t run = s[threadIdx.x] - tot;  // exclusive prefix of this thread
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = s[threadIdx.x];
+}
+
+__global__ void scan_add_kernel(int64_t n, int64_t *__restrict__ out, const int64_t *__restrict__ offs) {
+  const int64_t i = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+  const int64_t off = offs[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    const int64_t j = i + (int64_t)k * kScanThreads;
+    if (j < n) out[j] += off;
+  }
+}
+
+// int64 -> int64 variant for the recursive level
+__global__ void scan_block64_kernel(int64_t n, const int64_t *__restrict__ in, int64_t *__restrict__ out,
+                                    int64_t *__restrict__ sums) {
+  __shared__ int64_t s[kScanThreads];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t tot = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    v[k] = base + k < n ? in[base + k] : 0;
+    tot += v[k];
+  }
+  s[threadIdx.x] = tot;
+  __syncthreads();
+  for (int o = 1; o < kScanThreads; o <<= 1) {
+    const int64_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+    __syncthreads();
+    s[threadIdx.x] += t;
+    __syncthreads();
+  }
+  int64_t run = s[threadIdx.x] - tot;
+#pragma unroll
+  for (int k = 0; k < kScanItems; k++) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = s[threadIdx.x];
+}
+
+__global__ void set_total_kernel(int64_t n, const int32_t *in, int64_t *out) {
+  // out[n] = out[n-1] + in[n-1] (or 0 when n == 0)
+  if (threadIdx.x == 0 && blockIdx.x == 0) out[n] = n > 0 ? out[n - 1] + (int64_t)in[n - 1] : 0;
+}
+
+}  // namespace
+
+struct qg_gtree {
+  int device = 0;
+  int64_t n = 0, nsys = 0, nnodes = 0, G = 0, np_list = 0, nc_list = 0;
+  int leaf_max = 8, n_crit = 64;
+  bool built = false, walked = false;
+  std::vector<int64_t> h_sys_off;
+  // particles
+  DBuf<int64_t> perm;
+  DBuf<double> xs, ms;
+  DBuf<int32_t> psys;
+  DBuf<int64_t> sys_off;
+  DBuf<unsigned long long> bmin, bmax;
+  DBuf<double> lo, scale;
+  // sort scratch
+  DBuf<unsigned long long> keys, keys2;
+  DBuf<int32_t> vals, vals2, hist;
+  DBuf<int64_t> hoff;
+  // tree
+  DBuf<int64_t> nbeg, nend, range;
+  DBuf<int32_t> nlevel, nparent, nfirst, nnchild, nsysid, node_of, flag;
+  DBuf<int64_t> excl;
+  DBuf<double> centre, half, side, com, mass, q;
+  std::vector<int64_t> level_begin;
+  DBuf<int32_t> sys_root;
+  // groups and lists
+  DBuf<int32_t> gflag, gnode_at, group_node, cnt_p, cnt_c;
+  DBuf<int64_t> gidx, group_off, plist_off, clist_off;
+  DBuf<int32_t> plist_idx, clist_idx;
+  DBuf<int64_t> scan_tmp[5];
+  DBuf<int> err;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+#define GT_CUDA(call)                                                   \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess)                                              \
+      return e_ == cudaErrorMemoryAllocation ? QG_ERR_NOMEM : QG_ERR_CUDA; \
+  } while (0)
+
+// Exclusive scan of an int64 array in place: block scans, the block sums
+// scanned recursively (one scratch level per recursion), then added back.
+qg_status scan_inplace64(qg_gtree *t, int64_t m, int64_t *arr, int lvl, cudaStream_t s) {
+  if (m <= 1) {
+    if (m == 1) GT_CUDA(cudaMemsetAsync(arr, 0, sizeof(int64_t), s));
+    return QG_OK;
+  }
+  if (lvl >= 4) return QG_ERR_ARG;  // beyond 2^40 elements
+  const int64_t mb = (m + kScanTile - 1) / kScanTile;
+  GT_CUDA(t->scan_tmp[lvl].reserve(mb));
+  scan_block64_kernel<<<(unsigned)mb, kScanThreads, 0, s>>>(m, arr, arr, t->scan_tmp[lvl].p);
+  GT_CUDA(cudaGetLastError());
+  if (mb > 1) {
+    const qg_status st = scan_inplace64(t, mb, t->scan_tmp[lvl].p, lvl + 1, s);
+    if (st != QG_OK) return st;
+    scan_add_kernel<<<(unsigned)mb, kScanThreads, 0, s>>>(m, arr, t->scan_tmp[lvl].p);
+    GT_CUDA(cudaGetLastError());
+  }
+  return QG_OK;
+}
+
+// out[0..n) = exclusive scan of the int32 counts in; out[n] = their total.
+// out must hold n + 1 elements.
+qg_status scan_excl(qg_gtree *t, int64_t n, const int32_t *in, int64_t *out, cudaStream_t s) {
+  if (n > 0) {
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    GT_CUDA(t->scan_tmp[0].reserve(nb));
+    scan_block_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(n, in, out, t->scan_tmp[0].p);
+    GT_CUDA(cudaGetLastError());
+    if (nb > 1) {
+      const qg_status st = scan_inplace64(t, nb, t->scan_tmp[0].p, 1, s);
+      if (st != QG_OK) return st;
+      scan_add_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(n, out, t->scan_tmp[0].p);
+      GT_CUDA(cudaGetLastError());
+    }
+  }
+  set_total_kernel<<<1, 1, 0, s>>>(n, in, out);
+  GT_CUDA(cudaGetLastError());
+  return QG_OK;
+}
+
+// ------------------------------------------------------------------ radix sort
+// Stable LSD radix sort of (uint64 key, int32 value) pairs by the low `bits`
+// bits, 8 bits per pass.  Per pass: per-tile digit histograms, an exclusive
+// scan over (digit, tile), and a scatter that ranks equal digits in tile order
+// (warp by warp, 32 keys at a time with __match_any_sync).
+
+__global__ void sort_hist_kernel(int64_t n, const unsigned long long *__restrict__ keys, int shift,
+                                 int32_t *__restrict__ hist, int64_t nblocks) {
+  __shared__ int32_t c[256];
+  c[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+  for (int k = threadIdx.x; k < kSortTile; k += kSortThreads) {
+    const int64_t i = base + k;
+    if (i < n) atomicAdd(&c[(keys[i] >> shift) & 255], 1);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = c[threadIdx.x];
+}
+
+__global__ void sort_scatter_kernel(int64_t n, const unsigned long long *__restrict__ kin,
+                                    const int32_t *__restrict__ vin, unsigned long long *__restrict__ kout,
+                                    int32_t *__restrict__ vout, int shift, const int64_t *__restrict__ offs,
+                                    int64_t nblocks) {
+  __shared__ int32_t wc[kSortThreads / 32][256];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int d = lane; d < 256; d += 32) wc[w][d] = 0;
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  // warp w owns keys [base + w * 32 * kSortItems, ...) in order
+  const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)w * 32 * kSortItems;
+  unsigned long long key[kSortItems];
+  int32_t val[kSortItems], rank[kSortItems];
+  int dig[kSortItems];
+#pragma unroll
+  for (int c = 0; c < kSortItems; c++) {
+    const int64_t i = base + (int64_t)c * 32 + lane;
+    const bool valid = i < n;
+    key[c] = valid ? kin[i] : 0ull;
+    val[c] = valid ? vin[i] : 0;
+    const int d = valid ? (int)((key[c] >> shift) & 255) : 256;
+    dig[c] = d;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const int before = valid ? wc[w][d] : 0;
+    rank[c] = before + __popc(peers & lt);
+    __syncwarp();
+    const int leader = __ffs(peers) - 1;
+    if (valid && lane == leader) wc[w][d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: exclusive prefix over the warps
+  if (threadIdx.x < 256) {
+    int run = 0;
+    for (int v = 0; v < kSortThreads / 32; v++) {
+      const int t = wc[v][threadIdx.x];
+      wc[v][threadIdx.x] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < kSortItems; c++) {
+    const int d = dig[c];
+    if (d < 256) {
+      const int64_t pos = offs[(int64_t)d * nblocks + blockIdx.x] + wc[w][d] + rank[c];
+      kout[pos] = key[c];
+      vout[pos] = val[c];
+    }
+  }
+}
+
+qg_status radix_sort(qg_gtree *t, int64_t n, int bits, cudaStream_t s) {
+  // sorts t->keys / t->vals in place (ping-pong with keys2 / vals2)
+  if (n <= 1) return QG_OK;
+  const int64_t nb = (n + kSortTile - 1) / kSortTile;
+  GT_CUDA(t->keys2.reserve(n));
+  GT_CUDA(t->vals2.reserve(n));
+  GT_CUDA(t->hist.reserve(256 * nb));
+  GT_CUDA(t->hoff.reserve(256 * nb + 1));
+  unsigned long long *ka = t->keys.p, *kb = t->keys2.p;
+  int32_t *va = t->vals.p, *vb = t->vals2.p;
+  int passes = 0;
+  for (int shift = 0; shift < bits; shift += 8, passes++) {
+    sort_hist_kernel<<<(unsigned)nb, kSortThreads, 0, s>>>(n, ka, shift, t->hist.p, nb);
+    GT_CUDA(cudaGetLastError());
+    qg_status st = scan_excl(t, 256 * nb, t->hist.p, t->hoff.p, s);
+    if (st != QG_OK) return st;
+    sort_scatter_kernel<<<(unsigned)nb, kSortThreads, 0, s>>>(n, ka, va, kb, vb, shift, t->hoff.p, nb);
+    GT_CUDA(cudaGetLastError());
+    std::swap(ka, kb);
+    std::swap(va, vb);
+  }
+  if (passes & 1) {
+    GT_CUDA(cudaMemcpyAsync(t->keys.p, ka, n * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, s));
+    GT_CUDA(cudaMemcpyAsync(t->vals.p, va, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  }
+  return QG_OK;
+}
+
+// ------------------------------------------------------------------ keys
+
+__device__ __forceinline__ unsigned long long ordered(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__host__ __device__ inline double unordered(unsigned long long k) {
+  const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+  double v;
+  memcpy(&v, &b, sizeof v);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long spread3(unsigned long long v) {
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+__global__ void psys_kernel(int64_t n, int64_t nsys, const int64_t *__restrict__ sys_off, int32_t *psys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = nsys;  // largest s with sys_off[s] <= i
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) / 2;
+      if (sys_off[mid] <= i) lo = mid; else hi = mid;
+    }
+    psys[i] = (int32_t)lo;
+  }
+}
+
+// per-system min / max of every coordinate (ordered integer encodings)
+__global__ void bbox_kernel(int64_t n, const double *__restrict__ x, const int32_t *__restrict__ psys,
+                            unsigned long long *bmin, unsigned long long *bmax) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    const bool valid = i < n;
+    const int s = valid ? psys[i] : -1;
+    const int s0 = __shfl_sync(0xffffffffu, s, 0);
+    const bool uniform = __all_sync(0xffffffffu, !valid || s == s0);
+    for (int d = 0; d < 3; d++) {
+      unsigned long long kmn = valid ? ordered(x[3 * i + d]) : ~0ull;
+      unsigned long long kmx = valid ? kmn : 0ull;
+      if (uniform) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmn, o);
+          const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmx, o);
+          kmn = a < kmn ? a : kmn;
+          kmx = b > kmx ? b : kmx;
+        }
+        if (lane == 0) {
+          atomicMin(&bmin[3 * s0 + d], kmn);
+          atomicMax(&bmax[3 * s0 + d], kmx);
+        }
+      } else if (valid) {
+        atomicMin(&bmin[3 * s + d], kmn);
+        atomicMax(&bmax[3 * s + d], kmx);
+      }
+    }
+  }
+}
+
+__global__ void fill_ull_kernel(int64_t n, unsigned long long *p, unsigned long long v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
+}
+
+__global__ void keys_kernel(int64_t n, const double *__restrict__ x, const int32_t *__restrict__ psys,
+                            const double *__restrict__ lo, const double *__restrict__ scale,
+                            unsigned long long *__restrict__ keys, int32_t *__restrict__ vals) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int s = psys[i];
+    unsigned long long k = 0;
+    for (int d = 0; d < 3; d++) {
+      const double f = __dmul_rn(__dsub_rn(x[3 * i + d], lo[3 * s + d]), scale[s]);
+      long long c = (long long)floor(f);
+      c = c < 0 ? 0 : (c > (1ll << kMaxLevel) - 1 ? (1ll << kMaxLevel) - 1 : c);
+      k |= spread3((unsigned long long)c) << (2 - d);
+    }
+    keys[i] = k;
+    vals[i] = (int32_t)i;
+  }
+}
+
+// after the Morton sort: the system of each sorted element as the next key
+__global__ void syskey_kernel(int64_t n, const int32_t *__restrict__ vals, const int32_t *__restrict__ psys,
+                              const unsigned long long *__restrict__ keys, unsigned long long *__restrict__ key2,
+                              int32_t *__restrict__ pos, unsigned long long *__restrict__ morton_copy) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    key2[i] = (unsigned long long)psys[vals[i]];
+    pos[i] = (int32_t)i;
+    morton_copy[i] = keys[i];
+  }
+}
+
+__global__ void gather_sorted_kernel(int64_t n, const int32_t *__restrict__ vals, const int32_t *__restrict__ pos,
+                                     const unsigned long long *__restrict__ morton_in,
+                                     unsigned long long *__restrict__ morton_out, const double *__restrict__ x,
+                                     const double *__restrict__ m, int64_t *__restrict__ perm,
+                                     double *__restrict__ xs, double *__restrict__ ms, int use_pos) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = use_pos ? pos[i] : i;           // position in the Morton-sorted order
+    const int64_t src = use_pos ? vals[j] : vals[i];  // input index
+    perm[i] = src;
+    if (use_pos) morton_out[i] = morton_in[j];
+    xs[3 * i] = x[3 * src];
+    xs[3 * i + 1] = x[3 * src + 1];
+    xs[3 * i + 2] = x[3 * src + 2];
+    ms[i] = m[src];
+  }
+}
+
+// ------------------------------------------------------------------ nodes
+
+__device__ __forceinline__ int digit_at(unsigned long long key, int level) {
+  return (int)((key >> (3 * (kMaxLevel - 1 - level))) & 7);
+}
+
+__global__ void mark_children_kernel(int64_t n, int level, int leaf_max, const unsigned long long *__restrict__ keys,
+                                     const int32_t *__restrict__ node_of, const int64_t *__restrict__ nbeg,
+                                     const int64_t *__restrict__ nend, int32_t *__restrict__ flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int p = node_of[i];
+    int f = 0;
+    if (p >= 0 && nend[p] - nbeg[p] > leaf_max && level < kMaxLevel) {
+      const int d = digit_at(keys[i], level);
+      f = (i == nbeg[p] || digit_at(keys[i - 1], level) != d) ? 1 : 0;
+    }
+    flag[i] = f;
+  }
+}
+
+__global__ void emit_children_kernel(int64_t n, int level, int32_t base, const unsigned long long *__restrict__ keys,
+                                     int32_t *__restrict__ node_of, const int32_t *__restrict__ flag,
+                                     const int64_t *__restrict__ excl, const int64_t *__restrict__ nend_parent_src,
+                                     int64_t *__restrict__ nbeg, int32_t *__restrict__ nlevel,
+                                     int32_t *__restrict__ nparent, int32_t *__restrict__ nfirst,
+                                     int32_t *__restrict__ nnchild, int32_t *__restrict__ nsysid,
+                                     double *__restrict__ centre, double *__restrict__ half, int leaf_max) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int p = node_of[i];
+    if (p < 0) continue;
+    if (!(nend_parent_src[p] - nbeg[p] > leaf_max && level < kMaxLevel)) {
+      node_of[i] = -1;  // p is a leaf: this particle is done
+      continue;
+    }
+    const int32_t c = base + (int32_t)(excl[i] + flag[i]) - 1;  // the child holding i
+    node_of[i] = c;
+    if (flag[i]) {
+      nbeg[c] = i;
+      nlevel[c] = level + 1;
+      nparent[c] = p;
+      nfirst[c] = -1;
+      nnchild[c] = 0;
+      nsysid[c] = nsysid[p];
+      const int o = digit_at(keys[i], level);
+      const double h = half[p] * 0.5;
+      centre[3 * c] = centre[3 * p] + (((o >> 2) & 1) ? h : -h);
+      centre[3 * c + 1] = centre[3 * p + 1] + (((o >> 1) & 1) ? h : -h);
+      centre[3 * c + 2] = centre[3 * p + 2] + ((o & 1) ? h : -h);
+      half[c] = h;
+    }
+  }
+}
+
+__global__ void finish_children_kernel(int32_t lo, int32_t hi, int64_t *__restrict__ nbeg, int64_t *__restrict__ nend,
+                                       const int32_t *__restrict__ nparent, int32_t *__restrict__ nfirst,
+                                       int32_t *__restrict__ nnchild) {
+  for (int64_t c = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < hi; c += (int64_t)gridDim.x * blockDim.x) {
+    const int p = nparent[c];
+    nend[c] = (c + 1 < hi && nparent[c + 1] == p) ? nbeg[c + 1] : nend[p];
+    if (c == lo || nparent[c - 1] != p) nfirst[p] = (int32_t)c;
+    atomicAdd(&nnchild[p], 1);
+  }
+}
+
+// ------------------------------------------------------------------ moments (Eq. 2)
+
+__global__ void moments_kernel(int32_t lo, int32_t hi, const int64_t *__restrict__ nbeg,
+                               const int64_t *__restrict__ nend, const int32_t *__restrict__ nfirst,
+                               const int32_t *__restrict__ nnchild, const double *__restrict__ xs,
+                               const double *__restrict__ ms, double *__restrict__ com, double *__restrict__ mass,
+                               double *__restrict__ q, double *__restrict__ side, const double *__restrict__ half,
+                               int64_t *__restrict__ range) {
+  for (int64_t j = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < hi; j += (int64_t)gridDim.x * blockDim.x) {
+    double M = 0.0, c0 = 0.0, c1 = 0.0, c2 = 0.0;
+    double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0, q4 = 0.0, q5 = 0.0;
+    const int nc = nnchild[j];
+    if (nc == 0) {
+      const int64_t b = nbeg[j], e = nend[j];
+      for (int64_t i = b; i < e; i++) {
+        M += ms[i];
+        c0 += ms[i] * xs[3 * i];
+        c1 += ms[i] * xs[3 * i + 1];
+        c2 += ms[i] * xs[3 * i + 2];
+      }
+      if (M > 0) {
+        c0 /= M;
+        c1 /= M;
+        c2 /= M;
+      }
+      for (int64_t i = b; i < e; i++) {
+        const double r0 = xs[3 * i] - c0, r1 = xs[3 * i + 1] - c1, r2c = xs[3 * i + 2] - c2;
+        const double r2 = r0 * r0 + r1 * r1 + r2c * r2c;
+        const double mi = ms[i];
+        q0 += mi * (3 * r0 * r0 - r2);
+        q1 += mi * (3 * r0 * r1);
+        q2 += mi * (3 * r0 * r2c);
+        q3 += mi * (3 * r1 * r1 - r2);
+        q4 += mi * (3 * r1 * r2c);
+        q5 += mi * (3 * r2c * r2c - r2);
+      }
+    } else {
+      const int f = nfirst[j];
+      for (int ch = 0; ch < nc; ch++) {
+        const int cj = f + ch;
+        M += mass[cj];
+        c0 += mass[cj] * com[3 * cj];
+        c1 += mass[cj] * com[3 * cj + 1];
+        c2 += mass[cj] * com[3 * cj + 2];
+      }
+      if (M > 0) {
+        c0 /= M;
+        c1 /= M;
+        c2 /= M;
+      }
+      for (int ch = 0; ch < nc; ch++) {
+        const int cj = f + ch;
+        const double mc = mass[cj];
+        const double r0 = com[3 * cj] - c0, r1 = com[3 * cj + 1] - c1, r2c = com[3 * cj + 2] - c2;
+        const double r2 = r0 * r0 + r1 * r1 + r2c * r2c;
+        const double *qc = q + 6 * cj;
+        q0 += qc[0] + mc * (3 * r0 * r0 - r2);
+        q1 += qc[1] + mc * (3 * r0 * r1);
+        q2 += qc[2] + mc * (3 * r0 * r2c);
+        q3 += qc[3] + mc * (3 * r1 * r1 - r2);
+        q4 += qc[4] + mc * (3 * r1 * r2c);
+        q5 += qc[5] + mc * (3 * r2c * r2c - r2);
+      }
+    }
+    mass[j] = M;
+    com[3 * j] = c0;
+    com[3 * j + 1] = c1;
+    com[3 * j + 2] = c2;
+    q[6 * j] = q0;
+    q[6 * j + 1] = q1;
+    q[6 * j + 2] = q2;
+    q[6 * j + 3] = q3;
+    q[6 * j + 4] = q4;
+    q[6 * j + 5] = q5;
+    side[j] = 2.0 * half[j];
+    range[2 * j] = nbeg[j];
+    range[2 * j + 1] = nend[j];
+  }
+}
+
+// ------------------------------------------------------------------ groups
+
+// group: (count <= n_crit or leaf) and (root or parent count > n_crit)
+__global__ void group_mark_kernel(int32_t nn, int n_crit, const int64_t *__restrict__ nbeg,
+                                  const int64_t *__restrict__ nend, const int32_t *__restrict__ nparent,
+                                  const int32_t *__restrict__ nnchild, int32_t *__restrict__ gflag,
+                                  int32_t *__restrict__ gnode_at) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nn; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cnt = nend[j] - nbeg[j];
+    const int p = nparent[j];
+    const bool mine = cnt <= n_crit || nnchild[j] == 0;
+    const bool reached = p < 0 || nend[p] - nbeg[p] > n_crit;
+    if (mine && reached) {
+      gflag[nbeg[j]] = 1;
+      gnode_at[nbeg[j]] = (int32_t)j;
+    }
+  }
+}
+
+__global__ void group_emit_kernel(int64_t n, const int32_t *__restrict__ gflag, const int64_t *__restrict__ gidx,
+                                  const int32_t *__restrict__ gnode_at, int64_t *__restrict__ group_off,
+                                  int32_t *__restrict__ group_node) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (gflag[i]) {
+      group_off[gidx[i]] = i;
+      group_node[gidx[i]] = gnode_at[i];
+    }
+  }
+}
+
+__global__ void group_last_kernel(int64_t G, int64_t n, int64_t *group_off) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) group_off[G] = n;
+}
+
+// ------------------------------------------------------------------ walk
+
+// One thread per group, depth first, children in order (the host's order).
+// fill == 0: count list entries; fill == 1: write them at the offsets.
+__global__ void walk_kernel(int64_t G, int fill, double theta2, const int64_t *__restrict__ group_off,
+                            const int32_t *__restrict__ group_node, const int32_t *__restrict__ nsysid,
+                            const int32_t *__restrict__ sys_root, const double *__restrict__ xs,
+                            const int64_t *__restrict__ nbeg, const int64_t *__restrict__ nend,
+                            const int32_t *__restrict__ nfirst, const int32_t *__restrict__ nnchild,
+                            const double *__restrict__ centre, const double *__restrict__ side,
+                            const double *__restrict__ com, int32_t *__restrict__ cnt_p, int32_t *__restrict__ cnt_c,
+                            const int64_t *__restrict__ plist_off, const int64_t *__restrict__ clist_off,
+                            int32_t *__restrict__ plist_idx, int32_t *__restrict__ clist_idx, int *err) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  const int64_t gb = group_off[g], ge = group_off[g + 1];
+  double bmin0 = INFINITY, bmin1 = INFINITY, bmin2 = INFINITY;
+  double bmax0 = -INFINITY, bmax1 = -INFINITY, bmax2 = -INFINITY;
+  for (int64_t i = gb; i < ge; i++) {
+    bmin0 = fmin(bmin0, xs[3 * i]);
+    bmin1 = fmin(bmin1, xs[3 * i + 1]);
+    bmin2 = fmin(bmin2, xs[3 * i + 2]);
+    bmax0 = fmax(bmax0, xs[3 * i]);
+    bmax1 = fmax(bmax1, xs[3 * i + 1]);
+    bmax2 = fmax(bmax2, xs[3 * i + 2]);
+  }
+  int32_t stack[kStack];
+  int sp = 0;
+  stack[sp++] = sys_root[nsysid[group_node[g]]];
+  int64_t np = 0, nc = 0;
+  const int64_t po = fill ? plist_off[g] : 0, co = fill ? clist_off[g] : 0;
+  while (sp > 0) {
+    const int32_t k = stack[--sp];
+    bool open = true;
+    if (theta2 > 0.0 && !(nbeg[k] < ge && nend[k] > gb)) {
+      const double h = 0.5 * side[k];
+      const double cc0 = centre[3 * k], cc1 = centre[3 * k + 1], cc2 = centre[3 * k + 2];
+      bool meets = true;
+      if (cc0 + h < bmin0 || cc0 - h > bmax0) meets = false;
+      if (cc1 + h < bmin1 || cc1 - h > bmax1) meets = false;
+      if (cc2 + h < bmin2 || cc2 - h > bmax2) meets = false;
+      if (!meets) {
+        double d2 = 0.0;
+        const double x0 = com[3 * k], x1 = com[3 * k + 1], x2 = com[3 * k + 2];
+        const double e0 = x0 < bmin0 ? bmin0 - x0 : (x0 > bmax0 ? x0 - bmax0 : 0.0);
+        d2 += e0 * e0;
+        const double e1 = x1 < bmin1 ? bmin1 - x1 : (x1 > bmax1 ? x1 - bmax1 : 0.0);
+        d2 += e1 * e1;
+        const double e2 = x2 < bmin2 ? bmin2 - x2 : (x2 > bmax2 ? x2 - bmax2 : 0.0);
+        d2 += e2 * e2;
+        if (side[k] * side[k] < theta2 * d2) open = false;
+      }
+    }
+    if (!open) {
+      if (fill) clist_idx[co + nc] = k;
+      nc++;
+    } else if (nnchild[k] == 0) {
+      const int64_t b = nbeg[k], e = nend[k];
+      if (fill)
+        for (int64_t i = b; i < e; i++) plist_idx[po + np + (i - b)] = (int32_t)i;
+      np += e - b;
+    } else {
+      const int f = nfirst[k], ncld = nnchild[k];
+      if (sp + ncld > kStack) {  // cannot happen for 21 levels; refuse rather than overflow
+        atomicOr(err, 1);
+        break;
+      }
+      for (int c = ncld - 1; c >= 0; c--) stack[sp++] = f + c;
+    }
+  }
+  if (!fill) {
+    cnt_p[g] = (int32_t)min(np, (int64_t)INT32_MAX);
+    cnt_c[g] = (int32_t)min(nc, (int64_t)INT32_MAX);
+  }
+}
+
+__global__ void unsort_kernel(int64_t n, int k, const int64_t *__restrict__ perm, const double *__restrict__ in,
+                              double *__restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = perm[i];
+    for (int c = 0; c < k; c++) out[o * k + c] = in[i * k + c];
+  }
+}
+
+__global__ void roots_kernel(int64_t nsys, const int64_t *__restrict__ sys_off, const double *__restrict__ lo,
+                             const double *__restrict__ width, const int32_t *__restrict__ root_of_sys,
+                             int64_t *nbeg, int64_t *nend, int32_t *nlevel, int32_t *nparent, int32_t *nfirst,
+                             int32_t *nnchild, int32_t *nsysid, double *centre, double *half) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nsys; s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = root_of_sys[s];
+    if (r < 0) continue;
+    nbeg[r] = sys_off[s];
+    nend[r] = sys_off[s + 1];
+    nlevel[r] = 0;
+    nparent[r] = -1;
+    nfirst[r] = -1;
+    nnchild[r] = 0;
+    nsysid[r] = (int32_t)s;
+    centre[3 * r] = lo[3 * s] + 0.5 * width[s];
+    centre[3 * r + 1] = lo[3 * s + 1] + 0.5 * width[s];
+    centre[3 * r + 2] = lo[3 * s + 2] + 0.5 * width[s];
+    half[r] = 0.5 * width[s];
+  }
+}
+
+__global__ void node_of_roots_kernel(int64_t n, const int32_t *__restrict__ psys_sorted,
+                                     const int32_t *__restrict__ root_of_sys, int32_t *__restrict__ node_of) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    node_of[i] = root_of_sys[psys_sorted[i]];
+}
+
+__global__ void sorted_sys_kernel(int64_t n, const int64_t *__restrict__ perm, const int32_t *__restrict__ psys,
+                                  int32_t *__restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = psys[perm[i]];
+}
+
+int grid1(int64_t n) { return blocks_for(n, 256); }
+
+}  // namespace
+
+// ======================================================================= ABI
+
+extern "C" {
+
+qg_status qg_gtree_create(qg_gtree **out, int device) {
+  if (!out) return QG_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return QG_ERR_ARG;
+  qg_gtree *t = new (std::nothrow) qg_gtree;
+  if (!t) return QG_ERR_NOMEM;
+  t->device = device;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != device) cudaSetDevice(device);
+  bool ok = true;
+  for (auto &e : t->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+  if (ok) ok = t->err.reserve(1) == cudaSuccess;
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  if (!ok) {
+    qg_gtree_destroy(t);
+    return QG_ERR_CUDA;
+  }
+  *out = t;
+  return QG_OK;
+}
+
+void qg_gtree_destroy(qg_gtree *t) {
+  if (!t) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != t->device) cudaSetDevice(t->device);
+  for (auto &e : t->ev)
+    if (e) cudaEventDestroy(e);
+  t->perm.release(); t->xs.release(); t->ms.release(); t->psys.release(); t->sys_off.release();
+  t->bmin.release(); t->bmax.release(); t->lo.release(); t->scale.release();
+  t->keys.release(); t->keys2.release(); t->vals.release(); t->vals2.release(); t->hist.release(); t->hoff.release();
+  t->nbeg.release(); t->nend.release(); t->range.release(); t->nlevel.release(); t->nparent.release();
+  t->nfirst.release(); t->nnchild.release(); t->nsysid.release(); t->node_of.release(); t->flag.release();
+  t->excl.release(); t->centre.release(); t->half.release(); t->side.release(); t->com.release();
+  t->mass.release(); t->q.release(); t->sys_root.release(); t->gflag.release(); t->gnode_at.release();
+  t->group_node.release(); t->cnt_p.release(); t->cnt_c.release(); t->gidx.release(); t->group_off.release();
+  t->plist_off.release(); t->clist_off.release(); t->plist_idx.release(); t->clist_idx.release();
+  for (auto &b : t->scan_tmp) b.release();
+  t->err.release();
+  if (prev >= 0 && prev != t->device) cudaSetDevice(prev);
+  delete t;
+}
+
+static qg_status build_impl(qg_gtree *t, int64_t n, const double *x, const double *m, int64_t nsys,
+                            const int64_t *sys_off, int leaf_max, int n_crit, cudaStream_t s) {
+  t->built = t->walked = false;
+  t->n = n;
+  t->nsys = nsys;
+  t->leaf_max = leaf_max;
+  t->n_crit = n_crit;
+  t->h_sys_off.assign(sys_off, sys_off + nsys + 1);
+  GT_CUDA(cudaEventRecord(t->ev[0], s));
+  GT_CUDA(t->sys_off.reserve(nsys + 1));
+  GT_CUDA(cudaMemcpyAsync(t->sys_off.p, sys_off, (nsys + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  GT_CUDA(t->psys.reserve(n));
+  GT_CUDA(t->perm.reserve(n));
+  GT_CUDA(t->xs.reserve(3 * n));
+  GT_CUDA(t->ms.reserve(n));
+  GT_CUDA(t->keys.reserve(n));
+  GT_CUDA(t->vals.reserve(n));
+  GT_CUDA(t->bmin.reserve(3 * nsys));
+  GT_CUDA(t->bmax.reserve(3 * nsys));
+  if (n > 0) {
+    psys_kernel<<<grid1(n), 256, 0, s>>>(n, nsys, t->sys_off.p, t->psys.p);
+    GT_CUDA(cudaGetLastError());
+  }
+  fill_ull_kernel<<<grid1(3 * nsys), 256, 0, s>>>(3 * nsys, t->bmin.p, ~0ull);
+  fill_ull_kernel<<<grid1(3 * nsys), 256, 0, s>>>(3 * nsys, t->bmax.p, 0ull);
+  GT_CUDA(cudaGetLastError());
+  if (n > 0) {
+    bbox_kernel<<<grid1(n), 256, 0, s>>>(n, x, t->psys.p, t->bmin.p, t->bmax.p);
+    GT_CUDA(cudaGetLastError());
+  }
+  // per system cube on the host, the host builder's expressions exactly
+  std::vector<unsigned long long> hmn(3 * nsys), hmx(3 * nsys);
+  if (nsys > 0) {
+    GT_CUDA(cudaMemcpyAsync(hmn.data(), t->bmin.p, 3 * nsys * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaMemcpyAsync(hmx.data(), t->bmax.p, 3 * nsys * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  }
+  GT_CUDA(cudaStreamSynchronize(s));
+  std::vector<double> hlo(3 * nsys), hwidth(nsys), hscale(nsys);
+  std::vector<int32_t> hroot(nsys, -1);
+  int32_t nroots = 0;
+  for (int64_t q = 0; q < nsys; q++) {
+    const int64_t b = sys_off[q], e = sys_off[q + 1];
+    double mn[3], mx[3];
+    for (int d = 0; d < 3; d++) {
+      mn[d] = e > b ? unordered(hmn[3 * q + d]) : INFINITY;
+      mx[d] = e > b ? unordered(hmx[3 * q + d]) : -INFINITY;
+    }
+    double w = 0.0;
+    for (int d = 0; d < 3; d++) w = std::max(w, mx[d] - mn[d]);
+    if (!(w > 0.0)) w = 1.0;
+    w *= 1.0 + 1e-9;
+    for (int d = 0; d < 3; d++) {
+      const double c = 0.5 * (mn[d] + mx[d]);
+      hlo[3 * q + d] = e > b ? c - 0.5 * w : 0.0;
+    }
+    hwidth[q] = w;
+    hscale[q] = (double)(1u << kMaxLevel) / w;
+    if (e > b) hroot[q] = nroots++;
+  }
+  GT_CUDA(t->lo.reserve(3 * nsys));
+  GT_CUDA(t->scale.reserve(2 * nsys));
+  GT_CUDA(t->sys_root.reserve(nsys));
+  GT_CUDA(cudaMemcpyAsync(t->lo.p, hlo.data(), 3 * nsys * sizeof(double), cudaMemcpyHostToDevice, s));
+  GT_CUDA(cudaMemcpyAsync(t->scale.p, hscale.data(), nsys * sizeof(double), cudaMemcpyHostToDevice, s));
+  GT_CUDA(cudaMemcpyAsync(t->scale.p + nsys, hwidth.data(), nsys * sizeof(double), cudaMemcpyHostToDevice, s));
+  GT_CUDA(cudaMemcpyAsync(t->sys_root.p, hroot.data(), nsys * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  if (n > 0) {
+    keys_kernel<<<grid1(n), 256, 0, s>>>(n, x, t->psys.p, t->lo.p, t->scale.p, t->keys.p, t->vals.p);
+    GT_CUDA(cudaGetLastError());
+  }
+  qg_status st = radix_sort(t, n, 64, s);  // Morton keys (bit 63 is always 0)
+  if (st != QG_OK) return st;
+  GT_CUDA(t->flag.reserve(n + 1));
+  if (nsys > 1 && n > 0) {
+    // stable second sort by system: (system, Morton) order, systems contiguous
+    GT_CUDA(t->excl.reserve(n + 1));  // reused as scratch below
+    DBuf<unsigned long long> morton;
+    GT_CUDA(morton.reserve(n));
+    DBuf<int32_t> morton_vals;
+    GT_CUDA(morton_vals.reserve(n));
+    GT_CUDA(cudaMemcpyAsync(morton_vals.p, t->vals.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    syskey_kernel<<<grid1(n), 256, 0, s>>>(n, t->vals.p, t->psys.p, t->keys.p, t->keys.p, t->vals.p, morton.p);
+    GT_CUDA(cudaGetLastError());
+    int bits = 8;
+    while ((1ll << bits) < nsys) bits += 8;
+    st = radix_sort(t, n, bits, s);
+    if (st != QG_OK) {
+      morton.release();
+      morton_vals.release();
+      return st;
+    }
+    gather_sorted_kernel<<<grid1(n), 256, 0, s>>>(n, morton_vals.p, t->vals.p, morton.p, t->keys.p, x, m,
+                                                  t->perm.p, t->xs.p, t->ms.p, 1);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    morton.release();
+    morton_vals.release();
+    if (e != cudaSuccess) return QG_ERR_CUDA;
+  } else if (n > 0) {
+    gather_sorted_kernel<<<grid1(n), 256, 0, s>>>(n, t->vals.p, nullptr, nullptr, nullptr, x, m, t->perm.p,
+                                                  t->xs.p, t->ms.p, 0);
+    GT_CUDA(cudaGetLastError());
+  }
+  // ---- nodes, level by level
+  size_t cap = (size_t)std::max<int64_t>(1024, n / 2 + nroots + 16);
+  auto reserve_nodes = [&](size_t need, size_t keep) -> qg_status {
+    GT_CUDA(t->nbeg.grow(need, keep, s));
+    GT_CUDA(t->nend.grow(need, keep, s));
+    GT_CUDA(t->nlevel.grow(need, keep, s));
+    GT_CUDA(t->nparent.grow(need, keep, s));
+    GT_CUDA(t->nfirst.grow(need, keep, s));
+    GT_CUDA(t->nnchild.grow(need, keep, s));
+    GT_CUDA(t->nsysid.grow(need, keep, s));
+    GT_CUDA(t->centre.grow(3 * need, 3 * keep, s));
+    GT_CUDA(t->half.grow(need, keep, s));
+    return QG_OK;
+  };
+  st = reserve_nodes(cap, 0);
+  if (st != QG_OK) return st;
+  GT_CUDA(t->node_of.reserve(n));
+  GT_CUDA(t->excl.reserve(n + 1));
+  roots_kernel<<<grid1(nsys), 256, 0, s>>>(nsys, t->sys_off.p, t->lo.p, t->scale.p + nsys, t->sys_root.p,
+                                           t->nbeg.p, t->nend.p, t->nlevel.p, t->nparent.p, t->nfirst.p,
+                                           t->nnchild.p, t->nsysid.p, t->centre.p, t->half.p);
+  GT_CUDA(cudaGetLastError());
+  if (n > 0) {
+    // the particles' systems in sorted order, then their root
+    sorted_sys_kernel<<<grid1(n), 256, 0, s>>>(n, t->perm.p, t->psys.p, t->flag.p);
+    node_of_roots_kernel<<<grid1(n), 256, 0, s>>>(n, t->flag.p, t->sys_root.p, t->node_of.p);
+    GT_CUDA(cudaGetLastError());
+  }
+  t->level_begin.assign(1, 0);
+  int64_t lb = 0, le = nroots;
+  for (int level = 0; level < kMaxLevel && n > 0 && le > lb; level++) {
+    t->level_begin.push_back(le);
+    mark_children_kernel<<<grid1(n), 256, 0, s>>>(n, level, leaf_max, t->keys.p, t->node_of.p, t->nbeg.p, t->nend.p,
+                                                  t->flag.p);
+    GT_CUDA(cudaGetLastError());
+    st = scan_excl(t, n, t->flag.p, t->excl.p, s);
+    if (st != QG_OK) return st;
+    int64_t C = 0;
+    GT_CUDA(cudaMemcpyAsync(&C, t->excl.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaStreamSynchronize(s));
+    if (le + C >= INT32_MAX) return QG_ERR_ARG;
+    if ((size_t)(le + C) > t->nbeg.cap) {
+      st = reserve_nodes((size_t)(le + C), (size_t)le);
+      if (st != QG_OK) return st;
+    }
+    emit_children_kernel<<<grid1(n), 256, 0, s>>>(n, level, (int32_t)le, t->keys.p, t->node_of.p, t->flag.p,
+                                                  t->excl.p, t->nend.p, t->nbeg.p, t->nlevel.p, t->nparent.p,
+                                                  t->nfirst.p, t->nnchild.p, t->nsysid.p, t->centre.p, t->half.p,
+                                                  leaf_max);
+    GT_CUDA(cudaGetLastError());
+    if (C == 0) break;
+    finish_children_kernel<<<grid1(C), 256, 0, s>>>((int32_t)le, (int32_t)(le + C), t->nbeg.p, t->nend.p,
+                                                    t->nparent.p, t->nfirst.p, t->nnchild.p);
+    GT_CUDA(cudaGetLastError());
+    lb = le;
+    le += C;
+  }
+  const int64_t nn = le;
+  t->nnodes = nn;
+  if (t->level_begin.back() != nn) t->level_begin.push_back(nn);
+  // ---- moments, deepest level first
+  GT_CUDA(t->com.reserve(3 * nn));
+  GT_CUDA(t->mass.reserve(nn));
+  GT_CUDA(t->q.reserve(6 * nn));
+  GT_CUDA(t->side.reserve(nn));
+  GT_CUDA(t->range.reserve(2 * nn));
+  for (int l = (int)t->level_begin.size() - 2; l >= 0; l--) {
+    const int64_t a = t->level_begin[l], b = t->level_begin[l + 1];
+    if (b > a)
+      moments_kernel<<<grid1(b - a), 256, 0, s>>>((int32_t)a, (int32_t)b, t->nbeg.p, t->nend.p, t->nfirst.p,
+                                                  t->nnchild.p, t->xs.p, t->ms.p, t->com.p, t->mass.p, t->q.p,
+                                                  t->side.p, t->half.p, t->range.p);
+    GT_CUDA(cudaGetLastError());
+  }
+  // ---- groups
+  GT_CUDA(t->gflag.reserve(n + 1));
+  GT_CUDA(t->gnode_at.reserve(n + 1));
+  GT_CUDA(t->gidx.reserve(n + 1));
+  if (n > 0) GT_CUDA(cudaMemsetAsync(t->gflag.p, 0, n * sizeof(int32_t), s));
+  if (nn > 0)
+    group_mark_kernel<<<grid1(nn), 256, 0, s>>>((int32_t)nn, n_crit, t->nbeg.p, t->nend.p, t->nparent.p,
+                                                t->nnchild.p, t->gflag.p, t->gnode_at.p);
+  GT_CUDA(cudaGetLastError());
+  st = scan_excl(t, n, t->gflag.p, t->gidx.p, s);
+  if (st != QG_OK) return st;
+  int64_t G = 0;
+  GT_CUDA(cudaMemcpyAsync(&G, t->gidx.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GT_CUDA(cudaStreamSynchronize(s));
+  t->G = G;
+  GT_CUDA(t->group_off.reserve(G + 1));
+  GT_CUDA(t->group_node.reserve(G + 1));
+  if (n > 0)
+    group_emit_kernel<<<grid1(n), 256, 0, s>>>(n, t->gflag.p, t->gidx.p, t->gnode_at.p, t->group_off.p,
+                                               t->group_node.p);
+  group_last_kernel<<<1, 1, 0, s>>>(G, n, t->group_off.p);
+  GT_CUDA(cudaGetLastError());
+  GT_CUDA(cudaEventRecord(t->ev[1], s));
+  GT_CUDA(cudaStreamSynchronize(s));
+  t->built = true;
+  return QG_OK;
+}
+
+qg_status qg_gtree_build(qg_gtree *t, int64_t n, const double *x, const double *m, int64_t nsys,
+                         const int64_t *sys_off, int leaf_max, int n_crit, void *stream) {
+  if (!t || n < 0 || n >= INT32_MAX || nsys < 1 || !sys_off || leaf_max < 1 || n_crit < 1) return QG_ERR_ARG;
+  if (n > 0 && (!x || !m)) return QG_ERR_ARG;
+  if (sys_off[0] != 0 || sys_off[nsys] != n) return QG_ERR_ARG;
+  for (int64_t q = 0; q < nsys; q++)
+    if (sys_off[q + 1] < sys_off[q]) return QG_ERR_ARG;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != t->device) cudaSetDevice(t->device);
+  const qg_status st = build_impl(t, n, x, m, nsys, sys_off, leaf_max, n_crit, (cudaStream_t)stream);
+  if (prev >= 0 && prev != t->device) cudaSetDevice(prev);
+  return st;
+}
+
+static qg_status walk_impl(qg_gtree *t, double theta, cudaStream_t s) {
+  t->walked = false;
+  const int64_t G = t->G;
+  const double theta2 = theta > 0 ? theta * theta : 0.0;
+  GT_CUDA(cudaEventRecord(t->ev[2], s));
+  GT_CUDA(t->cnt_p.reserve(G + 1));
+  GT_CUDA(t->cnt_c.reserve(G + 1));
+  GT_CUDA(t->plist_off.reserve(G + 1));
+  GT_CUDA(t->clist_off.reserve(G + 1));
+  GT_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(int), s));
+  const int wb = 64;
+  const unsigned wg = (unsigned)std::max<int64_t>(1, (G + wb - 1) / wb);
+  if (G > 0) {
+    walk_kernel<<<wg, wb, 0, s>>>(G, 0, theta2, t->group_off.p, t->group_node.p, t->nsysid.p, t->sys_root.p,
+                                  t->xs.p, t->nbeg.p, t->nend.p, t->nfirst.p, t->nnchild.p, t->centre.p, t->side.p,
+                                  t->com.p, t->cnt_p.p, t->cnt_c.p, nullptr, nullptr, nullptr, nullptr, t->err.p);
+    GT_CUDA(cudaGetLastError());
+  }
+  qg_status st = scan_excl(t, G, t->cnt_p.p, t->plist_off.p, s);
+  if (st != QG_OK) return st;
+  st = scan_excl(t, G, t->cnt_c.p, t->clist_off.p, s);
+  if (st != QG_OK) return st;
+  int64_t tot[2] = {0, 0};
+  int herr = 0;
+  GT_CUDA(cudaMemcpyAsync(&tot[0], t->plist_off.p + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GT_CUDA(cudaMemcpyAsync(&tot[1], t->clist_off.p + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GT_CUDA(cudaMemcpyAsync(&herr, t->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GT_CUDA(cudaStreamSynchronize(s));
+  if (herr) return QG_ERR_STATE;
+  GT_CUDA(t->plist_idx.reserve(tot[0]));
+  GT_CUDA(t->clist_idx.reserve(tot[1]));
+  if (G > 0) {
+    walk_kernel<<<wg, wb, 0, s>>>(G, 1, theta2, t->group_off.p, t->group_node.p, t->nsysid.p, t->sys_root.p,
+                                  t->xs.p, t->nbeg.p, t->nend.p, t->nfirst.p, t->nnchild.p, t->centre.p, t->side.p,
+                                  t->com.p, t->cnt_p.p, t->cnt_c.p, t->plist_off.p, t->clist_off.p, t->plist_idx.p,
+                                  t->clist_idx.p, t->err.p);
+    GT_CUDA(cudaGetLastError());
+  }
+  GT_CUDA(cudaEventRecord(t->ev[3], s));
+  GT_CUDA(cudaMemcpyAsync(&herr, t->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GT_CUDA(cudaStreamSynchronize(s));
+  if (herr) return QG_ERR_STATE;
+  t->np_list = tot[0];
+  t->nc_list = tot[1];
+  t->walked = true;
+  return QG_OK;
+}
+
+qg_status qg_gtree_walk(qg_gtree *t, double theta, void *stream) {
+  if (!t || !std::isfinite(theta)) return QG_ERR_ARG;
+  if (!t->built) return QG_ERR_STATE;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != t->device) cudaSetDevice(t->device);
+  const qg_status st = walk_impl(t, theta, (cudaStream_t)stream);
+  if (prev >= 0 && prev != t->device) cudaSetDevice(prev);
+  return st;
+}
+
+qg_status qg_gtree_sizes(const qg_gtree *t, int64_t *n, int64_t *nnodes, int64_t *ngroups, int64_t *n_plist,
+                         int64_t *n_clist) {
+  if (!t) return QG_ERR_ARG;
+  if (n) *n = t->n;
+  if (nnodes) *nnodes = t->built ? t->nnodes : 0;
+  if (ngroups) *ngroups = t->built ? t->G : 0;
+  if (n_plist) *n_plist = t->walked ? t->np_list : 0;
+  if (n_clist) *n_clist = t->walked ? t->nc_list : 0;
+  return QG_OK;
+}
+
+qg_status qg_gtree_arrays(const qg_gtree *t, const int64_t **perm, const double **xs, const double **ms,
+                          const int64_t **node_range, const int32_t **node_level, const double **cell_com,
+                          const double **cell_m, const double **cell_q, const double **cell_side,
+                          const int64_t **group_off, const int64_t **plist_off, const int32_t **plist_idx,
+                          const int64_t **clist_off, const int32_t **clist_idx) {
+  if (!t || !t->built) return QG_ERR_STATE;
+  if (perm) *perm = t->perm.p;
+  if (xs) *xs = t->xs.p;
+  if (ms) *ms = t->ms.p;
+  if (node_range) *node_range = t->range.p;
+  if (node_level) *node_level = t->nlevel.p;
+  if (cell_com) *cell_com = t->com.p;
+  if (cell_m) *cell_m = t->mass.p;
+  if (cell_q) *cell_q = t->q.p;
+  if (cell_side) *cell_side = t->side.p;
+  if (group_off) *group_off = t->group_off.p;
+  if (plist_off) *plist_off = t->walked ? t->plist_off.p : nullptr;
+  if (plist_idx) *plist_idx = t->walked ? t->plist_idx.p : nullptr;
+  if (clist_off) *clist_off = t->walked ? t->clist_off.p : nullptr;
+  if (clist_idx) *clist_idx = t->walked ? t->clist_idx.p : nullptr;
+  return QG_OK;
+}
+
+qg_status qg_gtree_attach(qg_gtree *t, qg_ctx *ctx, double eps2_all, void *stream) {
+  if (!t || !ctx) return QG_ERR_ARG;
+  if (!t->built || !t->walked) return QG_ERR_STATE;
+  qg_status st = qg_set_sinks_dev(ctx, t->n, t->xs.p, nullptr, eps2_all, t->G, t->group_off.p, stream);
+  if (st != QG_OK) return st;
+  st = qg_set_sources_dev(ctx, t->n, t->xs.p, t->ms.p, t->plist_off.p, t->plist_idx.p, t->np_list, stream);
+  if (st != QG_OK) return st;
+  return qg_set_cells_dev(ctx, t->nnodes, t->com.p, t->mass.p, t->q.p, t->clist_off.p, t->clist_idx.p, t->nc_list,
+                          stream);
+}
+
+qg_status qg_gtree_unsort(const qg_gtree *t, const double *in, double *out, int k, void *stream) {
+  if (!t || !in || !out || k < 1) return QG_ERR_ARG;
+  if (!t->built) return QG_ERR_STATE;
+  if (t->n == 0) return QG_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != t->device) cudaSetDevice(t->device);
+  unsort_kernel<<<grid1(t->n), 256, 0, (cudaStream_t)stream>>>(t->n, k, t->perm.p, in, out);
+  const cudaError_t e = cudaGetLastError();
+  if (prev >= 0 && prev != t->device) cudaSetDevice(prev);
+  return e == cudaSuccess ? QG_OK : QG_ERR_CUDA;
+}
+
+qg_status qg_gtree_timing(const qg_gtree *t, float *build_ms, float *walk_ms) {
+  if (!t) return QG_ERR_ARG;
+  if (build_ms) {
+    if (!t->built || cudaEventElapsedTime(build_ms, t->ev[0], t->ev[1]) != cudaSuccess) return QG_ERR_STATE;
+  }
+  if (walk_ms) {
+    if (!t->walked || cudaEventElapsedTime(walk_ms, t->ev[2], t->ev[3]) != cudaSuccess) return QG_ERR_STATE;
+  }
+  return QG_OK;
+}
+
+}  // extern "C"

@@ -26,6 +26,16 @@ def test_cuda_library_exports_every_declared_symbol():
     assert set(names) == set(qgrav.SIGNATURES), set(names) ^ set(qgrav.SIGNATURES)
 
 
+def test_gpu_tree_symbols_are_exported_and_bound():
+    from paper_1812_07313_gb300 import gtree
+    L = qgrav.lib()
+    names = _declared("qg_gtree.h")
+    assert "qg_gtree_build" in names and "qg_gtree_walk" in names
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(gtree.SIGNATURES)
+
+
 def test_tree_library_exports_every_declared_symbol():
     L = ctypes.CDLL(_native.build_tree())
     for n in _declared("qg_tree.h"):

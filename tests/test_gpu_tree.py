@@ -1,0 +1,127 @@
+"""GPU tree build, moments, groups and walk (include/qg_gtree.h) against the
+host builder: the same sorted order, nodes, moments (bit for bit: both sides
+evaluate the same FP64 expressions without contraction), groups and lists;
+and a force step built entirely on the GPU against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_07313_gb300 import gtree, qgrav, workloads
+from paper_1812_07313_gb300 import tree as qtree
+from tests.parity_util import assert_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    qgrav.lib()
+
+
+def _sets():
+    yield "sphere_4k", workloads.small_set("sphere", 4096, 1, 1e-2), 8, 64, 0.5
+    yield "plummer_20k", workloads.small_set("plummer", 20000, 5, 1e-2), 8, 32, 0.6
+    yield "cube_30k", workloads.small_set("cube", 30000, 6, 1e-3), 8, 256, 0.5
+    yield "batched_6", workloads.batched_systems(nsys=6, seed=9, n_lo=300, n_hi=5000), 8, 64, 0.5
+    x = np.concatenate([np.zeros((40, 3)), np.random.default_rng(2).random((200, 3))])
+    yield "coincident", workloads.single_system("coincident", x, 1e-3), 8, 16, 0.5
+    yield "one", workloads.single_system("one", np.array([[0.5, 0.25, 0.125]]), 1e-2), 8, 64, 0.5
+
+
+CASES = list(_sets())
+
+
+def _gpu_tree(ps, leaf, ncrit, theta):
+    import torch
+    t = gtree.GpuTree(0)
+    t.build(torch.as_tensor(ps.x).cuda(), torch.as_tensor(ps.m).cuda(), ps.sys_off, leaf, ncrit)
+    t.walk(theta)
+    return t
+
+
+def _node_keys(rng, side):
+    return [(int(b), int(e), float(s)) for (b, e), s in zip(rng, side)]
+
+
+@pytest.mark.parametrize("name,ps,leaf,ncrit,theta", CASES, ids=[c[0] for c in CASES])
+def test_gpu_tree_equals_host_builder(name, ps, leaf, ncrit, theta):
+    h = qtree.Tree(ps.x, ps.m, ps.sys_off, leaf, ncrit)
+    L = h.walk(theta)
+    t = _gpu_tree(ps, leaf, ncrit, theta)
+    sz = t.sizes()
+    assert sz["n"] == h.n and sz["nnodes"] == h.nnodes and sz["ngroups"] == h.ngroups
+    assert np.array_equal(t.host("perm"), h.perm)
+    assert np.array_equal(t.host("xs"), h.x)
+    assert np.array_equal(t.host("group_off"), h.group_off)
+    # nodes: the same set, keyed by (sorted particle range, side length)
+    gk = _node_keys(t.host("node_range"), t.host("cell_side"))
+    hk = _node_keys(h.cell_range, h.cell_side)
+    assert len(set(gk)) == len(gk) and set(gk) == set(hk)
+    g_of = {k: i for i, k in enumerate(gk)}
+    h2g = np.array([g_of[k] for k in hk], dtype=np.int64)
+    assert np.array_equal(t.host("cell_m")[h2g], h.cell_m)
+    assert np.array_equal(t.host("cell_com")[h2g], h.cell_com)
+    assert np.array_equal(t.host("cell_q")[h2g], h.cell_q)
+    # lists: identical, cell entries mapped to the GPU numbering
+    assert np.array_equal(t.host("plist_off"), L.plist_off)
+    assert np.array_equal(t.host("plist_idx"), L.plist_idx)
+    assert np.array_equal(t.host("clist_off"), L.clist_off)
+    assert np.array_equal(t.host("clist_idx"), h2g[L.clist_idx])
+    build_ms, walk_ms = t.timing()
+    assert build_ms > 0 and walk_ms > 0
+    t.close()
+
+
+def test_gpu_built_step_matches_oracle_and_host_lists_exactly():
+    import torch
+    ps = workloads.small_set("plummer", 30000, 11, 1e-2)
+    eps2 = 1e-4
+    t = _gpu_tree(ps, 8, 64, 0.5)
+    ctx = qgrav.Context(0)
+    t.attach(ctx, eps2)
+    ctx.qg_run()
+    a, phi = ctx.qg_get_forces()
+    # the same step from the host builder's lists
+    h = qtree.Tree(ps.x, ps.m, ps.sys_off, 8, 64)
+    L = h.walk(0.5)
+    ctx2 = qgrav.Context(0)
+    ctx2.qg_set_sinks(h.x, h.group_off, eps2)
+    ctx2.qg_set_sources(h.x, h.m, L.plist_off, L.plist_idx)
+    ctx2.qg_set_cells(h.cell_com, h.cell_m, h.cell_q, L.clist_off, L.clist_idx)
+    ctx2.qg_run()
+    a2, phi2 = ctx2.qg_get_forces()
+    assert np.array_equal(a, a2) and np.array_equal(phi, phi2)
+    a_ref, phi_ref = oracle.expansion_forces(h.group_off, h.x, h.x, h.m, L.plist_off, L.plist_idx, h.cell_com,
+                                             h.cell_m, h.cell_q, L.clist_off, L.clist_idx, eps2_all=eps2)
+    assert_parity(a, phi, a_ref, phi_ref, label="gpu-built step")
+    # back to input order
+    ad = torch.empty((ps.n, 3), dtype=torch.float64, device="cuda")
+    pd = torch.empty(ps.n, dtype=torch.float64, device="cuda")
+    ctx.qg_get_forces_dev(ad, pd)
+    a_in = torch.empty_like(ad)
+    t.unsort(ad, a_in, 3)
+    torch.cuda.synchronize()
+    expect = np.empty_like(a)
+    expect[h.perm] = a
+    assert np.array_equal(a_in.cpu().numpy(), expect)
+    ctx.close()
+    ctx2.close()
+    t.close()
+
+
+def test_gpu_tree_rejects_bad_arguments():
+    import torch
+    t = gtree.GpuTree(0)
+    x = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
+    m = torch.ones(4, dtype=torch.float64, device="cuda")
+    with pytest.raises(qgrav.QGError):
+        t.build(x, m, np.array([0, 3]), 8, 64)  # offsets do not cover n
+    with pytest.raises(qgrav.QGError):
+        t.walk(0.5)  # nothing built
+    t.build(x, m, None, 8, 64)
+    t.walk(0.5)
+    assert t.sizes()["ngroups"] == 1
+    t.close()
