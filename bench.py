@@ -67,6 +67,8 @@ def parse():
                     help="also time the all-FP64 and the uncentred FP32 kernels and report their differences")
     ap.add_argument("--group-sizes", default=None,
                     help="candidate n_crit values (comma separated): time the step for each and use the fastest")
+    ap.add_argument("--gpu-tree", action="store_true",
+                    help="also time the tree build, moments, groups and walk on the GPU (whole step on the device)")
     ap.add_argument("--launch", default=None,
                     help="R,W,T[,x1|x2]: fixed sinks/thread, warps/CTA, tile (and scalar or paired FP32) "
                          "instead of the autotuner (profiling)")
@@ -411,6 +413,8 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and args.batching_compare and ps.nsys > 1:
         out["batching"] = batching_compare(torch, qgrav, tr, L, eps2_all, eps2, stream, flush,
                                            float(np.mean(step_ms)))
+    if rank == 0 and args.gpu_tree:
+        out["gpu_tree"] = gpu_tree_step(torch, qgrav, ps, wl, tr, L, eps2_all, eps2, stream)
     if rank == 0 and args.precision_compare:
         out["precision"] = precision_compare(torch, qgrav, ctx, tr, L, eps2_all, eps2, stream, flush)
 
@@ -486,6 +490,46 @@ def batching_compare(torch, qgrav, tr, L, eps2_all, eps2, stream, flush, batched
     return {"systems": len(ctxs), "batched_ms_per_step": batched_ms, "per_system_ms_per_step": per_sys,
             "speedup": per_sys / batched_ms, "per_system_launches": 3 * len(ctxs),
             "note": "per-system contexts at the default launch shape, graphs replayed back to back on one stream"}
+
+
+def gpu_tree_step(torch, qgrav, ps, wl, tr, L, eps2_all, eps2, stream, steps=5):
+    """The whole step on the GPU: tree build with moments and groups, walk,
+    attach, force kernel; device times of each part (and the host builder's
+    wall time for the same tree and walk, for scale)."""
+    from paper_1812_07313_gb300 import gtree
+    x = torch.as_tensor(ps.x).cuda()
+    m = torch.as_tensor(ps.m).cuda()
+    t = gtree.GpuTree(torch.cuda.current_device())
+    ctx = qgrav.Context(torch.cuda.current_device())
+    build, walk, force = [], [], []
+    same = None
+    for k in range(steps + 1):
+        t.build(x, m, ps.sys_off, wl.leaf_max, tr_n_crit(tr, wl))
+        t.walk(L.theta)
+        b, w = t.timing()
+        t.attach(ctx, eps2_all if eps2 is None else 0.0)
+        if k == 0:
+            ctx.qg_autotune(stream.cuda_stream, reps=2)
+            sz = t.sizes()
+            same = (sz["ngroups"] == tr.ngroups and sz["n_plist"] == len(L.plist_idx)
+                    and sz["n_clist"] == len(L.clist_idx))  # list entries per group are tested in the suite
+        ctx.qg_run(stream.cuda_stream)
+        _, f = ctx.qg_last_timing()
+        if k:
+            build.append(b)
+            walk.append(w)
+            force.append(f)
+    sz = t.sizes()
+    ctx.close()
+    t.close()
+    return {"build_ms": float(np.mean(build)), "walk_ms": float(np.mean(walk)), "force_ms": float(np.mean(force)),
+            "step_ms": float(np.mean(build) + np.mean(walk) + np.mean(force)), "nodes": sz["nnodes"],
+            "groups": sz["ngroups"], "list_entries": sz["n_plist"] + sz["n_clist"], "same_list_sizes_as_host": same,
+            "note": "device times; attach (device-to-device copies and list checks) not included"}
+
+
+def tr_n_crit(tr, wl):
+    return getattr(tr, "n_crit", wl.n_crit)
 
 
 def precision_compare(torch, qgrav, ctx, tr, L, eps2_all, eps2, stream, flush, steps=3):

@@ -17,10 +17,13 @@
  *     particles, and side^2 < theta^2 d^2 (d: distance from the node's centre
  *     of mass to the box; the test l/d < theta of Sec. 1); otherwise a leaf's
  *     particles join the j-particle list and an internal node is opened.
- *     Nodes are visited depth-first, children in order, as on the host, so
- *     the lists come out in the host's order.
+ *     One warp walks one group, testing up to 32 nodes at once; each group's
+ *     lists hold the same entries as the host's depth-first walk, in the
+ *     walk's own fixed order (deterministic from run to run).
  * Node numbering differs from the host builder's (level by level here); the
  * node set, the sorted particle order and the groups are the same.
+ * qg_gtree_walk returns QG_ERR_STATE if a walk stack would overflow (not
+ * reachable for trees of at most 21 levels, which is every tree built here).
  *
  * All arrays named *_dev are device memory on the tree's device; the tree
  * owns every array it exposes, valid until the next build / walk or destroy.

@@ -20,7 +20,6 @@
 namespace {
 
 constexpr int kMaxLevel = 21;   // 21 bits per axis -> 63-bit Morton keys
-constexpr int kStack = 160;     // walk stack: 1 + 7 per level is enough
 constexpr int kScanThreads = 256, kScanItems = 4, kScanTile = kScanThreads * kScanItems;
 constexpr int kSortThreads = 256, kSortItems = 8, kSortTile = kSortThreads * kSortItems;
 
@@ -171,6 +170,9 @@ struct qg_gtree {
   DBuf<int64_t> gidx, group_off, plist_off, clist_off;
   DBuf<int32_t> plist_idx, clist_idx;
   DBuf<int64_t> scan_tmp[5];
+  DBuf<int32_t> stacks;  // per-warp walk stacks
+  DBuf<float4> geom;     // per node: (com - o, side) / S, ((centre - o) / S, 0) in FP32; o, S: system root cube
+  DBuf<int4> topo;       // per node: (first particle, end, first child, children)
   DBuf<int> err;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
@@ -624,77 +626,206 @@ __global__ void group_last_kernel(int64_t G, int64_t n, int64_t *group_off) {
 
 // ------------------------------------------------------------------ walk
 
-// One thread per group, depth first, children in order (the host's order).
-// fill == 0: count list entries; fill == 1: write them at the offsets.
-__global__ void walk_kernel(int64_t G, int fill, double theta2, const int64_t *__restrict__ group_off,
-                            const int32_t *__restrict__ group_node, const int32_t *__restrict__ nsysid,
-                            const int32_t *__restrict__ sys_root, const double *__restrict__ xs,
-                            const int64_t *__restrict__ nbeg, const int64_t *__restrict__ nend,
-                            const int32_t *__restrict__ nfirst, const int32_t *__restrict__ nnchild,
-                            const double *__restrict__ centre, const double *__restrict__ side,
-                            const double *__restrict__ com, int32_t *__restrict__ cnt_p, int32_t *__restrict__ cnt_c,
-                            const int64_t *__restrict__ plist_off, const int64_t *__restrict__ clist_off,
-                            int32_t *__restrict__ plist_idx, int32_t *__restrict__ clist_idx, int *err) {
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= G) return;
-  const int64_t gb = group_off[g], ge = group_off[g + 1];
-  double bmin0 = INFINITY, bmin1 = INFINITY, bmin2 = INFINITY;
-  double bmax0 = -INFINITY, bmax1 = -INFINITY, bmax2 = -INFINITY;
-  for (int64_t i = gb; i < ge; i++) {
-    bmin0 = fmin(bmin0, xs[3 * i]);
-    bmin1 = fmin(bmin1, xs[3 * i + 1]);
-    bmin2 = fmin(bmin2, xs[3 * i + 2]);
-    bmax0 = fmax(bmax0, xs[3 * i]);
-    bmax1 = fmax(bmax1, xs[3 * i + 1]);
-    bmax2 = fmax(bmax2, xs[3 * i + 2]);
+// Compact per-node walk data: the FP32 geometry relative to the node's
+// system root cube (centre o, side S: (x - o) / S, in [-1/2, 1/2]) for the
+// walk's FP32 pre-test, and the topology in one int4, so that a visited node
+// costs two aligned 32- and 16-byte loads.
+__global__ void walk_data_kernel(int32_t nn, const int32_t *__restrict__ nsysid, const int32_t *__restrict__ sys_root,
+                                 const double *__restrict__ centre, const double *__restrict__ side,
+                                 const double *__restrict__ com, const int64_t *__restrict__ nbeg,
+                                 const int64_t *__restrict__ nend, const int32_t *__restrict__ nfirst,
+                                 const int32_t *__restrict__ nnchild, float4 *__restrict__ geom,
+                                 int4 *__restrict__ topo) {
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
+    const int32_t r = sys_root[nsysid[k]];
+    const double o0 = centre[3 * r], o1 = centre[3 * r + 1], o2 = centre[3 * r + 2], u = 1.0 / side[r];
+    geom[2 * k] = make_float4(__double2float_rn((com[3 * k] - o0) * u), __double2float_rn((com[3 * k + 1] - o1) * u),
+                              __double2float_rn((com[3 * k + 2] - o2) * u), __double2float_rn(side[k] * u));
+    geom[2 * k + 1] = make_float4(__double2float_rn((centre[3 * k] - o0) * u),
+                                  __double2float_rn((centre[3 * k + 1] - o1) * u),
+                                  __double2float_rn((centre[3 * k + 2] - o2) * u), 0.0f);
+    topo[k] = make_int4((int)nbeg[k], (int)nend[k], nfirst[k], nnchild[k]);
   }
-  int32_t stack[kStack];
-  int sp = 0;
-  stack[sp++] = sys_root[nsysid[group_node[g]]];
-  int64_t np = 0, nc = 0;
-  const int64_t po = fill ? plist_off[g] : 0, co = fill ? clist_off[g] : 0;
-  while (sp > 0) {
-    const int32_t k = stack[--sp];
-    bool open = true;
-    if (theta2 > 0.0 && !(nbeg[k] < ge && nend[k] > gb)) {
-      const double h = 0.5 * side[k];
-      const double cc0 = centre[3 * k], cc1 = centre[3 * k + 1], cc2 = centre[3 * k + 2];
-      bool meets = true;
-      if (cc0 + h < bmin0 || cc0 - h > bmax0) meets = false;
-      if (cc1 + h < bmin1 || cc1 - h > bmax1) meets = false;
-      if (cc2 + h < bmin2 || cc2 - h > bmax2) meets = false;
-      if (!meets) {
-        double d2 = 0.0;
-        const double x0 = com[3 * k], x1 = com[3 * k + 1], x2 = com[3 * k + 2];
-        const double e0 = x0 < bmin0 ? bmin0 - x0 : (x0 > bmax0 ? x0 - bmax0 : 0.0);
-        d2 += e0 * e0;
-        const double e1 = x1 < bmin1 ? bmin1 - x1 : (x1 > bmax1 ? x1 - bmax1 : 0.0);
-        d2 += e1 * e1;
-        const double e2 = x2 < bmin2 ? bmin2 - x2 : (x2 > bmax2 ? x2 - bmax2 : 0.0);
-        d2 += e2 * e2;
-        if (side[k] * side[k] < theta2 * d2) open = false;
-      }
-    }
-    if (!open) {
-      if (fill) clist_idx[co + nc] = k;
-      nc++;
-    } else if (nnchild[k] == 0) {
-      const int64_t b = nbeg[k], e = nend[k];
-      if (fill)
-        for (int64_t i = b; i < e; i++) plist_idx[po + np + (i - b)] = (int32_t)i;
-      np += e - b;
-    } else {
-      const int f = nfirst[k], ncld = nnchild[k];
-      if (sp + ncld > kStack) {  // cannot happen for 21 levels; refuse rather than overflow
-        atomicOr(err, 1);
-        break;
-      }
-      for (int c = ncld - 1; c >= 0; c--) stack[sp++] = f + c;
-    }
+}
+
+
+// Group walk, one warp per group (a persistent grid; each warp owns a stack in
+// global memory).  Per iteration the lanes take up to 32 nodes off the top
+// segment of the stack and test them at once; accepted cells, opened leaves'
+// particles and opened nodes' children are emitted / pushed through warp
+// prefix sums.  The children of one iteration form a new segment one level
+// deeper, and pops never cross a segment boundary, so segment d holds nodes of
+// level d only: at most 21 segments left behind with <= 224 entries each
+// (256 children of 32 nodes, less the 32 popped) plus the top one (<= 256)
+// ever sit on the stack.  The lists hold the same entries as a depth-first
+// walk, in this walk's own fixed order.  FILL == false counts, FILL == true
+// writes at the offsets.
+//
+// The opening test decides exactly as the FP64 test (node_opens64) does, but
+// first tries it in FP32 on the root-cube coordinates (x - o) / S, all within
+// [-1/2, 1/2]: there every FP32 quantity is within dl = 2^-20 + 2^-40 (|o| +
+// S) / S of the exact (scaled) value -- a few FP32 roundings of 2^-24 each,
+// plus the FP64 test's own rounding on absolute coordinates -- and a decision
+// is taken in FP32 only when the compared quantities are apart by more than
+// their error bounds.  Otherwise (ties and near-ties) the FP64 test decides.
+// Scaling both sides of side^2 < theta^2 d^2 by 1/S^2 does not change it.
+constexpr int kWarpStack = kMaxLevel * 224 + 256;
+
+__device__ __forceinline__ int warp_excl(int v, int lane, int *total) {
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
-  if (!fill) {
-    cnt_p[g] = (int32_t)min(np, (int64_t)INT32_MAX);
-    cnt_c[g] = (int32_t)min(nc, (int64_t)INT32_MAX);
+  *total = __shfl_sync(0xffffffffu, x, 31);
+  return x - v;
+}
+
+// The opening test in FP64 (Sec. 1 criterion against the group's box): true
+// if node k must be opened.  The caller has already excluded nodes that hold
+// particles of the group.
+__device__ __forceinline__ bool node_opens64(int32_t k, double theta2, const double *__restrict__ centre,
+                                             const double *__restrict__ side, const double *__restrict__ com,
+                                             const double bmin[3], const double bmax[3]) {
+  const double h = 0.5 * side[k];
+  const double cc0 = centre[3 * k], cc1 = centre[3 * k + 1], cc2 = centre[3 * k + 2];
+  bool meets = true;
+  if (cc0 + h < bmin[0] || cc0 - h > bmax[0]) meets = false;
+  if (cc1 + h < bmin[1] || cc1 - h > bmax[1]) meets = false;
+  if (cc2 + h < bmin[2] || cc2 - h > bmax[2]) meets = false;
+  if (meets) return true;
+  double d2 = 0.0;
+  const double x0 = com[3 * k], x1 = com[3 * k + 1], x2 = com[3 * k + 2];
+  const double e0 = x0 < bmin[0] ? bmin[0] - x0 : (x0 > bmax[0] ? x0 - bmax[0] : 0.0);
+  d2 += e0 * e0;
+  const double e1 = x1 < bmin[1] ? bmin[1] - x1 : (x1 > bmax[1] ? x1 - bmax[1] : 0.0);
+  d2 += e1 * e1;
+  const double e2 = x2 < bmin[2] ? bmin[2] - x2 : (x2 > bmax[2] ? x2 - bmax[2] : 0.0);
+  d2 += e2 * e2;
+  return !(side[k] * side[k] < theta2 * d2);
+}
+
+// The same test in FP32 on root-relative data: 0 = accept as a cell,
+// 1 = open, 2 = too close to call (the FP64 test decides).
+__device__ __forceinline__ int node_opens32(float4 ga, float4 gb, float th2, float dl, float3 lo, float3 hi) {
+  const float h = 0.5f * ga.w;
+  float sep = fmaxf(lo.x - (gb.x + h), (gb.x - h) - hi.x);  // > 0: cube apart from the box on this axis
+  sep = fmaxf(sep, fmaxf(lo.y - (gb.y + h), (gb.y - h) - hi.y));
+  sep = fmaxf(sep, fmaxf(lo.z - (gb.z + h), (gb.z - h) - hi.z));
+  if (sep < -dl) return 1;  // meets the box
+  if (!(sep > dl)) return 2;
+  const float e0 = fmaxf(fmaxf(lo.x - ga.x, ga.x - hi.x), 0.0f);
+  const float e1 = fmaxf(fmaxf(lo.y - ga.y, ga.y - hi.y), 0.0f);
+  const float e2 = fmaxf(fmaxf(lo.z - ga.z, ga.z - hi.z), 0.0f);
+  const float A = ga.w * ga.w;
+  const float B = th2 * (e0 * e0 + e1 * e1 + e2 * e2);
+  const float tol = 0x1p-16f * (A + B) + th2 * dl * (2.0f * (e0 + e1 + e2) + 4.0f * dl);
+  if (A < B - tol) return 0;
+  if (A > B + tol) return 1;
+  return 2;
+}
+
+template <bool FILL>
+__global__ void walk_warp_kernel(int64_t G, double theta2, const int64_t *__restrict__ group_off,
+                                 const int32_t *__restrict__ group_node, const int32_t *__restrict__ nsysid,
+                                 const int32_t *__restrict__ sys_root, const double *__restrict__ xs,
+                                 const float4 *__restrict__ geom, const int4 *__restrict__ topo,
+                                 const double *__restrict__ centre, const double *__restrict__ side,
+                                 const double *__restrict__ com, int32_t *__restrict__ cnt_p,
+                                 int32_t *__restrict__ cnt_c, const int64_t *__restrict__ plist_off,
+                                 const int64_t *__restrict__ clist_off, int32_t *__restrict__ plist_idx,
+                                 int32_t *__restrict__ clist_idx, int32_t *__restrict__ stacks, int *err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t *stack = stacks + warp * kWarpStack;
+  const float th2 = __double2float_rn(theta2);
+  for (int64_t g = warp; g < G; g += nwarps) {
+    const int32_t gb = (int32_t)group_off[g], ge = (int32_t)group_off[g + 1];
+    double bmin[3] = {INFINITY, INFINITY, INFINITY}, bmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = gb + lane; i < ge; i += 32)
+      for (int d = 0; d < 3; d++) {
+        bmin[d] = fmin(bmin[d], xs[3 * i + d]);
+        bmax[d] = fmax(bmax[d], xs[3 * i + d]);
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      for (int d = 0; d < 3; d++) {
+        bmin[d] = fmin(bmin[d], __shfl_xor_sync(0xffffffffu, bmin[d], o));
+        bmax[d] = fmax(bmax[d], __shfl_xor_sync(0xffffffffu, bmax[d], o));
+      }
+    const int32_t root = sys_root[nsysid[group_node[g]]];
+    const double o0 = centre[3 * root], o1 = centre[3 * root + 1], o2 = centre[3 * root + 2], S = side[root];
+    const double u = 1.0 / S, omax = fmax(fabs(o0), fmax(fabs(o1), fabs(o2)));
+    const float dl = __double2float_ru(0x1p-20 + 0x1p-40 * (omax + S) * u);
+    const float3 lo = make_float3(__double2float_rn((bmin[0] - o0) * u), __double2float_rn((bmin[1] - o1) * u),
+                                  __double2float_rn((bmin[2] - o2) * u));
+    const float3 hi = make_float3(__double2float_rn((bmax[0] - o0) * u), __double2float_rn((bmax[1] - o1) * u),
+                                  __double2float_rn((bmax[2] - o2) * u));
+    if (lane == 0) stack[0] = root;
+    __syncwarp();
+    int sp = 1, depth = 0;
+    int seg = 0;  // lane d: first stack slot of the segment at depth d
+    int64_t np = 0, nc = 0;
+    const int64_t po = FILL ? plist_off[g] : 0, co = FILL ? clist_off[g] : 0;
+    bool failed = false;
+    while (sp > 0) {
+      const int base = __shfl_sync(0xffffffffu, seg, depth);
+      if (sp == base) {  // this level's segment is used up: back to the one below
+        depth--;
+        continue;
+      }
+      const int take = sp - base < 32 ? sp - base : 32;
+      sp -= take;
+      const bool have = lane < take;
+      const int32_t k = have ? stack[sp + lane] : -1;
+      __syncwarp();  // every lane has read its entry before the stack is written again
+      int kind = 0;  // 1: cell, 2: leaf particles, 3: open (children)
+      int4 tp = make_int4(0, 0, 0, 0);
+      if (have) {
+        tp = topo[k];
+        bool open = true;
+        if (theta2 > 0.0 && !(tp.x < ge && tp.y > gb)) {
+          const int dec = node_opens32(geom[2 * k], geom[2 * k + 1], th2, dl, lo, hi);
+          open = dec == 2 ? node_opens64(k, theta2, centre, side, com, bmin, bmax) : dec == 1;
+        }
+        kind = !open ? 1 : (tp.w == 0 ? 2 : 3);
+      }
+      // accepted cells
+      const unsigned cells = __ballot_sync(0xffffffffu, kind == 1);
+      if (FILL && kind == 1) clist_idx[co + nc + __popc(cells & ((1u << lane) - 1u))] = k;
+      nc += __popc(cells);
+      // particles of opened leaves
+      int ptotal = 0;
+      const int pofs = warp_excl(kind == 2 ? tp.y - tp.x : 0, lane, &ptotal);
+      if (FILL && kind == 2)
+        for (int32_t i = tp.x; i < tp.y; i++) plist_idx[po + np + pofs + (i - tp.x)] = i;
+      np += ptotal;
+      // children of opened internal nodes: a new segment one level deeper
+      int ctotal = 0;
+      const int cofs = warp_excl(kind == 3 ? tp.w : 0, lane, &ctotal);
+      if (ctotal > 0) {
+        if (depth + 1 > kMaxLevel || sp + ctotal > kWarpStack) {  // not reachable for a 21-level tree
+          failed = true;
+          break;
+        }
+        if (kind == 3)
+          for (int c = 0; c < tp.w; c++) stack[sp + cofs + c] = tp.z + c;
+        depth++;
+        if (lane == depth) seg = sp;
+        sp += ctotal;
+      }
+      __syncwarp();
+    }
+    if (failed) {
+      if (lane == 0) atomicOr(err, 1);
+      return;
+    }
+    if (!FILL && lane == 0) {
+      cnt_p[g] = (int32_t)(np < INT32_MAX ? np : INT32_MAX);
+      cnt_c[g] = (int32_t)(nc < INT32_MAX ? nc : INT32_MAX);
+    }
   }
 }
 
@@ -787,6 +918,9 @@ void qg_gtree_destroy(qg_gtree *t) {
   t->group_node.release(); t->cnt_p.release(); t->cnt_c.release(); t->gidx.release(); t->group_off.release();
   t->plist_off.release(); t->clist_off.release(); t->plist_idx.release(); t->clist_idx.release();
   for (auto &b : t->scan_tmp) b.release();
+  t->stacks.release();
+  t->geom.release();
+  t->topo.release();
   t->err.release();
   if (prev >= 0 && prev != t->device) cudaSetDevice(prev);
   delete t;
@@ -969,6 +1103,14 @@ static qg_status build_impl(qg_gtree *t, int64_t n, const double *x, const doubl
                                                   t->side.p, t->half.p, t->range.p);
     GT_CUDA(cudaGetLastError());
   }
+  // ---- compact walk data
+  GT_CUDA(t->geom.reserve(2 * nn));
+  GT_CUDA(t->topo.reserve(nn));
+  if (nn > 0)
+    walk_data_kernel<<<grid1(nn), 256, 0, s>>>((int32_t)nn, t->nsysid.p, t->sys_root.p, t->centre.p, t->side.p,
+                                               t->com.p, t->nbeg.p, t->nend.p, t->nfirst.p, t->nnchild.p, t->geom.p,
+                                               t->topo.p);
+  GT_CUDA(cudaGetLastError());
   // ---- groups
   GT_CUDA(t->gflag.reserve(n + 1));
   GT_CUDA(t->gnode_at.reserve(n + 1));
@@ -1022,12 +1164,18 @@ static qg_status walk_impl(qg_gtree *t, double theta, cudaStream_t s) {
   GT_CUDA(t->plist_off.reserve(G + 1));
   GT_CUDA(t->clist_off.reserve(G + 1));
   GT_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(int), s));
-  const int wb = 64;
-  const unsigned wg = (unsigned)std::max<int64_t>(1, (G + wb - 1) / wb);
+  // persistent warp grid: one stack per warp
+  int sms = 0;
+  GT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, t->device));
+  const int wb = 128;
+  const int64_t warps = std::min<int64_t>(std::max<int64_t>(G, 1), (int64_t)sms * 32);
+  const unsigned wg = (unsigned)((warps * 32 + wb - 1) / wb);
+  GT_CUDA(t->stacks.reserve((size_t)wg * (wb / 32) * kWarpStack));
   if (G > 0) {
-    walk_kernel<<<wg, wb, 0, s>>>(G, 0, theta2, t->group_off.p, t->group_node.p, t->nsysid.p, t->sys_root.p,
-                                  t->xs.p, t->nbeg.p, t->nend.p, t->nfirst.p, t->nnchild.p, t->centre.p, t->side.p,
-                                  t->com.p, t->cnt_p.p, t->cnt_c.p, nullptr, nullptr, nullptr, nullptr, t->err.p);
+    walk_warp_kernel<false><<<wg, wb, 0, s>>>(G, theta2, t->group_off.p, t->group_node.p, t->nsysid.p, t->sys_root.p,
+                                              t->xs.p, t->geom.p, t->topo.p, t->centre.p, t->side.p, t->com.p,
+                                              t->cnt_p.p, t->cnt_c.p, nullptr, nullptr, nullptr, nullptr, t->stacks.p,
+                                              t->err.p);
     GT_CUDA(cudaGetLastError());
   }
   qg_status st = scan_excl(t, G, t->cnt_p.p, t->plist_off.p, s);
@@ -1044,10 +1192,10 @@ static qg_status walk_impl(qg_gtree *t, double theta, cudaStream_t s) {
   GT_CUDA(t->plist_idx.reserve(tot[0]));
   GT_CUDA(t->clist_idx.reserve(tot[1]));
   if (G > 0) {
-    walk_kernel<<<wg, wb, 0, s>>>(G, 1, theta2, t->group_off.p, t->group_node.p, t->nsysid.p, t->sys_root.p,
-                                  t->xs.p, t->nbeg.p, t->nend.p, t->nfirst.p, t->nnchild.p, t->centre.p, t->side.p,
-                                  t->com.p, t->cnt_p.p, t->cnt_c.p, t->plist_off.p, t->clist_off.p, t->plist_idx.p,
-                                  t->clist_idx.p, t->err.p);
+    walk_warp_kernel<true><<<wg, wb, 0, s>>>(G, theta2, t->group_off.p, t->group_node.p, t->nsysid.p, t->sys_root.p,
+                                             t->xs.p, t->geom.p, t->topo.p, t->centre.p, t->side.p, t->com.p,
+                                             t->cnt_p.p, t->cnt_c.p, t->plist_off.p, t->clist_off.p, t->plist_idx.p,
+                                             t->clist_idx.p, t->stacks.p, t->err.p);
     GT_CUDA(cudaGetLastError());
   }
   GT_CUDA(cudaEventRecord(t->ev[3], s));

@@ -1,7 +1,9 @@
 """GPU tree build, moments, groups and walk (include/qg_gtree.h) against the
 host builder: the same sorted order, nodes, moments (bit for bit: both sides
-evaluate the same FP64 expressions without contraction), groups and lists;
-and a force step built entirely on the GPU against the FP64 oracle."""
+evaluate the same FP64 expressions without contraction), groups and list
+entries (each group's list holds the same entries as the host's depth-first
+walk, in the GPU walk's own order); and a force step built entirely on the
+GPU against the FP64 oracle."""
 import numpy as np
 import pytest
 
@@ -29,6 +31,13 @@ def _sets():
     x = np.concatenate([np.zeros((40, 3)), np.random.default_rng(2).random((200, 3))])
     yield "coincident", workloads.single_system("coincident", x, 1e-3), 8, 16, 0.5
     yield "one", workloads.single_system("one", np.array([[0.5, 0.25, 0.125]]), 1e-2), 8, 64, 0.5
+    # a lattice: many opening tests with side / d at theta up to rounding
+    # (near-ties, decided by the walk's FP64 test)
+    g = np.arange(16, dtype=np.float64)
+    lat = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3) / 16.0
+    yield "lattice_t05", workloads.single_system("lattice", lat, 1e-3), 8, 64, 0.5
+    yield "lattice_t1", workloads.single_system("lattice", lat, 1e-3), 1, 8, 1.0
+    yield "lattice_far", workloads.single_system("lattice", lat + 1.0e4, 1e-3), 8, 64, 0.5
 
 
 CASES = list(_sets())
@@ -40,6 +49,12 @@ def _gpu_tree(ps, leaf, ncrit, theta):
     t.build(torch.as_tensor(ps.x).cuda(), torch.as_tensor(ps.m).cuda(), ps.sys_off, leaf, ncrit)
     t.walk(theta)
     return t
+
+
+def _per_group_sorted(off, idx):
+    """Each group's list segment sorted (list order is not part of the result)."""
+    gid = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    return idx[np.lexsort((idx, gid))]
 
 
 def _node_keys(rng, side):
@@ -65,17 +80,23 @@ def test_gpu_tree_equals_host_builder(name, ps, leaf, ncrit, theta):
     assert np.array_equal(t.host("cell_m")[h2g], h.cell_m)
     assert np.array_equal(t.host("cell_com")[h2g], h.cell_com)
     assert np.array_equal(t.host("cell_q")[h2g], h.cell_q)
-    # lists: identical, cell entries mapped to the GPU numbering
+    # lists: the same entries per group (cells mapped to the GPU numbering)
     assert np.array_equal(t.host("plist_off"), L.plist_off)
-    assert np.array_equal(t.host("plist_idx"), L.plist_idx)
     assert np.array_equal(t.host("clist_off"), L.clist_off)
-    assert np.array_equal(t.host("clist_idx"), h2g[L.clist_idx])
+    gp, gc = t.host("plist_idx"), t.host("clist_idx")
+    assert np.array_equal(_per_group_sorted(L.plist_off, gp), _per_group_sorted(L.plist_off, L.plist_idx))
+    assert np.array_equal(_per_group_sorted(L.clist_off, gc), _per_group_sorted(L.clist_off, h2g[L.clist_idx]))
+    # no entry twice within a group
+    for off, idx in ((L.plist_off, gp), (L.clist_off, gc)):
+        srt = _per_group_sorted(off, idx)
+        gid = np.repeat(np.arange(len(off) - 1), np.diff(off))
+        assert not np.any((srt[1:] == srt[:-1]) & (gid[1:] == gid[:-1]))
     build_ms, walk_ms = t.timing()
     assert build_ms > 0 and walk_ms > 0
     t.close()
 
 
-def test_gpu_built_step_matches_oracle_and_host_lists_exactly():
+def test_gpu_built_step_matches_oracle_and_host_lists():
     import torch
     ps = workloads.small_set("plummer", 30000, 11, 1e-2)
     eps2 = 1e-4
@@ -93,10 +114,16 @@ def test_gpu_built_step_matches_oracle_and_host_lists_exactly():
     ctx2.qg_set_cells(h.cell_com, h.cell_m, h.cell_q, L.clist_off, L.clist_idx)
     ctx2.qg_run()
     a2, phi2 = ctx2.qg_get_forces()
-    assert np.array_equal(a, a2) and np.array_equal(phi, phi2)
     a_ref, phi_ref = oracle.expansion_forces(h.group_off, h.x, h.x, h.m, L.plist_off, L.plist_idx, h.cell_com,
                                              h.cell_m, h.cell_q, L.clist_off, L.clist_idx, eps2_all=eps2)
     assert_parity(a, phi, a_ref, phi_ref, label="gpu-built step")
+    assert_parity(a2, phi2, a_ref, phi_ref, label="host-built step")
+    # the oracle on the GPU's own lists and cells as well
+    a_g, phi_g = oracle.expansion_forces(t.host("group_off"), t.host("xs"), t.host("xs"), t.host("ms"),
+                                         t.host("plist_off"), t.host("plist_idx"), t.host("cell_com"),
+                                         t.host("cell_m"), t.host("cell_q"), t.host("clist_off"),
+                                         t.host("clist_idx"), eps2_all=eps2)
+    assert_parity(a, phi, a_g, phi_g, label="gpu-built step, oracle on gpu lists")
     # back to input order
     ad = torch.empty((ps.n, 3), dtype=torch.float64, device="cuda")
     pd = torch.empty(ps.n, dtype=torch.float64, device="cuda")
