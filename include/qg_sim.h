@@ -1,0 +1,94 @@
+/*
+ * qg_sim.h -- time integration on the GPU: the leapfrog integrator the paper
+ * pairs with its tree code (Kodama & Ishiyama, arXiv:1812.07313, Sec. 5, the
+ * cold-collapse runs: G = M = 1, fixed step Delta t), with every force
+ * evaluation done by the GPU tree build, group walk and force kernel
+ * (qg_gtree.h, qgrav.h).  State stays in device memory between steps.
+ *
+ * One step of length dt is kick-drift-kick:
+ *     v += a(x) dt/2;   x += v dt;   a, phi = forces(x);   v += a dt/2
+ * where forces(x) rebuilds the oct-tree, the sink groups and the
+ * interaction lists from the current positions and evaluates Eq. 1 / Eq. 8
+ * (quadrupole cells, or monopole-only cells) on them.
+ *
+ * Particles keep the caller's order (the tree's sorted order is internal).
+ * Energies: K = 1/2 sum m v^2 and W = 1/2 sum m (phi + m / eps) -- the
+ * self pair that the force path includes in phi (-m/eps for eps > 0) is
+ * taken out again; with eps = 0 there is no self term.
+ *
+ * Streams: every step of a call runs on the given cuda_stream, or on the
+ * simulation's own stream when it is NULL; calls that return results to the
+ * host synchronise that stream.
+ *
+ * Every call returns a qg_status (QG_OK, QG_ERR_ARG, QG_ERR_CUDA,
+ * QG_ERR_NOMEM, QG_ERR_STATE) and leaves the simulation valid; host arrays
+ * are copied before returning and stay the caller's.  A step that fails
+ * after the drift leaves the state without matching forces: further steps
+ * return QG_ERR_STATE until qg_sim_set_state.
+ */
+#ifndef QG_SIM_H
+#define QG_SIM_H
+
+#include <stdint.h>
+
+#include "qgrav.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qg_sim qg_sim;
+
+typedef struct {
+  double theta;   /* opening angle of the group walk (> 0) */
+  double eps2;    /* Plummer softening squared, every particle */
+  int n_crit;     /* sink group size bound (>= 1) */
+  int leaf_max;   /* tree leaf size bound (>= 1) */
+  int expansion;  /* QG_QUAD or QG_MONO */
+  int autotune;   /* nonzero: qg_autotune the force launch on the first force evaluation */
+} qg_sim_params;
+
+/* Device time (CUDA events) of the parts of the last step, milliseconds,
+ * and its wall-clock time (host clock, the step's own synchronisations
+ * included). */
+typedef struct {
+  float build_ms, walk_ms, force_ms, integrate_ms;
+  double wall_ms;
+  int64_t groups, n_plist, n_clist, i_pp, i_pc;
+} qg_sim_times;
+
+/* force_opt may be NULL (defaults); its expansion field is overridden by
+ * params->expansion. */
+qg_status qg_sim_create(qg_sim **out, int device, const qg_sim_params *params, const qg_options *force_opt);
+void qg_sim_destroy(qg_sim *sim);
+
+/*
+ * Initial state from HOST arrays x [n][3], v [n][3], m [n] (n < 2^31) and
+ * sys_off [nsys+1] (independent systems, each with its own tree root;
+ * sys_off = {0, n} for one system).  Evaluates the forces at x, so that the
+ * first step can kick.
+ */
+qg_status qg_sim_set_state(qg_sim *sim, int64_t n, const double *x, const double *v, const double *m, int64_t nsys,
+                           const int64_t *sys_off, void *cuda_stream);
+
+/* nsteps kick-drift-kick steps of length dt (nsteps >= 0, dt finite). */
+qg_status qg_sim_step(qg_sim *sim, double dt, int64_t nsteps, void *cuda_stream);
+
+/* Copy the state to HOST arrays (any pointer may be NULL); synchronises. */
+qg_status qg_sim_get_state(qg_sim *sim, double *x, double *v, double *a, double *phi);
+
+/* Device pointers to the state (the simulation owns them; valid until the
+ * next qg_sim_set_state or qg_sim_destroy; any pointer may be NULL). */
+qg_status qg_sim_state_dev(const qg_sim *sim, const double **x, const double **v, const double **a,
+                           const double **phi, const double **m);
+
+/* Kinetic and potential energy, and total momentum p [3] (may be NULL), of
+ * the current state: FP64 reductions on the device in a fixed order. */
+qg_status qg_sim_energy(qg_sim *sim, double *kinetic, double *potential, double *momentum, void *cuda_stream);
+
+qg_status qg_sim_last_times(const qg_sim *sim, qg_sim_times *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

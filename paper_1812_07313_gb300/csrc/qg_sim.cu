@@ -1,0 +1,350 @@
+// qg_sim.cu -- leapfrog time integration on the GPU (include/qg_sim.h): the
+// kick-drift-kick step around the GPU tree build, group walk and force
+// kernel, state resident in device memory in the caller's particle order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "qg_gtree.h"
+#include "qg_sim.h"
+#include "qgrav.h"
+
+namespace {
+
+template <typename T>
+struct Buf {
+  T *p = nullptr;
+  size_t cap = 0;
+  cudaError_t reserve(size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e == cudaSuccess) cap = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+constexpr int kThreads = 256;
+constexpr int kRedBlocks = 592;  // fixed, so that the energy sums have a fixed order
+constexpr int kRedVals = 5;      // K, W, p_x, p_y, p_z
+
+unsigned blocks_for(int64_t work) {
+  const int64_t b = (work + kThreads - 1) / kThreads;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 64));
+}
+
+// v += a h; x += v dt over the flat [3n] arrays (the first kick and the drift).
+__global__ void kick_drift_kernel(int64_t n3, double *__restrict__ x, double *__restrict__ v,
+                                  const double *__restrict__ a, double h, double dt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+    const double vi = v[i] + a[i] * h;
+    v[i] = vi;
+    x[i] += vi * dt;
+  }
+}
+
+// Forces from the tree's sorted order back to the caller's order, and the
+// second kick (h = 0: store only).
+__global__ void unsort_kick_kernel(int64_t n, const int64_t *__restrict__ perm, const double *__restrict__ a_s,
+                                   const double *__restrict__ phi_s, double *__restrict__ a,
+                                   double *__restrict__ phi, double *__restrict__ v, double h, int kick) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = perm[i];
+    phi[j] = phi_s[i];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+      const double ad = a_s[3 * i + d];
+      a[3 * j + d] = ad;
+      if (kick) v[3 * j + d] += ad * h;
+    }
+  }
+}
+
+__device__ __forceinline__ void block_sum(double (&val)[kRedVals], double *sh) {
+  for (int k = 0; k < kRedVals; k++) sh[k * kThreads + threadIdx.x] = val[k];
+  __syncthreads();
+  for (int s = kThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s)
+      for (int k = 0; k < kRedVals; k++) sh[k * kThreads + threadIdx.x] += sh[k * kThreads + threadIdx.x + s];
+    __syncthreads();
+  }
+  for (int k = 0; k < kRedVals; k++) val[k] = sh[k * kThreads];
+}
+
+// Per block: K = 1/2 sum m v^2, W = 1/2 sum m (phi + m / eps), p = sum m v.
+__global__ void energy_partial_kernel(int64_t n, const double *__restrict__ v, const double *__restrict__ m,
+                                      const double *__restrict__ phi, double inv_eps, double *__restrict__ part) {
+  __shared__ double sh[kRedVals * kThreads];
+  double val[kRedVals] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    const double mi = m[i], v0 = v[3 * i], v1 = v[3 * i + 1], v2 = v[3 * i + 2];
+    val[0] += 0.5 * mi * (v0 * v0 + v1 * v1 + v2 * v2);
+    val[1] += 0.5 * mi * (phi[i] + mi * inv_eps);
+    val[2] += mi * v0;
+    val[3] += mi * v1;
+    val[4] += mi * v2;
+  }
+  block_sum(val, sh);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kRedVals; k++) part[k * kRedBlocks + blockIdx.x] = val[k];
+}
+
+__global__ void energy_final_kernel(const double *__restrict__ part, double *__restrict__ out) {
+  __shared__ double sh[kRedVals * kThreads];
+  double val[kRedVals] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < kRedBlocks; b += kThreads)
+    for (int k = 0; k < kRedVals; k++) val[k] += part[k * kRedBlocks + b];
+  block_sum(val, sh);
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kRedVals; k++) out[k] = val[k];
+}
+
+}  // namespace
+
+struct qg_sim {
+  int device = 0;
+  qg_sim_params prm{};
+  qg_options opt{};
+  qg_gtree *tree = nullptr;
+  qg_ctx *ctx = nullptr;
+  int64_t n = 0;
+  std::vector<int64_t> sys_off;
+  Buf<double> x, v, m, a, phi, a_s, phi_s, red;
+  bool has_state = false, tuned = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t stream = nullptr;  // used when the caller passes no stream
+  qg_sim_times times{};
+  // every call below runs on one stream, so the tree, force and integrator
+  // steps are ordered without further synchronisation
+  cudaStream_t use(void *caller) const { return caller ? (cudaStream_t)caller : stream; }
+};
+
+namespace {
+
+#define SIM_CUDA(call)                                                      \
+  do {                                                                      \
+    cudaError_t e_ = (call);                                                \
+    if (e_ != cudaSuccess)                                                  \
+      return e_ == cudaErrorMemoryAllocation ? QG_ERR_NOMEM : QG_ERR_CUDA;  \
+  } while (0)
+#define SIM_OK(call)                        \
+  do {                                      \
+    const qg_status st_ = (call);           \
+    if (st_ != QG_OK) return st_;           \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// forces(x) -> a, phi in the caller's order; with kick, also v += a h.
+qg_status evaluate(qg_sim *s, cudaStream_t st, bool kick, double h) {
+  SIM_OK(qg_gtree_build(s->tree, s->n, s->x.p, s->m.p, (int64_t)s->sys_off.size() - 1, s->sys_off.data(),
+                        s->prm.leaf_max, s->prm.n_crit, st));
+  SIM_OK(qg_gtree_walk(s->tree, s->prm.theta, st));
+  SIM_OK(qg_gtree_attach(s->tree, s->ctx, s->prm.eps2, st));
+  if (s->prm.autotune && !s->tuned) {
+    SIM_OK(qg_autotune(s->ctx, st, 2, nullptr, nullptr));
+    s->tuned = true;
+  }
+  SIM_OK(qg_run(s->ctx, st));
+  SIM_OK(qg_get_forces_dev(s->ctx, s->a_s.p, s->phi_s.p, st));
+  const int64_t *perm = nullptr;
+  SIM_OK(qg_gtree_arrays(s->tree, &perm, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                         nullptr, nullptr, nullptr, nullptr, nullptr));
+  SIM_CUDA(cudaEventRecord(s->ev[2], st));
+  unsort_kick_kernel<<<blocks_for(s->n), kThreads, 0, st>>>(s->n, perm, s->a_s.p, s->phi_s.p, s->a.p, s->phi.p,
+                                                            s->v.p, h, kick ? 1 : 0);
+  SIM_CUDA(cudaGetLastError());
+  SIM_CUDA(cudaEventRecord(s->ev[3], st));
+  SIM_CUDA(cudaStreamSynchronize(st));
+  float b = 0.f, w = 0.f, f = 0.f;
+  SIM_OK(qg_gtree_timing(s->tree, &b, &w));
+  SIM_OK(qg_last_timing(s->ctx, &f, nullptr));
+  s->times.build_ms = b;
+  s->times.walk_ms = w;
+  s->times.force_ms = f;
+  qg_stats stt{};
+  SIM_OK(qg_get_stats(s->ctx, &stt));
+  s->times.groups = stt.n_groups;
+  s->times.n_plist = stt.n_plist;
+  s->times.n_clist = stt.n_clist;
+  s->times.i_pp = stt.i_pp;
+  s->times.i_pc = stt.i_pc;
+  return QG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qg_status qg_sim_create(qg_sim **out, int device, const qg_sim_params *p, const qg_options *force_opt) {
+  if (!out || !p) return QG_ERR_ARG;
+  *out = nullptr;
+  if (!(p->theta > 0.0) || !std::isfinite(p->theta) || !(p->eps2 >= 0.0) || !std::isfinite(p->eps2) ||
+      p->n_crit < 1 || p->leaf_max < 1 || (p->expansion != QG_QUAD && p->expansion != QG_MONO))
+    return QG_ERR_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return QG_ERR_ARG;
+  DeviceGuard g(device);
+  qg_sim *s = new (std::nothrow) qg_sim();
+  if (!s) return QG_ERR_NOMEM;
+  s->device = device;
+  s->prm = *p;
+  if (force_opt) s->opt = *force_opt;
+  s->opt.expansion = p->expansion;
+  qg_status st = qg_gtree_create(&s->tree, device);
+  if (st == QG_OK) st = qg_create(&s->ctx, device, &s->opt);
+  for (int k = 0; k < 4 && st == QG_OK; k++)
+    if (cudaEventCreate(&s->ev[k]) != cudaSuccess) st = QG_ERR_CUDA;
+  if (st == QG_OK && s->red.reserve(kRedVals * kRedBlocks + kRedVals) != cudaSuccess) st = QG_ERR_NOMEM;
+  if (st == QG_OK && cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) st = QG_ERR_CUDA;
+  if (st != QG_OK) {
+    qg_sim_destroy(s);
+    return st;
+  }
+  *out = s;
+  return QG_OK;
+}
+
+void qg_sim_destroy(qg_sim *s) {
+  if (!s) return;
+  DeviceGuard g(s->device);
+  if (s->ctx) qg_destroy(s->ctx);
+  if (s->tree) qg_gtree_destroy(s->tree);
+  for (auto &e : s->ev)
+    if (e) cudaEventDestroy(e);
+  if (s->stream) {
+    cudaStreamSynchronize(s->stream);
+    cudaStreamDestroy(s->stream);
+  }
+  for (Buf<double> *b : {&s->x, &s->v, &s->m, &s->a, &s->phi, &s->a_s, &s->phi_s, &s->red}) b->release();
+  delete s;
+}
+
+qg_status qg_sim_set_state(qg_sim *s, int64_t n, const double *x, const double *v, const double *m, int64_t nsys,
+                           const int64_t *sys_off, void *stream) {
+  if (!s || n < 1 || n >= INT32_MAX || !x || !v || !m || nsys < 1 || !sys_off) return QG_ERR_ARG;
+  if (sys_off[0] != 0 || sys_off[nsys] != n) return QG_ERR_ARG;
+  for (int64_t q = 0; q < nsys; q++)
+    if (sys_off[q + 1] < sys_off[q]) return QG_ERR_ARG;
+  DeviceGuard g(s->device);
+  cudaStream_t st = s->use(stream);
+  s->has_state = false;
+  s->n = n;
+  s->sys_off.assign(sys_off, sys_off + nsys + 1);
+  SIM_CUDA(s->x.reserve(3 * n));
+  SIM_CUDA(s->v.reserve(3 * n));
+  SIM_CUDA(s->a.reserve(3 * n));
+  SIM_CUDA(s->a_s.reserve(3 * n));
+  SIM_CUDA(s->m.reserve(n));
+  SIM_CUDA(s->phi.reserve(n));
+  SIM_CUDA(s->phi_s.reserve(n));
+  SIM_CUDA(cudaMemcpyAsync(s->x.p, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+  SIM_CUDA(cudaMemcpyAsync(s->v.p, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+  SIM_CUDA(cudaMemcpyAsync(s->m.p, m, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  SIM_CUDA(cudaStreamSynchronize(st));
+  SIM_OK(evaluate(s, st, false, 0.0));
+  s->has_state = true;
+  return QG_OK;
+}
+
+qg_status qg_sim_step(qg_sim *s, double dt, int64_t nsteps, void *stream) {
+  if (!s || !std::isfinite(dt) || nsteps < 0) return QG_ERR_ARG;
+  if (!s->has_state) return QG_ERR_STATE;
+  DeviceGuard g(s->device);
+  cudaStream_t st = s->use(stream);
+  for (int64_t k = 0; k < nsteps; k++) {
+    const auto t0 = std::chrono::steady_clock::now();
+    SIM_CUDA(cudaEventRecord(s->ev[0], st));
+    kick_drift_kernel<<<blocks_for(3 * s->n), kThreads, 0, st>>>(3 * s->n, s->x.p, s->v.p, s->a.p, 0.5 * dt, dt);
+    SIM_CUDA(cudaGetLastError());
+    SIM_CUDA(cudaEventRecord(s->ev[1], st));
+    const qg_status e = evaluate(s, st, true, 0.5 * dt);
+    if (e != QG_OK) {
+      s->has_state = false;  // positions have moved but the forces are not theirs
+      return e;
+    }
+    float kd = 0.f, uk = 0.f;
+    SIM_CUDA(cudaEventElapsedTime(&kd, s->ev[0], s->ev[1]));
+    SIM_CUDA(cudaEventElapsedTime(&uk, s->ev[2], s->ev[3]));
+    s->times.integrate_ms = kd + uk;
+    s->times.wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return QG_OK;
+}
+
+qg_status qg_sim_get_state(qg_sim *s, double *x, double *v, double *a, double *phi) {
+  if (!s) return QG_ERR_ARG;
+  if (!s->has_state) return QG_ERR_STATE;
+  DeviceGuard g(s->device);
+  SIM_CUDA(cudaStreamSynchronize(s->stream));
+  const int64_t n = s->n;
+  if (x) SIM_CUDA(cudaMemcpy(x, s->x.p, 3 * n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (v) SIM_CUDA(cudaMemcpy(v, s->v.p, 3 * n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (a) SIM_CUDA(cudaMemcpy(a, s->a.p, 3 * n * sizeof(double), cudaMemcpyDeviceToHost));
+  if (phi) SIM_CUDA(cudaMemcpy(phi, s->phi.p, n * sizeof(double), cudaMemcpyDeviceToHost));
+  return QG_OK;
+}
+
+qg_status qg_sim_state_dev(const qg_sim *s, const double **x, const double **v, const double **a, const double **phi,
+                           const double **m) {
+  if (!s) return QG_ERR_ARG;
+  if (!s->has_state) return QG_ERR_STATE;
+  if (x) *x = s->x.p;
+  if (v) *v = s->v.p;
+  if (a) *a = s->a.p;
+  if (phi) *phi = s->phi.p;
+  if (m) *m = s->m.p;
+  return QG_OK;
+}
+
+qg_status qg_sim_energy(qg_sim *s, double *kinetic, double *potential, double *momentum, void *stream) {
+  if (!s) return QG_ERR_ARG;
+  if (!s->has_state) return QG_ERR_STATE;
+  DeviceGuard g(s->device);
+  cudaStream_t st = s->use(stream);
+  const double inv_eps = s->prm.eps2 > 0.0 ? 1.0 / std::sqrt(s->prm.eps2) : 0.0;
+  energy_partial_kernel<<<kRedBlocks, kThreads, 0, st>>>(s->n, s->v.p, s->m.p, s->phi.p, inv_eps, s->red.p);
+  energy_final_kernel<<<1, kThreads, 0, st>>>(s->red.p, s->red.p + kRedVals * kRedBlocks);
+  SIM_CUDA(cudaGetLastError());
+  double out[kRedVals];
+  SIM_CUDA(cudaMemcpyAsync(out, s->red.p + kRedVals * kRedBlocks, sizeof(out), cudaMemcpyDeviceToHost, st));
+  SIM_CUDA(cudaStreamSynchronize(st));
+  if (kinetic) *kinetic = out[0];
+  if (potential) *potential = out[1];
+  if (momentum) std::memcpy(momentum, out + 2, 3 * sizeof(double));
+  return QG_OK;
+}
+
+qg_status qg_sim_last_times(const qg_sim *s, qg_sim_times *out) {
+  if (!s || !out) return QG_ERR_ARG;
+  if (!s->has_state) return QG_ERR_STATE;
+  *out = s->times;
+  return QG_OK;
+}
+
+}  // extern "C"

@@ -180,6 +180,24 @@ def batched_systems(nsys=512, seed=4, n_lo=1024, n_hi=65536, eps=1e-2, spacing=1
                        meta={"kinds": ["plummer" if k else "hernquist" for k in kinds]})
 
 
+def cold_collapse(n, seed, virial=0.1, radius=1.0):
+    """Initial state of the cold-collapse runs (Sec. 5): a homogeneous sphere
+    of radius 1 and total mass 1 (G = 1), at rest except for isotropic
+    Gaussian velocities scaled so that the virial ratio 2K/|W| equals
+    ``virial``, with W = -3/5 G M^2 / R of the uniform sphere.  The velocity
+    distribution is not given in the paper; Gaussian is this generator's
+    choice.  Returns (x [n,3], v [n,3], m [n])."""
+    x = uniform_sphere(n, seed, radius)
+    rng = np.random.Generator(np.random.PCG64(seed + 1000003))
+    v = rng.standard_normal((n, 3))
+    v -= v.mean(axis=0)
+    m = np.full(n, 1.0 / n)
+    K_target = 0.5 * virial * 0.6 / radius
+    K = 0.5 * float(np.sum(m * np.sum(v * v, axis=1)))
+    v *= np.sqrt(K_target / K)
+    return x, v, m
+
+
 @dataclass(frozen=True)
 class Workload:
     name: str

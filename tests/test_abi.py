@@ -36,6 +36,16 @@ def test_gpu_tree_symbols_are_exported_and_bound():
     assert set(names) == set(gtree.SIGNATURES)
 
 
+def test_integrator_symbols_are_exported_and_bound():
+    from paper_1812_07313_gb300 import sim
+    L = qgrav.lib()
+    names = _declared("qg_sim.h")
+    assert "qg_sim_step" in names and "qg_sim_energy" in names
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(sim.SIGNATURES)
+
+
 def test_tree_library_exports_every_declared_symbol():
     L = ctypes.CDLL(_native.build_tree())
     for n in _declared("qg_tree.h"):

@@ -127,9 +127,10 @@ def test_gpu_built_step_matches_oracle_and_host_lists():
     # back to input order
     ad = torch.empty((ps.n, 3), dtype=torch.float64, device="cuda")
     pd = torch.empty(ps.n, dtype=torch.float64, device="cuda")
-    ctx.qg_get_forces_dev(ad, pd)
+    cs = torch.cuda.current_stream().cuda_stream  # one stream for the copy and the unsort
+    ctx.qg_get_forces_dev(ad, pd, cs)
     a_in = torch.empty_like(ad)
-    t.unsort(ad, a_in, 3)
+    t.unsort(ad, a_in, 3, cs)
     torch.cuda.synchronize()
     expect = np.empty_like(a)
     expect[h.perm] = a
