@@ -116,6 +116,26 @@ def hernquist(n, seed, a=1.0, rmax=100.0):
     return _isotropic(rng, n) * r[:, None]
 
 
+def exponential_disk(n, seed, r_d=1.0, z0=0.1, rmax=10.0):
+    """Exponential disk: surface density proportional to exp(-R / r_d) --
+    the cylindrical radius then follows a Gamma(2, r_d) distribution --
+    truncated at R <= rmax r_d (resampled), uniform azimuth, and a
+    sech^2(z / z0) vertical profile (z = z0 atanh(2U - 1)).  The paper gives
+    no disk parameters; r_d = 1, z0 = 0.1 r_d and the truncation at 10 r_d
+    are this generator's choice."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    R = rng.gamma(2.0, r_d, n)
+    bad = R > rmax * r_d
+    while bad.any():
+        R[bad] = rng.gamma(2.0, r_d, int(bad.sum()))
+        bad = R > rmax * r_d
+    phi = 2.0 * np.pi * rng.random(n)
+    u = rng.random(n)
+    u = np.clip(u, 1e-15, 1.0 - 1e-15)
+    z = z0 * np.arctanh(2.0 * u - 1.0)
+    return np.stack([R * np.cos(phi), R * np.sin(phi), z], axis=1)
+
+
 def clumpy_field(n, seed, nclumps=2000, clump_frac=0.7, slope=-1.9, mass_range=1000.0,
                  rs_lo=1e-3, rs_hi=1e-2, trunc=10.0):
     """Unit cube: clump_frac of the particles in Plummer clumps, the rest uniform."""
@@ -235,7 +255,7 @@ WORKLOADS = {
 
 
 def small_set(kind, n, seed, eps):
-    """Small sets for tests: 'sphere', 'cube', 'plummer', 'hernquist', 'clumpy'."""
+    """Small sets for tests: 'sphere', 'cube', 'plummer', 'hernquist', 'clumpy', 'disk'."""
     if kind == "sphere":
         x = uniform_sphere(n, seed)
     elif kind == "cube":
@@ -246,6 +266,8 @@ def small_set(kind, n, seed, eps):
         x = hernquist(n, seed)
     elif kind == "clumpy":
         x = clumpy_field(n, seed, nclumps=max(1, n // 200))
+    elif kind == "disk":
+        x = exponential_disk(n, seed)
     else:
         raise ValueError(kind)
     return single_system("%s_%d" % (kind, n), x, eps)

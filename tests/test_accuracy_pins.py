@@ -1,0 +1,89 @@
+"""The method's force error (Eq. 9) against the paper's accuracy study
+(Sec. 4, Figs. 1-2), with the FP64 oracle on lists from the host walk and
+direct summation on sampled groups, N = 65,536 per distribution:
+  * the error at 90% of the particles grows roughly as theta^(5/2) with
+    monopole cells and theta^(7/2) with quadrupole cells (Fig. 2);
+  * at equal theta the quadrupole error is the smaller one;
+  * with monopole cells the Plummer model has the smallest error and the
+    disk the largest (Sec. 4);
+  * on the homogeneous sphere, quadrupole theta 0.65 is about as accurate as
+    monopole theta 0.3 (Fig. 1, top).
+Also pins of the seeded disk generator (its distributions have closed forms).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1812_07313_gb300 import tree as qtree
+from paper_1812_07313_gb300 import workloads
+
+THETAS = (0.3, 0.4, 0.5, 0.6, 0.7, 0.8)
+N, EPS, N_CRIT, GROUPS = 65536, 1e-3, 64, 160
+
+
+def _p90_by_theta(kind, thetas=THETAS):
+    ps = workloads.small_set(kind, N, 7, EPS)
+    out, ref = {}, None
+    for th in thetas:
+        tr = qtree.Tree(ps.x, ps.m, ps.sys_off, 8, N_CRIT)
+        L = tr.walk(th)
+        if ref is None:  # the tree (and so the groups) does not depend on theta
+            groups = np.sort(np.random.default_rng(5).choice(tr.ngroups, GROUPS, replace=False))
+            sinks = np.concatenate([np.arange(tr.group_off[g], tr.group_off[g + 1]) for g in groups])
+            a_direct, _ = oracle.direct_forces(tr.x[sinks], tr.x, tr.m, eps2_all=EPS * EPS)
+            ref = (groups, sinks, a_direct)
+        groups, sinks, a_direct = ref
+        for quad in (False, True):
+            a, _ = oracle.expansion_forces(tr.group_off, tr.x, tr.x, tr.m, L.plist_off, L.plist_idx, tr.cell_com,
+                                           tr.cell_m, tr.cell_q, L.clist_off, L.clist_idx, eps2_all=EPS * EPS,
+                                           use_quad=quad, groups=groups)
+            out[("quad" if quad else "mono", th)] = float(np.percentile(oracle.relative_error(a[sinks], a_direct), 90))
+    return out
+
+
+@pytest.fixture(scope="module")
+def study():
+    return {k: _p90_by_theta(k) for k in ("sphere", "plummer", "disk")}
+
+
+def _slope(res, name):
+    p = np.array([res[(name, th)] for th in THETAS])
+    return float(np.polyfit(np.log(THETAS), np.log(p), 1)[0])
+
+
+@pytest.mark.parametrize("kind", ["sphere", "plummer", "disk"])
+def test_error_scaling_with_theta(study, kind):
+    mono, quad = _slope(study[kind], "mono"), _slope(study[kind], "quad")
+    print(kind, "slopes mono %.2f quad %.2f" % (mono, quad))
+    assert 2.0 <= mono <= 3.1  # ~5/2
+    assert 3.1 <= quad <= 4.4  # ~7/2
+    assert quad - mono >= 0.6
+
+
+@pytest.mark.parametrize("kind", ["sphere", "plummer", "disk"])
+def test_quadrupole_is_more_accurate_at_equal_theta(study, kind):
+    for th in THETAS:
+        assert study[kind][("quad", th)] < study[kind][("mono", th)], th
+
+
+def test_monopole_error_ordering_across_distributions(study):
+    for th in (0.3, 0.5, 0.7):
+        assert study["plummer"][("mono", th)] < study["sphere"][("mono", th)] < study["disk"][("mono", th)], th
+
+
+def test_sphere_quad_065_matches_mono_03():
+    res = _p90_by_theta("sphere", thetas=(0.3, 0.65))
+    r = res[("quad", 0.65)] / res[("mono", 0.3)]
+    print("sphere p90 quad 0.65 / mono 0.3 = %.2f" % r)
+    assert 0.5 <= r <= 2.0
+
+
+def test_disk_generator_distributions():
+    x = workloads.exponential_disk(200000, 3)
+    R = np.hypot(x[:, 0], x[:, 1])
+    # R ~ Gamma(2, 1) truncated at 10: mean 2 (to 1e-3), median 1.6783
+    assert abs(R.mean() - 2.0) < 0.01 and abs(np.median(R) - 1.6783) < 0.01 and R.max() <= 10.0
+    # sech^2(z / z0) with z0 = 0.1: mean |z| = z0 ln 2
+    assert abs(np.abs(x[:, 2]).mean() - 0.1 * np.log(2.0)) < 1e-3
+    # uniform azimuth: no net direction
+    assert np.abs(x[:, :2].mean(axis=0)).max() < 0.02

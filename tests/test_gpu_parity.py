@@ -37,6 +37,16 @@ def test_sphere_4k_mono(sphere4k):
     assert_parity(a, phi, a_ref, phi_ref, label="sphere_4k mono")
 
 
+@pytest.mark.parametrize("theta", [0.3, 0.65])
+def test_exponential_disk_quad_and_mono(theta):
+    """A thin exponential disk (the third distribution of the accuracy study)."""
+    case = Case(workloads.small_set("disk", 20000, 19, 1e-3), theta, 8, 64)
+    for exp, uq in ((qgrav.QG_QUAD, True), (qgrav.QG_MONO, False)):
+        a, phi, _ = case.gpu(qgrav.Options(expansion=exp))
+        a_ref, phi_ref = case.oracle(use_quad=uq)
+        assert_parity(a, phi, a_ref, phi_ref, label="disk theta %.2f %s" % (theta, "quad" if uq else "mono"))
+
+
 def test_sphere_4k_fp64_kernel(sphere4k):
     for exp, uq in ((qgrav.QG_QUAD, True), (qgrav.QG_MONO, False)):
         a, phi, _ = sphere4k.gpu(qgrav.Options(precision=qgrav.QG_FP64, expansion=exp))
