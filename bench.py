@@ -615,24 +615,32 @@ def kernel_hash():
 
 def _recorded_traffic(workload, launch):
     """DRAM bytes (read + write) per force-kernel launch from the ncu summary in
-    profiles/, when it was taken on this workload, launch shape and source."""
+    profiles/, when it was taken on this workload, launch shape and source
+    (the file holds one record per captured shape, separated by blank lines)."""
     path = os.path.join(ROOT, "profiles", "force_kernel_traffic.txt")
     if not os.path.exists(path):
         return None
-    rec = {}
+    recs, rec = [], {}
     with open(path) as f:
         for line in f:
-            if "=" in line and not line.lstrip().startswith("#"):
+            if not line.strip():
+                if rec:
+                    recs.append(rec)
+                rec = {}
+            elif "=" in line and not line.lstrip().startswith("#"):
                 k, v = line.split("=", 1)
                 rec[k.strip()] = v.strip()
+    if rec:
+        recs.append(rec)
     shape = "%d,%d,%d,%s" % (launch["sinks_per_thread"], launch["warps_per_group"], launch["tile_j"],
                              "x2" if launch.get("arith", "").startswith("paired") else "x1")
-    if rec.get("workload") != workload or rec.get("kernel_hash") != kernel_hash() or rec.get("launch") != shape:
-        return None
-    try:
-        return float(rec["bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    for r in recs:
+        if r.get("workload") == workload and r.get("kernel_hash") == kernel_hash() and r.get("launch") == shape:
+            try:
+                return float(r["bytes_per_launch"])
+            except (KeyError, ValueError):
+                return None
+    return None
 
 
 def main():
