@@ -203,7 +203,10 @@ __device__ __forceinline__ float warp_max(float v) {
 // up to 128 registers.
 template <typename Real, int R, bool PAIRED> struct Bounds {
   static constexpr int threads = R >= 8 ? 128 : 256;
-  static constexpr int min_blocks = (R >= 8 || sizeof(Real) == 8) ? 2 : (PAIRED && R >= 4 ? 2 : 4);
+  // R <= 4 scalar FP32: 3 blocks of 256 threads leaves 80 registers a thread
+  // (72 at R = 2), which still fits the six 128-thread CTAs that shared
+  // memory allows per SM; 4 blocks (64 registers) measured 2-3 % slower
+  static constexpr int min_blocks = (R >= 8 || sizeof(Real) == 8 || (PAIRED && R >= 4)) ? 2 : 3;
 };
 
 template <typename Real, int R, bool QUAD, bool GUARD, bool CENTRED, bool PAIRED>

@@ -171,6 +171,11 @@ struct qg_gtree {
   DBuf<int32_t> plist_idx, clist_idx;
   DBuf<int64_t> scan_tmp[5];
   DBuf<int32_t> stacks;  // per-warp walk stacks
+  // single-pass walk: per-warp staging areas, scratch lists in completion order
+  DBuf<int32_t> stage_p, stage_c, scratch_p, scratch_c;
+  DBuf<int64_t> gstart_p, gstart_c;
+  DBuf<unsigned long long> cursor;
+  int64_t stage_cap_p = int64_t(1) << 15, stage_cap_c = int64_t(1) << 14;
   DBuf<float4> geom;     // per node: (com - o, side) / S, ((centre - o) / S, 0) in FP32; o, S: system root cube
   DBuf<int4> topo;       // per node: (first particle, end, first child, children)
   DBuf<int> err;
@@ -726,13 +731,114 @@ __device__ __forceinline__ int node_opens32(float4 ga, float4 gb, float th2, flo
   return 2;
 }
 
+// Where one group's list entries go: particle entries at p[0, cap_p), cell
+// entries at c[0, cap_c); entries past a capacity (or with a null pointer)
+// are counted but not written.
+struct ListOut {
+  int32_t *p, *c;
+  int64_t cap_p, cap_c;
+};
+
+struct WalkTree {
+  const int64_t *group_off;
+  const int32_t *group_node, *nsysid, *sys_root;
+  const double *xs;
+  const float4 *geom;
+  const int4 *topo;
+  const double *centre, *side, *com;
+};
+
+// Walk group g with the calling warp; np, nc: its list sizes (warp-uniform).
+// Returns false if the stack would overflow (not reachable, see above).
+__device__ bool walk_group(const WalkTree &T, int64_t g, double theta2, float th2, int32_t *stack, ListOut out,
+                           int64_t &np, int64_t &nc) {
+  const int lane = threadIdx.x & 31;
+  const int32_t gb = (int32_t)T.group_off[g], ge = (int32_t)T.group_off[g + 1];
+  double bmin[3] = {INFINITY, INFINITY, INFINITY}, bmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = gb + lane; i < ge; i += 32)
+    for (int d = 0; d < 3; d++) {
+      bmin[d] = fmin(bmin[d], T.xs[3 * i + d]);
+      bmax[d] = fmax(bmax[d], T.xs[3 * i + d]);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    for (int d = 0; d < 3; d++) {
+      bmin[d] = fmin(bmin[d], __shfl_xor_sync(0xffffffffu, bmin[d], o));
+      bmax[d] = fmax(bmax[d], __shfl_xor_sync(0xffffffffu, bmax[d], o));
+    }
+  const int32_t root = T.sys_root[T.nsysid[T.group_node[g]]];
+  const double o0 = T.centre[3 * root], o1 = T.centre[3 * root + 1], o2 = T.centre[3 * root + 2], S = T.side[root];
+  const double u = 1.0 / S, omax = fmax(fabs(o0), fmax(fabs(o1), fabs(o2)));
+  const float dl = __double2float_ru(0x1p-20 + 0x1p-40 * (omax + S) * u);
+  const float3 lo = make_float3(__double2float_rn((bmin[0] - o0) * u), __double2float_rn((bmin[1] - o1) * u),
+                                __double2float_rn((bmin[2] - o2) * u));
+  const float3 hi = make_float3(__double2float_rn((bmax[0] - o0) * u), __double2float_rn((bmax[1] - o1) * u),
+                                __double2float_rn((bmax[2] - o2) * u));
+  __syncwarp();  // the previous group's last stack reads are done
+  if (lane == 0) stack[0] = root;
+  __syncwarp();
+  int sp = 1, depth = 0;
+  int seg = 0;  // lane d: first stack slot of the segment at depth d
+  np = 0;
+  nc = 0;
+  while (sp > 0) {
+    const int base = __shfl_sync(0xffffffffu, seg, depth);
+    if (sp == base) {  // this level's segment is used up: back to the one below
+      depth--;
+      continue;
+    }
+    const int take = sp - base < 32 ? sp - base : 32;
+    sp -= take;
+    const bool have = lane < take;
+    const int32_t k = have ? stack[sp + lane] : -1;
+    __syncwarp();  // every lane has read its entry before the stack is written again
+    int kind = 0;  // 1: cell, 2: leaf particles, 3: open (children)
+    int4 tp = make_int4(0, 0, 0, 0);
+    if (have) {
+      tp = T.topo[k];
+      bool open = true;
+      if (theta2 > 0.0 && !(tp.x < ge && tp.y > gb)) {
+        const int dec = node_opens32(T.geom[2 * k], T.geom[2 * k + 1], th2, dl, lo, hi);
+        open = dec == 2 ? node_opens64(k, theta2, T.centre, T.side, T.com, bmin, bmax) : dec == 1;
+      }
+      kind = !open ? 1 : (tp.w == 0 ? 2 : 3);
+    }
+    // accepted cells
+    const unsigned cells = __ballot_sync(0xffffffffu, kind == 1);
+    if (kind == 1 && out.c) {
+      const int64_t at = nc + __popc(cells & ((1u << lane) - 1u));
+      if (at < out.cap_c) out.c[at] = k;
+    }
+    nc += __popc(cells);
+    // particles of opened leaves
+    int ptotal = 0;
+    const int pofs = warp_excl(kind == 2 ? tp.y - tp.x : 0, lane, &ptotal);
+    if (kind == 2 && out.p)
+      for (int32_t i = tp.x; i < tp.y; i++) {
+        const int64_t at = np + pofs + (i - tp.x);
+        if (at < out.cap_p) out.p[at] = i;
+      }
+    np += ptotal;
+    // children of opened internal nodes: a new segment one level deeper
+    int ctotal = 0;
+    const int cofs = warp_excl(kind == 3 ? tp.w : 0, lane, &ctotal);
+    if (ctotal > 0) {
+      if (depth + 1 > kMaxLevel || sp + ctotal > kWarpStack) return false;  // not reachable for 21 levels
+      if (kind == 3)
+        for (int c = 0; c < tp.w; c++) stack[sp + cofs + c] = tp.z + c;
+      depth++;
+      if (lane == depth) seg = sp;
+      sp += ctotal;
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
+// Two-pass walk (the fallback): FILL == false counts each group's entries,
+// FILL == true writes them at the scanned offsets.
 template <bool FILL>
-__global__ void walk_warp_kernel(int64_t G, double theta2, const int64_t *__restrict__ group_off,
-                                 const int32_t *__restrict__ group_node, const int32_t *__restrict__ nsysid,
-                                 const int32_t *__restrict__ sys_root, const double *__restrict__ xs,
-                                 const float4 *__restrict__ geom, const int4 *__restrict__ topo,
-                                 const double *__restrict__ centre, const double *__restrict__ side,
-                                 const double *__restrict__ com, int32_t *__restrict__ cnt_p,
+__global__ void walk_warp_kernel(int64_t G, double theta2, WalkTree T, int32_t *__restrict__ cnt_p,
                                  int32_t *__restrict__ cnt_c, const int64_t *__restrict__ plist_off,
                                  const int64_t *__restrict__ clist_off, int32_t *__restrict__ plist_idx,
                                  int32_t *__restrict__ clist_idx, int32_t *__restrict__ stacks, int *err) {
@@ -742,83 +848,11 @@ __global__ void walk_warp_kernel(int64_t G, double theta2, const int64_t *__rest
   int32_t *stack = stacks + warp * kWarpStack;
   const float th2 = __double2float_rn(theta2);
   for (int64_t g = warp; g < G; g += nwarps) {
-    const int32_t gb = (int32_t)group_off[g], ge = (int32_t)group_off[g + 1];
-    double bmin[3] = {INFINITY, INFINITY, INFINITY}, bmax[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int64_t i = gb + lane; i < ge; i += 32)
-      for (int d = 0; d < 3; d++) {
-        bmin[d] = fmin(bmin[d], xs[3 * i + d]);
-        bmax[d] = fmax(bmax[d], xs[3 * i + d]);
-      }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-      for (int d = 0; d < 3; d++) {
-        bmin[d] = fmin(bmin[d], __shfl_xor_sync(0xffffffffu, bmin[d], o));
-        bmax[d] = fmax(bmax[d], __shfl_xor_sync(0xffffffffu, bmax[d], o));
-      }
-    const int32_t root = sys_root[nsysid[group_node[g]]];
-    const double o0 = centre[3 * root], o1 = centre[3 * root + 1], o2 = centre[3 * root + 2], S = side[root];
-    const double u = 1.0 / S, omax = fmax(fabs(o0), fmax(fabs(o1), fabs(o2)));
-    const float dl = __double2float_ru(0x1p-20 + 0x1p-40 * (omax + S) * u);
-    const float3 lo = make_float3(__double2float_rn((bmin[0] - o0) * u), __double2float_rn((bmin[1] - o1) * u),
-                                  __double2float_rn((bmin[2] - o2) * u));
-    const float3 hi = make_float3(__double2float_rn((bmax[0] - o0) * u), __double2float_rn((bmax[1] - o1) * u),
-                                  __double2float_rn((bmax[2] - o2) * u));
-    if (lane == 0) stack[0] = root;
-    __syncwarp();
-    int sp = 1, depth = 0;
-    int seg = 0;  // lane d: first stack slot of the segment at depth d
+    ListOut out{nullptr, nullptr, 0, 0};
+    if (FILL) out = ListOut{plist_idx + plist_off[g], clist_idx + clist_off[g], plist_off[g + 1] - plist_off[g],
+                            clist_off[g + 1] - clist_off[g]};
     int64_t np = 0, nc = 0;
-    const int64_t po = FILL ? plist_off[g] : 0, co = FILL ? clist_off[g] : 0;
-    bool failed = false;
-    while (sp > 0) {
-      const int base = __shfl_sync(0xffffffffu, seg, depth);
-      if (sp == base) {  // this level's segment is used up: back to the one below
-        depth--;
-        continue;
-      }
-      const int take = sp - base < 32 ? sp - base : 32;
-      sp -= take;
-      const bool have = lane < take;
-      const int32_t k = have ? stack[sp + lane] : -1;
-      __syncwarp();  // every lane has read its entry before the stack is written again
-      int kind = 0;  // 1: cell, 2: leaf particles, 3: open (children)
-      int4 tp = make_int4(0, 0, 0, 0);
-      if (have) {
-        tp = topo[k];
-        bool open = true;
-        if (theta2 > 0.0 && !(tp.x < ge && tp.y > gb)) {
-          const int dec = node_opens32(geom[2 * k], geom[2 * k + 1], th2, dl, lo, hi);
-          open = dec == 2 ? node_opens64(k, theta2, centre, side, com, bmin, bmax) : dec == 1;
-        }
-        kind = !open ? 1 : (tp.w == 0 ? 2 : 3);
-      }
-      // accepted cells
-      const unsigned cells = __ballot_sync(0xffffffffu, kind == 1);
-      if (FILL && kind == 1) clist_idx[co + nc + __popc(cells & ((1u << lane) - 1u))] = k;
-      nc += __popc(cells);
-      // particles of opened leaves
-      int ptotal = 0;
-      const int pofs = warp_excl(kind == 2 ? tp.y - tp.x : 0, lane, &ptotal);
-      if (FILL && kind == 2)
-        for (int32_t i = tp.x; i < tp.y; i++) plist_idx[po + np + pofs + (i - tp.x)] = i;
-      np += ptotal;
-      // children of opened internal nodes: a new segment one level deeper
-      int ctotal = 0;
-      const int cofs = warp_excl(kind == 3 ? tp.w : 0, lane, &ctotal);
-      if (ctotal > 0) {
-        if (depth + 1 > kMaxLevel || sp + ctotal > kWarpStack) {  // not reachable for a 21-level tree
-          failed = true;
-          break;
-        }
-        if (kind == 3)
-          for (int c = 0; c < tp.w; c++) stack[sp + cofs + c] = tp.z + c;
-        depth++;
-        if (lane == depth) seg = sp;
-        sp += ctotal;
-      }
-      __syncwarp();
-    }
-    if (failed) {
+    if (!walk_group(T, g, theta2, th2, stack, out, np, nc)) {
       if (lane == 0) atomicOr(err, 1);
       return;
     }
@@ -826,6 +860,74 @@ __global__ void walk_warp_kernel(int64_t G, double theta2, const int64_t *__rest
       cnt_p[g] = (int32_t)(np < INT32_MAX ? np : INT32_MAX);
       cnt_c[g] = (int32_t)(nc < INT32_MAX ? nc : INT32_MAX);
     }
+  }
+}
+
+// Single-pass walk: warps take groups from a shared counter, write each
+// group's entries to their own staging area (capacities sp_cap, sc_cap),
+// then reserve the group's place in the scratch lists with one atomic add per
+// list and copy it there (groups land in completion order; gstart / cnt
+// record where).  cursor[0]: next group, [1], [2]: particle / cell entries
+// reserved so far (the exact totals, even when they exceed the scratch
+// capacities).  err bit 0: stack, bit 1: a group longer than its staging
+// area, bit 2: scratch too small.
+__global__ void walk_single_kernel(int64_t G, double theta2, WalkTree T, int32_t *__restrict__ stage_p,
+                                   int32_t *__restrict__ stage_c, int64_t sp_cap, int64_t sc_cap,
+                                   int32_t *__restrict__ scratch_p, int32_t *__restrict__ scratch_c, int64_t cap_p,
+                                   int64_t cap_c, unsigned long long *__restrict__ cursor,
+                                   int64_t *__restrict__ gstart_p, int64_t *__restrict__ gstart_c,
+                                   int32_t *__restrict__ cnt_p, int32_t *__restrict__ cnt_c,
+                                   int32_t *__restrict__ stacks, int *err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int32_t *stack = stacks + warp * kWarpStack;
+  int32_t *mp = stage_p + warp * sp_cap, *mc = stage_c + warp * sc_cap;
+  const float th2 = __double2float_rn(theta2);
+  for (;;) {
+    unsigned long long gg = 0;
+    if (lane == 0) gg = atomicAdd(&cursor[0], 1ull);
+    const int64_t g = (int64_t)__shfl_sync(0xffffffffu, gg, 0);
+    if (g >= G) return;
+    int64_t np = 0, nc = 0;
+    if (!walk_group(T, g, theta2, th2, stack, ListOut{mp, mc, sp_cap, sc_cap}, np, nc)) {
+      if (lane == 0) atomicOr(err, 1);
+      return;
+    }
+    unsigned long long bp = 0, bc = 0;
+    if (lane == 0) {
+      bp = atomicAdd(&cursor[1], (unsigned long long)np);
+      bc = atomicAdd(&cursor[2], (unsigned long long)nc);
+    }
+    bp = __shfl_sync(0xffffffffu, bp, 0);
+    bc = __shfl_sync(0xffffffffu, bc, 0);
+    __syncwarp();  // the staging writes of all lanes are visible to the copy
+    if (np > sp_cap || nc > sc_cap) {
+      if (lane == 0) atomicOr(err, 2);
+    } else if ((int64_t)bp + np > cap_p || (int64_t)bc + nc > cap_c) {
+      if (lane == 0) atomicOr(err, 4);
+    } else {
+      for (int64_t i = lane; i < np; i += 32) scratch_p[bp + i] = mp[i];
+      for (int64_t i = lane; i < nc; i += 32) scratch_c[bc + i] = mc[i];
+    }
+    if (lane == 0) {
+      gstart_p[g] = (int64_t)bp;
+      gstart_c[g] = (int64_t)bc;
+      cnt_p[g] = (int32_t)(np < INT32_MAX ? np : INT32_MAX);
+      cnt_c[g] = (int32_t)(nc < INT32_MAX ? nc : INT32_MAX);
+    }
+    __syncwarp();  // the copy has read the staging area before the next group writes it
+  }
+}
+
+// Scratch lists (groups in completion order) to CSR order: one warp per group.
+__global__ void lists_to_csr_kernel(int64_t G, const int64_t *__restrict__ gstart, const int64_t *__restrict__ off,
+                                    const int32_t *__restrict__ scratch, int32_t *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = warp; g < G; g += nwarps) {
+    const int64_t s = gstart[g], o = off[g], n = off[g + 1] - off[g];
+    for (int64_t i = lane; i < n; i += 32) out[o + i] = scratch[s + i];
   }
 }
 
@@ -919,6 +1021,10 @@ void qg_gtree_destroy(qg_gtree *t) {
   t->plist_off.release(); t->clist_off.release(); t->plist_idx.release(); t->clist_idx.release();
   for (auto &b : t->scan_tmp) b.release();
   t->stacks.release();
+  for (DBuf<int32_t> *b : {&t->stage_p, &t->stage_c, &t->scratch_p, &t->scratch_c}) b->release();
+  t->gstart_p.release();
+  t->gstart_c.release();
+  t->cursor.release();
   t->geom.release();
   t->topo.release();
   t->err.release();
@@ -1154,6 +1260,91 @@ qg_status qg_gtree_build(qg_gtree *t, int64_t n, const double *x, const double *
   return st;
 }
 
+// Two-pass walk: count, scan, fill (the fallback of the single pass).
+static qg_status walk_two_pass(qg_gtree *t, double theta2, const WalkTree &T, unsigned wg, int wb, cudaStream_t s,
+                               int64_t tot[2]) {
+  const int64_t G = t->G;
+  if (G > 0) {
+    walk_warp_kernel<false><<<wg, wb, 0, s>>>(G, theta2, T, t->cnt_p.p, t->cnt_c.p, nullptr, nullptr, nullptr,
+                                              nullptr, t->stacks.p, t->err.p);
+    GT_CUDA(cudaGetLastError());
+  }
+  qg_status st = scan_excl(t, G, t->cnt_p.p, t->plist_off.p, s);
+  if (st != QG_OK) return st;
+  st = scan_excl(t, G, t->cnt_c.p, t->clist_off.p, s);
+  if (st != QG_OK) return st;
+  int herr = 0;
+  GT_CUDA(cudaMemcpyAsync(&tot[0], t->plist_off.p + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GT_CUDA(cudaMemcpyAsync(&tot[1], t->clist_off.p + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  GT_CUDA(cudaMemcpyAsync(&herr, t->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  GT_CUDA(cudaStreamSynchronize(s));
+  if (herr) return QG_ERR_STATE;
+  GT_CUDA(t->plist_idx.reserve(tot[0]));
+  GT_CUDA(t->clist_idx.reserve(tot[1]));
+  if (G > 0) {
+    walk_warp_kernel<true><<<wg, wb, 0, s>>>(G, theta2, T, t->cnt_p.p, t->cnt_c.p, t->plist_off.p, t->clist_off.p,
+                                             t->plist_idx.p, t->clist_idx.p, t->stacks.p, t->err.p);
+    GT_CUDA(cudaGetLastError());
+  }
+  return QG_OK;
+}
+
+// Single-pass walk; *done = false when a group outgrew its staging area (the
+// caller then walks in two passes; the staging areas are doubled for the
+// next walk).
+static qg_status walk_single_pass(qg_gtree *t, double theta2, const WalkTree &T, unsigned wg, int wb,
+                                  cudaStream_t s, int64_t tot[2], bool *done) {
+  const int64_t G = t->G, nw = (int64_t)wg * (wb / 32);
+  *done = false;
+  GT_CUDA(t->stage_p.reserve((size_t)(nw * t->stage_cap_p)));
+  GT_CUDA(t->stage_c.reserve((size_t)(nw * t->stage_cap_c)));
+  GT_CUDA(t->gstart_p.reserve(G));
+  GT_CUDA(t->gstart_c.reserve(G));
+  GT_CUDA(t->cursor.reserve(3));
+  int64_t want_p = std::max<int64_t>(1024, 48 * t->n), want_c = std::max<int64_t>(1024, 24 * t->n);
+  for (int attempt = 0; attempt < 2; attempt++) {
+    GT_CUDA(t->scratch_p.reserve((size_t)std::max<int64_t>(want_p, (int64_t)t->scratch_p.cap)));
+    GT_CUDA(t->scratch_c.reserve((size_t)std::max<int64_t>(want_c, (int64_t)t->scratch_c.cap)));
+    GT_CUDA(cudaMemsetAsync(t->cursor.p, 0, 3 * sizeof(unsigned long long), s));
+    GT_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(int), s));
+    walk_single_kernel<<<wg, wb, 0, s>>>(G, theta2, T, t->stage_p.p, t->stage_c.p, t->stage_cap_p, t->stage_cap_c,
+                                         t->scratch_p.p, t->scratch_c.p, (int64_t)t->scratch_p.cap,
+                                         (int64_t)t->scratch_c.cap, t->cursor.p, t->gstart_p.p, t->gstart_c.p,
+                                         t->cnt_p.p, t->cnt_c.p, t->stacks.p, t->err.p);
+    GT_CUDA(cudaGetLastError());
+    unsigned long long cur[3] = {0, 0, 0};
+    int herr = 0;
+    GT_CUDA(cudaMemcpyAsync(cur, t->cursor.p, sizeof(cur), cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaMemcpyAsync(&herr, t->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaStreamSynchronize(s));
+    if (herr & 1) return QG_ERR_STATE;
+    if (herr & 2) {  // a list longer than a staging area
+      t->stage_cap_p = std::min<int64_t>(t->stage_cap_p * 2, int64_t(1) << 24);
+      t->stage_cap_c = std::min<int64_t>(t->stage_cap_c * 2, int64_t(1) << 24);
+      return QG_OK;
+    }
+    tot[0] = (int64_t)cur[1];
+    tot[1] = (int64_t)cur[2];
+    if (herr & 4) {  // the scratch lists were too small: now the totals are known
+      want_p = tot[0] + tot[0] / 8 + 1024;
+      want_c = tot[1] + tot[1] / 8 + 1024;
+      continue;
+    }
+    qg_status st = scan_excl(t, G, t->cnt_p.p, t->plist_off.p, s);
+    if (st != QG_OK) return st;
+    st = scan_excl(t, G, t->cnt_c.p, t->clist_off.p, s);
+    if (st != QG_OK) return st;
+    GT_CUDA(t->plist_idx.reserve(tot[0]));
+    GT_CUDA(t->clist_idx.reserve(tot[1]));
+    lists_to_csr_kernel<<<wg, wb, 0, s>>>(G, t->gstart_p.p, t->plist_off.p, t->scratch_p.p, t->plist_idx.p);
+    lists_to_csr_kernel<<<wg, wb, 0, s>>>(G, t->gstart_c.p, t->clist_off.p, t->scratch_c.p, t->clist_idx.p);
+    GT_CUDA(cudaGetLastError());
+    *done = true;
+    return QG_OK;
+  }
+  return QG_OK;  // not reached: the second attempt has room for the exact totals
+}
+
 static qg_status walk_impl(qg_gtree *t, double theta, cudaStream_t s) {
   t->walked = false;
   const int64_t G = t->G;
@@ -1164,40 +1355,27 @@ static qg_status walk_impl(qg_gtree *t, double theta, cudaStream_t s) {
   GT_CUDA(t->plist_off.reserve(G + 1));
   GT_CUDA(t->clist_off.reserve(G + 1));
   GT_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(int), s));
-  // persistent warp grid: one stack per warp
+  // persistent warp grid: one stack (and staging area) per warp
   int sms = 0;
   GT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, t->device));
   const int wb = 128;
   const int64_t warps = std::min<int64_t>(std::max<int64_t>(G, 1), (int64_t)sms * 32);
   const unsigned wg = (unsigned)((warps * 32 + wb - 1) / wb);
   GT_CUDA(t->stacks.reserve((size_t)wg * (wb / 32) * kWarpStack));
-  if (G > 0) {
-    walk_warp_kernel<false><<<wg, wb, 0, s>>>(G, theta2, t->group_off.p, t->group_node.p, t->nsysid.p, t->sys_root.p,
-                                              t->xs.p, t->geom.p, t->topo.p, t->centre.p, t->side.p, t->com.p,
-                                              t->cnt_p.p, t->cnt_c.p, nullptr, nullptr, nullptr, nullptr, t->stacks.p,
-                                              t->err.p);
-    GT_CUDA(cudaGetLastError());
-  }
-  qg_status st = scan_excl(t, G, t->cnt_p.p, t->plist_off.p, s);
-  if (st != QG_OK) return st;
-  st = scan_excl(t, G, t->cnt_c.p, t->clist_off.p, s);
-  if (st != QG_OK) return st;
+  const WalkTree T{t->group_off.p, t->group_node.p, t->nsysid.p, t->sys_root.p, t->xs.p, t->geom.p,
+                   t->topo.p, t->centre.p, t->side.p, t->com.p};
   int64_t tot[2] = {0, 0};
-  int herr = 0;
-  GT_CUDA(cudaMemcpyAsync(&tot[0], t->plist_off.p + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  GT_CUDA(cudaMemcpyAsync(&tot[1], t->clist_off.p + G, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  GT_CUDA(cudaMemcpyAsync(&herr, t->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
-  GT_CUDA(cudaStreamSynchronize(s));
-  if (herr) return QG_ERR_STATE;
-  GT_CUDA(t->plist_idx.reserve(tot[0]));
-  GT_CUDA(t->clist_idx.reserve(tot[1]));
+  bool done = false;
   if (G > 0) {
-    walk_warp_kernel<true><<<wg, wb, 0, s>>>(G, theta2, t->group_off.p, t->group_node.p, t->nsysid.p, t->sys_root.p,
-                                             t->xs.p, t->geom.p, t->topo.p, t->centre.p, t->side.p, t->com.p,
-                                             t->cnt_p.p, t->cnt_c.p, t->plist_off.p, t->clist_off.p, t->plist_idx.p,
-                                             t->clist_idx.p, t->stacks.p, t->err.p);
-    GT_CUDA(cudaGetLastError());
+    const qg_status st = walk_single_pass(t, theta2, T, wg, wb, s, tot, &done);
+    if (st != QG_OK) return st;
   }
+  if (!done) {
+    GT_CUDA(cudaMemsetAsync(t->err.p, 0, sizeof(int), s));
+    const qg_status st = walk_two_pass(t, theta2, T, wg, wb, s, tot);
+    if (st != QG_OK) return st;
+  }
+  int herr = 0;
   GT_CUDA(cudaEventRecord(t->ev[3], s));
   GT_CUDA(cudaMemcpyAsync(&herr, t->err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   GT_CUDA(cudaStreamSynchronize(s));

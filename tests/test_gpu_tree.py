@@ -96,6 +96,30 @@ def test_gpu_tree_equals_host_builder(name, ps, leaf, ncrit, theta):
     t.close()
 
 
+@pytest.mark.parametrize("n", [3000, 40000])
+def test_walk_that_opens_everything(n):
+    """theta = 0 opens every node: each group's particle list is all n
+    particles.  Far more entries than the walk's first guess of the list
+    size (it walks again with the exact totals), and at n = 40000 longer
+    lists than a warp's staging area (it falls back to two passes); a later
+    walk of the same tree at theta 0.5 still matches the host."""
+    ps = workloads.small_set("plummer", n, 23, 1e-2)
+    h = qtree.Tree(ps.x, ps.m, ps.sys_off, 8, 64)
+    t = _gpu_tree(ps, 8, 64, 0.0)
+    L0 = h.walk(0.0)
+    assert t.sizes()["n_plist"] == len(L0.plist_idx) == h.ngroups * n
+    assert np.array_equal(t.host("plist_off"), L0.plist_off)
+    assert np.array_equal(_per_group_sorted(L0.plist_off, t.host("plist_idx")),
+                          _per_group_sorted(L0.plist_off, L0.plist_idx))
+    assert t.sizes()["n_clist"] == 0
+    t.walk(0.5)
+    L = h.walk(0.5)
+    assert np.array_equal(t.host("plist_off"), L.plist_off) and np.array_equal(t.host("clist_off"), L.clist_off)
+    assert np.array_equal(_per_group_sorted(L.plist_off, t.host("plist_idx")),
+                          _per_group_sorted(L.plist_off, L.plist_idx))
+    t.close()
+
+
 def test_gpu_built_step_matches_oracle_and_host_lists():
     import torch
     ps = workloads.small_set("plummer", 30000, 11, 1e-2)
