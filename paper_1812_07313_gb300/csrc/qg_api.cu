@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "qg_devbuf.h"
 #include "qg_internal.h"
 #include "qg_queue.cuh"
 #include "qgrav.h"
@@ -71,26 +72,7 @@ __global__ void check_index_kernel(int64_t cnt, const int32_t *__restrict__ idx,
 
 // ------------------------------------------------------------------ buffers
 
-template <typename T>
-struct DevBuf {
-  T *p = nullptr;
-  size_t cap = 0;  // elements
-  cudaError_t reserve(size_t n) {
-    if (n <= cap && p) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-    if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
-    if (e == cudaSuccess) cap = n;
-    return e;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-  }
-};
+using qg::DevBuf;
 
 }  // namespace
 

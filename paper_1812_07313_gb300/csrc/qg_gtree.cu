@@ -14,6 +14,7 @@
 #include <new>
 #include <vector>
 
+#include "qg_devbuf.h"
 #include "qg_gtree.h"
 #include "qgrav.h"
 
@@ -24,39 +25,7 @@ constexpr int kScanThreads = 256, kScanItems = 4, kScanTile = kScanThreads * kSc
 constexpr int kSortThreads = 256, kSortItems = 8, kSortTile = kSortThreads * kSortItems;
 
 template <typename T>
-struct DBuf {
-  T *p = nullptr;
-  size_t cap = 0;
-  cudaError_t reserve(size_t n) {
-    if (n <= cap && p) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-    if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
-    if (e == cudaSuccess) cap = n;
-    return e;
-  }
-  // grow keeping the first `keep` elements
-  cudaError_t grow(size_t n, size_t keep, cudaStream_t s) {
-    if (n <= cap && p) return cudaSuccess;
-    size_t c = std::max(n, cap * 2);
-    T *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, c * sizeof(T));
-    if (e != cudaSuccess) return e;
-    if (keep && p) e = cudaMemcpyAsync(q, p, keep * sizeof(T), cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (p) cudaFree(p);
-    p = q;
-    cap = c;
-    return e;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-  }
-};
+using DBuf = qg::DevBuf<T>;
 
 int blocks_for(int64_t n, int per_block) {
   const int64_t b = (n + per_block - 1) / per_block;

@@ -11,6 +11,7 @@
 #include <new>
 #include <vector>
 
+#include "qg_devbuf.h"
 #include "qg_gtree.h"
 #include "qg_sim.h"
 #include "qgrav.h"
@@ -18,25 +19,7 @@
 namespace {
 
 template <typename T>
-struct Buf {
-  T *p = nullptr;
-  size_t cap = 0;
-  cudaError_t reserve(size_t n) {
-    if (n <= cap && p) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-    if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
-    if (e == cudaSuccess) cap = n;
-    return e;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-  }
-};
+using Buf = qg::DevBuf<T>;
 
 constexpr int kThreads = 256;
 constexpr int kRedBlocks = 592;  // fixed, so that the energy sums have a fixed order
