@@ -67,8 +67,9 @@ def parse():
                     help="also time the all-FP64 and the uncentred FP32 kernels and report their differences")
     ap.add_argument("--group-sizes", default=None,
                     help="candidate n_crit values (comma separated): time the step for each and use the fastest")
-    ap.add_argument("--gpu-tree", action="store_true",
-                    help="also time the tree build, moments, groups and walk on the GPU (whole step on the device)")
+    ap.add_argument("--no-gpu-tree", action="store_true",
+                    help="skip timing the tree build, moments, groups and walk on the GPU (whole step on the device)")
+    ap.add_argument("--gpu-tree", action="store_true", help=argparse.SUPPRESS)  # the default; kept for old commands
     ap.add_argument("--launch", default=None,
                     help="R,W,T[,x1|x2]: fixed sinks/thread, warps/CTA, tile (and scalar or paired FP32) "
                          "instead of the autotuner (profiling)")
@@ -413,7 +414,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and args.batching_compare and ps.nsys > 1:
         out["batching"] = batching_compare(torch, qgrav, tr, L, eps2_all, eps2, stream, flush,
                                            float(np.mean(step_ms)))
-    if rank == 0 and args.gpu_tree:
+    if rank == 0 and not args.no_gpu_tree:
         out["gpu_tree"] = gpu_tree_step(torch, qgrav, ps, wl, tr, L, eps2_all, eps2, stream)
     if rank == 0 and args.precision_compare:
         out["precision"] = precision_compare(torch, qgrav, ctx, tr, L, eps2_all, eps2, stream, flush)

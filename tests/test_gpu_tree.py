@@ -164,6 +164,39 @@ def test_gpu_built_step_matches_oracle_and_host_lists():
     t.close()
 
 
+@pytest.mark.parametrize("name", ["cube_1m", "plummer_4m"])
+def test_full_size_gpu_built_step_sampled(name):
+    """The whole step on the GPU at full size (tree, moments, groups, walk,
+    force kernel), against the oracle on the GPU's own lists for sampled
+    groups (the largest and the longest-listed among them)."""
+    import torch
+    wl = workloads.WORKLOADS[name]
+    ps = wl.particles()
+    eps2 = float(ps.eps[0]) ** 2
+    t = gtree.GpuTree(0)
+    t.build(torch.as_tensor(ps.x).cuda(), torch.as_tensor(ps.m).cuda(), ps.sys_off, wl.leaf_max, wl.n_crit)
+    t.walk(wl.theta)
+    ctx = qgrav.Context(0)
+    t.attach(ctx, eps2)
+    ctx.qg_autotune(None, reps=1)
+    ctx.qg_run()
+    a, phi = ctx.qg_get_forces()
+    ctx.close()
+    h = {k: t.host(k) for k in ("group_off", "xs", "ms", "plist_off", "plist_idx", "cell_com", "cell_m", "cell_q",
+                                "clist_off", "clist_idx")}
+    t.close()
+    G = len(h["group_off"]) - 1
+    ni = np.diff(h["group_off"])
+    nl = np.diff(h["plist_off"]) + np.diff(h["clist_off"])
+    rng = np.random.default_rng(4)
+    groups = np.array(sorted(set(rng.choice(G, 46, replace=False).tolist()) | {int(np.argmax(ni)), int(np.argmax(nl))}))
+    a_ref, phi_ref = oracle.expansion_forces(h["group_off"], h["xs"], h["xs"], h["ms"], h["plist_off"],
+                                             h["plist_idx"], h["cell_com"], h["cell_m"], h["cell_q"],
+                                             h["clist_off"], h["clist_idx"], eps2_all=eps2, groups=groups)
+    sinks = np.concatenate([np.arange(h["group_off"][g], h["group_off"][g + 1]) for g in groups])
+    assert_parity(a[sinks], phi[sinks], a_ref[sinks], phi_ref[sinks], label="%s gpu-built" % name)
+
+
 def test_gpu_tree_rejects_bad_arguments():
     import torch
     t = gtree.GpuTree(0)
