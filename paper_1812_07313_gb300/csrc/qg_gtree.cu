@@ -336,38 +336,65 @@ __global__ void psys_kernel(int64_t n, int64_t nsys, const int64_t *__restrict__
 }
 
 // per-system min / max of every coordinate (ordered integer encodings)
-__global__ void bbox_kernel(int64_t n, const double *__restrict__ x, const int32_t *__restrict__ psys,
+// Per-system bounding box (ordered-integer min / max).  Each warp scans one
+// contiguous chunk and keeps a running box while the system does not change
+// (systems are contiguous ranges), so the atomics are one set per warp and
+// system met instead of one per 32 particles.
+__global__ void bbox_kernel(int64_t n, int64_t chunk, const double *__restrict__ x, const int32_t *__restrict__ psys,
                             unsigned long long *bmin, unsigned long long *bmax) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
-    const int64_t i = base + lane;
-    const bool valid = i < n;
-    const int s = valid ? psys[i] : -1;
-    const int s0 = __shfl_sync(0xffffffffu, s, 0);
-    const bool uniform = __all_sync(0xffffffffu, !valid || s == s0);
-    for (int d = 0; d < 3; d++) {
-      unsigned long long kmn = valid ? ordered(x[3 * i + d]) : ~0ull;
-      unsigned long long kmx = valid ? kmn : 0ull;
-      if (uniform) {
+  const int64_t b0 = warp * chunk, b1 = min(n, b0 + chunk);
+  int cur = -1;
+  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+  auto flush = [&]() {
+    if (cur < 0) return;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const unsigned long long a = __shfl_xor_sync(0xffffffffu, kmn, o);
-          const unsigned long long b = __shfl_xor_sync(0xffffffffu, kmx, o);
-          kmn = a < kmn ? a : kmn;
-          kmx = b > kmx ? b : kmx;
-        }
-        if (lane == 0) {
-          atomicMin(&bmin[3 * s0 + d], kmn);
-          atomicMax(&bmax[3 * s0 + d], kmx);
-        }
-      } else if (valid) {
-        atomicMin(&bmin[3 * s + d], kmn);
-        atomicMax(&bmax[3 * s + d], kmx);
+    for (int d = 0; d < 3; d++) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn[d], o);
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, mx[d], o);
+        mn[d] = a < mn[d] ? a : mn[d];
+        mx[d] = b > mx[d] ? b : mx[d];
       }
+      if (lane == 0) {
+        atomicMin(&bmin[3 * cur + d], mn[d]);
+        atomicMax(&bmax[3 * cur + d], mx[d]);
+      }
+      mn[d] = ~0ull;
+      mx[d] = 0ull;
+    }
+  };
+  for (int64_t base = b0; base < b1; base += 32) {
+    const int64_t i = base + lane;
+    const bool valid = i < b1;
+    const int sy = valid ? psys[i] : -1;
+    const int s0 = __shfl_sync(0xffffffffu, sy, 0);
+    if (__all_sync(0xffffffffu, !valid || sy == s0)) {
+      if (s0 != cur) {
+        flush();
+        cur = s0;
+      }
+      if (valid)
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          const unsigned long long k = ordered(x[3 * i + d]);
+          mn[d] = k < mn[d] ? k : mn[d];
+          mx[d] = k > mx[d] ? k : mx[d];
+        }
+    } else {  // a system boundary inside these 32 particles
+      flush();
+      cur = -1;
+      if (valid)
+        for (int d = 0; d < 3; d++) {
+          const unsigned long long k = ordered(x[3 * i + d]);
+          atomicMin(&bmin[3 * sy + d], k);
+          atomicMax(&bmax[3 * sy + d], k);
+        }
     }
   }
+  flush();
 }
 
 __global__ void fill_ull_kernel(int64_t n, unsigned long long *p, unsigned long long v) {
@@ -486,7 +513,7 @@ __global__ void finish_children_kernel(int32_t lo, int32_t hi, int64_t *__restri
 
 // ------------------------------------------------------------------ moments (Eq. 2)
 
-__global__ void moments_kernel(int32_t lo, int32_t hi, const int64_t *__restrict__ nbeg,
+__global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64_t *__restrict__ nbeg,
                                const int64_t *__restrict__ nend, const int32_t *__restrict__ nfirst,
                                const int32_t *__restrict__ nnchild, const double *__restrict__ xs,
                                const double *__restrict__ ms, double *__restrict__ com, double *__restrict__ mass,
@@ -496,6 +523,7 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, const int64_t *__restrict
     double M = 0.0, c0 = 0.0, c1 = 0.0, c2 = 0.0;
     double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0, q4 = 0.0, q5 = 0.0;
     const int nc = nnchild[j];
+    if ((nc != 0) != (internal != 0)) continue;
     if (nc == 0) {
       const int64_t b = nbeg[j], e = nend[j];
       for (int64_t i = b; i < e; i++) {
@@ -1028,7 +1056,11 @@ static qg_status build_impl(qg_gtree *t, int64_t n, const double *x, const doubl
   fill_ull_kernel<<<grid1(3 * nsys), 256, 0, s>>>(3 * nsys, t->bmax.p, 0ull);
   GT_CUDA(cudaGetLastError());
   if (n > 0) {
-    bbox_kernel<<<grid1(n), 256, 0, s>>>(n, x, t->psys.p, t->bmin.p, t->bmax.p);
+    int sms = 0;
+    GT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, t->device));
+    const int64_t bw = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 32, (n + 1023) / 1024));
+    const int64_t chunk = ((n + bw - 1) / bw + 31) / 32 * 32;
+    bbox_kernel<<<(unsigned)((bw + 7) / 8), 256, 0, s>>>(n, chunk, x, t->psys.p, t->bmin.p, t->bmax.p);
     GT_CUDA(cudaGetLastError());
   }
   // per system cube on the host, the host builder's expressions exactly
@@ -1170,10 +1202,17 @@ static qg_status build_impl(qg_gtree *t, int64_t n, const double *x, const doubl
   GT_CUDA(t->q.reserve(6 * nn));
   GT_CUDA(t->side.reserve(nn));
   GT_CUDA(t->range.reserve(2 * nn));
+  // every leaf at once (their moments come from particles only), then the
+  // internal nodes level by level, deepest first
+  if (nn > 0)
+    moments_kernel<<<grid1(nn), 256, 0, s>>>(0, (int32_t)nn, 0, t->nbeg.p, t->nend.p, t->nfirst.p, t->nnchild.p,
+                                             t->xs.p, t->ms.p, t->com.p, t->mass.p, t->q.p, t->side.p, t->half.p,
+                                             t->range.p);
+  GT_CUDA(cudaGetLastError());
   for (int l = (int)t->level_begin.size() - 2; l >= 0; l--) {
     const int64_t a = t->level_begin[l], b = t->level_begin[l + 1];
-    if (b > a)
-      moments_kernel<<<grid1(b - a), 256, 0, s>>>((int32_t)a, (int32_t)b, t->nbeg.p, t->nend.p, t->nfirst.p,
+    if (b > a && l + 2 < (int)t->level_begin.size())  // the deepest level holds leaves only
+      moments_kernel<<<grid1(b - a), 256, 0, s>>>((int32_t)a, (int32_t)b, 1, t->nbeg.p, t->nend.p, t->nfirst.p,
                                                   t->nnchild.p, t->xs.p, t->ms.p, t->com.p, t->mass.p, t->q.p,
                                                   t->side.p, t->half.p, t->range.p);
     GT_CUDA(cudaGetLastError());
