@@ -605,13 +605,18 @@ KERNEL_SOURCES = ("qg_force.cuh", "qg_force_f32.cu", "qg_internal.h")
 
 
 def kernel_hash():
-    """Hash of the sources the FP32 force kernel is compiled from: a recorded
-    DRAM traffic figure is used only while it matches."""
+    """Hash of the sources the FP32 force kernel is compiled from, comments and
+    blank space removed: a recorded DRAM traffic figure is used only while
+    the code it was measured on is unchanged."""
     import hashlib
+    import re
     h = hashlib.sha1()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1812_07313_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1812_07313_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:12]
 
 

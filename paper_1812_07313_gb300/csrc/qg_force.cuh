@@ -196,16 +196,14 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 // Launch bounds per variant: the largest block it is launched with and the
-// CTAs per SM the register budget must allow.  Scalar R <= 4 is held to 64
-// registers (8 CTAs of 128 threads per SM); the paired R = 4 form carries
-// twice the j-entry registers and gets up to 128; R = 8 keeps 8 sinks x 4 sums in
-// registers and is limited to 128 threads; the all-FP64 comparison form gets
-// up to 128 registers.
+// CTAs per SM the register budget must allow.  Scalar R <= 4: 3 blocks of 256
+// threads leaves 80 registers a thread (72 used at R = 2), which still fits
+// the six 128-thread CTAs that shared memory allows per SM (64 registers
+// measured 2-3 % slower); the paired R = 4 form carries twice the j-entry
+// registers and gets up to 128; R = 8 keeps 8 sinks x 4 sums in registers and
+// is limited to 128 threads; the all-FP64 comparison form gets up to 128.
 template <typename Real, int R, bool PAIRED> struct Bounds {
   static constexpr int threads = R >= 8 ? 128 : 256;
-  // R <= 4 scalar FP32: 3 blocks of 256 threads leaves 80 registers a thread
-  // (72 at R = 2), which still fits the six 128-thread CTAs that shared
-  // memory allows per SM; 4 blocks (64 registers) measured 2-3 % slower
   static constexpr int min_blocks = (R >= 8 || sizeof(Real) == 8 || (PAIRED && R >= 4)) ? 2 : 3;
 };
 
