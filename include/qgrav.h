@@ -179,6 +179,26 @@ qg_status qg_get_forces(qg_ctx *ctx, double *a, double *phi);
 /* Device-to-device copy of the results into caller buffers on `cuda_stream`. */
 qg_status qg_get_forces_dev(qg_ctx *ctx, double *a, double *phi, void *cuda_stream);
 
+/*
+ * One evaluation from HOST arrays: the inputs of qg_set_sinks, qg_set_sources
+ * and qg_set_cells (same meaning, layout and checks), then the forces written
+ * to a [n][3] and phi [n] (host).  The sinks, sources and cells are copied
+ * first; the particle and cell lists follow in four chunks of groups on a
+ * second stream while the force kernel runs over the chunks already copied,
+ * and each chunk's results are copied back as soon as its kernel ends.  When
+ * src_x is the same array as sink_x (and ns == n) it is copied once.  The
+ * results are bit for bit those of the separate calls at the same options.
+ * Afterwards the context holds these inputs (qg_run, qg_get_forces,
+ * qg_autotune, qg_last_timing work on them).  Synchronous.  A list entry
+ * outside [0, ns) or [0, nc) gives QG_ERR_ARG; the kernel reads a valid
+ * record in its place, so nothing is read out of bounds.
+ */
+qg_status qg_evaluate_host(qg_ctx *ctx, int64_t n, const double *sink_x, const float *sink_eps2, double eps2_all,
+                           int64_t ngroups, const int64_t *group_off, int64_t ns, const double *src_x,
+                           const double *src_m, const int64_t *plist_off, const int32_t *plist_idx, int64_t nc,
+                           const double *cell_com, const double *cell_m, const double *cell_q,
+                           const int64_t *clist_off, const int32_t *clist_idx, double *a, double *phi);
+
 qg_status qg_get_stats(const qg_ctx *ctx, qg_stats *out);
 
 /*

@@ -62,6 +62,19 @@ __global__ void pack_cells_kernel(int64_t nc, const double *__restrict__ com, co
   }
 }
 
+// Index check that also makes the list safe to read: an entry outside
+// [0, n) is counted in *bad and replaced by 0 (a kernel already queued behind
+// this one then reads a valid record, and its caller fails with QG_ERR_ARG).
+__global__ void sanitize_index_kernel(int64_t cnt, int32_t *__restrict__ idx, int64_t n, int *bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = idx[i];
+    if (v < 0 || (int64_t)v >= n) {
+      atomicOr(bad, 1);
+      idx[i] = 0;
+    }
+  }
+}
+
 // Index check of a device list: sets *bad when an entry is outside [0, n).
 __global__ void check_index_kernel(int64_t cnt, const int32_t *__restrict__ idx, int64_t n, int *bad) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
@@ -123,6 +136,11 @@ struct qg_ctx {
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   bool graph_valid = false;
+  bool timed = false;  // ev[] hold the last run's step / force times
+  // qg_evaluate_host: streams for the copies in and out, events per chunk
+  cudaStream_t copy_in = nullptr, copy_out = nullptr, chunk_stream[4] = {};
+  cudaEvent_t chunk_in[8] = {}, chunk_done[8] = {}, inputs_ready = nullptr, packed = nullptr;
+  DevBuf<double> stage_src;  // source positions when they are not the sinks' array
   qg_stats stats{};
   // chosen launch
   const void *kernel = nullptr;
@@ -168,6 +186,7 @@ void invalidate(qg_ctx *c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);
   c->exec = nullptr;
   c->graph_valid = false;
+  c->timed = false;
 }
 
 bool valid_options(const qg_options &o, std::string &why) {
@@ -264,6 +283,37 @@ qg_status choose_kernel(qg_ctx *c) {
   return QG_OK;
 }
 
+// Kernel parameters for groups [g0, g0 + G): the offset arrays and the queue
+// are passed from g0 on, so the queue's (relative) group numbers index them
+// directly; sink, list and output positions stay absolute.
+qg::ForceParams force_params(qg_ctx *c, int64_t g0, int64_t G, int *head) {
+  qg::ForceParams p{};
+  p.sink_x = c->sink_x.p;
+  p.sink_eps2 = c->has_eps2 ? c->sink_eps2.p : nullptr;
+  p.eps2_all = c->eps2_all;
+  p.group_off = c->goff.p + g0;
+  p.src = c->src.p;
+  p.src_m64 = c->src_m64.p;
+  p.plist_off = c->poff.p + g0;
+  p.plist_idx = c->pidx.p;
+  p.cell_pm = c->cell_pm.p;
+  p.cell_m64 = c->cell_m64.p;
+  p.cell_q = c->cell_q.p;
+  p.cell_q64 = c->cell_q64.p;
+  p.clist_off = c->coff.p + g0;
+  p.clist_idx = c->cidx.p;
+  p.queue = c->queue.p + g0;
+  p.nitems = (int32_t)G;
+  p.head = head;
+  p.a = c->a.p;
+  p.phi = c->phi.p;
+  p.tile = c->tile;
+  p.flush_j = c->flush;
+  p.zero = 0.0f;
+  p.one = 1.0f;
+  return p;
+}
+
 // Record the queue build and the persistent force launch on stream s.
 qg_status record_step(qg_ctx *c, cudaStream_t s) {
   const int64_t G = c->G;
@@ -276,30 +326,7 @@ qg_status record_step(qg_ctx *c, cudaStream_t s) {
   QG_CUDA(c, cudaGetLastError());
   queue_scatter_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->bucket.p, hist, cursor, c->queue.p);
   QG_CUDA(c, cudaGetLastError());
-  qg::ForceParams p{};
-  p.sink_x = c->sink_x.p;
-  p.sink_eps2 = c->has_eps2 ? c->sink_eps2.p : nullptr;
-  p.eps2_all = c->eps2_all;
-  p.group_off = c->goff.p;
-  p.src = c->src.p;
-  p.src_m64 = c->src_m64.p;
-  p.plist_off = c->poff.p;
-  p.plist_idx = c->pidx.p;
-  p.cell_pm = c->cell_pm.p;
-  p.cell_m64 = c->cell_m64.p;
-  p.cell_q = c->cell_q.p;
-  p.cell_q64 = c->cell_q64.p;
-  p.clist_off = c->coff.p;
-  p.clist_idx = c->cidx.p;
-  p.queue = c->queue.p;
-  p.nitems = (int32_t)G;
-  p.head = head;
-  p.a = c->a.p;
-  p.phi = c->phi.p;
-  p.tile = c->tile;
-  p.flush_j = c->flush;
-  p.zero = 0.0f;
-  p.one = 1.0f;
+  qg::ForceParams p = force_params(c, 0, G, head);
   const int grid = (int)std::min<int64_t>(c->grid, std::max<int64_t>(G, 1));
   c->stats.grid = grid;
   void *args[] = {&p};
@@ -433,6 +460,19 @@ void qg_destroy(qg_ctx *c) {
   c->a.release(); c->phi.release(); c->scratch.release(); c->bucket.release(); c->queue.release();
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
+  for (int k = 0; k < 8; k++) {
+    if (c->chunk_in[k]) cudaEventDestroy(c->chunk_in[k]);
+    if (c->chunk_done[k]) cudaEventDestroy(c->chunk_done[k]);
+  }
+  if (c->inputs_ready) cudaEventDestroy(c->inputs_ready);
+  if (c->packed) cudaEventDestroy(c->packed);
+  c->stage_src.release();
+  for (cudaStream_t t : {c->copy_in, c->copy_out, c->chunk_stream[0], c->chunk_stream[1], c->chunk_stream[2],
+                         c->chunk_stream[3]})
+    if (t) {
+      cudaStreamSynchronize(t);
+      cudaStreamDestroy(t);
+    }
   if (c->stream) cudaStreamDestroy(c->stream);
   delete c;
 }
@@ -669,6 +709,7 @@ qg_status qg_run(qg_ctx *c, void *stream) {
   if (st != QG_OK) return st;
   QG_CUDA(c, cudaGraphLaunch(c->exec, s));
   c->ran = true;
+  c->timed = true;
   return QG_OK;
 }
 
@@ -771,11 +812,198 @@ qg_status qg_autotune(qg_ctx *c, void *stream, int reps, qg_options *best, float
 
 qg_status qg_last_timing(qg_ctx *c, float *step_ms, float *force_ms) {
   if (!c) return QG_ERR_ARG;
-  if (!c->ran || !c->graph_valid) return fail(c, QG_ERR_STATE, "qg_last_timing: no timed run");
+  if (!c->ran || !c->timed) return fail(c, QG_ERR_STATE, "qg_last_timing: no timed run");
   DeviceGuard dg(c->device);
   QG_CUDA(c, cudaStreamSynchronize(c->last_stream));
   if (step_ms) QG_CUDA(c, cudaEventElapsedTime(step_ms, c->ev[0], c->ev[2]));
   if (force_ms) QG_CUDA(c, cudaEventElapsedTime(force_ms, c->ev[1], c->ev[2]));
+  return QG_OK;
+}
+
+// One evaluation from host arrays with the list copies overlapped: the
+// sinks, sources and cells are copied (and packed) first, the two lists
+// follow in chunks of groups on a second stream while the force kernel runs
+// on the chunks already there, and each chunk's results are copied back on a
+// third stream as soon as its kernel ends.
+qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const float *sink_eps2, double eps2_all,
+                           int64_t ngroups, const int64_t *group_off, int64_t ns, const double *src_x,
+                           const double *src_m, const int64_t *plist_off, const int32_t *plist_idx, int64_t nc,
+                           const double *cell_com, const double *cell_m, const double *cell_q,
+                           const int64_t *clist_off, const int32_t *clist_idx, double *a, double *phi) {
+  if (!c) return QG_ERR_ARG;
+  constexpr int kChunks = 4;
+  // inputs must not change under a step that is still running
+  if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+  c->sinks_ok = c->src_ok = c->cells_ok = false;
+  c->ran = false;
+  invalidate(c);
+  // ---- host-side checks (the same as the qg_set_* calls)
+  if (n < 0 || ngroups < 0 || ngroups >= INT32_MAX || !group_off || (n > 0 && (!sink_x || !a || !phi)))
+    return fail(c, QG_ERR_ARG, "qg_evaluate_host: bad sink sizes or NULL pointer");
+  if (!std::isfinite(eps2_all) || eps2_all < 0) return fail(c, QG_ERR_ARG, "qg_evaluate_host: eps2_all must be >= 0");
+  if (ns < 0 || ns >= INT32_MAX || !plist_off || (ns > 0 && (!src_x || !src_m)))
+    return fail(c, QG_ERR_ARG, "qg_evaluate_host: bad source sizes or NULL pointer");
+  if (nc < 0 || nc >= INT32_MAX || !clist_off || (nc > 0 && (!cell_com || !cell_m || !cell_q)))
+    return fail(c, QG_ERR_ARG, "qg_evaluate_host: bad cell sizes or NULL pointer");
+  const int64_t G = ngroups;
+  if (!valid_offsets(group_off, G, n)) return fail(c, QG_ERR_ARG, "qg_evaluate_host: bad group offsets");
+  if (!valid_offsets_any_total(plist_off, G) || !valid_offsets_any_total(clist_off, G))
+    return fail(c, QG_ERR_ARG, "qg_evaluate_host: bad list offsets");
+  const int64_t np_tot = plist_off[G], nc_tot = clist_off[G];
+  if ((np_tot > 0 && !plist_idx) || (nc_tot > 0 && !clist_idx))
+    return fail(c, QG_ERR_ARG, "qg_evaluate_host: list_idx is NULL");
+  bool pos = eps2_all > 0;
+  if (sink_eps2) {
+    pos = true;
+    for (int64_t i = 0; i < n; i++) {
+      if (!(sink_eps2[i] >= 0.f) || !std::isfinite(sink_eps2[i]))
+        return fail(c, QG_ERR_ARG, "qg_evaluate_host: eps2[%lld] invalid", (long long)i);
+      if (!(sink_eps2[i] > 0.f)) pos = false;
+    }
+  }
+  DeviceGuard dg(c->device);
+  cudaStream_t s = c->stream;
+  if (!c->copy_in) QG_CUDA(c, cudaStreamCreateWithFlags(&c->copy_in, cudaStreamNonBlocking));
+  if (!c->copy_out) QG_CUDA(c, cudaStreamCreateWithFlags(&c->copy_out, cudaStreamNonBlocking));
+  if (!c->inputs_ready) QG_CUDA(c, cudaEventCreateWithFlags(&c->inputs_ready, cudaEventDisableTiming));
+  if (!c->packed) QG_CUDA(c, cudaEventCreateWithFlags(&c->packed, cudaEventDisableTiming));
+  for (int k = 0; k < kChunks; k++) {
+    if (!c->chunk_stream[k]) QG_CUDA(c, cudaStreamCreateWithFlags(&c->chunk_stream[k], cudaStreamNonBlocking));
+    if (!c->chunk_in[k]) QG_CUDA(c, cudaEventCreateWithFlags(&c->chunk_in[k], cudaEventDisableTiming));
+    if (!c->chunk_done[k]) QG_CUDA(c, cudaEventCreateWithFlags(&c->chunk_done[k], cudaEventDisableTiming));
+  }
+  c->n = n;
+  c->G = G;
+  c->has_eps2 = sink_eps2 != nullptr;
+  c->eps2_all = eps2_all;
+  c->eps_positive = pos;
+  qg_status st = choose_kernel(c);
+  if (st != QG_OK) return st;
+  // ---- outputs, queue and per-chunk scratch (hist, cursor, head, bad);
+  // allocations first, before any copy is queued
+  constexpr int kScr = 2 * kBuckets + 2;
+  cudaError_t e;
+  if ((e = c->scratch.reserve(kChunks * kScr)) != cudaSuccess || (e = c->bucket.reserve(G)) != cudaSuccess ||
+      (e = c->queue.reserve(G)) != cudaSuccess || (e = c->a.reserve(3 * std::max<int64_t>(n, 1))) != cudaSuccess ||
+      (e = c->phi.reserve(std::max<int64_t>(n, 1))) != cudaSuccess || (e = c->pidx.reserve(np_tot)) != cudaSuccess ||
+      (e = c->cidx.reserve(nc_tot)) != cudaSuccess)
+    return fail(c, QG_ERR_NOMEM, "device allocation: %s", cudaGetErrorString(e));
+  // ---- sinks, sources and cells: every host-to-device copy goes on one
+  // stream (copy_in), these first and the list chunks after them, so the
+  // copy engine takes them in that order; the packing waits for them on s.
+  // One copy of x when the sinks are the sources.
+  cudaStream_t ci_s = c->copy_in;
+  if ((st = upload(c, c->sink_x, sink_x, 3 * n, ci_s)) != QG_OK) return st;
+  if (sink_eps2 && (st = upload(c, c->sink_eps2, sink_eps2, n, ci_s)) != QG_OK) return st;
+  if ((st = upload(c, c->goff, group_off, G + 1, ci_s)) != QG_OK) return st;
+  if ((st = upload(c, c->poff, plist_off, G + 1, ci_s)) != QG_OK) return st;
+  if ((st = upload(c, c->coff, clist_off, G + 1, ci_s)) != QG_OK) return st;
+  if ((st = upload(c, c->src_m64, src_m, ns, ci_s)) != QG_OK) return st;
+  const bool same_x = src_x == sink_x && ns == n;
+  if (!same_x && (st = upload(c, c->stage_src, src_x, 3 * ns, ci_s)) != QG_OK) return st;
+  if ((st = upload(c, c->stage_x, cell_com, 3 * nc, ci_s)) != QG_OK) return st;
+  if ((st = upload(c, c->cell_m64, cell_m, nc, ci_s)) != QG_OK) return st;
+  if (c->cell_pm.reserve(nc) != cudaSuccess || c->cell_q.reserve(2 * nc) != cudaSuccess ||
+      c->cell_q64.reserve(6 * nc) != cudaSuccess || c->src.reserve(ns) != cudaSuccess)
+    return fail(c, QG_ERR_NOMEM, "source or cell allocation");
+  if ((st = upload(c, c->cell_q64, cell_q, 6 * nc, ci_s)) != QG_OK) return st;
+  QG_CUDA(c, cudaEventRecord(c->inputs_ready, ci_s));
+  QG_CUDA(c, cudaStreamWaitEvent(s, c->inputs_ready, 0));
+  if (ns)
+    pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, same_x ? c->sink_x.p : c->stage_src.p, c->src_m64.p,
+                                                      c->src.p);
+  if (nc)
+    pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, c->stage_x.p, c->cell_m64.p, c->cell_q64.p,
+                                                         c->cell_pm.p, c->cell_q.p, c->cell_q64.p);
+  QG_CUDA(c, cudaGetLastError());
+  QG_CUDA(c, cudaMemsetAsync(c->scratch.p, 0, kChunks * kScr * sizeof(int), s));
+  QG_CUDA(c, cudaEventRecord(c->ev[0], s));
+  QG_CUDA(c, cudaEventRecord(c->packed, s));
+  // ---- chunks of groups with about equal list entries
+  int64_t gb[kChunks + 1];
+  gb[0] = 0;
+  {
+    const int64_t total = np_tot + nc_tot;
+    int64_t g = 0;
+    for (int k = 1; k < kChunks; k++) {
+      const int64_t want = total / kChunks * k;
+      while (g < G && plist_off[g] + clist_off[g] < want) g++;
+      gb[k] = g;
+    }
+    gb[kChunks] = G;
+  }
+  for (int k = 0; k < kChunks; k++) {
+    const int64_t g0 = gb[k], g1 = gb[k + 1];
+    const int64_t p0 = plist_off[g0], p1 = plist_off[g1], c0 = clist_off[g0], c1 = clist_off[g1];
+    if (p1 > p0)
+      QG_CUDA(c, cudaMemcpyAsync(c->pidx.p + p0, plist_idx + p0, (p1 - p0) * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, c->copy_in));
+    if (c1 > c0)
+      QG_CUDA(c, cudaMemcpyAsync(c->cidx.p + c0, clist_idx + c0, (c1 - c0) * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, c->copy_in));
+    QG_CUDA(c, cudaEventRecord(c->chunk_in[k], c->copy_in));
+  }
+  // each chunk on its own stream, so that a chunk's kernel fills the SMs its
+  // predecessor's last groups leave idle
+  const double cell_ops = c->opt.expansion == QG_QUAD ? 33.0 : 13.0;
+  for (int k = 0; k < kChunks; k++) {
+    const int64_t g0 = gb[k], g1 = gb[k + 1], Gk = g1 - g0;
+    int *hist = c->scratch.p + k * kScr, *cursor = hist + kBuckets, *head = cursor + kBuckets, *bad = head + 1;
+    cudaStream_t sk = c->chunk_stream[k];
+    QG_CUDA(c, cudaStreamWaitEvent(sk, c->packed, 0));
+    QG_CUDA(c, cudaStreamWaitEvent(sk, c->chunk_in[k], 0));
+    if (Gk > 0) {
+      const int64_t p0 = plist_off[g0], p1 = plist_off[g1], c0 = clist_off[g0], c1 = clist_off[g1];
+      if (p1 > p0) sanitize_index_kernel<<<grid_for(p1 - p0, 256), 256, 0, sk>>>(p1 - p0, c->pidx.p + p0, ns, bad);
+      if (c1 > c0) sanitize_index_kernel<<<grid_for(c1 - c0, 256), 256, 0, sk>>>(c1 - c0, c->cidx.p + c0, nc, bad);
+      queue_hist_kernel<<<grid_for(Gk, 256), 256, 0, sk>>>(Gk, c->goff.p + g0, c->poff.p + g0, c->coff.p + g0,
+                                                           cell_ops, c->bucket.p + g0, hist);
+      queue_scatter_kernel<<<grid_for(Gk, 256), 256, 0, sk>>>(Gk, c->bucket.p + g0, hist, cursor, c->queue.p + g0);
+      QG_CUDA(c, cudaGetLastError());
+      qg::ForceParams fp = force_params(c, g0, Gk, head);
+      const int grid = (int)std::min<int64_t>(c->grid, Gk);
+      void *args[] = {&fp};
+      if (k == 0) QG_CUDA(c, cudaEventRecord(c->ev[1], sk));
+      QG_CUDA(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(c->nthreads), args, c->smem, sk));
+    } else if (k == 0) {
+      QG_CUDA(c, cudaEventRecord(c->ev[1], sk));
+    }
+    QG_CUDA(c, cudaEventRecord(c->chunk_done[k], sk));
+    QG_CUDA(c, cudaStreamWaitEvent(s, c->chunk_done[k], 0));
+    // results of this chunk's sinks back to the host
+    const int64_t s0 = group_off[g0], s1 = group_off[g1];
+    QG_CUDA(c, cudaStreamWaitEvent(c->copy_out, c->chunk_done[k], 0));
+    if (s1 > s0) {
+      QG_CUDA(c, cudaMemcpyAsync(a + 3 * s0, c->a.p + 3 * s0, 3 * (s1 - s0) * sizeof(double),
+                                 cudaMemcpyDeviceToHost, c->copy_out));
+      QG_CUDA(c, cudaMemcpyAsync(phi + s0, c->phi.p + s0, (s1 - s0) * sizeof(double), cudaMemcpyDeviceToHost,
+                                 c->copy_out));
+    }
+  }
+  QG_CUDA(c, cudaEventRecord(c->ev[2], s));
+  c->stats.grid = (int)std::min<int64_t>(c->grid, std::max<int64_t>(G, 1));
+  int hbad[kChunks] = {0, 0, 0, 0};
+  for (int k = 0; k < kChunks; k++)
+    QG_CUDA(c, cudaMemcpyAsync(&hbad[k], c->scratch.p + k * kScr + 2 * kBuckets + 1, sizeof(int),
+                               cudaMemcpyDeviceToHost, c->copy_out));
+  QG_CUDA(c, cudaStreamSynchronize(c->copy_out));
+  QG_CUDA(c, cudaStreamSynchronize(s));
+  for (int k = 0; k < kChunks; k++)
+    if (hbad[k]) return fail(c, QG_ERR_ARG, "qg_evaluate_host: list entry outside its source or cell range");
+  // the context now holds these inputs, as after the qg_set_* calls and qg_run
+  c->h_goff.assign(group_off, group_off + G + 1);
+  c->h_poff.assign(plist_off, plist_off + G + 1);
+  c->h_coff.assign(clist_off, clist_off + G + 1);
+  c->ns = ns;
+  c->nc = nc;
+  c->G_src = c->G_cell = G;
+  c->np_list = np_tot;
+  c->nc_list = nc_tot;
+  c->sinks_ok = c->src_ok = c->cells_ok = true;
+  c->ran = true;
+  c->timed = true;
+  c->last_stream = s;
+  update_counts(c);
   return QG_OK;
 }
 

@@ -47,6 +47,8 @@ SIGNATURES = {
     "qg_get_forces": ([_vp, _vp, _vp], _int),
     "qg_get_forces_dev": ([_vp, _vp, _vp, _vp], _int),
     "qg_get_stats": ([_vp, _vp], _int),
+    "qg_evaluate_host": ([_vp, _i64, _vp, _vp, _dbl, _i64, _vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp, _vp,
+                          _vp, _vp, _vp], _int),
     "qg_last_error": ([_vp], ctypes.c_char_p),
     "qg_last_timing": ([_vp, _vp, _vp], _int),
     "qg_autotune": ([_vp, _vp, _int, _vp, _vp], _int),
@@ -247,6 +249,39 @@ class Context:
         assert a.flags.c_contiguous and a.dtype == np.float64 and a.size == 3 * self.n
         assert phi.flags.c_contiguous and phi.dtype == np.float64 and phi.size == self.n
         self._ok(self._L.qg_get_forces(self._h, _hp(a), _hp(phi)), "qg_get_forces")
+        return a, phi
+
+    def qg_evaluate_host(self, x, group_off, eps2_all, eps2, src_x, src_m, plist_off, plist_idx, cell_com, cell_m,
+                         cell_q, clist_off, clist_idx, a=None, phi=None):
+        """One pipelined evaluation from host arrays (the inputs of the three
+        qg_set_* calls); returns (a, phi).  Pass the same array as x and src_x
+        to have it copied once; a / phi may be preallocated (pinned) outputs."""
+        x = _host(x, np.float64, (-1, 3))
+        g = _host(group_off, np.int64)
+        e = None if eps2 is None else _host(eps2, np.float32)
+        sx = _host(src_x, np.float64, (-1, 3))
+        sm = _host(src_m, np.float64)
+        po, pi = _host(plist_off, np.int64), _host(plist_idx, np.int32)
+        com, cm, cq = _host(cell_com, np.float64, (-1, 3)), _host(cell_m, np.float64), _host(cell_q, np.float64, (-1, 6))
+        co, ci = _host(clist_off, np.int64), _host(clist_idx, np.int32)
+        G = len(g) - 1
+        if g.ndim != 1 or G < 0 or (e is not None and len(e) != len(x)):
+            raise ValueError("qg_evaluate_host: group_off must have ngroups+1 entries, eps2 one per sink")
+        for off, idx, what in ((po, pi, "particle"), (co, ci, "cell")):
+            if len(off) != G + 1 or off[-1] != len(idx):
+                raise ValueError("qg_evaluate_host: %s list offsets do not match the groups or the list" % what)
+        if len(sx) != len(sm) or not (len(com) == len(cm) == len(cq)):
+            raise ValueError("qg_evaluate_host: source or cell arrays differ in length")
+        n = len(x)
+        a = np.empty((n, 3)) if a is None else a
+        phi = np.empty(n) if phi is None else phi
+        if a.shape != (n, 3) or phi.shape != (n,) or a.dtype != np.float64 or phi.dtype != np.float64 \
+                or not (a.flags.c_contiguous and phi.flags.c_contiguous):
+            raise ValueError("qg_evaluate_host: a must be float64 [n,3] and phi float64 [n], contiguous")
+        self._ok(self._L.qg_evaluate_host(self._h, n, _hp(x), _hp(e), float(eps2_all), G, _hp(g), len(sm), _hp(sx),
+                                          _hp(sm), _hp(po), _hp(pi), len(cm), _hp(com), _hp(cm), _hp(cq), _hp(co),
+                                          _hp(ci), _hp(a), _hp(phi)), "qg_evaluate_host")
+        self.n, self.G = n, G
         return a, phi
 
     def qg_get_forces_dev(self, a, phi, stream=None):

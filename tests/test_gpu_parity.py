@@ -47,6 +47,66 @@ def test_exponential_disk_quad_and_mono(theta):
         assert_parity(a, phi, a_ref, phi_ref, label="disk theta %.2f %s" % (theta, "quad" if uq else "mono"))
 
 
+def _evaluate_host(case, ctx, same_x=True, idx_fix=None):
+    t, L = case.tree, case.lists
+    pi, ci = L.plist_idx, L.clist_idx
+    if idx_fix is not None:
+        pi, ci = idx_fix(pi.copy(), ci.copy())
+    src_x = t.x if same_x else t.x.copy()
+    return ctx.qg_evaluate_host(t.x, t.group_off, case.eps2_all, case.eps2, src_x, t.m, L.plist_off, pi,
+                                t.cell_com, t.cell_m, t.cell_q, L.clist_off, ci)
+
+
+@pytest.mark.parametrize("name", ["sphere", "batched"])
+def test_pipelined_host_evaluation_equals_the_separate_calls(name):
+    """qg_evaluate_host (list copies overlapped with the kernel, four chunks
+    of groups) gives bit for bit the results of qg_set_* + qg_run at the same
+    options, with the positions copied once or twice, and leaves the
+    context holding the inputs."""
+    if name == "sphere":
+        case = Case(workloads.small_set("sphere", 6000, 31, 1e-2), 0.5, 8, 64)
+    else:
+        case = Case(workloads.batched_systems(nsys=6, seed=9, n_lo=300, n_hi=5000), 0.5, 8, 64)
+    opts = qgrav.Options(sinks_per_thread=4, warps_per_group=2, tile_j=128)
+    a_ref, phi_ref, st_ref = case.gpu(opts)
+    ctx = qgrav.Context(0, opts)
+    for same in (True, False):
+        a, phi = _evaluate_host(case, ctx, same_x=same)
+        assert np.array_equal(a, a_ref) and np.array_equal(phi, phi_ref)
+    st = ctx.qg_get_stats()
+    assert st["i_pp"] == st_ref["i_pp"] and st["i_pc"] == st_ref["i_pc"]
+    ctx.qg_run()  # the context holds the inputs: a graph step on them
+    a2, phi2 = ctx.qg_get_forces()
+    assert np.array_equal(a2, a_ref) and np.array_equal(phi2, phi_ref)
+    ctx.qg_last_timing()
+    a_o, phi_o = case.oracle()
+    assert_parity(a, phi, a_o, phi_o, label="%s pipelined" % name)
+    ctx.close()
+
+
+def test_pipelined_host_evaluation_rejects_bad_entries():
+    case = Case(workloads.small_set("plummer", 3000, 5, 1e-2), 0.5, 8, 64)
+    ctx = qgrav.Context(0)
+
+    def bad_cell(pi, ci):
+        ci[len(ci) // 2] = len(case.tree.cell_m) + 5
+        return pi, ci
+
+    def bad_particle(pi, ci):
+        pi[-1] = -1
+        return pi, ci
+
+    for fix in (bad_cell, bad_particle):
+        with pytest.raises(qgrav.QGError):
+            _evaluate_host(case, ctx, idx_fix=fix)
+        with pytest.raises(qgrav.QGError):
+            ctx.qg_run()  # the failed call left no runnable inputs
+    a, phi = _evaluate_host(case, ctx)  # and the context is still usable
+    a_o, phi_o = case.oracle()
+    assert_parity(a, phi, a_o, phi_o, label="after rejected inputs")
+    ctx.close()
+
+
 def test_sphere_4k_fp64_kernel(sphere4k):
     for exp, uq in ((qgrav.QG_QUAD, True), (qgrav.QG_MONO, False)):
         a, phi, _ = sphere4k.gpu(qgrav.Options(precision=qgrav.QG_FP64, expansion=exp))
