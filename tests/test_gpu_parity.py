@@ -84,6 +84,31 @@ def test_pipelined_host_evaluation_equals_the_separate_calls(name):
     ctx.close()
 
 
+def test_pipelined_host_evaluation_edge_cases():
+    ctx = qgrav.Context(0)
+    z3, z1 = np.zeros((0, 3)), np.zeros(0)
+    off0 = np.zeros(1, dtype=np.int64)
+    i0 = np.zeros(0, dtype=np.int32)
+    # nothing at all
+    a, phi = ctx.qg_evaluate_host(z3, off0, 1e-4, None, z3, z1, off0, i0, z3, z1, np.zeros((0, 6)), off0, i0)
+    assert a.shape == (0, 3) and phi.shape == (0,)
+    # sinks in groups whose lists are all empty (and an empty group): zero force and potential
+    x = np.random.default_rng(1).random((50, 3))
+    goff = np.array([0, 20, 20, 50], dtype=np.int64)
+    lo = np.zeros(4, dtype=np.int64)
+    a, phi = ctx.qg_evaluate_host(x, goff, 1e-4, None, x, np.full(50, 0.02), lo, i0, z3, z1, np.zeros((0, 6)),
+                                  lo, i0)
+    assert np.all(a == 0.0) and np.all(phi == 0.0)
+    # one group only (fewer groups than chunks), zero softening on the guarded path
+    ps = workloads.small_set("sphere", 300, 3, 0.0)
+    case = Case(ps, 0.5, 8, 512)
+    assert case.tree.ngroups == 1
+    a, phi = _evaluate_host(case, ctx)
+    a_o, phi_o = case.oracle()
+    assert_parity(a, phi, a_o, phi_o, label="one group, eps 0")
+    ctx.close()
+
+
 def test_pipelined_host_evaluation_rejects_bad_entries():
     case = Case(workloads.small_set("plummer", 3000, 5, 1e-2), 0.5, 8, 64)
     ctx = qgrav.Context(0)

@@ -96,6 +96,40 @@ def test_gpu_tree_equals_host_builder(name, ps, leaf, ncrit, theta):
     t.close()
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_random_parameters_match_the_host(seed):
+    """Seeded random distributions, leaf sizes, group sizes, opening angles
+    and system splits: nodes, moments and per-group lists as on the host."""
+    rng = np.random.default_rng(100 + seed)
+    kind = ["sphere", "cube", "plummer", "hernquist", "clumpy", "disk"][seed]
+    n = int(rng.integers(500, 20000))
+    ps = workloads.small_set(kind, n, 200 + seed, 1e-3)
+    nsys = int(rng.integers(1, 4))
+    cuts = np.sort(rng.choice(np.arange(1, n), nsys - 1, replace=False)) if nsys > 1 else np.zeros(0, np.int64)
+    sys_off = np.concatenate([[0], cuts, [n]]).astype(np.int64)
+    leaf = int(rng.integers(1, 17))
+    ncrit = int(rng.integers(leaf, 300))
+    theta = float(rng.uniform(0.2, 1.0))
+    h = qtree.Tree(ps.x, ps.m, sys_off, leaf, ncrit)
+    L = h.walk(theta)
+    import torch
+    t = gtree.GpuTree(0)
+    t.build(torch.as_tensor(ps.x).cuda(), torch.as_tensor(ps.m).cuda(), sys_off, leaf, ncrit)
+    t.walk(theta)
+    assert t.sizes()["nnodes"] == h.nnodes and t.sizes()["ngroups"] == h.ngroups
+    assert np.array_equal(t.host("perm"), h.perm) and np.array_equal(t.host("group_off"), h.group_off)
+    gk = _node_keys(t.host("node_range"), t.host("cell_side"))
+    g_of = {k: i for i, k in enumerate(gk)}
+    h2g = np.array([g_of[k] for k in _node_keys(h.cell_range, h.cell_side)], dtype=np.int64)
+    assert np.array_equal(t.host("cell_q")[h2g], h.cell_q)
+    assert np.array_equal(t.host("plist_off"), L.plist_off) and np.array_equal(t.host("clist_off"), L.clist_off)
+    assert np.array_equal(_per_group_sorted(L.plist_off, t.host("plist_idx")),
+                          _per_group_sorted(L.plist_off, L.plist_idx))
+    assert np.array_equal(_per_group_sorted(L.clist_off, t.host("clist_idx")),
+                          _per_group_sorted(L.clist_off, h2g[L.clist_idx]))
+    t.close()
+
+
 @pytest.mark.parametrize("n", [3000, 40000])
 def test_walk_that_opens_everything(n):
     """theta = 0 opens every node: each group's particle list is all n
