@@ -672,6 +672,8 @@ __global__ void walk_data_kernel(int32_t nn, const int32_t *__restrict__ nsysid,
 // their error bounds.  Otherwise (ties and near-ties) the FP64 test decides.
 // Scaling both sides of side^2 < theta^2 d^2 by 1/S^2 does not change it.
 constexpr int kWarpStack = kMaxLevel * 224 + 256;
+constexpr int kWalkBlock = 128;       // threads per block of the walk kernels
+constexpr int kWalkBlocksPerSM = 10;  // the single-pass walk's register bound (48): 40 warps per SM
 
 __device__ __forceinline__ int warp_excl(int v, int lane, int *total) {
   int x = v;
@@ -748,7 +750,7 @@ struct WalkTree {
 // Walk group g with the calling warp; np, nc: its list sizes (warp-uniform).
 // Returns false if the stack would overflow (not reachable, see above).
 __device__ bool walk_group(const WalkTree &T, int64_t g, double theta2, float th2, int32_t *stack, ListOut out,
-                           int64_t &np, int64_t &nc) {
+                           int64_t &np, int64_t &nc, double *box64) {
   const int lane = threadIdx.x & 31;
   const int32_t gb = (int32_t)T.group_off[g], ge = (int32_t)T.group_off[g + 1];
   double bmin[3] = {INFINITY, INFINITY, INFINITY}, bmax[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -771,8 +773,16 @@ __device__ bool walk_group(const WalkTree &T, int64_t g, double theta2, float th
                                 __double2float_rn((bmin[2] - o2) * u));
   const float3 hi = make_float3(__double2float_rn((bmax[0] - o0) * u), __double2float_rn((bmax[1] - o1) * u),
                                 __double2float_rn((bmax[2] - o2) * u));
-  __syncwarp();  // the previous group's last stack reads are done
-  if (lane == 0) stack[0] = root;
+  __syncwarp();  // the previous group's last stack and box reads are done
+  if (lane == 0) {
+    stack[0] = root;
+    // the FP64 box, only needed by the (rare) FP64 decisions, waits in shared
+    // memory instead of twelve registers
+    for (int d = 0; d < 3; d++) {
+      box64[d] = bmin[d];
+      box64[3 + d] = bmax[d];
+    }
+  }
   __syncwarp();
   int sp = 1, depth = 0;
   int seg = 0;  // lane d: first stack slot of the segment at depth d
@@ -796,7 +806,7 @@ __device__ bool walk_group(const WalkTree &T, int64_t g, double theta2, float th
       bool open = true;
       if (theta2 > 0.0 && !(tp.x < ge && tp.y > gb)) {
         const int dec = node_opens32(T.geom[2 * k], T.geom[2 * k + 1], th2, dl, lo, hi);
-        open = dec == 2 ? node_opens64(k, theta2, T.centre, T.side, T.com, bmin, bmax) : dec == 1;
+        open = dec == 2 ? node_opens64(k, theta2, T.centre, T.side, T.com, box64, box64 + 3) : dec == 1;
       }
       kind = !open ? 1 : (tp.w == 0 ? 2 : 3);
     }
@@ -843,13 +853,14 @@ __global__ void walk_warp_kernel(int64_t G, double theta2, WalkTree T, int32_t *
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int32_t *stack = stacks + warp * kWarpStack;
+  __shared__ double s_box[kWalkBlock / 32][6];
   const float th2 = __double2float_rn(theta2);
   for (int64_t g = warp; g < G; g += nwarps) {
     ListOut out{nullptr, nullptr, 0, 0};
     if (FILL) out = ListOut{plist_idx + plist_off[g], clist_idx + clist_off[g], plist_off[g + 1] - plist_off[g],
                             clist_off[g + 1] - clist_off[g]};
     int64_t np = 0, nc = 0;
-    if (!walk_group(T, g, theta2, th2, stack, out, np, nc)) {
+    if (!walk_group(T, g, theta2, th2, stack, out, np, nc, s_box[threadIdx.x >> 5])) {
       if (lane == 0) atomicOr(err, 1);
       return;
     }
@@ -868,7 +879,7 @@ __global__ void walk_warp_kernel(int64_t G, double theta2, WalkTree T, int32_t *
 // reserved so far (the exact totals, even when they exceed the scratch
 // capacities).  err bit 0: stack, bit 1: a group longer than its staging
 // area, bit 2: scratch too small.
-__global__ void walk_single_kernel(int64_t G, double theta2, WalkTree T, int32_t *__restrict__ stage_p,
+__global__ void __launch_bounds__(kWalkBlock, kWalkBlocksPerSM) walk_single_kernel(int64_t G, double theta2, WalkTree T, int32_t *__restrict__ stage_p,
                                    int32_t *__restrict__ stage_c, int64_t sp_cap, int64_t sc_cap,
                                    int32_t *__restrict__ scratch_p, int32_t *__restrict__ scratch_c, int64_t cap_p,
                                    int64_t cap_c, unsigned long long *__restrict__ cursor,
@@ -878,6 +889,7 @@ __global__ void walk_single_kernel(int64_t G, double theta2, WalkTree T, int32_t
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int32_t *stack = stacks + warp * kWarpStack;
+  __shared__ double s_box[kWalkBlock / 32][6];
   int32_t *mp = stage_p + warp * sp_cap, *mc = stage_c + warp * sc_cap;
   const float th2 = __double2float_rn(theta2);
   for (;;) {
@@ -886,7 +898,7 @@ __global__ void walk_single_kernel(int64_t G, double theta2, WalkTree T, int32_t
     const int64_t g = (int64_t)__shfl_sync(0xffffffffu, gg, 0);
     if (g >= G) return;
     int64_t np = 0, nc = 0;
-    if (!walk_group(T, g, theta2, th2, stack, ListOut{mp, mc, sp_cap, sc_cap}, np, nc)) {
+    if (!walk_group(T, g, theta2, th2, stack, ListOut{mp, mc, sp_cap, sc_cap}, np, nc, s_box[threadIdx.x >> 5])) {
       if (lane == 0) atomicOr(err, 1);
       return;
     }
@@ -1366,8 +1378,8 @@ static qg_status walk_impl(qg_gtree *t, double theta, cudaStream_t s) {
   // persistent warp grid: one stack (and staging area) per warp
   int sms = 0;
   GT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, t->device));
-  const int wb = 128;
-  const int64_t warps = std::min<int64_t>(std::max<int64_t>(G, 1), (int64_t)sms * 32);
+  const int wb = kWalkBlock;
+  const int64_t warps = std::min<int64_t>(std::max<int64_t>(G, 1), (int64_t)sms * 4 * kWalkBlocksPerSM);
   const unsigned wg = (unsigned)((warps * 32 + wb - 1) / wb);
   GT_CUDA(t->stacks.reserve((size_t)wg * (wb / 32) * kWarpStack));
   const WalkTree T{t->group_off.p, t->group_node.p, t->nsysid.p, t->sys_root.p, t->xs.p, t->geom.p,
