@@ -15,7 +15,7 @@ def _need_gpu():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    qgrav.lib()  # a GPU machine without the library is a failure, not a skip
+    qgrav.lib()  # a GPU without the built library is a failure, not a skip
 
 
 @pytest.fixture(scope="module")
