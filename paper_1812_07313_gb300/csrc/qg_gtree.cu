@@ -537,17 +537,26 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
         c1 /= M;
         c2 /= M;
       }
+      // Q = 3 S - tr(S) I with S = sum m r r^T, the host builder's expressions
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
       for (int64_t i = b; i < e; i++) {
         const double r0 = xs[3 * i] - c0, r1 = xs[3 * i + 1] - c1, r2c = xs[3 * i + 2] - c2;
-        const double r2 = r0 * r0 + r1 * r1 + r2c * r2c;
         const double mi = ms[i];
-        q0 += mi * (3 * r0 * r0 - r2);
-        q1 += mi * (3 * r0 * r1);
-        q2 += mi * (3 * r0 * r2c);
-        q3 += mi * (3 * r1 * r1 - r2);
-        q4 += mi * (3 * r1 * r2c);
-        q5 += mi * (3 * r2c * r2c - r2);
+        const double m0 = mi * r0, m1 = mi * r1, m2 = mi * r2c;
+        s0 += m0 * r0;
+        s1 += m0 * r1;
+        s2 += m0 * r2c;
+        s3 += m1 * r1;
+        s4 += m1 * r2c;
+        s5 += m2 * r2c;
       }
+      const double tr = s0 + s3 + s5;
+      q0 = 3 * s0 - tr;
+      q1 = 3 * s1;
+      q2 = 3 * s2;
+      q3 = 3 * s3 - tr;
+      q4 = 3 * s4;
+      q5 = 3 * s5 - tr;
     } else {
       const int f = nfirst[j];
       for (int ch = 0; ch < nc; ch++) {
@@ -562,19 +571,34 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
         c1 /= M;
         c2 /= M;
       }
+      // parallel-axis shift: Q = sum Q_c + 3 S - tr(S) I with S = sum m_c d d^T
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
       for (int ch = 0; ch < nc; ch++) {
         const int cj = f + ch;
         const double mc = mass[cj];
         const double r0 = com[3 * cj] - c0, r1 = com[3 * cj + 1] - c1, r2c = com[3 * cj + 2] - c2;
-        const double r2 = r0 * r0 + r1 * r1 + r2c * r2c;
+        const double m0 = mc * r0, m1 = mc * r1, m2 = mc * r2c;
+        s0 += m0 * r0;
+        s1 += m0 * r1;
+        s2 += m0 * r2c;
+        s3 += m1 * r1;
+        s4 += m1 * r2c;
+        s5 += m2 * r2c;
         const double *qc = q + 6 * cj;
-        q0 += qc[0] + mc * (3 * r0 * r0 - r2);
-        q1 += qc[1] + mc * (3 * r0 * r1);
-        q2 += qc[2] + mc * (3 * r0 * r2c);
-        q3 += qc[3] + mc * (3 * r1 * r1 - r2);
-        q4 += qc[4] + mc * (3 * r1 * r2c);
-        q5 += qc[5] + mc * (3 * r2c * r2c - r2);
+        q0 += qc[0];
+        q1 += qc[1];
+        q2 += qc[2];
+        q3 += qc[3];
+        q4 += qc[4];
+        q5 += qc[5];
       }
+      const double tr = s0 + s3 + s5;
+      q0 = q0 + (3 * s0 - tr);
+      q1 = q1 + 3 * s1;
+      q2 = q2 + 3 * s2;
+      q3 = q3 + (3 * s3 - tr);
+      q4 = q4 + 3 * s4;
+      q5 = q5 + (3 * s5 - tr);
     }
     mass[j] = M;
     com[3 * j] = c0;

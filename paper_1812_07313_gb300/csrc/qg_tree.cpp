@@ -267,17 +267,27 @@ extern "C" int qgt_build(int64_t n, const double *x, const double *m, int64_t ns
             for (int d = 0; d < 3; d++) c[d] += t->ms[i] * t->xs[3 * i + d];
           }
           if (M > 0) for (int d = 0; d < 3; d++) c[d] /= M;
+          // Eq. 2 as Q = 3 S - tr(S) I with S = sum m r r^T (the same sum,
+          // fewer operations; the GPU builder evaluates the same expressions)
+          double sm[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
           for (int64_t i = nd.begin; i < nd.end; i++) {
-            double r[3] = {t->xs[3 * i] - c[0], t->xs[3 * i + 1] - c[1], t->xs[3 * i + 2] - c[2]};
-            double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-            double mi = t->ms[i];
-            qq[0] += mi * (3 * r[0] * r[0] - r2);
-            qq[1] += mi * (3 * r[0] * r[1]);
-            qq[2] += mi * (3 * r[0] * r[2]);
-            qq[3] += mi * (3 * r[1] * r[1] - r2);
-            qq[4] += mi * (3 * r[1] * r[2]);
-            qq[5] += mi * (3 * r[2] * r[2] - r2);
+            const double r[3] = {t->xs[3 * i] - c[0], t->xs[3 * i + 1] - c[1], t->xs[3 * i + 2] - c[2]};
+            const double mi = t->ms[i];
+            const double m0 = mi * r[0], m1 = mi * r[1], m2 = mi * r[2];
+            sm[0] += m0 * r[0];
+            sm[1] += m0 * r[1];
+            sm[2] += m0 * r[2];
+            sm[3] += m1 * r[1];
+            sm[4] += m1 * r[2];
+            sm[5] += m2 * r[2];
           }
+          const double tr = sm[0] + sm[3] + sm[5];
+          qq[0] = 3 * sm[0] - tr;
+          qq[1] = 3 * sm[1];
+          qq[2] = 3 * sm[2];
+          qq[3] = 3 * sm[3] - tr;
+          qq[4] = 3 * sm[4];
+          qq[5] = 3 * sm[5] - tr;
         } else {
           for (int ch = 0; ch < nd.nchild; ch++) {
             const int64_t cj = nd.first_child + ch;
@@ -285,20 +295,30 @@ extern "C" int qgt_build(int64_t n, const double *x, const double *m, int64_t ns
             for (int d = 0; d < 3; d++) c[d] += t->mass[cj] * t->com[3 * cj + d];
           }
           if (M > 0) for (int d = 0; d < 3; d++) c[d] /= M;
-          // parallel-axis shift of each child's tensor to the parent's COM
+          // parallel-axis shift of each child's tensor to the parent's COM:
+          // Q = sum Q_c + 3 S - tr(S) I with S = sum m_c d d^T
+          double sm[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, qs[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
           for (int ch = 0; ch < nd.nchild; ch++) {
             const int64_t cj = nd.first_child + ch;
             const double mc = t->mass[cj];
-            double r[3] = {t->com[3 * cj] - c[0], t->com[3 * cj + 1] - c[1], t->com[3 * cj + 2] - c[2]};
-            double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+            const double r[3] = {t->com[3 * cj] - c[0], t->com[3 * cj + 1] - c[1], t->com[3 * cj + 2] - c[2]};
+            const double m0 = mc * r[0], m1 = mc * r[1], m2 = mc * r[2];
+            sm[0] += m0 * r[0];
+            sm[1] += m0 * r[1];
+            sm[2] += m0 * r[2];
+            sm[3] += m1 * r[1];
+            sm[4] += m1 * r[2];
+            sm[5] += m2 * r[2];
             const double *qc = &t->q[6 * cj];
-            qq[0] += qc[0] + mc * (3 * r[0] * r[0] - r2);
-            qq[1] += qc[1] + mc * (3 * r[0] * r[1]);
-            qq[2] += qc[2] + mc * (3 * r[0] * r[2]);
-            qq[3] += qc[3] + mc * (3 * r[1] * r[1] - r2);
-            qq[4] += qc[4] + mc * (3 * r[1] * r[2]);
-            qq[5] += qc[5] + mc * (3 * r[2] * r[2] - r2);
+            for (int k = 0; k < 6; k++) qs[k] += qc[k];
           }
+          const double tr = sm[0] + sm[3] + sm[5];
+          qq[0] = qs[0] + (3 * sm[0] - tr);
+          qq[1] = qs[1] + 3 * sm[1];
+          qq[2] = qs[2] + 3 * sm[2];
+          qq[3] = qs[3] + (3 * sm[3] - tr);
+          qq[4] = qs[4] + 3 * sm[4];
+          qq[5] = qs[5] + (3 * sm[5] - tr);
         }
         t->mass[j] = M;
       }
