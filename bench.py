@@ -205,7 +205,8 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     wl, ps, tr, L, eps2_all, eps2, _ = build_case(args.workload, args.theta)
-    per_step = max(1.0, 150.0 / max(args.steps + args.warmup, 1))
+    # about 150 s of oracle work in all, at most --cpu-seconds per step
+    per_step = max(0.2, min(args.cpu_seconds, 150.0 / max(args.steps + args.warmup, 1)))
     total_int, total_t = 0, 0.0
     for s in range(args.warmup + args.steps):
         groups, work = oracle_sample(tr, L, eps2_all, eps2, per_step, seed=1000 + s)
