@@ -72,7 +72,12 @@ def _forces(t, theta, eps2, expansion, tune=True):
     return a, f, st
 
 
-def accuracy(kind, n=65536, seed=7, eps=1e-3, thetas=(0.3, 0.4, 0.5, 0.6, 0.65, 0.7, 0.75, 0.8), n_crit=64,
+# the paper's pairs of comparable accuracy (Sec. 4, Fig. 1): (monopole theta, quadrupole theta)
+FIG1_PAIRS = {"sphere": ((0.3, 0.65), (0.5, 0.75)), "plummer": ((0.3, 0.4), (0.5, 0.6)),
+              "disk": ((0.3, 0.45), (0.5, 0.65))}
+
+
+def accuracy(kind, n=65536, seed=7, eps=1e-3, thetas=(0.3, 0.4, 0.45, 0.5, 0.6, 0.65, 0.7, 0.75, 0.8), n_crit=64,
              leaf_max=8):
     torch = _torch()
     ps = workloads.small_set(kind, n, seed, eps)
@@ -97,8 +102,15 @@ def accuracy(kind, n=65536, seed=7, eps=1e-3, thetas=(0.3, 0.4, 0.5, 0.6, 0.65, 
         th = np.array([r["theta"] for r in rows if r["cells"] == name])
         p = np.array([r["p90"] for r in rows if r["cells"] == name])
         slopes[name] = float(np.polyfit(np.log(th), np.log(p), 1)[0])
+    pairs = []
+    for tm, tq in FIG1_PAIRS[kind]:
+        rm = next(r for r in rows if r["cells"] == "mono" and r["theta"] == tm)
+        rq = next(r for r in rows if r["cells"] == "quad" and r["theta"] == tq)
+        pairs.append({"theta_mono": tm, "theta_quad": tq,
+                      "mono": {k: rm[k] for k in ("p10", "p50", "p90", "p99")},
+                      "quad": {k: rq[k] for k in ("p10", "p50", "p90", "p99")}})
     return {"distribution": KINDS[kind], "n": n, "eps": eps, "n_crit": n_crit, "rows": rows,
-            "cdf_error_levels": cdf_at.tolist(), "p90_slope": slopes}
+            "cdf_error_levels": cdf_at.tolist(), "p90_slope": slopes, "fig1_pairs": pairs}
 
 
 def table2(kind, theta_mono, theta_quad, n=1 << 22, seed=11, eps=1e-3, n_crit=256, leaf_max=8, reps=5,
