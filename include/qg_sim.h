@@ -12,6 +12,9 @@
  * (quadrupole cells, or monopole-only cells) on them.
  *
  * Particles keep the caller's order (the tree's sorted order is internal).
+ * Softening: params->eps2 for every particle, or a per-particle eps^2 given
+ * with the state (each sink's own softening, as the force path's per-sink
+ * eps2; e.g. one value per independent system).
  * Energies: K = 1/2 sum m v^2 and W = 1/2 sum m (phi + m / eps) -- the
  * self pair that the force path includes in phi (-m/eps for eps > 0) is
  * taken out again; with eps = 0 there is no self term.
@@ -65,11 +68,12 @@ void qg_sim_destroy(qg_sim *sim);
 /*
  * Initial state from HOST arrays x [n][3], v [n][3], m [n] (n < 2^31) and
  * sys_off [nsys+1] (independent systems, each with its own tree root;
- * sys_off = {0, n} for one system).  Evaluates the forces at x, so that the
- * first step can kick.
+ * sys_off = {0, n} for one system).  eps2 [n] (host, may be NULL): each
+ * particle's squared softening, finite and >= 0, used instead of
+ * params->eps2.  Evaluates the forces at x, so that the first step can kick.
  */
-qg_status qg_sim_set_state(qg_sim *sim, int64_t n, const double *x, const double *v, const double *m, int64_t nsys,
-                           const int64_t *sys_off, void *cuda_stream);
+qg_status qg_sim_set_state(qg_sim *sim, int64_t n, const double *x, const double *v, const double *m,
+                           const float *eps2, int64_t nsys, const int64_t *sys_off, void *cuda_stream);
 
 /* nsteps kick-drift-kick steps of length dt (nsteps >= 0, dt finite). */
 qg_status qg_sim_step(qg_sim *sim, double dt, int64_t nsteps, void *cuda_stream);

@@ -41,12 +41,17 @@ def leapfrog_kdk(x, v, m, dt, nsteps, accel, a=None):
 
 
 def energies(v, m, phi, eps2):
-    """(K, W, p) in double, the self pair removed from W when eps2 > 0."""
+    """(K, W, p) in double, the self pair removed from W where eps2 > 0.
+
+    eps2: one squared softening for all particles, or one per particle."""
     v = np.asarray(v, dtype=np.float64)
     m = np.asarray(m, dtype=np.float64)
     phi = np.asarray(phi, dtype=np.float64)
     K = 0.5 * float(np.sum(m * np.sum(v * v, axis=1)))
-    self_term = m / np.sqrt(eps2) if eps2 > 0 else np.zeros_like(m)
+    e2 = np.broadcast_to(np.asarray(eps2, dtype=np.float64), m.shape)
+    self_term = np.zeros_like(m)
+    pos = e2 > 0
+    self_term[pos] = m[pos] / np.sqrt(e2[pos])
     W = 0.5 * float(np.sum(m * (phi + self_term)))
     p = (m[:, None] * v).sum(axis=0)
     return K, W, p

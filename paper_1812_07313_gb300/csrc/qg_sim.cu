@@ -68,15 +68,25 @@ __device__ __forceinline__ void block_sum(double (&val)[kRedVals], double *sh) {
   for (int k = 0; k < kRedVals; k++) val[k] = sh[k * kThreads];
 }
 
-// Per block: K = 1/2 sum m v^2, W = 1/2 sum m (phi + m / eps), p = sum m v.
+// Per-particle softening in the tree's sorted order: eps2_s[i] = eps2[perm[i]].
+__global__ void gather_eps2_kernel(int64_t n, const int64_t *__restrict__ perm, const float *__restrict__ eps2,
+                                   float *__restrict__ eps2_s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    eps2_s[i] = eps2[perm[i]];
+}
+
+// Per block: K = 1/2 sum m v^2, W = 1/2 sum m (phi + m / eps), p = sum m v
+// (eps per particle when eps2 is given, else 1/eps = inv_eps for all).
 __global__ void energy_partial_kernel(int64_t n, const double *__restrict__ v, const double *__restrict__ m,
-                                      const double *__restrict__ phi, double inv_eps, double *__restrict__ part) {
+                                      const double *__restrict__ phi, double inv_eps, const float *__restrict__ eps2,
+                                      double *__restrict__ part) {
   __shared__ double sh[kRedVals * kThreads];
   double val[kRedVals] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
     const double mi = m[i], v0 = v[3 * i], v1 = v[3 * i + 1], v2 = v[3 * i + 2];
     val[0] += 0.5 * mi * (v0 * v0 + v1 * v1 + v2 * v2);
-    val[1] += 0.5 * mi * (phi[i] + mi * inv_eps);
+    const double ie = eps2 ? (eps2[i] > 0.f ? 1.0 / sqrt((double)eps2[i]) : 0.0) : inv_eps;
+    val[1] += 0.5 * mi * (phi[i] + mi * ie);
     val[2] += mi * v0;
     val[3] += mi * v1;
     val[4] += mi * v2;
@@ -107,6 +117,8 @@ struct qg_sim {
   int64_t n = 0;
   std::vector<int64_t> sys_off;
   Buf<double> x, v, m, a, phi, a_s, phi_s, red;
+  Buf<float> eps2, eps2_s;  // per-particle softening (caller order, sorted order)
+  bool per_particle_eps = false;
   bool has_state = false, tuned = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t stream = nullptr;  // used when the caller passes no stream
@@ -148,7 +160,23 @@ qg_status evaluate(qg_sim *s, cudaStream_t st, bool kick, double h) {
   SIM_OK(qg_gtree_build(s->tree, s->n, s->x.p, s->m.p, (int64_t)s->sys_off.size() - 1, s->sys_off.data(),
                         s->prm.leaf_max, s->prm.n_crit, st));
   SIM_OK(qg_gtree_walk(s->tree, s->prm.theta, st));
-  SIM_OK(qg_gtree_attach(s->tree, s->ctx, s->prm.eps2, st));
+  if (s->per_particle_eps) {
+    // the tree's arrays, with each sink's own softening in sorted order
+    const int64_t *perm = nullptr, *goff = nullptr, *poff = nullptr, *coff = nullptr;
+    const double *xs = nullptr, *ms = nullptr, *ccom = nullptr, *cm = nullptr, *cq = nullptr;
+    const int32_t *pidx = nullptr, *cidx = nullptr;
+    SIM_OK(qg_gtree_arrays(s->tree, &perm, &xs, &ms, nullptr, nullptr, &ccom, &cm, &cq, nullptr, &goff, &poff, &pidx,
+                           &coff, &cidx));
+    int64_t nn = 0, G = 0, np = 0, nc = 0;
+    SIM_OK(qg_gtree_sizes(s->tree, nullptr, &nn, &G, &np, &nc));
+    gather_eps2_kernel<<<blocks_for(s->n), kThreads, 0, st>>>(s->n, perm, s->eps2.p, s->eps2_s.p);
+    SIM_CUDA(cudaGetLastError());
+    SIM_OK(qg_set_sinks_dev(s->ctx, s->n, xs, s->eps2_s.p, 0.0, G, goff, st));
+    SIM_OK(qg_set_sources_dev(s->ctx, s->n, xs, ms, poff, pidx, np, st));
+    SIM_OK(qg_set_cells_dev(s->ctx, nn, ccom, cm, cq, coff, cidx, nc, st));
+  } else {
+    SIM_OK(qg_gtree_attach(s->tree, s->ctx, s->prm.eps2, st));
+  }
   if (s->prm.autotune && !s->tuned) {
     SIM_OK(qg_autotune(s->ctx, st, 2, nullptr, nullptr));
     s->tuned = true;
@@ -225,15 +253,20 @@ void qg_sim_destroy(qg_sim *s) {
     cudaStreamDestroy(s->stream);
   }
   for (Buf<double> *b : {&s->x, &s->v, &s->m, &s->a, &s->phi, &s->a_s, &s->phi_s, &s->red}) b->release();
+  s->eps2.release();
+  s->eps2_s.release();
   delete s;
 }
 
-qg_status qg_sim_set_state(qg_sim *s, int64_t n, const double *x, const double *v, const double *m, int64_t nsys,
-                           const int64_t *sys_off, void *stream) {
+qg_status qg_sim_set_state(qg_sim *s, int64_t n, const double *x, const double *v, const double *m,
+                           const float *eps2, int64_t nsys, const int64_t *sys_off, void *stream) {
   if (!s || n < 1 || n >= INT32_MAX || !x || !v || !m || nsys < 1 || !sys_off) return QG_ERR_ARG;
   if (sys_off[0] != 0 || sys_off[nsys] != n) return QG_ERR_ARG;
   for (int64_t q = 0; q < nsys; q++)
     if (sys_off[q + 1] < sys_off[q]) return QG_ERR_ARG;
+  if (eps2)
+    for (int64_t i = 0; i < n; i++)
+      if (!(eps2[i] >= 0.f) || !std::isfinite(eps2[i])) return QG_ERR_ARG;
   DeviceGuard g(s->device);
   cudaStream_t st = s->use(stream);
   s->has_state = false;
@@ -249,6 +282,12 @@ qg_status qg_sim_set_state(qg_sim *s, int64_t n, const double *x, const double *
   SIM_CUDA(cudaMemcpyAsync(s->x.p, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
   SIM_CUDA(cudaMemcpyAsync(s->v.p, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
   SIM_CUDA(cudaMemcpyAsync(s->m.p, m, n * sizeof(double), cudaMemcpyHostToDevice, st));
+  s->per_particle_eps = eps2 != nullptr;
+  if (eps2) {
+    SIM_CUDA(s->eps2.reserve(n));
+    SIM_CUDA(s->eps2_s.reserve(n));
+    SIM_CUDA(cudaMemcpyAsync(s->eps2.p, eps2, n * sizeof(float), cudaMemcpyHostToDevice, st));
+  }
   SIM_CUDA(cudaStreamSynchronize(st));
   SIM_OK(evaluate(s, st, false, 0.0));
   s->has_state = true;
@@ -311,7 +350,8 @@ qg_status qg_sim_energy(qg_sim *s, double *kinetic, double *potential, double *m
   DeviceGuard g(s->device);
   cudaStream_t st = s->use(stream);
   const double inv_eps = s->prm.eps2 > 0.0 ? 1.0 / std::sqrt(s->prm.eps2) : 0.0;
-  energy_partial_kernel<<<kRedBlocks, kThreads, 0, st>>>(s->n, s->v.p, s->m.p, s->phi.p, inv_eps, s->red.p);
+  energy_partial_kernel<<<kRedBlocks, kThreads, 0, st>>>(s->n, s->v.p, s->m.p, s->phi.p, inv_eps,
+                                                         s->per_particle_eps ? s->eps2.p : nullptr, s->red.p);
   energy_final_kernel<<<1, kThreads, 0, st>>>(s->red.p, s->red.p + kRedVals * kRedBlocks);
   SIM_CUDA(cudaGetLastError());
   double out[kRedVals];

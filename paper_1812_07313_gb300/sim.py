@@ -33,7 +33,7 @@ class qg_sim_times(ctypes.Structure):
 SIGNATURES = {
     "qg_sim_create": ([ctypes.POINTER(_vp), _int, _vp, _vp], _int),
     "qg_sim_destroy": ([_vp], None),
-    "qg_sim_set_state": ([_vp, _i64, _vp, _vp, _vp, _i64, _vp, _vp], _int),
+    "qg_sim_set_state": ([_vp, _i64, _vp, _vp, _vp, _vp, _i64, _vp, _vp], _int),
     "qg_sim_step": ([_vp, _dbl, _i64, _vp], _int),
     "qg_sim_get_state": ([_vp, _vp, _vp, _vp, _vp], _int),
     "qg_sim_state_dev": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
@@ -101,16 +101,19 @@ class Simulation:
         except Exception:
             pass
 
-    def set_state(self, x, v, m, sys_off=None, stream=None):
+    def set_state(self, x, v, m, sys_off=None, stream=None, eps2=None):
+        """eps2: optional per-particle squared softening (else params.eps2 for all)."""
         x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
         n = len(x)
         v = np.ascontiguousarray(v, dtype=np.float64).reshape(n, 3)
         m = np.ascontiguousarray(m, dtype=np.float64).reshape(n)
+        e = None if eps2 is None else np.ascontiguousarray(eps2, dtype=np.float32).reshape(n)
         so = np.array([0, n], dtype=np.int64) if sys_off is None else np.ascontiguousarray(sys_off, np.int64)
         if so.ndim != 1 or len(so) < 2 or so[0] != 0 or so[-1] != n:
             raise ValueError("sys_off must run from 0 to n")
-        self._ok(self._L.qg_sim_set_state(self._h, n, x.ctypes.data, v.ctypes.data, m.ctypes.data, len(so) - 1,
-                                          so.ctypes.data, stream), "qg_sim_set_state")
+        self._ok(self._L.qg_sim_set_state(self._h, n, x.ctypes.data, v.ctypes.data, m.ctypes.data,
+                                          None if e is None else e.ctypes.data, len(so) - 1, so.ctypes.data, stream),
+                 "qg_sim_set_state")
         self.n = n
 
     def step(self, dt, nsteps=1, stream=None):

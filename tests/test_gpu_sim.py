@@ -98,6 +98,50 @@ def test_cold_collapse_conserves_energy_before_collapse():
     s.close()
 
 
+def test_per_particle_softening_matches_the_oracle_leapfrog():
+    # independent systems, each with its own softening (one value per system)
+    ps = workloads.batched_systems(nsys=3, seed=11, n_lo=800, n_hi=3000)
+    n = len(ps.m)
+    sys_of = np.repeat(np.arange(3), np.diff(ps.sys_off))
+    e2 = (np.array([1e-2, 3e-2, 2e-3])[sys_of] ** 2).astype(np.float32)
+    rng = np.random.default_rng(5)
+    v0 = 0.05 * rng.standard_normal((n, 3))
+    dt, steps = 2e-3, 2
+    s = sim.Simulation(sim.Params(theta=0.5, eps2=0.0, n_crit=64))
+    s.set_state(ps.x, v0, ps.m, ps.sys_off, eps2=e2)
+
+    def accel(x):
+        t = qtree.Tree(x, ps.m, ps.sys_off, 8, 64)
+        L = t.walk(0.5)
+        a_s, phi_s = oracle.expansion_forces(t.group_off, t.x, t.x, t.m, L.plist_off, L.plist_idx, t.cell_com,
+                                             t.cell_m, t.cell_q, L.clist_off, L.clist_idx,
+                                             sink_eps2=e2[t.perm].astype(np.float64))
+        a = np.empty_like(a_s)
+        phi = np.empty_like(phi_s)
+        a[t.perm] = a_s
+        phi[t.perm] = phi_s
+        return a, phi
+
+    _, _, a1, phi1 = s.state()
+    a0, phi0 = accel(ps.x)
+    assert_parity(a1, phi1, a0, phi0, label="per-particle softening, initial")
+    K, W, _ = s.energy()
+    Kr, Wr, _ = integrate.energies(v0, ps.m, phi1, e2)
+    assert abs(K - Kr) <= 1e-13 * Kr and abs(W - Wr) <= 1e-12 * abs(Wr)
+    s.step(dt, steps)
+    x, v, a, phi = s.state()
+    xr, vr, ar, phir = integrate.leapfrog_kdk(ps.x, v0, ps.m, dt, steps, accel, a=a0)
+    assert_parity(a, phi, ar, phir, label="per-particle softening, after %d steps" % steps)
+    dv = summary(rel_err(v - v0, vr - v0))
+    assert dv["median"] <= TOL_MEDIAN and dv["p99"] <= TOL_P99
+    s.close()
+    with pytest.raises(qgrav.QGError):
+        s2 = sim.Simulation(sim.Params(theta=0.5))
+        bad = e2.copy()
+        bad[3] = -1.0
+        s2.set_state(ps.x, v0, ps.m, ps.sys_off, eps2=bad)
+
+
 def test_batched_systems_step_like_each_system_alone():
     # every system has its own root, so its tree, groups and lists -- and, at
     # one launch shape, its forces -- are the same in the batch and alone

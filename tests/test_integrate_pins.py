@@ -63,6 +63,16 @@ def test_energies_of_the_two_body_state_and_their_conservation():
     assert errs[1] < 1e-5 and 3.5 < errs[0] / errs[1] < 4.5
 
 
+def test_energies_with_per_particle_softening():
+    # each sink feels its own softening: W = -1/2 (m1 m2 / sqrt(d^2 + e1^2) + m2 m1 / sqrt(d^2 + e2^2))
+    x = np.array([[0.5, 0.0, 0.0], [-0.5, 0.0, 0.0]])
+    m = np.array([0.5, 0.5])
+    e2 = np.array([0.01, 0.04])
+    _, phi = oracle.direct_forces(x, x, m, sink_eps2=e2)
+    _, W, _ = integrate.energies(np.zeros((2, 3)), m, phi, e2)
+    assert abs(W + 0.5 * (0.25 / math.sqrt(1.01) + 0.25 / math.sqrt(1.04))) < 1e-15
+
+
 def test_leapfrog_is_time_reversible():
     rng = np.random.default_rng(12)
     n = 32
