@@ -3,6 +3,10 @@
 Argument marshalling only: the build, moments, groups and walk run in
 ``libqgrav.so``.  Inputs are torch CUDA tensors; ``GpuTree.host(...)`` copies
 a result array to numpy (for tests and inspection).
+
+    python -m paper_1812_07313_gb300.gtree --workload plummer_4m --repeat 3
+
+builds and walks a named workload's tree and prints the device times.
 """
 from __future__ import annotations
 
@@ -135,3 +139,32 @@ class GpuTree:
         b, w = ctypes.c_float(), ctypes.c_float()
         self._ok(self._L.qg_gtree_timing(self._h, ctypes.addressof(b), ctypes.addressof(w)), "qg_gtree_timing")
         return b.value, w.value
+
+
+def main():
+    import argparse
+    import json
+
+    import torch
+
+    from . import workloads
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="plummer_4m")
+    ap.add_argument("--theta", type=float, default=None)
+    ap.add_argument("--repeat", type=int, default=3)
+    args = ap.parse_args()
+    wl = workloads.WORKLOADS[args.workload]
+    ps = wl.particles()
+    x, m = torch.as_tensor(ps.x).cuda(), torch.as_tensor(ps.m).cuda()
+    t = GpuTree(0)
+    theta = wl.theta if args.theta is None else args.theta
+    for k in range(args.repeat):
+        t.build(x, m, ps.sys_off, wl.leaf_max, wl.n_crit)
+        t.walk(theta)
+        b, w = t.timing()
+        print(json.dumps({"workload": args.workload, "pass": k, "build_ms": b, "walk_ms": w, **t.sizes()}), flush=True)
+    t.close()
+
+
+if __name__ == "__main__":
+    main()
