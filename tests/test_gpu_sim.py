@@ -142,6 +142,18 @@ def test_per_particle_softening_matches_the_oracle_leapfrog():
         s2.set_state(ps.x, v0, ps.m, ps.sys_off, eps2=bad)
 
 
+def test_single_particle_moves_freely():
+    s = sim.Simulation(sim.Params(theta=0.5, eps2=1e-4, n_crit=8, autotune=False))
+    s.set_state(np.array([[0.25, -0.5, 1.0]]), np.array([[0.1, 0.0, -0.2]]), np.array([2.0]))
+    s.step(0.5, 4)
+    x, v, a, phi = s.state()
+    assert np.allclose(x, [[0.45, -0.5, 0.6]], rtol=0, atol=1e-15) and np.array_equal(v, [[0.1, 0.0, -0.2]])
+    assert np.array_equal(a, np.zeros((1, 3))) and abs(phi[0] + 2.0 / 1e-2) < 1e-9  # only its own pair, -m/eps
+    K, W, p = s.energy()
+    assert abs(K - 0.05) < 1e-15 and abs(W) < 1e-9 and np.allclose(p, [0.2, 0.0, -0.4])
+    s.close()
+
+
 def test_batched_systems_step_like_each_system_alone():
     # every system has its own root, so its tree, groups and lists -- and, at
     # one launch shape, its forces -- are the same in the batch and alone

@@ -38,6 +38,10 @@ def _sets():
     yield "lattice_t05", workloads.single_system("lattice", lat, 1e-3), 8, 64, 0.5
     yield "lattice_t1", workloads.single_system("lattice", lat, 1e-3), 1, 8, 1.0
     yield "lattice_far", workloads.single_system("lattice", lat + 1.0e4, 1e-3), 8, 64, 0.5
+    # systems that are empty (first, middle and last) next to populated ones
+    pe = workloads.small_set("plummer", 3000, 17, 1e-2)
+    pe.sys_off = np.array([0, 0, 1200, 1200, 3000, 3000], dtype=np.int64)
+    yield "empty_systems", pe, 8, 64, 0.5
 
 
 CASES = list(_sets())
