@@ -919,14 +919,16 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
   QG_CUDA(c, cudaMemsetAsync(c->scratch.p, 0, kChunks * kScr * sizeof(int), s));
   QG_CUDA(c, cudaEventRecord(c->ev[0], s));
   QG_CUDA(c, cudaEventRecord(c->packed, s));
-  // ---- chunks of groups with about equal list entries
+  // ---- chunks of groups by list entries: 1/8, 1/4, 1/4, 3/8 of them, so
+  // that the first kernel waits for a small first copy
   int64_t gb[kChunks + 1];
   gb[0] = 0;
   {
     const int64_t total = np_tot + nc_tot;
+    const int eighths[kChunks] = {1, 3, 5, 8};  // cumulative, in eighths
     int64_t g = 0;
     for (int k = 1; k < kChunks; k++) {
-      const int64_t want = total / kChunks * k;
+      const int64_t want = total / 8 * eighths[k - 1];
       while (g < G && plist_off[g] + clist_off[g] < want) g++;
       gb[k] = g;
     }
