@@ -684,8 +684,10 @@ __global__ void walk_data_kernel(int32_t nn, const int32_t *__restrict__ nsysid,
 // level d only: at most 21 segments left behind with <= 224 entries each
 // (256 children of 32 nodes, less the 32 popped) plus the top one (<= 256)
 // ever sit on the stack.  The lists hold the same entries as a depth-first
-// walk, in this walk's own fixed order.  FILL == false counts, FILL == true
-// writes at the offsets.
+// walk, in this walk's own fixed order.  walk_group walks one group;
+// walk_single_kernel (one pass, groups taken from a counter, lists staged per
+// warp and placed with one atomic add per list) and walk_warp_kernel (count,
+// then fill at scanned offsets: the fallback) drive it.
 //
 // The opening test decides exactly as the FP64 test (node_opens64) does, but
 // first tries it in FP32 on the root-cube coordinates (x - o) / S, all within
