@@ -188,13 +188,39 @@ def oracle_sample(tr, L, eps2_all, eps2, seconds, seed=0):
     return order[:max(k, 1)], work
 
 
-def run_oracle(tr, L, eps2_all, eps2, groups):
+def run_oracle(tr, L, eps2_all, eps2, groups, threads=1):
+    """Seconds the oracle takes on these groups (threads > 1: its groups split
+    over that many host threads; the arithmetic of each group is unchanged)."""
     import oracle
-    t0 = time.perf_counter()
-    oracle.expansion_forces(tr.group_off, tr.x, tr.x, tr.m, L.plist_off, L.plist_idx, tr.cell_com, tr.cell_m,
-                            tr.cell_q, L.clist_off, L.clist_idx, eps2_all=eps2_all,
-                            sink_eps2=None if eps2 is None else eps2.astype(np.float64), groups=groups)
-    return time.perf_counter() - t0
+    oracle.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        oracle.expansion_forces(tr.group_off, tr.x, tr.x, tr.m, L.plist_off, L.plist_idx, tr.cell_com, tr.cell_m,
+                                tr.cell_q, L.clist_off, L.clist_idx, eps2_all=eps2_all,
+                                sink_eps2=None if eps2 is None else eps2.astype(np.float64), groups=groups)
+        return time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+    import subprocess
+    try:
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
 
 
 # ---------------------------------------------------------------- reference arm
@@ -433,6 +459,12 @@ def run_ours(args, rank, world, local_rank):
         out["cpu_baseline"] = {"value": float(work[groups].sum() / dt), "unit": UNIT, "cores": 1, "kind": "oracle",
                                "sample": "%d of %d groups in seeded random order, %d interactions, %.1f s"
                                          % (len(groups), tr.ngroups, int(work[groups].sum()), dt)}
+        # the same sample with the oracle's groups split over every host core
+        ncores = os.cpu_count() or 1
+        dtp = run_oracle(tr, L, eps2_all, eps2, groups, threads=ncores)
+        out["cpu_baseline_all_cores"] = {"value": float(work[groups].sum() / dtp), "unit": UNIT, "cores": ncores,
+                                         "kind": "oracle, groups split over host threads (OpenMP)",
+                                         "cpu": cpu_model(), "sample": "the cpu_baseline sample, %.2f s" % dtp}
     ctx.close()
     if rank == 0:
         print(json.dumps(out))

@@ -16,6 +16,8 @@ Functions and the passages of the paper they follow:
                              tree algorithm (Sec. 3.4)
   * ``direct_forces``     -- direct summation, the reference of Eq. 9
   * ``relative_error``    -- Eq. 9
+  * ``set_threads``       -- optional split of expansion_forces' groups over
+                             host threads (for the multi-core CPU baseline)
 """
 from __future__ import annotations
 
@@ -45,7 +47,7 @@ def build(force: bool = False) -> str:
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call([
             "gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-            "-fno-fast-math", _SRC, "-o", tmp, "-lm"])
+            "-fno-fast-math", "-fopenmp", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -57,6 +59,8 @@ def _load():
             lib = ctypes.CDLL(build())
             lib.qgo_cell_moments.argtypes = [ctypes.c_int64, _d, _d, _d, _d, _d]
             lib.qgo_cell_moments.restype = ctypes.c_int
+            lib.qgo_set_threads.argtypes = [ctypes.c_int]
+            lib.qgo_set_threads.restype = None
             lib.qgo_expansion_forces.argtypes = [
                 ctypes.c_int64, _i64, _d, _d, ctypes.c_double,
                 _d, _d, _i64, _i32,
@@ -192,6 +196,13 @@ def direct_forces(sink_x, src_x, src_m, eps2_all=0.0, sink_eps2=None):
     if rc != 0:
         raise ValueError("qgo_direct_forces: bad arguments")
     return a, phi
+
+
+def set_threads(n):
+    """Host threads over which expansion_forces splits its groups (1: the
+    plain serial oracle).  Each group is still one thread's serial loop, so
+    the results are the same for any n."""
+    _load().qgo_set_threads(int(n))
 
 
 def relative_error(a_test, a_ref):

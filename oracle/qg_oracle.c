@@ -158,6 +158,13 @@ static void cell_term(const double xi[3], double eps2,
 /* listed groups, whose sinks' a/phi are the only ones written.          */
 /* a is [n][3], phi is [n].                                              */
 /* ------------------------------------------------------------------ */
+/* Host threads over which qgo_expansion_forces splits its groups (default 1:
+ * the plain serial oracle).  A group is always evaluated by one thread, in
+ * the order below, so the results do not depend on the thread count. */
+static int qgo_threads = 1;
+
+void qgo_set_threads(int n) { qgo_threads = n < 1 ? 1 : n; }
+
 int qgo_expansion_forces(int64_t ngroups, const int64_t *group_off,
                          const double *sink_x, const double *sink_eps2,
                          double eps2_all,
@@ -176,6 +183,12 @@ int qgo_expansion_forces(int64_t ngroups, const int64_t *group_off,
     for (int64_t t = 0; t < nloop; t++) {
         int64_t g = groups ? groups[t] : t;
         if (g < 0 || g >= ngroups) return QGO_ERR_ARG;
+    }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(qgo_threads) if (qgo_threads > 1)
+#endif
+    for (int64_t t = 0; t < nloop; t++) {
+        int64_t g = groups ? groups[t] : t;
         for (int64_t i = group_off[g]; i < group_off[g + 1]; i++) {
             const double *xi = &sink_x[3 * i];
             double eps2 = eps2_of(sink_eps2, eps2_all, i);

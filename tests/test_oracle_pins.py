@@ -237,3 +237,21 @@ def test_error_falls_with_theta_and_quad_beats_mono():
     assert 1.5 < s_mono < 3.5, s_mono
     assert 2.5 < s_quad < 5.0, s_quad
     assert s_quad > s_mono
+
+
+def test_threaded_oracle_gives_identical_results():
+    """Splitting the groups over host threads changes no bit of the result."""
+    from paper_1812_07313_gb300 import tree as qtree
+    from paper_1812_07313_gb300 import workloads
+    ps = workloads.small_set("plummer", 8000, 21, 1e-2)
+    t = qtree.Tree(ps.x, ps.m, ps.sys_off, 8, 64)
+    L = t.walk(0.5)
+    args = (t.group_off, t.x, t.x, t.m, L.plist_off, L.plist_idx, t.cell_com, t.cell_m, t.cell_q, L.clist_off,
+            L.clist_idx)
+    a1, p1 = oracle.expansion_forces(*args, eps2_all=1e-4)
+    try:
+        oracle.set_threads(4)
+        a2, p2 = oracle.expansion_forces(*args, eps2_all=1e-4)
+    finally:
+        oracle.set_threads(1)
+    assert np.array_equal(a1, a2) and np.array_equal(p1, p2)
