@@ -44,6 +44,10 @@ DESCR = {
     "clumpy_16m": "2^24 particles in the unit cube, 70% in 2000 Plummer clumps + 30% uniform, eps=5e-5, "
                   "n_crit=256",
 }
+# The paper's own kernel speed, quoted as context (another machine, not a target): about 7e8
+# particle-cell interactions/s at large N on one core of the CPU it names (Sec. 5, Fig. 4).
+PAPER_CONTEXT = {"cell_interactions_per_s": 7e8, "cpu": "Intel Xeon E5-2683 v4 (2.1 GHz), 1 core",
+                 "code": "AVX2 FP32, approximate rsqrt, -ffast-math"}
 # Algorithmic FP32 instructions per interaction (FMA = 1): quad 33, mono 13
 OPS_QUAD, OPS_MONO = 33, 13
 
@@ -429,6 +433,7 @@ def run_ours(args, rank, world, local_rank):
                       "l2": "flushed before every timed step (256 MiB device write, outside the step events)",
                       "parallelism": "replicas" if world > 1 else "single GPU",
                       "host_tree_s": host_times},
+           "paper_context": PAPER_CONTEXT,
            "roofline": roofline, "gpu_launches": 3 * args.steps, "clocks": clocks,
            "wall_s_timed_loop": t_wall}
 
