@@ -45,7 +45,7 @@ DESCR = {
                   "n_crit=256",
 }
 # The paper's own kernel speed, quoted as context (another machine, not a target): about 7e8
-# particle-cell interactions/s at large N on one core of the CPU it names (Sec. 5, Fig. 4).
+# particle-cell interactions/s at large N on one core of the CPU it names (Sec. 5.2).
 PAPER_CONTEXT = {"cell_interactions_per_s": 7e8, "cpu": "Intel Xeon E5-2683 v4 (2.1 GHz), 1 core",
                  "code": "AVX2 FP32, approximate rsqrt, -ffast-math"}
 # Algorithmic FP32 instructions per interaction (FMA = 1): quad 33, mono 13
