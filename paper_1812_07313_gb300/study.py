@@ -1,4 +1,4 @@
-"""The paper's accuracy study and its Table 2, on the GPU path.
+"""The paper's accuracy study and its Table 3, on the GPU path.
 
 ``accuracy``: the force error of Eq. 9 for every particle of a 65,536-body
 homogeneous sphere, Plummer model or exponential disk (Sec. 4, Figs. 1-2):
@@ -7,12 +7,12 @@ from FP64 direct summation on the GPU; percentiles and the cumulative
 distribution per theta, monopole-only and quadrupole cells, and the fitted
 slope of the 90% error against theta (the paper finds about 5/2 and 7/2).
 
-``table2``: the wall-clock split of one force evaluation for 4,194,304
-particles (Table 2): T_construct (tree, moments, groups), T_traverse (group
+``table3``: the wall-clock split of one force evaluation for 4,194,304
+particles (Table 3): T_construct (tree, moments, groups), T_traverse (group
 walk), T_force (force kernel), monopole-only against quadrupole at the
 paper's paired thetas, with the 90% error of each row on sampled sinks.
 
-    python -m paper_1812_07313_gb300.study --accuracy --table2
+    python -m paper_1812_07313_gb300.study --accuracy --table3
 """
 from __future__ import annotations
 
@@ -24,11 +24,11 @@ import numpy as np
 from . import gtree, qgrav, workloads
 
 KINDS = {"sphere": "homogeneous sphere", "plummer": "Plummer model", "disk": "exponential disk"}
-# Table 2's rows: (distribution, monopole theta, quadrupole theta)
-TABLE2_PAIRS = [("sphere", 0.3, 0.65), ("sphere", 0.5, 0.75), ("plummer", 0.3, 0.4), ("plummer", 0.5, 0.6),
+# Table 3's rows: (distribution, monopole theta, quadrupole theta)
+TABLE3_PAIRS = [("sphere", 0.3, 0.65), ("sphere", 0.5, 0.75), ("plummer", 0.3, 0.4), ("plummer", 0.5, 0.6),
                 ("disk", 0.3, 0.45), ("disk", 0.5, 0.65)]
 # the paper's T_total [s] of those rows, monopole then quadrupole (Xeon E5-2683 v4, one core)
-TABLE2_PAPER = {("sphere", 0.3): 23.99, ("sphere", 0.65): 10.88, ("sphere", 0.5): 10.26, ("sphere", 0.75): 8.35,
+TABLE3_PAPER = {("sphere", 0.3): 23.99, ("sphere", 0.65): 10.88, ("sphere", 0.5): 10.26, ("sphere", 0.75): 8.35,
                 ("plummer", 0.3): 41.23, ("plummer", 0.4): 44.65, ("plummer", 0.5): 15.13, ("plummer", 0.6): 22.26,
                 ("disk", 0.3): 28.01, ("disk", 0.45): 24.86, ("disk", 0.5): 11.75, ("disk", 0.65): 12.67}
 
@@ -113,7 +113,7 @@ def accuracy(kind, n=65536, seed=7, eps=1e-3, thetas=(0.3, 0.4, 0.45, 0.5, 0.6, 
             "cdf_error_levels": cdf_at.tolist(), "p90_slope": slopes, "fig1_pairs": pairs}
 
 
-def table2(kind, theta_mono, theta_quad, n=1 << 22, seed=11, eps=1e-3, n_crit=256, leaf_max=8, reps=5,
+def table3(kind, theta_mono, theta_quad, n=1 << 22, seed=11, eps=1e-3, n_crit=256, leaf_max=8, reps=5,
            sample_groups=48):
     torch = _torch()
     ps = workloads.small_set(kind, n, seed, eps)
@@ -152,7 +152,7 @@ def table2(kind, theta_mono, theta_quad, n=1 << 22, seed=11, eps=1e-3, n_crit=25
                     "T_traverse_ms": tt, "T_force_ms": tf, "T_total_ms": tc + tt + tf,
                     "p90": float(np.percentile(e, 90)), "p99": float(np.percentile(e, 99)),
                     "sampled_sinks": int(len(sample)), "i_pp": int(st["i_pp"]), "i_pc": int(st["i_pc"]),
-                    "paper_T_total_s": TABLE2_PAPER.get((kind, th))})
+                    "paper_T_total_s": TABLE3_PAPER.get((kind, th))})
     t.close()
     base = out[0]["T_total_ms"]
     for r in out:
@@ -163,7 +163,7 @@ def table2(kind, theta_mono, theta_quad, n=1 << 22, seed=11, eps=1e-3, n_crit=25
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--accuracy", action="store_true")
-    ap.add_argument("--table2", action="store_true")
+    ap.add_argument("--table3", action="store_true")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     res = {}
@@ -173,11 +173,11 @@ def main():
             print(json.dumps({"distribution": r["distribution"], "p90_slope": r["p90_slope"],
                               "p90": {"%s %.2f" % (x["cells"], x["theta"]): x["p90"] for x in r["rows"]}}),
                   flush=True)
-    if args.table2:
-        res["table2"] = []
-        for kind, tm, tq in TABLE2_PAIRS:
-            rows = table2(kind, tm, tq)
-            res["table2"].extend(rows)
+    if args.table3:
+        res["table3"] = []
+        for kind, tm, tq in TABLE3_PAIRS:
+            rows = table3(kind, tm, tq)
+            res["table3"].extend(rows)
             for r in rows:
                 print(json.dumps(r), flush=True)
     if args.out:
