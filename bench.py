@@ -262,7 +262,7 @@ def run_reference(args, rank, world):
 
 def equal_error(torch, qgrav, tr, eps2_all, thetas, flush, stream, steps):
     """For each quadrupole theta: time quadrupole steps, measure their p99 of
-    Eq. 9 against FP64 GPU direct summation on 4096 seeded sinks, find by
+    Eq. 8 against FP64 GPU direct summation on 4096 seeded sinks, find by
     bisection the largest monopole-only theta whose p99 is no larger, and time
     monopole-only steps there (both launch shapes autotuned)."""
     rng = np.random.default_rng(12345)

@@ -8,7 +8,7 @@
  * One step of length dt is kick-drift-kick:
  *     v += a(x) dt/2;   x += v dt;   a, phi = forces(x);   v += a dt/2
  * where forces(x) rebuilds the oct-tree, the sink groups and the
- * interaction lists from the current positions and evaluates Eq. 1 / Eq. 8
+ * interaction lists from the current positions and evaluates Eq. 1 / Eq. 7
  * (quadrupole cells, or monopole-only cells) on them.
  *
  * Particles keep the caller's order (the tree's sorted order is internal).

@@ -13,7 +13,7 @@
  *         phi_i   -= phi_mono + phi_quad                            (Eq. 1)
  *         a_i     += (phi_mono + 5 phi_quad) / rhat^2 r - Q_c r / rhat^5
  *   with r = r_j - r_i and rhat^2 = |r|^2 + eps_i^2.  The acceleration is
- *   -grad of Eq. 1 (Eq. 7); the leading minus sign printed in Eq. 8 is a
+ *   -grad of Eq. 1 (Eq. 6); the leading minus sign printed in Eq. 7 is a
  *   typesetting slip (it would make gravity repulsive) and is not applied.
  *   G = 1: masses carry G.  phi is the physical (negative) potential.
  *   A pair with rhat^2 == 0 exactly (zero softening, coincident points)
@@ -212,7 +212,7 @@ const char *qg_last_error(const qg_ctx *ctx);
 
 /*
  * Direct summation on the GPU (the reference of the paper's force-error
- * measure, Eq. 9): every source acts on every sink as a Plummer point mass,
+ * measure, Eq. 8): every source acts on every sink as a Plummer point mass,
  * all in FP64.  Device pointers: sink_x [nsink][3], src_x [nsrc][3],
  * src_m [nsrc], outputs a [nsink][3], phi [nsink].  Pairs with rhat^2 == 0
  * are skipped.  Synchronous.  Used to measure the method's own error; it is

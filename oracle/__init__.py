@@ -11,11 +11,11 @@ marshals numpy arrays through ctypes.
 
 Functions and the passages of the paper they follow:
   * ``cell_moments``      -- Eq. 2 (quadrupole tensor about the centre of mass)
-  * ``expansion_forces``  -- Eq. 1, Eqs. 4-5 and Eq. 8 (sign as -grad of Eq. 1),
+  * ``expansion_forces``  -- Eq. 1, Eqs. 4-5 and Eq. 7 (sign as -grad of Eq. 1),
                              over the shared interaction lists of the modified
                              tree algorithm (Sec. 3.4)
-  * ``direct_forces``     -- direct summation, the reference of Eq. 9
-  * ``relative_error``    -- Eq. 9
+  * ``direct_forces``     -- direct summation, the reference of Eq. 8
+  * ``relative_error``    -- Eq. 8
   * ``set_threads``       -- optional split of expansion_forces' groups over
                              host threads (for the multi-core CPU baseline)
 """
@@ -145,7 +145,7 @@ def cell_moments(x, m):
 def expansion_forces(group_off, sink_x, src_x, src_m, plist_off, plist_idx,
                      cell_com, cell_m, cell_q, clist_off, clist_idx,
                      eps2_all=0.0, sink_eps2=None, use_quad=True, groups=None):
-    """Eq. 1 / Eq. 8 over grouped interaction lists, all in double.
+    """Eq. 1 / Eq. 7 over grouped interaction lists, all in double.
 
     Returns (a [n,3], phi [n]).  With ``groups`` given, only those groups are
     evaluated and the other sinks' rows are NaN.
@@ -206,7 +206,7 @@ def set_threads(n):
 
 
 def relative_error(a_test, a_ref):
-    """Eq. 9: |a_test - a_ref| / |a_ref| per sink."""
+    """Eq. 8: |a_test - a_ref| / |a_ref| per sink."""
     a_test = np.asarray(a_test, dtype=np.float64)
     a_ref = np.asarray(a_ref, dtype=np.float64)
     return np.linalg.norm(a_test - a_ref, axis=1) / np.linalg.norm(a_ref, axis=1)

@@ -17,7 +17,7 @@
  *   - r_ij = r_j - r_i, rhat^2 = |r_ij|^2 + eps_i^2 (Plummer softening in
  *     every term, including the rhat^5 of the quadrupole term, Eq. 1).
  *   - phi is the physical potential, negative (Eq. 1).
- *   - a = -grad phi (Eq. 7).  Eq. 8 as printed carries a leading minus sign
+ *   - a = -grad phi (Eq. 6).  Eq. 7 as printed carries a leading minus sign
  *     which, with r_ij = r_j - r_i, would make gravity repulsive; -grad of
  *     Eq. 1 worked out by hand (and the paper's own step list, which adds the
  *     first term and subtracts the second) gives
@@ -109,7 +109,7 @@ static void particle_term(const double xi[3], double eps2,
 
 /* ------------------------------------------------------------------ */
 /* One tree cell acting on one sink: Eq. 1 (potential), Eqs. 4-5 and the */
-/* sign-corrected Eq. 8 (acceleration).  With use_quad == 0 the cell is  */
+/* sign-corrected Eq. 7 (acceleration).  With use_quad == 0 the cell is  */
 /* a point mass at its centre of mass (monopole-only tree code).         */
 /* ------------------------------------------------------------------ */
 static void cell_term(const double xi[3], double eps2,
@@ -142,7 +142,7 @@ static void cell_term(const double xi[3], double eps2,
     double phi_mono = mj / rhat;                 /* Eq. 4 */
     double phi_quad = dQd / (2.0 * rhat5);       /* Eq. 5 */
     *pot -= phi_mono + phi_quad;                 /* Eq. 1 */
-    for (int a = 0; a < 3; a++)                  /* Eq. 8, sign corrected */
+    for (int a = 0; a < 3; a++)                  /* Eq. 7, sign corrected */
         acc[a] += (phi_mono + 5.0 * phi_quad) / rhat2 * d[a] - Qd[a] / rhat5;
 }
 
@@ -214,7 +214,7 @@ int qgo_expansion_forces(int64_t ngroups, const int64_t *group_off,
 
 /* ------------------------------------------------------------------ */
 /* Direct O(N^2) summation (the "direct particle-particle method" that   */
-/* Eq. 9 measures the tree force against): every source particle acts on */
+/* Eq. 8 measures the tree force against): every source particle acts on */
 /* every listed sink as a Plummer point mass.  sinks[k] (k < nsink) are  */
 /* [3] positions; eps2 per sink or global.  Pairs with rhat^2 == 0 are   */
 /* skipped, so a sink that is also a source with eps = 0 gets no self    */

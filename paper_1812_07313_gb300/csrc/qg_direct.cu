@@ -1,5 +1,5 @@
 // qg_direct.cu -- direct O(N^2) summation on the GPU in FP64: the reference
-// of the paper's relative force error (Eq. 9), used to measure the tree
+// of the paper's relative force error (Eq. 8), used to measure the tree
 // method's own error.  Not part of the timed force step.
 #include <cuda_runtime.h>
 

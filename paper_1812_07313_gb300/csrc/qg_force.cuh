@@ -1,5 +1,5 @@
 // qg_force.cuh -- the persistent group-force kernel (monopole particles +
-// quadrupole cells, Kodama & Ishiyama arXiv:1812.07313, Eqs. 1, 4-8).
+// quadrupole cells, Kodama & Ishiyama arXiv:1812.07313, Eqs. 1, 4-7).
 //
 // One CTA evaluates one sink group at a time, taking group ids from a
 // device work queue (ordered by descending cost) with an atomic counter.
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
         }
       }
 
-      // ---- 3-4. cell part of the list (Eq. 1 / Eq. 8, or monopole) --------
+      // ---- 3-4. cell part of the list (Eq. 1 / Eq. 7, or monopole) --------
       for (int64_t base = c0; base < c1; base += TK) {
         const int cnt = (int)min((int64_t)TK, c1 - base);
         __syncthreads();  // the previous tile's readers are done

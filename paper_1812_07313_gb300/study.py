@@ -1,6 +1,6 @@
 """The paper's accuracy study and its Table 3, on the GPU path.
 
-``accuracy``: the force error of Eq. 9 for every particle of a 65,536-body
+``accuracy``: the force error of Eq. 8 for every particle of a 65,536-body
 homogeneous sphere, Plummer model or exponential disk (Sec. 4, Figs. 1-2):
 the tree forces from the GPU tree, walk and FP32 force kernel, the reference
 from FP64 direct summation on the GPU; percentiles and the cumulative

@@ -1,4 +1,4 @@
-"""The method's force error (Eq. 9) against the paper's accuracy study
+"""The method's force error (Eq. 8) against the paper's accuracy study
 (Sec. 4, Figs. 1-2), with the FP64 oracle on lists from the host walk and
 direct summation on sampled groups, N = 65,536 per distribution:
   * the error at 90% of the particles grows roughly as theta^(5/2) with

@@ -17,7 +17,7 @@ PINS = [
 
 # (description, text in the oracle source, replacement)
 MUTANTS = [
-    ("5 of Eq. 8 -> 4", "(phi_mono + 5.0 * phi_quad)", "(phi_mono + 4.0 * phi_quad)"),
+    ("5 of Eq. 7 -> 4", "(phi_mono + 5.0 * phi_quad)", "(phi_mono + 4.0 * phi_quad)"),
     ("1/2 of Eq. 5 dropped", "dQd / (2.0 * rhat5)", "dQd / (1.0 * rhat5)"),
     ("sign of the Q r term", "- Qd[a] / rhat5", "+ Qd[a] / rhat5"),
     ("Q transposed index", "{ q[1], q[3], q[4] },", "{ q[2], q[3], q[4] },"),

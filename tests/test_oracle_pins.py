@@ -3,7 +3,7 @@
 Each test fixes the oracle to a closed form, a brute-force sum, an invariant or
 a limit that the paper and the mathematics determine, so that a plausible slip
 in the oracle (a dropped term, a wrong sign, the 1/2 of Eq. 5 or the 5 of
-Eq. 8 misplaced, a transposed Q index) fails at least one of them.
+Eq. 7 misplaced, a transposed Q index) fails at least one of them.
 """
 import os
 
@@ -104,7 +104,7 @@ def test_one_particle_cell_is_point_mass():
     np.testing.assert_allclose(phi, phid, rtol=1e-14)
 
 
-# ---------------------------------------------------------------- Eq. 1 / Eq. 8
+# ---------------------------------------------------------------- Eq. 1 / Eq. 7
 
 @pytest.mark.parametrize("use_quad,slope", [(False, 2.0), (True, 3.0)])
 def test_expansion_error_order(use_quad, slope):
@@ -130,8 +130,8 @@ def test_expansion_error_order(use_quad, slope):
 
 
 def test_force_is_minus_gradient_of_potential():
-    """Central differences of the oracle's phi reproduce its a (Eq. 7): this
-    fixes the sign and every coefficient of Eq. 8 against Eq. 1."""
+    """Central differences of the oracle's phi reproduce its a (Eq. 6): this
+    fixes the sign and every coefficient of Eq. 7 against Eq. 1."""
     rng = np.random.default_rng(7)
     src = rng.uniform(-1, 1, (9, 3)) + np.array([2.0, 0, 0])
     srcm = rng.uniform(0.1, 1.0, 9)
@@ -214,7 +214,7 @@ def test_theta_zero_is_direct_summation():
 
 
 def test_error_falls_with_theta_and_quad_beats_mono():
-    """p90 of Eq. 9 falls as theta shrinks; with quadrupoles it is lower than
+    """p90 of Eq. 8 falls as theta shrinks; with quadrupoles it is lower than
     monopole-only at the same theta and falls more steeply (Sec. 4: roughly
     theta^(5/2) and theta^(7/2))."""
     ps, tr = _tree("sphere", 8192, 31, 1e-2, n_crit=64)
