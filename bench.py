@@ -607,9 +607,12 @@ def precision_compare(torch, qgrav, ctx, tr, L, eps2_all, eps2, stream, flush, s
 
 def e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world, options=None, steps=5):
     """The step through the C-ABI from pinned host arrays: qg_evaluate_host
-    copies the sinks, sources and cells, streams the lists in while the
-    kernel runs on the groups already there, and copies the results back
-    (the positions are one array, sinks and sources: copied once)."""
+    copies the sinks, sources and cells (the positions are one array, sinks
+    and sources: copied once); on a coherent CPU-GPU link the force kernel
+    then reads the lists from host memory and writes the results there,
+    else the lists are copied in chunks while the kernel runs on the groups
+    already there and the results copied back.  Either way every input byte
+    crosses to the device and every result byte back, each step."""
     tdt = {np.dtype("float64"): torch.float64, np.dtype("int64"): torch.int64,
            np.dtype("int32"): torch.int32, np.dtype("float32"): torch.float32}
 
@@ -636,10 +639,13 @@ def e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world, options=None, steps=5
     for _ in range(steps):
         step()
     dt = (time.perf_counter() - t0) / steps
+    in_place = bool(ctx.qg_get_stats()["eval_in_place"])
     ctx.close()
+    route = ("lists read and results written in place by the force kernel over the coherent CPU-GPU link"
+             if in_place else "list copies overlapped with the force kernel, results copied back")
     return {"value": world * inter / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-            "ms_per_step": dt * 1e3, "api": "qg_evaluate_host (pinned host arrays in and out, list copies "
-                                            "overlapped with the force kernel), wall clock"}
+            "ms_per_step": dt * 1e3, "lists_in_place": in_place,
+            "api": "qg_evaluate_host (pinned host arrays in and out; %s), wall clock" % route}
 
 
 # the translation unit of the FP32 force kernels (its launch shape is part of the record's key)

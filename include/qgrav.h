@@ -104,6 +104,8 @@ typedef struct {
   int32_t warps_per_group;
   int32_t flush_j;
   int32_t paired;             /* 1 if the paired-FP32 form runs              */
+  int32_t eval_in_place;      /* 1 if the last qg_evaluate_host read the
+                                 lists and wrote the results in place       */
 } qg_stats;
 
 /* Create a context on CUDA device `device`.  opt may be NULL (defaults). */
@@ -183,15 +185,25 @@ qg_status qg_get_forces_dev(qg_ctx *ctx, double *a, double *phi, void *cuda_stre
  * One evaluation from HOST arrays: the inputs of qg_set_sinks, qg_set_sources
  * and qg_set_cells (same meaning, layout and checks), then the forces written
  * to a [n][3] and phi [n] (host).  The sinks, sources and cells are copied
- * first; the particle and cell lists follow in four chunks of groups on a
- * second stream while the force kernel runs over the chunks already copied,
- * and each chunk's results are copied back as soon as its kernel ends.  When
- * src_x is the same array as sink_x (and ns == n) it is copied once.  The
- * results are bit for bit those of the separate calls at the same options.
- * Afterwards the context holds these inputs (qg_run, qg_get_forces,
+ * first (one copy of x when src_x is the same array as sink_x and ns == n).
+ * The lists then take one of two routes:
+ *   - in place, when plist_idx, clist_idx, a and phi are all page-locked
+ *     (cudaHostAlloc / cudaHostRegister), the GPU reads host memory
+ *     through the host's page tables (a coherent CPU-GPU link, as on
+ *     Grace-Blackwell) and the options select the FP32 centred precision in
+ *     the scalar form: one persistent force launch reads every list index
+ *     from host memory, checks it and keeps it in the context's device
+ *     lists, and writes the results to the device and to a / phi; nothing
+ *     is copied back;
+ *   - otherwise copied in four chunks of groups while the force kernel runs
+ *     over the chunks already there, each chunk's results copied back as
+ *     soon as its kernel ends.
+ * qg_stats.eval_in_place tells which.  Either way the results are bit for
+ * bit those of the separate calls at the same options, and afterwards the
+ * context holds these inputs and results (qg_run, qg_get_forces,
  * qg_autotune, qg_last_timing work on them).  Synchronous.  A list entry
- * outside [0, ns) or [0, nc) gives QG_ERR_ARG; the kernel reads a valid
- * record in its place, so nothing is read out of bounds.
+ * outside [0, ns) or [0, nc) gives QG_ERR_ARG; the kernel reads entry 0 in
+ * its place, so nothing is read out of bounds.
  */
 qg_status qg_evaluate_host(qg_ctx *ctx, int64_t n, const double *sink_x, const float *sink_eps2, double eps2_all,
                            int64_t ngroups, const int64_t *group_off, int64_t ns, const double *src_x,

@@ -141,9 +141,12 @@ struct qg_ctx {
   cudaStream_t copy_in = nullptr, copy_out = nullptr, chunk_stream[4] = {};
   cudaEvent_t chunk_in[8] = {}, chunk_done[8] = {}, inputs_ready = nullptr, packed = nullptr;
   DevBuf<double> stage_src;  // source positions when they are not the sinks' array
+  int coherent_host = -1;    // device reads host memory through the host's page tables (-1: not asked yet)
   qg_stats stats{};
-  // chosen launch
-  const void *kernel = nullptr;
+  // chosen launch (kernel_inplace: the same variant reading its lists from
+  // host memory, or null where none is built)
+  const void *kernel = nullptr, *kernel_inplace = nullptr;
+  int grid_inplace = 0;
   int R = 4, nthreads = 128, tile = 256, flush = 128, grid = 0;
   size_t smem = 0;
 };
@@ -268,6 +271,19 @@ qg_status choose_kernel(qg_ctx *c) {
   QG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, nt, smem));
   if (per_sm < 1) return fail(c, QG_ERR_ARG, "force kernel does not fit on an SM (smem %zu)", smem);
   c->kernel = k;
+  c->kernel_inplace = nullptr;
+  if (o.precision == QG_FP32_CENTRED && !paired) {
+    const void *ki = qg::force_kernel_inplace(R, quad, guard);
+    int per_sm_i = 0;
+    if (ki) {
+      QG_CUDA(c, cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      QG_CUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_i, ki, nt, smem));
+    }
+    if (per_sm_i >= 1) {
+      c->kernel_inplace = ki;
+      c->grid_inplace = per_sm_i * c->num_sms;
+    }
+  }
   c->R = R;
   c->nthreads = nt;
   c->tile = tile;
@@ -820,11 +836,34 @@ qg_status qg_last_timing(qg_ctx *c, float *step_ms, float *force_ms) {
   return QG_OK;
 }
 
-// One evaluation from host arrays with the list copies overlapped: the
-// sinks, sources and cells are copied (and packed) first, the two lists
-// follow in chunks of groups on a second stream while the force kernel runs
-// on the chunks already there, and each chunk's results are copied back on a
-// third stream as soon as its kernel ends.
+// Device address of page-locked host memory at h, or nullptr when the
+// device cannot address it in place.  In-place access is only used on a GPU
+// that reads host memory through the host's own page tables (a coherent
+// CPU-GPU link): there every valid host address is reachable, so an array
+// that starts in a page-locked allocation and runs past its end still reads
+// correctly.
+const void *in_place(qg_ctx *c, const void *h) {
+  if (c->coherent_host < 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrPageableMemoryAccessUsesHostPageTables, c->device) != cudaSuccess)
+      v = 0;
+    c->coherent_host = v ? 1 : 0;
+  }
+  if (!c->coherent_host || !h) return nullptr;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+// One evaluation from host arrays.  The sinks, sources and cells are copied
+// (and packed) first.  The lists are then either read in place by one
+// persistent launch (page-locked host memory on a coherent link) or copied
+// in chunks of groups on a second stream while the force kernel runs on the
+// chunks already there, each chunk's results copied back on a third stream
+// as soon as its kernel ends.
 qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const float *sink_eps2, double eps2_all,
                            int64_t ngroups, const int64_t *group_off, int64_t ns, const double *src_x,
                            const double *src_m, const int64_t *plist_off, const int32_t *plist_idx, int64_t nc,
@@ -852,6 +891,9 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
   const int64_t np_tot = plist_off[G], nc_tot = clist_off[G];
   if ((np_tot > 0 && !plist_idx) || (nc_tot > 0 && !clist_idx))
     return fail(c, QG_ERR_ARG, "qg_evaluate_host: list_idx is NULL");
+  // with no sources (cells) every entry of a non-empty list is out of range
+  if ((np_tot > 0 && ns == 0) || (nc_tot > 0 && nc == 0))
+    return fail(c, QG_ERR_ARG, "qg_evaluate_host: list entries but no sources or cells");
   bool pos = eps2_all > 0;
   if (sink_eps2) {
     pos = true;
@@ -918,80 +960,120 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
   QG_CUDA(c, cudaGetLastError());
   QG_CUDA(c, cudaMemsetAsync(c->scratch.p, 0, kChunks * kScr * sizeof(int), s));
   QG_CUDA(c, cudaEventRecord(c->ev[0], s));
-  QG_CUDA(c, cudaEventRecord(c->packed, s));
-  // ---- chunks of groups by list entries: 1/8, 1/4, 1/4, 3/8 of them, so
-  // that the first kernel waits for a small first copy
-  int64_t gb[kChunks + 1];
-  gb[0] = 0;
-  {
-    const int64_t total = np_tot + nc_tot;
-    const int eighths[kChunks] = {1, 3, 5, 8};  // cumulative, in eighths
-    int64_t g = 0;
-    for (int k = 1; k < kChunks; k++) {
-      const int64_t want = total / 8 * eighths[k - 1];
-      while (g < G && plist_off[g] + clist_off[g] < want) g++;
-      gb[k] = g;
+  // ---- in place: lists and results in page-locked memory the device reads
+  // and writes over a coherent link (FP32 centred, scalar form).  One queue
+  // and one persistent launch over all groups; the kernel reads each list
+  // index from the host, checks it and keeps it in the device lists, and
+  // writes the results both to the device buffers and to a / phi.  No list
+  // copy, no copy back.
+  const void *pi_h = np_tot > 0 ? in_place(c, plist_idx) : nullptr, *ci_h = nc_tot > 0 ? in_place(c, clist_idx) : nullptr;
+  const void *a_h = n > 0 ? in_place(c, a) : nullptr, *phi_h = n > 0 ? in_place(c, phi) : nullptr;
+  const bool direct = c->kernel_inplace && n > 0 && G > 0 && (np_tot == 0 || pi_h) && (nc_tot == 0 || ci_h) && a_h &&
+                      phi_h;
+  c->stats.eval_in_place = direct ? 1 : 0;
+  if (direct) {
+    int *hist = c->scratch.p, *cursor = hist + kBuckets, *head = cursor + kBuckets, *bad = head + 1;
+    const double cell_ops = c->opt.expansion == QG_QUAD ? 33.0 : 13.0;
+    queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->goff.p, c->poff.p, c->coff.p, cell_ops, c->bucket.p,
+                                                        hist);
+    queue_scatter_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->bucket.p, hist, cursor, c->queue.p);
+    QG_CUDA(c, cudaGetLastError());
+    qg::ForceParams fp = force_params(c, 0, G, head);
+    fp.plist_idx = static_cast<const int32_t *>(pi_h);
+    fp.clist_idx = static_cast<const int32_t *>(ci_h);
+    fp.plist_keep = c->pidx.p;
+    fp.clist_keep = c->cidx.p;
+    fp.n_src = (int32_t)ns;
+    fp.n_cell = (int32_t)nc;
+    fp.bad = bad;
+    fp.a_host = static_cast<double *>(const_cast<void *>(a_h));
+    fp.phi_host = static_cast<double *>(const_cast<void *>(phi_h));
+    const int grid = (int)std::min<int64_t>(c->grid_inplace, G);
+    void *args[] = {&fp};
+    QG_CUDA(c, cudaEventRecord(c->ev[1], s));
+    QG_CUDA(c, cudaLaunchKernel(c->kernel_inplace, dim3(grid), dim3(c->nthreads), args, c->smem, s));
+    QG_CUDA(c, cudaEventRecord(c->ev[2], s));
+    c->stats.grid = grid;
+    int hbad = 0;
+    QG_CUDA(c, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    QG_CUDA(c, cudaStreamSynchronize(s));
+    if (hbad) return fail(c, QG_ERR_ARG, "qg_evaluate_host: list entry outside its source or cell range");
+  } else {
+    QG_CUDA(c, cudaEventRecord(c->packed, s));
+    // ---- chunks of groups by list entries: 1/8, 1/4, 1/4, 3/8 of them, so
+    // that the first kernel waits for a small first copy
+    int64_t gb[kChunks + 1];
+    gb[0] = 0;
+    {
+      const int64_t total = np_tot + nc_tot;
+      const int eighths[kChunks] = {1, 3, 5, 8};  // cumulative, in eighths
+      int64_t g = 0;
+      for (int k = 1; k < kChunks; k++) {
+        const int64_t want = total / 8 * eighths[k - 1];
+        while (g < G && plist_off[g] + clist_off[g] < want) g++;
+        gb[k] = g;
+      }
+      gb[kChunks] = G;
     }
-    gb[kChunks] = G;
-  }
-  for (int k = 0; k < kChunks; k++) {
-    const int64_t g0 = gb[k], g1 = gb[k + 1];
-    const int64_t p0 = plist_off[g0], p1 = plist_off[g1], c0 = clist_off[g0], c1 = clist_off[g1];
-    if (p1 > p0)
-      QG_CUDA(c, cudaMemcpyAsync(c->pidx.p + p0, plist_idx + p0, (p1 - p0) * sizeof(int32_t),
-                                 cudaMemcpyHostToDevice, c->copy_in));
-    if (c1 > c0)
-      QG_CUDA(c, cudaMemcpyAsync(c->cidx.p + c0, clist_idx + c0, (c1 - c0) * sizeof(int32_t),
-                                 cudaMemcpyHostToDevice, c->copy_in));
-    QG_CUDA(c, cudaEventRecord(c->chunk_in[k], c->copy_in));
-  }
-  // each chunk on its own stream, so that a chunk's kernel fills the SMs its
-  // predecessor's last groups leave idle
-  const double cell_ops = c->opt.expansion == QG_QUAD ? 33.0 : 13.0;
-  for (int k = 0; k < kChunks; k++) {
-    const int64_t g0 = gb[k], g1 = gb[k + 1], Gk = g1 - g0;
-    int *hist = c->scratch.p + k * kScr, *cursor = hist + kBuckets, *head = cursor + kBuckets, *bad = head + 1;
-    cudaStream_t sk = c->chunk_stream[k];
-    QG_CUDA(c, cudaStreamWaitEvent(sk, c->packed, 0));
-    QG_CUDA(c, cudaStreamWaitEvent(sk, c->chunk_in[k], 0));
-    if (Gk > 0) {
+    for (int k = 0; k < kChunks; k++) {
+      const int64_t g0 = gb[k], g1 = gb[k + 1];
       const int64_t p0 = plist_off[g0], p1 = plist_off[g1], c0 = clist_off[g0], c1 = clist_off[g1];
-      if (p1 > p0) sanitize_index_kernel<<<grid_for(p1 - p0, 256), 256, 0, sk>>>(p1 - p0, c->pidx.p + p0, ns, bad);
-      if (c1 > c0) sanitize_index_kernel<<<grid_for(c1 - c0, 256), 256, 0, sk>>>(c1 - c0, c->cidx.p + c0, nc, bad);
-      queue_hist_kernel<<<grid_for(Gk, 256), 256, 0, sk>>>(Gk, c->goff.p + g0, c->poff.p + g0, c->coff.p + g0,
-                                                           cell_ops, c->bucket.p + g0, hist);
-      queue_scatter_kernel<<<grid_for(Gk, 256), 256, 0, sk>>>(Gk, c->bucket.p + g0, hist, cursor, c->queue.p + g0);
-      QG_CUDA(c, cudaGetLastError());
-      qg::ForceParams fp = force_params(c, g0, Gk, head);
-      const int grid = (int)std::min<int64_t>(c->grid, Gk);
-      void *args[] = {&fp};
-      if (k == 0) QG_CUDA(c, cudaEventRecord(c->ev[1], sk));
-      QG_CUDA(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(c->nthreads), args, c->smem, sk));
-    } else if (k == 0) {
-      QG_CUDA(c, cudaEventRecord(c->ev[1], sk));
+      if (p1 > p0)
+        QG_CUDA(c, cudaMemcpyAsync(c->pidx.p + p0, plist_idx + p0, (p1 - p0) * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, c->copy_in));
+      if (c1 > c0)
+        QG_CUDA(c, cudaMemcpyAsync(c->cidx.p + c0, clist_idx + c0, (c1 - c0) * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, c->copy_in));
+      QG_CUDA(c, cudaEventRecord(c->chunk_in[k], c->copy_in));
     }
-    QG_CUDA(c, cudaEventRecord(c->chunk_done[k], sk));
-    QG_CUDA(c, cudaStreamWaitEvent(s, c->chunk_done[k], 0));
-    // results of this chunk's sinks back to the host
-    const int64_t s0 = group_off[g0], s1 = group_off[g1];
-    QG_CUDA(c, cudaStreamWaitEvent(c->copy_out, c->chunk_done[k], 0));
-    if (s1 > s0) {
-      QG_CUDA(c, cudaMemcpyAsync(a + 3 * s0, c->a.p + 3 * s0, 3 * (s1 - s0) * sizeof(double),
+    // each chunk on its own stream, so that a chunk's kernel fills the SMs its
+    // predecessor's last groups leave idle
+    const double cell_ops = c->opt.expansion == QG_QUAD ? 33.0 : 13.0;
+    for (int k = 0; k < kChunks; k++) {
+      const int64_t g0 = gb[k], g1 = gb[k + 1], Gk = g1 - g0;
+      int *hist = c->scratch.p + k * kScr, *cursor = hist + kBuckets, *head = cursor + kBuckets, *bad = head + 1;
+      cudaStream_t sk = c->chunk_stream[k];
+      QG_CUDA(c, cudaStreamWaitEvent(sk, c->packed, 0));
+      QG_CUDA(c, cudaStreamWaitEvent(sk, c->chunk_in[k], 0));
+      if (Gk > 0) {
+        const int64_t p0 = plist_off[g0], p1 = plist_off[g1], c0 = clist_off[g0], c1 = clist_off[g1];
+        if (p1 > p0) sanitize_index_kernel<<<grid_for(p1 - p0, 256), 256, 0, sk>>>(p1 - p0, c->pidx.p + p0, ns, bad);
+        if (c1 > c0) sanitize_index_kernel<<<grid_for(c1 - c0, 256), 256, 0, sk>>>(c1 - c0, c->cidx.p + c0, nc, bad);
+        queue_hist_kernel<<<grid_for(Gk, 256), 256, 0, sk>>>(Gk, c->goff.p + g0, c->poff.p + g0, c->coff.p + g0,
+                                                             cell_ops, c->bucket.p + g0, hist);
+        queue_scatter_kernel<<<grid_for(Gk, 256), 256, 0, sk>>>(Gk, c->bucket.p + g0, hist, cursor, c->queue.p + g0);
+        QG_CUDA(c, cudaGetLastError());
+        qg::ForceParams fp = force_params(c, g0, Gk, head);
+        const int grid = (int)std::min<int64_t>(c->grid, Gk);
+        void *args[] = {&fp};
+        if (k == 0) QG_CUDA(c, cudaEventRecord(c->ev[1], sk));
+        QG_CUDA(c, cudaLaunchKernel(c->kernel, dim3(grid), dim3(c->nthreads), args, c->smem, sk));
+      } else if (k == 0) {
+        QG_CUDA(c, cudaEventRecord(c->ev[1], sk));
+      }
+      QG_CUDA(c, cudaEventRecord(c->chunk_done[k], sk));
+      QG_CUDA(c, cudaStreamWaitEvent(s, c->chunk_done[k], 0));
+      // results of this chunk's sinks back to the host
+      const int64_t s0 = group_off[g0], s1 = group_off[g1];
+      QG_CUDA(c, cudaStreamWaitEvent(c->copy_out, c->chunk_done[k], 0));
+      if (s1 > s0) {
+        QG_CUDA(c, cudaMemcpyAsync(a + 3 * s0, c->a.p + 3 * s0, 3 * (s1 - s0) * sizeof(double),
+                                   cudaMemcpyDeviceToHost, c->copy_out));
+        QG_CUDA(c, cudaMemcpyAsync(phi + s0, c->phi.p + s0, (s1 - s0) * sizeof(double), cudaMemcpyDeviceToHost,
+                                   c->copy_out));
+      }
+    }
+    QG_CUDA(c, cudaEventRecord(c->ev[2], s));
+    c->stats.grid = (int)std::min<int64_t>(c->grid, std::max<int64_t>(G, 1));
+    int hbad[kChunks] = {0, 0, 0, 0};
+    for (int k = 0; k < kChunks; k++)
+      QG_CUDA(c, cudaMemcpyAsync(&hbad[k], c->scratch.p + k * kScr + 2 * kBuckets + 1, sizeof(int),
                                  cudaMemcpyDeviceToHost, c->copy_out));
-      QG_CUDA(c, cudaMemcpyAsync(phi + s0, c->phi.p + s0, (s1 - s0) * sizeof(double), cudaMemcpyDeviceToHost,
-                                 c->copy_out));
-    }
+    QG_CUDA(c, cudaStreamSynchronize(c->copy_out));
+    QG_CUDA(c, cudaStreamSynchronize(s));
+    for (int k = 0; k < kChunks; k++)
+      if (hbad[k]) return fail(c, QG_ERR_ARG, "qg_evaluate_host: list entry outside its source or cell range");
   }
-  QG_CUDA(c, cudaEventRecord(c->ev[2], s));
-  c->stats.grid = (int)std::min<int64_t>(c->grid, std::max<int64_t>(G, 1));
-  int hbad[kChunks] = {0, 0, 0, 0};
-  for (int k = 0; k < kChunks; k++)
-    QG_CUDA(c, cudaMemcpyAsync(&hbad[k], c->scratch.p + k * kScr + 2 * kBuckets + 1, sizeof(int),
-                               cudaMemcpyDeviceToHost, c->copy_out));
-  QG_CUDA(c, cudaStreamSynchronize(c->copy_out));
-  QG_CUDA(c, cudaStreamSynchronize(s));
-  for (int k = 0; k < kChunks; k++)
-    if (hbad[k]) return fail(c, QG_ERR_ARG, "qg_evaluate_host: list entry outside its source or cell range");
   // the context now holds these inputs, as after the qg_set_* calls and qg_run
   c->h_goff.assign(group_off, group_off + G + 1);
   c->h_poff.assign(plist_off, plist_off + G + 1);

@@ -195,6 +195,18 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+// A list index read in place from host memory: checked against its array
+// (an entry outside it counts in *bad and becomes 0, a valid record) and
+// kept on the device at its list position.
+__device__ __forceinline__ int keep_index(int j, int lim, int32_t *keep, int *bad) {
+  if ((unsigned)j >= (unsigned)lim) {
+    atomicOr(bad, 1);
+    j = 0;
+  }
+  *keep = j;
+  return j;
+}
+
 // Launch bounds per variant: the largest block it is launched with and the
 // CTAs per SM the register budget must allow.  Scalar R <= 4: 3 blocks of 256
 // threads leaves 80 registers a thread (72 used at R = 2), which still fits
@@ -207,7 +219,12 @@ template <typename Real, int R, bool PAIRED> struct Bounds {
   static constexpr int min_blocks = (R >= 8 || sizeof(Real) == 8 || (PAIRED && R >= 4)) ? 2 : 3;
 };
 
-template <typename Real, int R, bool QUAD, bool GUARD, bool CENTRED, bool PAIRED>
+// INPLACE: the lists are read from host memory (checked and kept as they
+// are read, ForceParams::plist_keep) and the results also written to host
+// memory (ForceParams::a_host), a[] through shared memory so that a warp
+// writes consecutive words.  A separate instantiation, so that the kernel
+// the graph replays carries none of it.
+template <typename Real, int R, bool QUAD, bool GUARD, bool CENTRED, bool PAIRED, bool INPLACE = false>
 __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real, R, PAIRED>::min_blocks)
     force_kernel(const ForceParams p) {
   static_assert(!PAIRED || (sizeof(Real) == 4 && R % 2 == 0), "paired arithmetic: FP32, even R");
@@ -249,7 +266,16 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
     const int g = p.queue[item];
     const int64_t s0 = p.group_off[g];
     const int ni = (int)(p.group_off[g + 1] - s0);
-    if (ni <= 0) continue;
+    constexpr bool keep = INPLACE;
+    if (ni <= 0) {
+      if (keep) {  // no sinks: the lists are only checked and kept
+        for (int64_t e = p.plist_off[g] + tid; e < p.plist_off[g + 1]; e += NT)
+          keep_index(p.plist_idx[e], p.n_src, p.plist_keep + e, p.bad);
+        for (int64_t e = p.clist_off[g] + tid; e < p.clist_off[g + 1]; e += NT)
+          keep_index(p.clist_idx[e], p.n_cell, p.clist_keep + e, p.bad);
+      }
+      continue;
+    }
 
     // ---- 1. group centre: bounding box of the sinks ----------------------
     double cx = 0.0, cy = 0.0, cz = 0.0;
@@ -396,8 +422,12 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
           for (int t = tid; t < cnt; t += 2 * NT) {
             const int t1 = t + NT;
             const bool first = t == tid;
-            const int j0 = first ? pf0 : p.plist_idx[base + t];
-            const int j1 = t1 < cnt ? (first ? pf1 : p.plist_idx[base + t1]) : j0;
+            int j0 = first ? pf0 : p.plist_idx[base + t];
+            int j1 = t1 < cnt ? (first ? pf1 : p.plist_idx[base + t1]) : j0;
+            if (keep) {
+              j0 = keep_index(j0, p.n_src, p.plist_keep + base + t, p.bad);
+              j1 = t1 < cnt ? keep_index(j1, p.n_src, p.plist_keep + base + t1, p.bad) : j0;
+            }
             const PosMass v0 = p.src[j0];
             const PosMass v1 = p.src[j1];
             put_p(t, v0, j0);
@@ -405,7 +435,8 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
           }
         } else {
           for (int t = tid; t < cnt; t += NT) {
-            const int j = t == tid ? pf0 : (t == tid + NT ? pf1 : p.plist_idx[base + t]);
+            int j = t == tid ? pf0 : (t == tid + NT ? pf1 : p.plist_idx[base + t]);
+            if (keep) j = keep_index(j, p.n_src, p.plist_keep + base + t, p.bad);
             put_p(t, p.src[j], j);
           }
         }
@@ -473,8 +504,12 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
           for (int t = tid; t < cnt; t += 2 * NT) {
             const int t1 = t + NT;
             const bool first = t == tid;
-            const int j0 = first ? pf0 : p.clist_idx[base + t];
-            const int j1 = t1 < cnt ? (first ? pf1 : p.clist_idx[base + t1]) : j0;
+            int j0 = first ? pf0 : p.clist_idx[base + t];
+            int j1 = t1 < cnt ? (first ? pf1 : p.clist_idx[base + t1]) : j0;
+            if (keep) {
+              j0 = keep_index(j0, p.n_cell, p.clist_keep + base + t, p.bad);
+              j1 = t1 < cnt ? keep_index(j1, p.n_cell, p.clist_keep + base + t1, p.bad) : j0;
+            }
             const PosMass v0 = p.cell_pm[j0];
             const PosMass v1 = p.cell_pm[j1];
             const bool fq = QUAD && sizeof(Real) == 4;
@@ -485,7 +520,8 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
           }
         } else {
           for (int t = tid; t < cnt; t += NT) {
-            const int j = t == tid ? pf0 : (t == tid + NT ? pf1 : p.clist_idx[base + t]);
+            int j = t == tid ? pf0 : (t == tid + NT ? pf1 : p.clist_idx[base + t]);
+            if (keep) j = keep_index(j, p.n_cell, p.clist_keep + base + t, p.bad);
             const bool fq = QUAD && sizeof(Real) == 4;
             put_c(t, p.cell_pm[j], j, fq ? p.cell_q[2 * j] : zero4, fq ? p.cell_q[2 * j + 1] : zero4);
           }
@@ -547,18 +583,60 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
       // ---- 5. FP64 merge of the K streams, fixed order ----------------------
       if (active) fold();
       __syncthreads();
-      for (int i = tid; i < nch; i += NT) {
-        const int si = i % S, ri = i / S;
-        double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
-        for (int kk = 0; kk < K; kk++) {
-          const double *a = acc64 + 4 * ri * NT + kk * S + si;
-          m0 += a[0]; m1 += a[NT]; m2 += a[2 * NT]; m3 += a[3 * NT];
+      if constexpr (!INPLACE) {
+        for (int i = tid; i < nch; i += NT) {
+          const int si = i % S, ri = i / S;
+          double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+          for (int kk = 0; kk < K; kk++) {
+            const double *a = acc64 + 4 * ri * NT + kk * S + si;
+            m0 += a[0]; m1 += a[NT]; m2 += a[2 * NT]; m3 += a[3 * NT];
+          }
+          const int64_t o = s0 + sb + i;
+          p.a[3 * o] = m0;
+          p.a[3 * o + 1] = m1;
+          p.a[3 * o + 2] = m2;
+          p.phi[o] = -m3;  // physical potential, Eq. 1
         }
-        const int64_t o = s0 + sb + i;
-        p.a[3 * o] = m0;
-        p.a[3 * o + 1] = m1;
-        p.a[3 * o + 2] = m2;
-        p.phi[o] = -m3;  // physical potential, Eq. 1
+      } else {
+        // the same sums, written to the device and to host memory
+        double m[R][3];  // sink i = tid + r NT
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          const int i = tid + r * NT;
+          m[r][0] = m[r][1] = m[r][2] = 0.0;
+          if (i < nch) {
+            const int si = i % S, ri = i / S;
+            double m3 = 0.0;
+            for (int kk = 0; kk < K; kk++) {
+              const double *a = acc64 + 4 * ri * NT + kk * S + si;
+              m[r][0] += a[0]; m[r][1] += a[NT]; m[r][2] += a[2 * NT]; m3 += a[3 * NT];
+            }
+            const int64_t o = s0 + sb + i;
+            p.phi[o] = -m3;
+            p.phi_host[o] = -m3;
+          }
+        }
+        // a[3o + c] through shared memory, so that consecutive threads write
+        // consecutive words (host memory takes scattered 8-byte words at a
+        // third of the rate of whole lines)
+        __syncthreads();  // every thread has read acc64
+        double *out = acc64;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          const int i = tid + r * NT;
+          if (i < nch) {
+            out[3 * i] = m[r][0];
+            out[3 * i + 1] = m[r][1];
+            out[3 * i + 2] = m[r][2];
+          }
+        }
+        __syncthreads();
+        double *ag = p.a + 3 * (s0 + sb), *ah = p.a_host + 3 * (s0 + sb);
+        for (int t = tid; t < 3 * nch; t += NT) {
+          const double v = out[t];
+          ag[t] = v;
+          ah[t] = v;
+        }
       }
     }
   }

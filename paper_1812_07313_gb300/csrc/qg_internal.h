@@ -77,6 +77,18 @@ struct ForceParams {
   int32_t *head;
   double *a;
   double *phi;
+  // In-place kernels only (lists read from host memory): every index is
+  // checked against n_src / n_cell as it is read (an entry outside its
+  // array sets *bad and reads entry 0) and the checked index is written to
+  // the keep array (device) at the same position, so the device ends up
+  // holding the whole list.
+  int32_t *plist_keep;
+  int32_t *clist_keep;
+  int32_t n_src, n_cell;
+  int *bad;
+  // In-place kernels only: the results' second copy, in host memory.
+  double *a_host;
+  double *phi_host;
   int32_t tile;     // list entries per shared-memory tile
   int32_t flush_j;  // entries per thread between FP32 -> FP64 folds
   float zero, one;  // 0 and 1, as runtime values (see Pair2 in qg_force.cuh)
@@ -96,5 +108,6 @@ inline size_t force_smem_bytes(bool fp64, bool paired, int R, int nthreads, int 
 const void *force_kernel_f32(int R, bool quad, bool guard, bool centred);
 const void *force_kernel_f32x2(int R, bool quad, bool guard);
 const void *force_kernel_f64(int R, bool quad, bool guard);
+const void *force_kernel_inplace(int R, bool quad, bool guard);  // FP32 centred, scalar
 
 }  // namespace qg

@@ -71,7 +71,7 @@ class qg_stats(ctypes.Structure):
                 ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("sinks_per_thread", ctypes.c_int32), ("tile_j", ctypes.c_int32),
                 ("warps_per_group", ctypes.c_int32), ("flush_j", ctypes.c_int32),
-                ("paired", ctypes.c_int32)]
+                ("paired", ctypes.c_int32), ("eval_in_place", ctypes.c_int32)]
 
 
 _lib = None
@@ -253,9 +253,11 @@ class Context:
 
     def qg_evaluate_host(self, x, group_off, eps2_all, eps2, src_x, src_m, plist_off, plist_idx, cell_com, cell_m,
                          cell_q, clist_off, clist_idx, a=None, phi=None):
-        """One pipelined evaluation from host arrays (the inputs of the three
-        qg_set_* calls); returns (a, phi).  Pass the same array as x and src_x
-        to have it copied once; a / phi may be preallocated (pinned) outputs."""
+        """One evaluation from host arrays (the inputs of the three qg_set_*
+        calls); returns (a, phi).  Pass the same array as x and src_x to have
+        it copied once; a / phi may be preallocated outputs.  With the lists
+        and a / phi in page-locked memory the kernel reads the lists and
+        writes the results in place (qg_get_stats()["eval_in_place"])."""
         x = _host(x, np.float64, (-1, 3))
         g = _host(group_off, np.int64)
         e = None if eps2 is None else _host(eps2, np.float32)

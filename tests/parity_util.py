@@ -36,7 +36,9 @@ class Case:
         wl = workloads.WORKLOADS[name]
         return cls(wl.particles(), wl.theta if theta is None else theta, wl.leaf_max, wl.n_crit)
 
-    def gpu(self, options=None, ctx=None):
+    def gpu(self, options=None, ctx=None, autotune=False):
+        """Forces from the CUDA path; autotune: at the launch shape qg_autotune
+        picks (the benchmark's configuration)."""
         t, L = self.tree, self.lists
         own = ctx is None
         if own:
@@ -46,6 +48,8 @@ class Case:
         ctx.qg_set_sinks(t.x, t.group_off, self.eps2_all, self.eps2)
         ctx.qg_set_sources(t.x, t.m, L.plist_off, L.plist_idx)
         ctx.qg_set_cells(t.cell_com, t.cell_m, t.cell_q, L.clist_off, L.clist_idx)
+        if autotune:
+            ctx.qg_autotune(None, reps=1)
         ctx.qg_run()
         a, phi = ctx.qg_get_forces()
         stats = ctx.qg_get_stats()

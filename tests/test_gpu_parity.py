@@ -1,5 +1,7 @@
 """CUDA path (through the qg_* C-ABI) against the FP64 oracle, element by element
 on the same seeded inputs and lists."""
+import zlib
+
 import numpy as np
 import pytest
 
@@ -47,22 +49,42 @@ def test_exponential_disk_quad_and_mono(theta):
         assert_parity(a, phi, a_ref, phi_ref, label="disk theta %.2f %s" % (theta, "quad" if uq else "mono"))
 
 
-def _evaluate_host(case, ctx, same_x=True, idx_fix=None):
+def _pin(x):
+    import torch
+    tdt = {np.dtype(np.float64): torch.float64, np.dtype(np.int32): torch.int32, np.dtype(np.int64): torch.int64}
+    t = torch.empty(tuple(x.shape), dtype=tdt[np.asarray(x).dtype], pin_memory=True)
+    t.numpy()[...] = x
+    return t
+
+
+def _evaluate_host(case, ctx, same_x=True, idx_fix=None, pinned=False):
+    """qg_evaluate_host on the case's inputs; pinned: lists and outputs in
+    page-locked memory (the in-place route on a coherent link)."""
     t, L = case.tree, case.lists
     pi, ci = L.plist_idx, L.clist_idx
     if idx_fix is not None:
         pi, ci = idx_fix(pi.copy(), ci.copy())
     src_x = t.x if same_x else t.x.copy()
-    return ctx.qg_evaluate_host(t.x, t.group_off, case.eps2_all, case.eps2, src_x, t.m, L.plist_off, pi,
-                                t.cell_com, t.cell_m, t.cell_q, L.clist_off, ci)
+    keep = []
+    a_out = phi_out = None
+    if pinned:
+        keep = [_pin(pi), _pin(ci), _pin(np.zeros((t.n, 3))), _pin(np.zeros(t.n))]
+        pi, ci, a_out, phi_out = (k.numpy() for k in keep)
+    out = ctx.qg_evaluate_host(t.x, t.group_off, case.eps2_all, case.eps2, src_x, t.m, L.plist_off, pi,
+                               t.cell_com, t.cell_m, t.cell_q, L.clist_off, ci, a_out, phi_out)
+    if pinned:
+        out = tuple(np.array(o) for o in out)  # off the pinned buffers before they are freed
+    return out
 
 
+@pytest.mark.parametrize("pinned", [False, True])
 @pytest.mark.parametrize("name", ["sphere", "batched"])
-def test_pipelined_host_evaluation_equals_the_separate_calls(name):
-    """qg_evaluate_host (list copies overlapped with the kernel, four chunks
-    of groups) gives bit for bit the results of qg_set_* + qg_run at the same
-    options, with the positions copied once or twice, and leaves the
-    context holding the inputs."""
+def test_pipelined_host_evaluation_equals_the_separate_calls(name, pinned):
+    """qg_evaluate_host gives bit for bit the results of qg_set_* + qg_run at
+    the same options, with the positions copied once or twice, and leaves
+    the context holding the inputs: by both routes, list copies overlapped
+    with the kernel in four chunks of groups (pageable lists) and lists read
+    in place by the kernel (page-locked lists and outputs)."""
     if name == "sphere":
         case = Case(workloads.small_set("sphere", 6000, 31, 1e-2), 0.5, 8, 64)
     else:
@@ -71,10 +93,13 @@ def test_pipelined_host_evaluation_equals_the_separate_calls(name):
     a_ref, phi_ref, st_ref = case.gpu(opts)
     ctx = qgrav.Context(0, opts)
     for same in (True, False):
-        a, phi = _evaluate_host(case, ctx, same_x=same)
+        a, phi = _evaluate_host(case, ctx, same_x=same, pinned=pinned)
         assert np.array_equal(a, a_ref) and np.array_equal(phi, phi_ref)
     st = ctx.qg_get_stats()
     assert st["i_pp"] == st_ref["i_pp"] and st["i_pc"] == st_ref["i_pc"]
+    assert st["eval_in_place"] == (1 if pinned else 0)
+    a_d, phi_d = ctx.qg_get_forces()  # the device holds the same results
+    assert np.array_equal(a_d, a_ref) and np.array_equal(phi_d, phi_ref)
     ctx.qg_run()  # the context holds the inputs: a graph step on them
     a2, phi2 = ctx.qg_get_forces()
     assert np.array_equal(a2, a_ref) and np.array_equal(phi2, phi_ref)
@@ -84,7 +109,8 @@ def test_pipelined_host_evaluation_equals_the_separate_calls(name):
     ctx.close()
 
 
-def test_pipelined_host_evaluation_edge_cases():
+@pytest.mark.parametrize("pinned", [False, True])
+def test_pipelined_host_evaluation_edge_cases(pinned):
     ctx = qgrav.Context(0)
     z3, z1 = np.zeros((0, 3)), np.zeros(0)
     off0 = np.zeros(1, dtype=np.int64)
@@ -96,20 +122,30 @@ def test_pipelined_host_evaluation_edge_cases():
     x = np.random.default_rng(1).random((50, 3))
     goff = np.array([0, 20, 20, 50], dtype=np.int64)
     lo = np.zeros(4, dtype=np.int64)
+    outs = (_pin(np.ones((50, 3))), _pin(np.ones(50))) if pinned else (None, None)
     a, phi = ctx.qg_evaluate_host(x, goff, 1e-4, None, x, np.full(50, 0.02), lo, i0, z3, z1, np.zeros((0, 6)),
-                                  lo, i0)
+                                  lo, i0, *(o.numpy() if pinned else o for o in outs))
     assert np.all(a == 0.0) and np.all(phi == 0.0)
+    assert ctx.qg_get_stats()["eval_in_place"] == (1 if pinned else 0)
     # one group only (fewer groups than chunks), zero softening on the guarded path
     ps = workloads.small_set("sphere", 300, 3, 0.0)
     case = Case(ps, 0.5, 8, 512)
     assert case.tree.ngroups == 1
-    a, phi = _evaluate_host(case, ctx)
+    a, phi = _evaluate_host(case, ctx, pinned=pinned)
     a_o, phi_o = case.oracle()
     assert_parity(a, phi, a_o, phi_o, label="one group, eps 0")
+    # a group larger than one pass of the CTA (several sink chunks re-read its list)
+    ps = workloads.small_set("plummer", 3000, 4, 1e-2)
+    case = Case(ps, 0.5, 8, 3000)
+    assert case.tree.ngroups == 1
+    a_ref, phi_ref, _ = case.gpu(qgrav.Options(sinks_per_thread=2, warps_per_group=2), ctx=ctx)
+    a, phi = _evaluate_host(case, ctx, pinned=pinned)
+    assert np.array_equal(a, a_ref) and np.array_equal(phi, phi_ref)
     ctx.close()
 
 
-def test_pipelined_host_evaluation_rejects_bad_entries():
+@pytest.mark.parametrize("pinned", [False, True])
+def test_pipelined_host_evaluation_rejects_bad_entries(pinned):
     case = Case(workloads.small_set("plummer", 3000, 5, 1e-2), 0.5, 8, 64)
     ctx = qgrav.Context(0)
 
@@ -122,13 +158,36 @@ def test_pipelined_host_evaluation_rejects_bad_entries():
         return pi, ci
 
     for fix in (bad_cell, bad_particle):
-        with pytest.raises(qgrav.QGError):
-            _evaluate_host(case, ctx, idx_fix=fix)
+        with pytest.raises(qgrav.QGError) as e:
+            _evaluate_host(case, ctx, idx_fix=fix, pinned=pinned)
+        assert e.value.status == qgrav.QG_ERR_ARG
         with pytest.raises(qgrav.QGError):
             ctx.qg_run()  # the failed call left no runnable inputs
-    a, phi = _evaluate_host(case, ctx)  # and the context is still usable
+    a, phi = _evaluate_host(case, ctx, pinned=pinned)  # and the context is still usable
+    assert ctx.qg_get_stats()["eval_in_place"] == (1 if pinned else 0)
     a_o, phi_o = case.oracle()
     assert_parity(a, phi, a_o, phi_o, label="after rejected inputs")
+    # a bad entry in the list of a group with no sinks is found too
+    x = np.random.default_rng(2).random((40, 3))
+    goff = np.array([0, 40, 40], dtype=np.int64)
+    po = np.array([0, 5, 8], dtype=np.int64)
+    pi = np.array([0, 1, 2, 3, 4, 5, 6, 40], dtype=np.int32)
+    co = np.zeros(3, dtype=np.int64)
+    i0 = np.zeros(0, dtype=np.int32)
+    if pinned:
+        kp = [_pin(pi), _pin(np.zeros((40, 3))), _pin(np.zeros(40))]
+        args = (kp[0].numpy(), kp[1].numpy(), kp[2].numpy())
+    else:
+        args = (pi, None, None)
+    with pytest.raises(qgrav.QGError) as e:
+        ctx.qg_evaluate_host(x, goff, 1e-4, None, x, np.full(40, 0.025), po, args[0], np.zeros((0, 3)),
+                             np.zeros(0), np.zeros((0, 6)), co, i0, args[1], args[2])
+    assert e.value.status == qgrav.QG_ERR_ARG
+    # list entries with no sources at all are refused on the host
+    with pytest.raises(qgrav.QGError) as e:
+        ctx.qg_evaluate_host(x, goff, 1e-4, None, np.zeros((0, 3)), np.zeros(0), po, pi, np.zeros((0, 3)),
+                             np.zeros(0), np.zeros((0, 6)), co, i0)
+    assert e.value.status == qgrav.QG_ERR_ARG
     ctx.close()
 
 
@@ -402,8 +461,8 @@ def test_full_size_sampled(name, theta, k):
     oracle evaluates a seeded sample of groups (plus the largest group and
     the one with the longest list)."""
     case = Case.workload(name, theta)
-    a, phi, st = case.gpu()
-    groups = case.sample_groups(k, seed=hash(name) % 1000)
+    a, phi, st = case.gpu(autotune=True)
+    groups = case.sample_groups(k, seed=zlib.crc32(name.encode()) % 1000)
     a_ref, phi_ref = case.oracle(groups=groups)
     s = case.sinks_of(groups)
     assert_parity(a[s], phi[s], a_ref[s], phi_ref[s], label="%s theta=%.2f" % (name, theta))
@@ -417,3 +476,33 @@ def test_plummer_4m_fp64_kernel_sampled():
     a_ref, phi_ref = case.oracle(groups=groups)
     s = case.sinks_of(groups)
     assert_parity(a[s], phi[s], a_ref[s], phi_ref[s], med=TOL_FP64, p99=TOL_FP64, label="plummer fp64")
+
+
+def test_cube_1m_monopole_cells_at_equal_error_theta_sampled():
+    """Monopole cells (Eq. 4 alone) at the full cube size and theta 0.3, the
+    opening angle whose error matches quadrupole cells at 0.65 (Fig. 1), in the
+    autotuned launch shape."""
+    case = Case.workload("cube_1m", 0.3)
+    a, phi, _ = case.gpu(qgrav.Options(expansion=qgrav.QG_MONO), autotune=True)
+    groups = case.sample_groups(60, seed=17)
+    a_ref, phi_ref = case.oracle(use_quad=False, groups=groups)
+    s = case.sinks_of(groups)
+    assert_parity(a[s], phi[s], a_ref[s], phi_ref[s], label="cube_1m mono theta=0.30")
+
+
+def test_cube_1m_pipelined_host_evaluation():
+    """The one-call host entry point at the full cube size, in the autotuned
+    launch shape, by both routes: bit for bit the separate calls, and the
+    oracle on a sample."""
+    case = Case.workload("cube_1m")
+    ctx = qgrav.Context(0)
+    a_ref, phi_ref, _ = case.gpu(ctx=ctx, autotune=True)
+    for pinned in (False, True):
+        a, phi = _evaluate_host(case, ctx, pinned=pinned)
+        assert ctx.qg_get_stats()["eval_in_place"] == (1 if pinned else 0)
+        assert np.array_equal(a, a_ref) and np.array_equal(phi, phi_ref)
+    ctx.close()
+    groups = case.sample_groups(80, seed=23)
+    a_o, phi_o = case.oracle(groups=groups)
+    s = case.sinks_of(groups)
+    assert_parity(a[s], phi[s], a_o[s], phi_o[s], label="cube_1m pipelined")
