@@ -142,6 +142,7 @@ struct qg_ctx {
   cudaEvent_t chunk_in[8] = {}, chunk_done[8] = {}, inputs_ready = nullptr, packed = nullptr;
   DevBuf<double> stage_src;  // source positions when they are not the sinks' array
   int coherent_host = -1;    // device reads host memory through the host's page tables (-1: not asked yet)
+  int *hbad = nullptr;       // page-locked [4]: bad-entry flags read back per chunk
   qg_stats stats{};
   // chosen launch (kernel_inplace: the same variant reading its lists from
   // host memory, or null where none is built)
@@ -490,6 +491,7 @@ void qg_destroy(qg_ctx *c) {
       cudaStreamDestroy(t);
     }
   if (c->stream) cudaStreamDestroy(c->stream);
+  if (c->hbad) cudaFreeHost(c->hbad);
   delete c;
 }
 
@@ -885,30 +887,24 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
   if (nc < 0 || nc >= INT32_MAX || !clist_off || (nc > 0 && (!cell_com || !cell_m || !cell_q)))
     return fail(c, QG_ERR_ARG, "qg_evaluate_host: bad cell sizes or NULL pointer");
   const int64_t G = ngroups;
-  if (!valid_offsets(group_off, G, n)) return fail(c, QG_ERR_ARG, "qg_evaluate_host: bad group offsets");
-  if (!valid_offsets_any_total(plist_off, G) || !valid_offsets_any_total(clist_off, G))
-    return fail(c, QG_ERR_ARG, "qg_evaluate_host: bad list offsets");
+  // the offsets' end points here; that they never decrease is checked while
+  // the first copies run (no kernel is queued before that)
+  if (group_off[0] != 0 || group_off[G] != n) return fail(c, QG_ERR_ARG, "qg_evaluate_host: bad group offsets");
   const int64_t np_tot = plist_off[G], nc_tot = clist_off[G];
+  if (plist_off[0] != 0 || clist_off[0] != 0 || np_tot < 0 || nc_tot < 0)
+    return fail(c, QG_ERR_ARG, "qg_evaluate_host: bad list offsets");
   if ((np_tot > 0 && !plist_idx) || (nc_tot > 0 && !clist_idx))
     return fail(c, QG_ERR_ARG, "qg_evaluate_host: list_idx is NULL");
   // with no sources (cells) every entry of a non-empty list is out of range
   if ((np_tot > 0 && ns == 0) || (nc_tot > 0 && nc == 0))
     return fail(c, QG_ERR_ARG, "qg_evaluate_host: list entries but no sources or cells");
-  bool pos = eps2_all > 0;
-  if (sink_eps2) {
-    pos = true;
-    for (int64_t i = 0; i < n; i++) {
-      if (!(sink_eps2[i] >= 0.f) || !std::isfinite(sink_eps2[i]))
-        return fail(c, QG_ERR_ARG, "qg_evaluate_host: eps2[%lld] invalid", (long long)i);
-      if (!(sink_eps2[i] > 0.f)) pos = false;
-    }
-  }
   DeviceGuard dg(c->device);
   cudaStream_t s = c->stream;
   if (!c->copy_in) QG_CUDA(c, cudaStreamCreateWithFlags(&c->copy_in, cudaStreamNonBlocking));
   if (!c->copy_out) QG_CUDA(c, cudaStreamCreateWithFlags(&c->copy_out, cudaStreamNonBlocking));
   if (!c->inputs_ready) QG_CUDA(c, cudaEventCreateWithFlags(&c->inputs_ready, cudaEventDisableTiming));
   if (!c->packed) QG_CUDA(c, cudaEventCreateWithFlags(&c->packed, cudaEventDisableTiming));
+  if (!c->hbad) QG_CUDA(c, cudaMallocHost(&c->hbad, kChunks * sizeof(int)));
   for (int k = 0; k < kChunks; k++) {
     if (!c->chunk_stream[k]) QG_CUDA(c, cudaStreamCreateWithFlags(&c->chunk_stream[k], cudaStreamNonBlocking));
     if (!c->chunk_in[k]) QG_CUDA(c, cudaEventCreateWithFlags(&c->chunk_in[k], cudaEventDisableTiming));
@@ -918,9 +914,7 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
   c->G = G;
   c->has_eps2 = sink_eps2 != nullptr;
   c->eps2_all = eps2_all;
-  c->eps_positive = pos;
-  qg_status st = choose_kernel(c);
-  if (st != QG_OK) return st;
+  qg_status st;
   // ---- outputs, queue and per-chunk scratch (hist, cursor, head, bad);
   // allocations first, before any copy is queued
   constexpr int kScr = 2 * kBuckets + 2;
@@ -950,6 +944,29 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
     return fail(c, QG_ERR_NOMEM, "source or cell allocation");
   if ((st = upload(c, c->cell_q64, cell_q, 6 * nc, ci_s)) != QG_OK) return st;
   QG_CUDA(c, cudaEventRecord(c->inputs_ready, ci_s));
+  // ---- the host-side checks that take a pass over the offsets or the
+  // softenings, while those copies run; the kernel choice depends on them
+  bool ok = valid_offsets(group_off, G, n) && valid_offsets_any_total(plist_off, G) &&
+            valid_offsets_any_total(clist_off, G);
+  bool pos = eps2_all > 0;
+  int64_t bad_eps = -1;
+  if (ok && sink_eps2) {
+    pos = true;
+    for (int64_t i = 0; i < n && bad_eps < 0; i++) {
+      if (!(sink_eps2[i] >= 0.f) || !std::isfinite(sink_eps2[i])) bad_eps = i;
+      if (!(sink_eps2[i] > 0.f)) pos = false;
+    }
+  }
+  if (!ok || bad_eps >= 0) {
+    cudaStreamSynchronize(ci_s);  // the copies still read the caller's arrays
+    if (!ok) return fail(c, QG_ERR_ARG, "qg_evaluate_host: offsets decrease");
+    return fail(c, QG_ERR_ARG, "qg_evaluate_host: eps2[%lld] invalid", (long long)bad_eps);
+  }
+  c->eps_positive = pos;
+  if ((st = choose_kernel(c)) != QG_OK) {
+    cudaStreamSynchronize(ci_s);
+    return st;
+  }
   QG_CUDA(c, cudaStreamWaitEvent(s, c->inputs_ready, 0));
   if (ns)
     pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, same_x ? c->sink_x.p : c->stage_src.p, c->src_m64.p,
@@ -994,10 +1011,7 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
     QG_CUDA(c, cudaLaunchKernel(c->kernel_inplace, dim3(grid), dim3(c->nthreads), args, c->smem, s));
     QG_CUDA(c, cudaEventRecord(c->ev[2], s));
     c->stats.grid = grid;
-    int hbad = 0;
-    QG_CUDA(c, cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
-    QG_CUDA(c, cudaStreamSynchronize(s));
-    if (hbad) return fail(c, QG_ERR_ARG, "qg_evaluate_host: list entry outside its source or cell range");
+    QG_CUDA(c, cudaMemcpyAsync(c->hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
   } else {
     QG_CUDA(c, cudaEventRecord(c->packed, s));
     // ---- chunks of groups by list entries: 1/8, 1/4, 1/4, 3/8 of them, so
@@ -1065,16 +1079,12 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
     }
     QG_CUDA(c, cudaEventRecord(c->ev[2], s));
     c->stats.grid = (int)std::min<int64_t>(c->grid, std::max<int64_t>(G, 1));
-    int hbad[kChunks] = {0, 0, 0, 0};
     for (int k = 0; k < kChunks; k++)
-      QG_CUDA(c, cudaMemcpyAsync(&hbad[k], c->scratch.p + k * kScr + 2 * kBuckets + 1, sizeof(int),
+      QG_CUDA(c, cudaMemcpyAsync(&c->hbad[k], c->scratch.p + k * kScr + 2 * kBuckets + 1, sizeof(int),
                                  cudaMemcpyDeviceToHost, c->copy_out));
-    QG_CUDA(c, cudaStreamSynchronize(c->copy_out));
-    QG_CUDA(c, cudaStreamSynchronize(s));
-    for (int k = 0; k < kChunks; k++)
-      if (hbad[k]) return fail(c, QG_ERR_ARG, "qg_evaluate_host: list entry outside its source or cell range");
   }
-  // the context now holds these inputs, as after the qg_set_* calls and qg_run
+  // the context now holds these inputs, as after the qg_set_* calls and
+  // qg_run (recorded while the kernel runs; undone below if an entry was bad)
   c->h_goff.assign(group_off, group_off + G + 1);
   c->h_poff.assign(plist_off, plist_off + G + 1);
   c->h_coff.assign(clist_off, clist_off + G + 1);
@@ -1084,10 +1094,17 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
   c->np_list = np_tot;
   c->nc_list = nc_tot;
   c->sinks_ok = c->src_ok = c->cells_ok = true;
+  update_counts(c);
+  c->last_stream = s;
+  if (!direct) QG_CUDA(c, cudaStreamSynchronize(c->copy_out));
+  QG_CUDA(c, cudaStreamSynchronize(s));
+  for (int k = 0; k < (direct ? 1 : kChunks); k++)
+    if (c->hbad[k]) {
+      c->sinks_ok = c->src_ok = c->cells_ok = false;
+      return fail(c, QG_ERR_ARG, "qg_evaluate_host: list entry outside its source or cell range");
+    }
   c->ran = true;
   c->timed = true;
-  c->last_stream = s;
-  update_counts(c);
   return QG_OK;
 }
 

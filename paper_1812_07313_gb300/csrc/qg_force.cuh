@@ -393,12 +393,24 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
 
       // The first two list indices this thread stages from the next tile are
       // loaded one tile ahead (during the current tile's arithmetic), so the
-      // gather of a tile waits for one memory round trip instead of two.
-      int pf0 = -1, pf1 = -1;
+      // gather of a tile waits for one memory round trip instead of two.  The
+      // in-place form, whose lists are in host memory (a round trip several
+      // times longer), loads the first four ahead.
+      int pf0 = -1, pf1 = -1, pf2 = -1, pf3 = -1;
       auto prefetch = [&](const int32_t *idx, int64_t b, int64_t end) {
         const int c = (int)min((int64_t)TK, end - b);
         pf0 = tid < c ? __ldg(idx + b + tid) : -1;
         pf1 = tid + NT < c ? __ldg(idx + b + tid + NT) : -1;
+        if constexpr (INPLACE) {
+          pf2 = tid + 2 * NT < c ? __ldg(idx + b + tid + 2 * NT) : -1;
+          pf3 = tid + 3 * NT < c ? __ldg(idx + b + tid + 3 * NT) : -1;
+        }
+      };
+      // in-place form: index of entry t of the tile at base, from the
+      // registers loaded ahead where there is one
+      auto ahead = [&](const int32_t *idx, int64_t base, int t) -> int {
+        const int u = t - tid;
+        return u == 0 ? pf0 : u == NT ? pf1 : u == 2 * NT ? pf2 : u == 3 * NT ? pf3 : idx[base + t];
       };
       if (p0 < p1) prefetch(p.plist_idx, p0, p1);
       else if (c0 < c1) prefetch(p.clist_idx, c0, c1);
@@ -421,9 +433,15 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
         if constexpr (QG_GATHER2 != 0) {
           for (int t = tid; t < cnt; t += 2 * NT) {
             const int t1 = t + NT;
-            const bool first = t == tid;
-            int j0 = first ? pf0 : p.plist_idx[base + t];
-            int j1 = t1 < cnt ? (first ? pf1 : p.plist_idx[base + t1]) : j0;
+            [[maybe_unused]] const bool first = t == tid;
+            int j0, j1;
+            if constexpr (INPLACE) {
+              j0 = ahead(p.plist_idx, base, t);
+              j1 = t1 < cnt ? ahead(p.plist_idx, base, t1) : j0;
+            } else {
+              j0 = first ? pf0 : p.plist_idx[base + t];
+              j1 = t1 < cnt ? (first ? pf1 : p.plist_idx[base + t1]) : j0;
+            }
             if (keep) {
               j0 = keep_index(j0, p.n_src, p.plist_keep + base + t, p.bad);
               j1 = t1 < cnt ? keep_index(j1, p.n_src, p.plist_keep + base + t1, p.bad) : j0;
@@ -435,7 +453,7 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
           }
         } else {
           for (int t = tid; t < cnt; t += NT) {
-            int j = t == tid ? pf0 : (t == tid + NT ? pf1 : p.plist_idx[base + t]);
+            int j = INPLACE ? ahead(p.plist_idx, base, t) : t == tid ? pf0 : (t == tid + NT ? pf1 : p.plist_idx[base + t]);
             if (keep) j = keep_index(j, p.n_src, p.plist_keep + base + t, p.bad);
             put_p(t, p.src[j], j);
           }
@@ -503,9 +521,15 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
         if constexpr (QG_GATHER2 != 0) {
           for (int t = tid; t < cnt; t += 2 * NT) {
             const int t1 = t + NT;
-            const bool first = t == tid;
-            int j0 = first ? pf0 : p.clist_idx[base + t];
-            int j1 = t1 < cnt ? (first ? pf1 : p.clist_idx[base + t1]) : j0;
+            [[maybe_unused]] const bool first = t == tid;
+            int j0, j1;
+            if constexpr (INPLACE) {
+              j0 = ahead(p.clist_idx, base, t);
+              j1 = t1 < cnt ? ahead(p.clist_idx, base, t1) : j0;
+            } else {
+              j0 = first ? pf0 : p.clist_idx[base + t];
+              j1 = t1 < cnt ? (first ? pf1 : p.clist_idx[base + t1]) : j0;
+            }
             if (keep) {
               j0 = keep_index(j0, p.n_cell, p.clist_keep + base + t, p.bad);
               j1 = t1 < cnt ? keep_index(j1, p.n_cell, p.clist_keep + base + t1, p.bad) : j0;
@@ -520,7 +544,7 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
           }
         } else {
           for (int t = tid; t < cnt; t += NT) {
-            int j = t == tid ? pf0 : (t == tid + NT ? pf1 : p.clist_idx[base + t]);
+            int j = INPLACE ? ahead(p.clist_idx, base, t) : t == tid ? pf0 : (t == tid + NT ? pf1 : p.clist_idx[base + t]);
             if (keep) j = keep_index(j, p.n_cell, p.clist_keep + base + t, p.bad);
             const bool fq = QUAD && sizeof(Real) == 4;
             put_c(t, p.cell_pm[j], j, fq ? p.cell_q[2 * j] : zero4, fq ? p.cell_q[2 * j + 1] : zero4);

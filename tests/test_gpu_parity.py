@@ -188,6 +188,19 @@ def test_pipelined_host_evaluation_rejects_bad_entries(pinned):
         ctx.qg_evaluate_host(x, goff, 1e-4, None, np.zeros((0, 3)), np.zeros(0), po, pi, np.zeros((0, 3)),
                              np.zeros(0), np.zeros((0, 6)), co, i0)
     assert e.value.status == qgrav.QG_ERR_ARG
+    # offsets that decrease, and an invalid softening, are found on the host
+    # (while the first copies run) before any kernel is queued
+    pi_ok = np.array([0, 1, 2, 3, 4, 5, 6, 7], dtype=np.int32)
+    for go, pof, e2 in ((np.array([0, 41, 40], dtype=np.int64), po, None),
+                        (goff, np.array([0, 9, 8], dtype=np.int64), None),
+                        (goff, po, np.where(np.arange(40) == 17, -1.0, 0.01).astype(np.float32))):
+        with pytest.raises(qgrav.QGError) as e:
+            ctx.qg_evaluate_host(x, go, 1e-4, e2, x, np.full(40, 0.025), pof, pi_ok, np.zeros((0, 3)), np.zeros(0),
+                                 np.zeros((0, 6)), co, i0)
+        assert e.value.status == qgrav.QG_ERR_ARG
+    a, phi = ctx.qg_evaluate_host(x, goff, 1e-4, None, x, np.full(40, 0.025), po, pi_ok, np.zeros((0, 3)),
+                                  np.zeros(0), np.zeros((0, 6)), co, i0)
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(phi))
     ctx.close()
 
 
