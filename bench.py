@@ -446,16 +446,17 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and args.batching_compare and ps.nsys > 1:
         out["batching"] = batching_compare(torch, qgrav, tr, L, eps2_all, eps2, stream, flush,
                                            float(np.mean(step_ms)))
-    if rank == 0 and not args.no_gpu_tree:
-        out["gpu_tree"] = gpu_tree_step(torch, qgrav, ps, wl, tr, L, eps2_all, eps2, stream)
-    if rank == 0 and args.precision_compare:
-        out["precision"] = precision_compare(torch, qgrav, ctx, tr, L, eps2_all, eps2, stream, flush)
-
-    # end to end through the C-ABI with host buffers (pinned), every step
+    # the chosen launch shape, for the legs below
     chosen = qgrav.Options(sinks_per_thread=launch["sinks_per_thread"], warps_per_group=launch["warps_per_group"],
                            tile_j=launch["tile_j"],
                            arith=qgrav.QG_ARITH_PAIRED if launch.get("arith", "").startswith("paired")
                            else qgrav.QG_ARITH_SCALAR)
+    if rank == 0 and not args.no_gpu_tree:
+        out["gpu_tree"] = gpu_tree_step(torch, qgrav, ps, wl, tr, L, eps2_all, eps2, stream, chosen)
+    if rank == 0 and args.precision_compare:
+        out["precision"] = precision_compare(torch, qgrav, ctx, tr, L, eps2_all, eps2, stream, flush)
+
+    # end to end through the C-ABI with host buffers (pinned), every step
     out["e2e"] = e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world, chosen)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -535,15 +536,16 @@ def batching_compare(torch, qgrav, tr, L, eps2_all, eps2, stream, flush, batched
             "note": "per-system contexts at the default launch shape, graphs replayed back to back on one stream"}
 
 
-def gpu_tree_step(torch, qgrav, ps, wl, tr, L, eps2_all, eps2, stream, steps=5):
+def gpu_tree_step(torch, qgrav, ps, wl, tr, L, eps2_all, eps2, stream, options, steps=5):
     """The whole step on the GPU: tree build with moments and groups, walk,
-    attach, force kernel; device times of each part (and the host builder's
-    wall time for the same tree and walk, for scale)."""
+    attach, force kernel at the launch shape of the step above (the GPU
+    builds the same groups and lists as the host); device times of each
+    part."""
     from paper_1812_07313_gb300 import gtree
     x = torch.as_tensor(ps.x).cuda()
     m = torch.as_tensor(ps.m).cuda()
     t = gtree.GpuTree(torch.cuda.current_device())
-    ctx = qgrav.Context(torch.cuda.current_device())
+    ctx = qgrav.Context(torch.cuda.current_device(), options)
     build, walk, force = [], [], []
     same = None
     for k in range(steps + 1):
@@ -552,7 +554,6 @@ def gpu_tree_step(torch, qgrav, ps, wl, tr, L, eps2_all, eps2, stream, steps=5):
         b, w = t.timing()
         t.attach(ctx, eps2_all if eps2 is None else 0.0)
         if k == 0:
-            ctx.qg_autotune(stream.cuda_stream, reps=2)
             sz = t.sizes()
             same = (sz["ngroups"] == tr.ngroups and sz["n_plist"] == len(L.plist_idx)
                     and sz["n_clist"] == len(L.clist_idx))  # list entries per group are tested in the suite
