@@ -129,7 +129,8 @@ struct qg_gtree {
   DBuf<int64_t> hoff;
   // tree
   DBuf<int64_t> nbeg, nend, range;
-  DBuf<int32_t> nlevel, nparent, nfirst, nnchild, nsysid, node_of, flag;
+  DBuf<int32_t> nlevel, nparent, nfirst, nnchild, nsysid, flag;
+  DBuf<int64_t> cstart;  // per level: the eight octant starts of each node
   DBuf<int64_t> excl;
   DBuf<double> centre, half, side, com, mass, q;
   std::vector<int64_t> level_begin;
@@ -453,61 +454,92 @@ __device__ __forceinline__ int digit_at(unsigned long long key, int level) {
   return (int)((key >> (3 * (kMaxLevel - 1 - level))) & 7);
 }
 
-__global__ void mark_children_kernel(int64_t n, int level, int leaf_max, const unsigned long long *__restrict__ keys,
-                                     const int32_t *__restrict__ node_of, const int64_t *__restrict__ nbeg,
-                                     const int64_t *__restrict__ nend, int32_t *__restrict__ flag) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int p = node_of[i];
-    int f = 0;
-    if (p >= 0 && nend[p] - nbeg[p] > leaf_max && level < kMaxLevel) {
-      const int d = digit_at(keys[i], level);
-      f = (i == nbeg[p] || digit_at(keys[i - 1], level) != d) ? 1 : 0;
-    }
-    flag[i] = f;
+// Children of the open nodes of one level (more than leaf_max particles,
+// level below kMaxLevel): eight lanes per node, lane o finds where octant o
+// starts in the node's key range -- the digit at this level never decreases
+// inside a node's range -- so octant o holds [start_o, start_o+1), the last
+// one ending at the node's end.  cnt[p - lb] = the non-empty octants;
+// cstart keeps the eight starts for the emit pass.  Launched with exactly
+// 8 (le - lb) threads rounded up to whole blocks (every lane of a warp
+// reaches the shuffles).
+__global__ void count_children_kernel(int32_t lb, int32_t le, int level, int leaf_max,
+                                      const unsigned long long *__restrict__ keys, const int64_t *__restrict__ nbeg,
+                                      const int64_t *__restrict__ nend, int64_t *__restrict__ cstart,
+                                      int32_t *__restrict__ cnt) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p = lb + (t >> 3);
+  const int o = (int)(t & 7);
+  const bool valid = p < le;
+  int64_t b = 0, e = 0;
+  if (valid) {
+    b = nbeg[p];
+    e = nend[p];
   }
+  const bool open = valid && e - b > leaf_max && level < kMaxLevel;
+  int64_t start = e;
+  if (open) {  // first index of [b, e) whose digit is >= o
+    int64_t lo = b, hi = e;
+    while (lo < hi) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      if (digit_at(keys[mid], level) < o) lo = mid + 1;
+      else hi = mid;
+    }
+    start = lo;
+  }
+  const int64_t next = __shfl_down_sync(0xffffffffu, start, 1);  // octant o + 1's start (same node for o < 7)
+  const bool nonempty = open && (o == 7 ? e : next) > start;
+  const unsigned g = threadIdx.x & 24u;  // this node's first lane in the warp
+  const unsigned mask = (__ballot_sync(0xffffffffu, nonempty) >> g) & 0xffu;
+  if (open) cstart[8 * (p - lb) + o] = start;
+  if (valid && o == 0) cnt[p - lb] = __popc(mask);
 }
 
-__global__ void emit_children_kernel(int64_t n, int level, int32_t base, const unsigned long long *__restrict__ keys,
-                                     int32_t *__restrict__ node_of, const int32_t *__restrict__ flag,
-                                     const int64_t *__restrict__ excl, const int64_t *__restrict__ nend_parent_src,
-                                     int64_t *__restrict__ nbeg, int32_t *__restrict__ nlevel,
-                                     int32_t *__restrict__ nparent, int32_t *__restrict__ nfirst,
-                                     int32_t *__restrict__ nnchild, int32_t *__restrict__ nsysid,
-                                     double *__restrict__ centre, double *__restrict__ half, int leaf_max) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int p = node_of[i];
-    if (p < 0) continue;
-    if (!(nend_parent_src[p] - nbeg[p] > leaf_max && level < kMaxLevel)) {
-      node_of[i] = -1;  // p is a leaf: this particle is done
-      continue;
-    }
-    const int32_t c = base + (int32_t)(excl[i] + flag[i]) - 1;  // the child holding i
-    node_of[i] = c;
-    if (flag[i]) {
-      nbeg[c] = i;
-      nlevel[c] = level + 1;
-      nparent[c] = p;
-      nfirst[c] = -1;
-      nnchild[c] = 0;
-      nsysid[c] = nsysid[p];
-      const int o = digit_at(keys[i], level);
-      const double h = half[p] * 0.5;
-      centre[3 * c] = centre[3 * p] + (((o >> 2) & 1) ? h : -h);
-      centre[3 * c + 1] = centre[3 * p + 1] + (((o >> 1) & 1) ? h : -h);
-      centre[3 * c + 2] = centre[3 * p + 2] + ((o & 1) ? h : -h);
-      half[c] = h;
-    }
+// The children themselves: child k of node p (octants in order, empty ones
+// skipped) is node base + excl[p - lb] + k; its range, level, parent,
+// system and cube; the parent's first child and child count.  Same launch
+// shape as count_children_kernel.
+__global__ void emit_children_kernel(int32_t lb, int32_t le, int32_t base, int level,
+                                     const int64_t *__restrict__ cstart, const int64_t *__restrict__ excl,
+                                     int64_t *__restrict__ nbeg, int64_t *__restrict__ nend,
+                                     int32_t *__restrict__ nlevel, int32_t *__restrict__ nparent,
+                                     int32_t *__restrict__ nfirst, int32_t *__restrict__ nnchild,
+                                     int32_t *__restrict__ nsysid, double *__restrict__ centre,
+                                     double *__restrict__ half) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t p = lb + (t >> 3);
+  const int o = (int)(t & 7);
+  const bool valid = p < le;
+  int64_t c0 = 0, cn = 0;
+  if (valid) {
+    c0 = excl[p - lb];
+    cn = excl[p - lb + 1] - c0;
   }
-}
-
-__global__ void finish_children_kernel(int32_t lo, int32_t hi, int64_t *__restrict__ nbeg, int64_t *__restrict__ nend,
-                                       const int32_t *__restrict__ nparent, int32_t *__restrict__ nfirst,
-                                       int32_t *__restrict__ nnchild) {
-  for (int64_t c = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < hi; c += (int64_t)gridDim.x * blockDim.x) {
-    const int p = nparent[c];
-    nend[c] = (c + 1 < hi && nparent[c + 1] == p) ? nbeg[c + 1] : nend[p];
-    if (c == lo || nparent[c - 1] != p) nfirst[p] = (int32_t)c;
-    atomicAdd(&nnchild[p], 1);
+  int64_t so = 0, eo = 0;
+  if (cn > 0) {
+    so = cstart[8 * (p - lb) + o];
+    eo = o == 7 ? nend[p] : cstart[8 * (p - lb) + o + 1];
+  }
+  const bool nonempty = cn > 0 && eo > so;
+  const unsigned g = threadIdx.x & 24u;
+  const unsigned mask = (__ballot_sync(0xffffffffu, nonempty) >> g) & 0xffu;
+  if (nonempty) {
+    const int32_t c = base + (int32_t)c0 + __popc(mask & ((1u << o) - 1u));
+    nbeg[c] = so;
+    nend[c] = eo;
+    nlevel[c] = level + 1;
+    nparent[c] = (int32_t)p;
+    nfirst[c] = -1;
+    nnchild[c] = 0;
+    nsysid[c] = nsysid[p];
+    const double h = half[p] * 0.5;
+    centre[3 * c] = centre[3 * p] + (((o >> 2) & 1) ? h : -h);
+    centre[3 * c + 1] = centre[3 * p + 1] + (((o >> 1) & 1) ? h : -h);
+    centre[3 * c + 2] = centre[3 * p + 2] + ((o & 1) ? h : -h);
+    half[c] = h;
+  }
+  if (o == 0 && cn > 0) {
+    nfirst[p] = base + (int32_t)c0;
+    nnchild[p] = (int32_t)cn;
   }
 }
 
@@ -995,18 +1027,6 @@ __global__ void roots_kernel(int64_t nsys, const int64_t *__restrict__ sys_off, 
   }
 }
 
-__global__ void node_of_roots_kernel(int64_t n, const int32_t *__restrict__ psys_sorted,
-                                     const int32_t *__restrict__ root_of_sys, int32_t *__restrict__ node_of) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    node_of[i] = root_of_sys[psys_sorted[i]];
-}
-
-__global__ void sorted_sys_kernel(int64_t n, const int64_t *__restrict__ perm, const int32_t *__restrict__ psys,
-                                  int32_t *__restrict__ out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = psys[perm[i]];
-}
-
 int grid1(int64_t n) { return blocks_for(n, 256); }
 
 }  // namespace
@@ -1049,7 +1069,7 @@ void qg_gtree_destroy(qg_gtree *t) {
   t->bmin.release(); t->bmax.release(); t->lo.release(); t->scale.release();
   t->keys.release(); t->keys2.release(); t->vals.release(); t->vals2.release(); t->hist.release(); t->hoff.release();
   t->nbeg.release(); t->nend.release(); t->range.release(); t->nlevel.release(); t->nparent.release();
-  t->nfirst.release(); t->nnchild.release(); t->nsysid.release(); t->node_of.release(); t->flag.release();
+  t->nfirst.release(); t->nnchild.release(); t->nsysid.release(); t->cstart.release(); t->flag.release();
   t->excl.release(); t->centre.release(); t->half.release(); t->side.release(); t->com.release();
   t->mass.release(); t->q.release(); t->sys_root.release(); t->gflag.release(); t->gnode_at.release();
   t->group_node.release(); t->cnt_p.release(); t->cnt_c.release(); t->gidx.release(); t->group_off.release();
@@ -1190,43 +1210,40 @@ static qg_status build_impl(qg_gtree *t, int64_t n, const double *x, const doubl
   };
   st = reserve_nodes(cap, 0);
   if (st != QG_OK) return st;
-  GT_CUDA(t->node_of.reserve(n));
-  GT_CUDA(t->excl.reserve(n + 1));
   roots_kernel<<<grid1(nsys), 256, 0, s>>>(nsys, t->sys_off.p, t->lo.p, t->scale.p + nsys, t->sys_root.p,
                                            t->nbeg.p, t->nend.p, t->nlevel.p, t->nparent.p, t->nfirst.p,
                                            t->nnchild.p, t->nsysid.p, t->centre.p, t->half.p);
   GT_CUDA(cudaGetLastError());
-  if (n > 0) {
-    // the particles' systems in sorted order, then their root
-    sorted_sys_kernel<<<grid1(n), 256, 0, s>>>(n, t->perm.p, t->psys.p, t->flag.p);
-    node_of_roots_kernel<<<grid1(n), 256, 0, s>>>(n, t->flag.p, t->sys_root.p, t->node_of.p);
-    GT_CUDA(cudaGetLastError());
-  }
+  // level by level: the open nodes of a level find their children by binary
+  // search in their key ranges; children are numbered by parent, then octant
   t->level_begin.assign(1, 0);
   int64_t lb = 0, le = nroots;
   for (int level = 0; level < kMaxLevel && n > 0 && le > lb; level++) {
     t->level_begin.push_back(le);
-    mark_children_kernel<<<grid1(n), 256, 0, s>>>(n, level, leaf_max, t->keys.p, t->node_of.p, t->nbeg.p, t->nend.p,
-                                                  t->flag.p);
+    const int64_t L = le - lb;
+    GT_CUDA(t->flag.reserve(L + 1));
+    GT_CUDA(t->excl.reserve(L + 1));
+    GT_CUDA(t->cstart.reserve(8 * L));
+    const int64_t nb = (8 * L + 255) / 256;
+    if (nb >= INT32_MAX) return QG_ERR_ARG;
+    count_children_kernel<<<(unsigned)nb, 256, 0, s>>>((int32_t)lb, (int32_t)le, level, leaf_max, t->keys.p,
+                                                       t->nbeg.p, t->nend.p, t->cstart.p, t->flag.p);
     GT_CUDA(cudaGetLastError());
-    st = scan_excl(t, n, t->flag.p, t->excl.p, s);
+    st = scan_excl(t, L, t->flag.p, t->excl.p, s);
     if (st != QG_OK) return st;
     int64_t C = 0;
-    GT_CUDA(cudaMemcpyAsync(&C, t->excl.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    GT_CUDA(cudaMemcpyAsync(&C, t->excl.p + L, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     GT_CUDA(cudaStreamSynchronize(s));
+    if (C == 0) break;
     if (le + C >= INT32_MAX) return QG_ERR_ARG;
     if ((size_t)(le + C) > t->nbeg.cap) {
       st = reserve_nodes((size_t)(le + C), (size_t)le);
       if (st != QG_OK) return st;
     }
-    emit_children_kernel<<<grid1(n), 256, 0, s>>>(n, level, (int32_t)le, t->keys.p, t->node_of.p, t->flag.p,
-                                                  t->excl.p, t->nend.p, t->nbeg.p, t->nlevel.p, t->nparent.p,
-                                                  t->nfirst.p, t->nnchild.p, t->nsysid.p, t->centre.p, t->half.p,
-                                                  leaf_max);
-    GT_CUDA(cudaGetLastError());
-    if (C == 0) break;
-    finish_children_kernel<<<grid1(C), 256, 0, s>>>((int32_t)le, (int32_t)(le + C), t->nbeg.p, t->nend.p,
-                                                    t->nparent.p, t->nfirst.p, t->nnchild.p);
+    emit_children_kernel<<<(unsigned)nb, 256, 0, s>>>((int32_t)lb, (int32_t)le, (int32_t)le, level, t->cstart.p,
+                                                      t->excl.p, t->nbeg.p, t->nend.p, t->nlevel.p, t->nparent.p,
+                                                      t->nfirst.p, t->nnchild.p, t->nsysid.p, t->centre.p,
+                                                      t->half.p);
     GT_CUDA(cudaGetLastError());
     lb = le;
     le += C;

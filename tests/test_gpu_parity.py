@@ -405,6 +405,34 @@ def test_zero_softening_skips_coincident_pairs():
     assert_parity(a, phi, a_ref, phi_ref, med=3e-6, p99=3e-5, label="eps=0")
 
 
+@pytest.mark.parametrize("origin", [0.0, 3000.0])
+def test_self_pair_adds_no_force_at_tiny_softening(origin):
+    """Every sink is also an entry of its own group's list.  With eps = 1e-9
+    its own pair must give dx = 0 exactly (sink and entry offsets rounded by
+    the same operations), else it adds a force of order m dx / eps^3; the
+    potential keeps the pair's -m/eps, as the oracle does."""
+    rng = np.random.default_rng(41)
+    n = 96
+    x = origin + rng.random((n, 3))
+    m = rng.uniform(0.5, 1.5, n) / n
+    goff = np.array([0, 40, 96], dtype=np.int64)   # two groups; each lists every particle
+    off = np.array([0, n, 2 * n], dtype=np.int64)
+    idx = np.concatenate([np.arange(n), np.arange(n)]).astype(np.int32)
+    eps2 = 1e-18
+    ctx = qgrav.Context(0)
+    ctx.qg_set_sinks(x, goff, eps2)
+    ctx.qg_set_sources(x, m, off, idx)
+    ctx.qg_set_cells(np.zeros((0, 3)), np.zeros(0), np.zeros((0, 6)), np.zeros(3, dtype=np.int64),
+                     np.zeros(0, dtype=np.int32))
+    ctx.qg_run()
+    a, phi = ctx.qg_get_forces()
+    ctx.close()
+    a_ref, phi_ref = oracle.expansion_forces(goff, x, x, m, off, idx, np.zeros((0, 3)), np.zeros(0),
+                                             np.zeros((0, 6)), np.zeros(3, dtype=np.int64),
+                                             np.zeros(0, dtype=np.int32), eps2_all=eps2)
+    assert_parity(a, phi, a_ref, phi_ref, med=1e-6, p99=1e-5, label="self pair, origin %g" % origin)
+
+
 def test_per_sink_softening():
     rng = np.random.default_rng(3)
     ps = workloads.small_set("plummer", 3000, 13, 0.02)
