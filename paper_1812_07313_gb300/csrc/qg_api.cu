@@ -774,13 +774,13 @@ qg_status qg_autotune(qg_ctx *c, void *stream, int reps, qg_options *best, float
   float chosen_ms = 0.f;
   bool have = false;
   if (c->G > 0) {
-    const int Rs[3] = {2, 4, 8}, Ws[3] = {2, 4, 8}, Ts[3] = {128, 256, 512};
+    const int Rs[3] = {2, 4, 8}, Ws[3] = {2, 4, 8}, Ts[4] = {128, 256, 512, 1024};
     const int As[2] = {QG_ARITH_PAIRED, QG_ARITH_SCALAR};
     const int n_arith = base.precision == QG_FP32_CENTRED ? 2 : 1;
     for (int ai = 0; ai < n_arith; ai++)
     for (int ri = 0; ri < 3; ri++)
       for (int wi = 0; wi < 3; wi++)
-        for (int ti = 0; ti < 3; ti++) {
+        for (int ti = 0; ti < 4; ti++) {
           qg_options o = base;
           o.sinks_per_thread = Rs[ri];
           o.warps_per_group = Ws[wi];

@@ -246,7 +246,7 @@ def test_autotuner_picks_a_supported_shape_and_keeps_parity(sphere4k):
     ctx.qg_set_cells(t.cell_com, t.cell_m, t.cell_q, L.clist_off, L.clist_idx)
     best, ms = ctx.qg_autotune(reps=2)
     assert best.sinks_per_thread in (2, 4, 8) and best.warps_per_group in (2, 4, 8)
-    assert best.tile_j in (128, 256, 512) and ms > 0
+    assert best.tile_j in (128, 256, 512, 1024) and ms > 0
     st = ctx.qg_get_stats()
     assert st["sinks_per_thread"] == best.sinks_per_thread and st["tile_j"] == best.tile_j
     a0, p0 = ctx.qg_get_forces()
@@ -441,6 +441,13 @@ def test_per_sink_softening():
     a, phi, _ = case.gpu()
     a_ref, phi_ref = case.oracle()
     assert_parity(a, phi, a_ref, phi_ref, label="per-sink eps")
+    # the one-call entry point by both routes, per-sink softening included
+    ctx = qgrav.Context(0)
+    for pinned in (False, True):
+        a2, phi2 = _evaluate_host(case, ctx, pinned=pinned)
+        assert ctx.qg_get_stats()["eval_in_place"] == (1 if pinned else 0)
+        assert np.array_equal(a2, a) and np.array_equal(phi2, phi)
+    ctx.close()
 
 
 def test_far_from_origin_needs_centring():
