@@ -62,6 +62,45 @@ __global__ void pack_cells_kernel(int64_t nc, const double *__restrict__ com, co
   }
 }
 
+// c_g for every group: the centre of the bounding box of its sinks, one warp
+// per group.  Offsets from the group's first sink are rounded to float, their
+// extremes found (exact, so in any order), and the centre formed in FP64:
+// c = x_first + (lo + hi) / 2.  The force kernels centre sinks and list
+// entries on it.
+__global__ void group_centre_kernel(int64_t G, const int64_t *__restrict__ goff, const double *__restrict__ x,
+                                    double *__restrict__ centre) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (gridDim.x * (int64_t)blockDim.x) >> 5;
+  for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
+    const int64_t s0 = goff[g], ni = goff[g + 1] - s0;
+    double c = 0.0;
+    if (ni > 0) {
+      const double b0 = x[3 * s0], b1 = x[3 * s0 + 1], b2 = x[3 * s0 + 2];
+      float mn0 = 0.f, mn1 = 0.f, mn2 = 0.f, mx0 = 0.f, mx1 = 0.f, mx2 = 0.f;
+      for (int64_t i = lane; i < ni; i += 32) {
+        const double *xi = x + 3 * (s0 + i);
+        const float o0 = qg::f64_to_f32_rn(xi[0] - b0);
+        const float o1 = qg::f64_to_f32_rn(xi[1] - b1);
+        const float o2 = qg::f64_to_f32_rn(xi[2] - b2);
+        mn0 = fminf(mn0, o0); mn1 = fminf(mn1, o1); mn2 = fminf(mn2, o2);
+        mx0 = fmaxf(mx0, o0); mx1 = fmaxf(mx1, o1); mx2 = fmaxf(mx2, o2);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        mn0 = fminf(mn0, __shfl_xor_sync(0xffffffffu, mn0, o));
+        mn1 = fminf(mn1, __shfl_xor_sync(0xffffffffu, mn1, o));
+        mn2 = fminf(mn2, __shfl_xor_sync(0xffffffffu, mn2, o));
+        mx0 = fmaxf(mx0, __shfl_xor_sync(0xffffffffu, mx0, o));
+        mx1 = fmaxf(mx1, __shfl_xor_sync(0xffffffffu, mx1, o));
+        mx2 = fmaxf(mx2, __shfl_xor_sync(0xffffffffu, mx2, o));
+      }
+      const float lo = lane == 0 ? mn0 : lane == 1 ? mn1 : mn2, hi = lane == 0 ? mx0 : lane == 1 ? mx1 : mx2;
+      const double base = lane == 0 ? b0 : lane == 1 ? b1 : b2;
+      c = base + 0.5 * ((double)lo + (double)hi);
+    }
+    if (lane < 3) centre[3 * g + lane] = c;
+  }
+}
+
 // Index check that also makes the list safe to read: an entry outside
 // [0, n) is counted in *bad and replaced by 0 (a kernel already queued behind
 // this one then reads a valid record, and its caller fails with QG_ERR_ARG).
@@ -106,6 +145,7 @@ struct qg_ctx {
   DevBuf<double> sink_x;
   DevBuf<float> sink_eps2;
   DevBuf<int64_t> goff;
+  DevBuf<double> gcentre;  // [G][3] bounding-box centre of each group
   std::vector<int64_t> h_goff;
   // sources
   int64_t ns = 0, G_src = -1, np_list = 0;
@@ -309,6 +349,7 @@ qg::ForceParams force_params(qg_ctx *c, int64_t g0, int64_t G, int *head) {
   p.sink_eps2 = c->has_eps2 ? c->sink_eps2.p : nullptr;
   p.eps2_all = c->eps2_all;
   p.group_off = c->goff.p + g0;
+  p.gcentre = c->gcentre.p + 3 * g0;
   p.src = c->src.p;
   p.src_m64 = c->src_m64.p;
   p.plist_off = c->poff.p + g0;
@@ -504,6 +545,17 @@ qg_status qg_set_options(qg_ctx *c, const qg_options *opt) {
   return QG_OK;
 }
 
+// Group centres of the sinks now on the device (sink_x, goff), on stream s.
+static qg_status group_centres(qg_ctx *c, int64_t G, cudaStream_t s) {
+  cudaError_t e = c->gcentre.reserve(3 * std::max<int64_t>(G, 1));
+  if (e != cudaSuccess) return fail(c, QG_ERR_NOMEM, "group centre allocation");
+  if (G > 0) {
+    group_centre_kernel<<<grid_for(32 * G, 256), 256, 0, s>>>(G, c->goff.p, c->sink_x.p, c->gcentre.p);
+    QG_CUDA(c, cudaGetLastError());
+  }
+  return QG_OK;
+}
+
 static qg_status set_sinks_common(qg_ctx *c, int64_t n, const double *x, const float *eps2, double eps2_all,
                                   int64_t ngroups, const int64_t *group_off, bool dev, cudaStream_t s) {
   // inputs must not change under a step that is still running
@@ -546,6 +598,7 @@ static qg_status set_sinks_common(qg_ctx *c, int64_t n, const double *x, const f
     if (eps2 && (st = upload(c, c->sink_eps2, eps2, n, s)) != QG_OK) return st;
     if ((st = upload(c, c->goff, group_off, ngroups + 1, s)) != QG_OK) return st;
   }
+  if ((st = group_centres(c, ngroups, s)) != QG_OK) return st;
   QG_CUDA(c, cudaStreamSynchronize(s));
   c->n = n;
   c->G = ngroups;
@@ -968,6 +1021,10 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
     return st;
   }
   QG_CUDA(c, cudaStreamWaitEvent(s, c->inputs_ready, 0));
+  if ((st = group_centres(c, G, s)) != QG_OK) {
+    cudaStreamSynchronize(ci_s);
+    return st;
+  }
   if (ns)
     pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, same_x ? c->sink_x.p : c->stage_src.p, c->src_m64.p,
                                                       c->src.p);

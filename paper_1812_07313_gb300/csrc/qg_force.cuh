@@ -4,7 +4,8 @@
 // One CTA evaluates one sink group at a time, taking group ids from a
 // device work queue (ordered by descending cost) with an atomic counter.
 // Inside the CTA:
-//   1. c_g = centre of the bounding box of the group's sinks (FP64).
+//   1. c_g = centre of the bounding box of the group's sinks (FP64, computed
+//      once per set of sinks by group_centre_kernel).
 //   2. sink offsets x_i - c_g are formed in FP64, cast to Real, kept in
 //      shared memory; each thread holds R sinks in registers.
 //   3. the group's list is staged tile by tile into shared memory:
@@ -234,8 +235,6 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
   using V2 = typename RT<Real>::v2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
-  __shared__ float s_box[8][6];
-  __shared__ double s_c[3];
 
   const int NT = blockDim.x;
   const int tid = threadIdx.x;
@@ -277,38 +276,13 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
       continue;
     }
 
-    // ---- 1. group centre: bounding box of the sinks ----------------------
+    // ---- 1. group centre: the bounding-box centre of the sinks, computed
+    // once when the sinks were set (group_centre_kernel)
     double cx = 0.0, cy = 0.0, cz = 0.0;
     if (CENTRED) {
-      const double x0 = p.sink_x[3 * s0], y0 = p.sink_x[3 * s0 + 1], z0 = p.sink_x[3 * s0 + 2];
-      float mn0 = 0.f, mn1 = 0.f, mn2 = 0.f, mx0 = 0.f, mx1 = 0.f, mx2 = 0.f;
-      for (int i = tid; i < ni; i += NT) {
-        const double *xi = p.sink_x + 3 * (s0 + i);
-        const float o0 = f64_to_f32_rn(xi[0] - x0);
-        const float o1 = f64_to_f32_rn(xi[1] - y0);
-        const float o2 = f64_to_f32_rn(xi[2] - z0);
-        mn0 = fminf(mn0, o0); mn1 = fminf(mn1, o1); mn2 = fminf(mn2, o2);
-        mx0 = fmaxf(mx0, o0); mx1 = fmaxf(mx1, o1); mx2 = fmaxf(mx2, o2);
-      }
-      mn0 = warp_min(mn0); mn1 = warp_min(mn1); mn2 = warp_min(mn2);
-      mx0 = warp_max(mx0); mx1 = warp_max(mx1); mx2 = warp_max(mx2);
-      const int w = tid >> 5;
-      if ((tid & 31) == 0) {
-        s_box[w][0] = mn0; s_box[w][1] = mn1; s_box[w][2] = mn2;
-        s_box[w][3] = mx0; s_box[w][4] = mx1; s_box[w][5] = mx2;
-      }
-      __syncthreads();
-      if (tid < 3) {
-        float lo = s_box[0][tid], hi = s_box[0][tid + 3];
-        for (int v = 1; v < (NT >> 5); v++) {
-          lo = fminf(lo, s_box[v][tid]);
-          hi = fmaxf(hi, s_box[v][tid + 3]);
-        }
-        const double base = tid == 0 ? x0 : (tid == 1 ? y0 : z0);
-        s_c[tid] = base + 0.5 * ((double)lo + (double)hi);
-      }
-      __syncthreads();
-      cx = s_c[0]; cy = s_c[1]; cz = s_c[2];
+      cx = p.gcentre[3 * g];
+      cy = p.gcentre[3 * g + 1];
+      cz = p.gcentre[3 * g + 2];
     }
 
     const int64_t p0 = p.plist_off[g], p1 = p.plist_off[g + 1];

@@ -62,6 +62,7 @@ struct ForceParams {
   const float *sink_eps2;
   double eps2_all;
   const int64_t *group_off;
+  const double *gcentre;  // [G][3] centre of each group's bounding box (centred kernels)
   const PosMass *src;
   const double *src_m64;
   const int64_t *plist_off;
