@@ -450,6 +450,15 @@ def test_per_sink_softening():
     ctx.close()
 
 
+def test_uncentred_fp32_holds_the_tolerance_near_the_origin(sphere4k):
+    """The ablation kernel (absolute coordinates cast to FP32, no centring)
+    on a set about the origin: the casts lose no more than the offsets'
+    rounding would, and the tolerance holds."""
+    a_ref, phi_ref = sphere4k.oracle()
+    a, phi, _ = sphere4k.gpu(qgrav.Options(precision=qgrav.QG_FP32_RAW))
+    assert_parity(a, phi, a_ref, phi_ref, label="raw fp32 near the origin")
+
+
 def test_far_from_origin_needs_centring():
     """Systems thousands of units from the origin: the centred FP32 path holds
     the tolerance; casting absolute coordinates (QG_FP32_RAW) cannot."""
