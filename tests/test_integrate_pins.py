@@ -1,7 +1,7 @@
 """Pins of the oracle leapfrog (oracle/integrate.py) against what mechanics
 fixes: a circular two-body orbit (closed form), second-order convergence,
-bounded energy error, time reversibility, and the energies of a known
-configuration."""
+bounded energy error, time reversibility, and the energies and momentum of
+known configurations."""
 import math
 
 import numpy as np
@@ -71,6 +71,18 @@ def test_energies_with_per_particle_softening():
     _, phi = oracle.direct_forces(x, x, m, sink_eps2=e2)
     _, W, _ = integrate.energies(np.zeros((2, 3)), m, phi, e2)
     assert abs(W + 0.5 * (0.25 / math.sqrt(1.01) + 0.25 / math.sqrt(1.04))) < 1e-15
+
+
+def test_energies_and_momentum_with_unequal_masses():
+    # masses 1 and 2 at distance 2, velocities (1, 0, 0) and (0, 1, 0):
+    # p = (1, 2, 0), K = (1 + 2) / 2, W = -m1 m2 / d = -1 (no softening)
+    x = np.array([[1.0, 0.0, 0.0], [-1.0, 0.0, 0.0]])
+    m = np.array([1.0, 2.0])
+    v = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    _, phi = oracle.direct_forces(x, x, m)
+    K, W, p = integrate.energies(v, m, phi, 0.0)
+    assert np.allclose(p, [1.0, 2.0, 0.0], rtol=0, atol=1e-15)
+    assert abs(K - 1.5) < 1e-15 and abs(W + 1.0) < 1e-15
 
 
 def test_leapfrog_is_time_reversible():
