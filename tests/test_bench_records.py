@@ -1,0 +1,59 @@
+"""bench.py's recorded DRAM traffic (profiles/force_kernel_traffic.txt) is
+used only for the workload, launch shape and force-kernel sources it was
+measured on; the source hash ignores comments and blank space."""
+import os
+import shutil
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+LAUNCH = {"sinks_per_thread": 4, "warps_per_group": 4, "tile_j": 512, "arith": "scalar f32"}
+
+
+def _records():
+    recs, rec = [], {}
+    with open(os.path.join(ROOT, "profiles", "force_kernel_traffic.txt")) as f:
+        for line in f:
+            if not line.strip():
+                if rec:
+                    recs.append(rec)
+                rec = {}
+            elif "=" in line and not line.lstrip().startswith("#"):
+                k, v = line.split("=", 1)
+                rec[k.strip()] = v.strip()
+    if rec:
+        recs.append(rec)
+    return recs
+
+
+def test_a_record_is_used_only_for_its_workload_shape_and_sources(monkeypatch):
+    recs = _records()
+    assert recs and all({"workload", "launch", "kernel_hash", "bytes_per_launch"} <= set(r) for r in recs)
+    r = next(r for r in recs if r["launch"] == "4,4,512,x1")
+    monkeypatch.setattr(bench, "kernel_hash", lambda: r["kernel_hash"])
+    assert bench._recorded_traffic(r["workload"], LAUNCH) == float(r["bytes_per_launch"])
+    assert bench._recorded_traffic("plummer_4m", LAUNCH) is None            # another workload
+    assert bench._recorded_traffic(r["workload"], dict(LAUNCH, tile_j=1024)) is None   # another shape
+    assert bench._recorded_traffic(r["workload"], dict(LAUNCH, arith="paired f32x2")) is None
+    monkeypatch.setattr(bench, "kernel_hash", lambda: "0" * 12)
+    assert bench._recorded_traffic(r["workload"], LAUNCH) is None            # other sources
+
+
+def test_the_source_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_1812_07313_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for f in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(ROOT, "paper_1812_07313_gb300", "csrc", f), csrc / f)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_hash()
+    assert len(h0) == 12
+    f = csrc / bench.KERNEL_SOURCES[0]
+    text = f.read_text()
+    f.write_text("// a new comment line\n" + text.replace("\n", "\n\n", 3) + "\n/* and a block comment */\n")
+    assert bench.kernel_hash() == h0
+    f.write_text(text.replace("#pragma once", "#pragma once\nstatic const int qg_unused_marker = 1;", 1))
+    assert bench.kernel_hash() != h0
