@@ -21,29 +21,33 @@ _i32 = _P(ctypes.c_int32)
 _lib = None
 
 
+def _bind(lib):
+    """Attach the qgt_* signatures to a loaded tree library."""
+    lib.qgt_build.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_int64, _i64, ctypes.c_int,
+                              ctypes.c_int, _P(ctypes.c_void_p)]
+    lib.qgt_build.restype = ctypes.c_int
+    lib.qgt_free.argtypes = [ctypes.c_void_p]
+    lib.qgt_free.restype = None
+    lib.qgt_sizes.argtypes = [ctypes.c_void_p, _i64, _i64, _i64]
+    lib.qgt_sizes.restype = ctypes.c_int
+    lib.qgt_perm.argtypes = [ctypes.c_void_p]
+    lib.qgt_perm.restype = _i64
+    lib.qgt_group_off.argtypes = [ctypes.c_void_p]
+    lib.qgt_group_off.restype = _i64
+    lib.qgt_nodes.argtypes = [ctypes.c_void_p, _P(_d), _P(_d), _P(_d), _P(_d), _P(_d),
+                              _P(_i64), _P(_i32)]
+    lib.qgt_nodes.restype = ctypes.c_int
+    lib.qgt_walk.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]
+    lib.qgt_walk.restype = ctypes.c_int
+    lib.qgt_lists.argtypes = [ctypes.c_void_p, _P(_i64), _P(_i32), _i64, _P(_i64), _P(_i32), _i64]
+    lib.qgt_lists.restype = ctypes.c_int
+    return lib
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = _native.load(_native.build_tree())
-        lib.qgt_build.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_int64, _i64, ctypes.c_int,
-                                  ctypes.c_int, _P(ctypes.c_void_p)]
-        lib.qgt_build.restype = ctypes.c_int
-        lib.qgt_free.argtypes = [ctypes.c_void_p]
-        lib.qgt_free.restype = None
-        lib.qgt_sizes.argtypes = [ctypes.c_void_p, _i64, _i64, _i64]
-        lib.qgt_sizes.restype = ctypes.c_int
-        lib.qgt_perm.argtypes = [ctypes.c_void_p]
-        lib.qgt_perm.restype = _i64
-        lib.qgt_group_off.argtypes = [ctypes.c_void_p]
-        lib.qgt_group_off.restype = _i64
-        lib.qgt_nodes.argtypes = [ctypes.c_void_p, _P(_d), _P(_d), _P(_d), _P(_d), _P(_d),
-                                  _P(_i64), _P(_i32)]
-        lib.qgt_nodes.restype = ctypes.c_int
-        lib.qgt_walk.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_int]
-        lib.qgt_walk.restype = ctypes.c_int
-        lib.qgt_lists.argtypes = [ctypes.c_void_p, _P(_i64), _P(_i32), _i64, _P(_i64), _P(_i32), _i64]
-        lib.qgt_lists.restype = ctypes.c_int
-        _lib = lib
+        _lib = _bind(_native.load(_native.build_tree()))
     return _lib
 
 
@@ -94,6 +98,7 @@ class Tree:
         if rc != 0:
             raise ValueError("qgt_build failed (%d)" % rc)
         self._h = h
+        self._L = lib  # the library that owns the handle: walks and frees go through it
         self.leaf_max, self.n_crit = leaf_max, n_crit
         nn, nnodes, ng = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         lib.qgt_sizes(h, ctypes.byref(nn), ctypes.byref(nnodes), ctypes.byref(ng))
@@ -120,7 +125,7 @@ class Tree:
         self.cell_sys = _copy(ps, k, np.int32)
 
     def walk(self, theta, nthreads=0) -> Lists:
-        lib = _load()
+        lib = self._L
         rc = lib.qgt_walk(self._h, float(theta), int(nthreads))
         if rc != 0:
             raise ValueError("qgt_walk failed (%d)" % rc)
@@ -135,6 +140,7 @@ class Tree:
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h is not None and _lib is not None:
-            _lib.qgt_free(h)
+        lib = getattr(self, "_L", None)
+        if h is not None and lib is not None:
+            lib.qgt_free(h)
             self._h = None

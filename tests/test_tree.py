@@ -22,6 +22,52 @@ def test_groups_partition_and_respect_n_crit(sphere):
     np.testing.assert_array_equal(tr.x, ps.x[tr.perm])
 
 
+def _parents(tr):
+    """Parent of each node: the node of twice the side whose range holds it."""
+    rng, side = tr.cell_range, tr.cell_side
+    parent = np.full(tr.nnodes, -1)
+    for k in range(tr.nnodes):
+        cand = np.nonzero((side == 2 * side[k]) & (rng[:, 0] <= rng[k, 0]) & (rng[:, 1] >= rng[k, 1])
+                          & (tr.cell_sys == tr.cell_sys[k]))[0]
+        assert len(cand) <= 1
+        if len(cand):
+            parent[k] = cand[0]
+    return parent
+
+
+def test_leaves_split_at_leaf_max_and_groups_are_maximal(sphere):
+    """A node is split exactly when it holds more than leaf_max particles
+    (Sec. 3.4's tree, leaf <= 8 here), and a group is a maximal node with at
+    most n_crit particles: its parent holds more."""
+    _, tr = sphere
+    parent = _parents(tr)
+    cnt = tr.cell_range[:, 1] - tr.cell_range[:, 0]
+    internal = np.zeros(tr.nnodes, bool)
+    internal[parent[parent >= 0]] = True
+    assert np.all(cnt[internal] > tr.leaf_max)
+    assert np.all(cnt[~internal] <= tr.leaf_max)
+    node_of_range = {(int(b), int(e)): k for k, (b, e) in enumerate(tr.cell_range)}
+    for g in range(tr.ngroups):
+        b, e = int(tr.group_off[g]), int(tr.group_off[g + 1])
+        k = node_of_range[(b, e)]  # a group is a node
+        assert e - b <= tr.n_crit
+        assert parent[k] < 0 or cnt[parent[k]] > tr.n_crit
+
+
+def test_lattice_groups_and_leaves_in_closed_form():
+    """A 16^3 lattice has nodes of exactly n_crit = 64 and leaf_max = 8
+    particles: the groups are the 64 level-2 cubes of 64 points, and the
+    tree stops at the 512 level-3 cubes of 8 points (1 + 8 + 64 + 512
+    nodes)."""
+    g = np.arange(16, dtype=np.float64)
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), axis=-1).reshape(-1, 3) / 16.0
+    tr = qtree.Tree(x, np.full(len(x), 1.0 / len(x)), None, 8, 64)
+    assert tr.ngroups == 64 and np.all(np.diff(tr.group_off) == 64)
+    assert tr.nnodes == 1 + 8 + 64 + 512
+    cnt = tr.cell_range[:, 1] - tr.cell_range[:, 0]
+    assert np.array_equal(np.sort(cnt), np.sort(np.repeat([4096, 512, 64, 8], [1, 8, 64, 512])))
+
+
 def test_leaves_and_ranges(sphere):
     _, tr = sphere
     cnt = tr.cell_range[:, 1] - tr.cell_range[:, 0]
@@ -72,6 +118,48 @@ def test_accepted_cells_satisfy_opening_test(sphere):
             assert ce <= b or cb >= e  # never holds the group's own particles
             d = np.linalg.norm(np.maximum(0, np.maximum(lo - tr.cell_com[c], tr.cell_com[c] - hi)))
             assert tr.cell_side[c] < theta * d
+
+
+def _acceptable(tr, k, b, e, lo, hi, theta):
+    """The walk's acceptance test for node k and the group of sinks [b, e) with
+    bounding box [lo, hi]: k holds none of the group's particles, its cube
+    does not meet the box, and side < theta * (distance of its centre of mass
+    from the box)."""
+    cb, ce = tr.cell_range[k]
+    if cb < e and ce > b:
+        return False
+    h = 0.5 * tr.cell_side[k]
+    c = tr.cell_centre[k]
+    if np.all(c + h >= lo) and np.all(c - h <= hi):
+        return False
+    d = np.linalg.norm(np.maximum(0, np.maximum(lo - tr.cell_com[k], tr.cell_com[k] - hi)))
+    return tr.cell_side[k] ** 2 < theta ** 2 * d ** 2
+
+
+def test_cells_are_opened_only_when_the_test_requires_it(sphere):
+    """The other direction of the opening test: the parent of every accepted
+    cell, and the leaf of every listed particle outside the group, failed the
+    acceptance test (the walk is not more conservative than theta asks)."""
+    _, tr = sphere
+    theta = 0.6
+    L = tr.walk(theta)
+    rng = tr.cell_range
+    parent = _parents(tr)
+    leaf_of = np.full(tr.n, -1)
+    is_parent = np.zeros(tr.nnodes, bool)
+    is_parent[parent[parent >= 0]] = True
+    for k in np.nonzero(~is_parent)[0]:
+        leaf_of[rng[k, 0]:rng[k, 1]] = k
+    assert np.all(leaf_of >= 0)
+    for g in range(0, tr.ngroups, 5):
+        b, e = tr.group_off[g], tr.group_off[g + 1]
+        lo, hi = tr.x[b:e].min(0), tr.x[b:e].max(0)
+        for c in L.clist_idx[L.clist_off[g]:L.clist_off[g + 1]]:
+            assert _acceptable(tr, c, b, e, lo, hi, theta)
+            assert parent[c] >= 0 and not _acceptable(tr, parent[c], b, e, lo, hi, theta)
+        for i in L.plist_idx[L.plist_off[g]:L.plist_off[g + 1]]:
+            if not b <= i < e:
+                assert not _acceptable(tr, leaf_of[i], b, e, lo, hi, theta)
 
 
 def test_multi_system_lists_stay_inside_their_system():
