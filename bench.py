@@ -48,8 +48,17 @@ DESCR = {
 # particle-cell interactions/s at large N on one core of the CPU it names (Sec. 5.2).
 PAPER_CONTEXT = {"cell_interactions_per_s": 7e8, "cpu": "Intel Xeon E5-2683 v4 (2.1 GHz), 1 core",
                  "code": "AVX2 FP32, approximate rsqrt, -ffast-math"}
+# Workloads measured into the default line's 'configs' record, with their legs: group-size
+# candidates, quadrupole thetas of the equal-error comparison, one launch per system vs batched.
+CONFIGS = {"batched_512": {"group_sizes": [64, 128, 256], "ee_thetas": (), "batching": True},
+           "clumpy_16m": {"group_sizes": None, "ee_thetas": (0.5,), "batching": False},
+           "plummer_4m": {"group_sizes": None, "ee_thetas": (0.5,), "batching": False}}
 # Algorithmic FP32 instructions per interaction (FMA = 1): quad 33, mono 13
 OPS_QUAD, OPS_MONO = 33, 13
+# FP32 forms of the force kernel (qg_stats.paired): name in the bench line and tag of the --launch flag
+ARITH_NAMES = {0: "scalar f32", 1: "paired f32x2", 2: "entry-paired f32x2"}
+ARITH_TAGS = {"scalar f32": "x1", "paired f32x2": "x2", "entry-paired f32x2": "xe"}
+ARITH_CODES = {"scalar f32": 1, "paired f32x2": 2, "entry-paired f32x2": 3}
 
 
 def parse():
@@ -61,8 +70,12 @@ def parse():
     ap.add_argument("--workload", default="cube_1m")
     ap.add_argument("--theta", type=float, default=None)
     ap.add_argument("--no-equal-error", action="store_true", help="skip the monopole equal-error search")
-    ap.add_argument("--equal-error-thetas", default="0.5",
+    ap.add_argument("--equal-error-thetas", default="0.3,0.5,0.7",
                     help="quadrupole thetas of the equal-error comparison (comma separated)")
+    ap.add_argument("--configs", default=None,
+                    help="other workloads measured into the line's 'configs' record (comma separated, or 'none'); "
+                         "default: %s for the default workload without --launch, else none" % ",".join(CONFIGS))
+    ap.add_argument("--config-steps", type=int, default=20, help="timed steps of each 'configs' workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--batching-compare", action="store_true",
@@ -75,8 +88,8 @@ def parse():
                     help="skip timing the tree build, moments, groups and walk on the GPU (whole step on the device)")
     ap.add_argument("--gpu-tree", action="store_true", help=argparse.SUPPRESS)  # the default; kept for old commands
     ap.add_argument("--launch", default=None,
-                    help="R,W,T[,x1|x2]: fixed sinks/thread, warps/CTA, tile (and scalar or paired FP32) "
-                         "instead of the autotuner (profiling)")
+                    help="R,W,T[,x1|x2|xe]: fixed sinks/thread, warps/CTA, tile (and scalar, sink-paired or "
+                         "entry-paired FP32) instead of the autotuner (profiling)")
     return ap.parse_args()
 
 
@@ -260,81 +273,214 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------- our arm
 
-def equal_error(torch, qgrav, tr, eps2_all, thetas, flush, stream, steps):
-    """For each quadrupole theta: time quadrupole steps, measure their p99 of
-    Eq. 8 against FP64 GPU direct summation on 4096 seeded sinks, find by
-    bisection the largest monopole-only theta whose p99 is no larger, and time
-    monopole-only steps there (both launch shapes autotuned)."""
+class GpuWorkload:
+    """A workload's particles on the device and its tree, groups and lists
+    built on the GPU (the same groups and lists as the host builder, in
+    milliseconds): the legs below walk it at any theta and hand the lists to
+    a force context."""
+
+    def __init__(self, torch, name, n_crit=None):
+        from paper_1812_07313_gb300 import gtree, workloads
+        self.name = name
+        self.wl = workloads.WORKLOADS[name]
+        self.ps = self.wl.particles()
+        if len(set(self.ps.eps.tolist())) != 1:
+            raise ValueError("%s: one softening for every particle is needed here" % name)
+        self.eps2_all = float(self.ps.eps[0]) ** 2
+        self.dev = torch.cuda.current_device()
+        self.x = torch.as_tensor(self.ps.x).cuda()
+        self.m = torch.as_tensor(self.ps.m).cuda()
+        self.tree = gtree.GpuTree(self.dev)
+        self.n_crit = None
+        self.theta = None
+        if n_crit is not None:
+            self.build(n_crit)
+
+    def build(self, n_crit, stream=None):
+        self.tree.build(self.x, self.m, self.ps.sys_off, self.wl.leaf_max, int(n_crit), stream)
+        self.n_crit = int(n_crit)
+        self.theta = None
+
+    def load(self, ctx, theta, stream=None):
+        """Walk at theta (unless the last walk was at it) and set ctx's inputs."""
+        if self.theta != theta:
+            self.tree.walk(theta, stream)
+            self.theta = theta
+        self.tree.attach(ctx, self.eps2_all, stream)
+
+    def sorted_positions(self):
+        return self.tree.host("xs"), self.tree.host("ms")
+
+    def close(self):
+        self.tree.close()
+
+
+def time_context(torch, ctx, stream, flush, steps, warmup, local_rank=0, autotune=True):
+    """Autotune (optional), warm up, then `steps` timed steps with the L2
+    flushed before each and the clocks sampled: (step ms, force ms, clocks)."""
+    if autotune:
+        ctx.qg_autotune(stream.cuda_stream, reps=3)
+    for _ in range(max(warmup, 1)):
+        ctx.qg_run(stream.cuda_stream)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    step_ms, force_ms = timed_steps(torch, ctx, stream, flush, steps)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    return step_ms, force_ms, clocks
+
+
+def roofline_of(i_pp, i_pc, force_ms, clocks, n_sm, stats, traffic=None):
+    """FP32-issue roofline of the force kernel: algorithmic FP32
+    lane-instructions (33 per particle-cell pair, 13 per particle pair, FMA =
+    1) per second of force-kernel time, against SMs x 128 lanes x the median
+    SM clock sampled during the timed region."""
+    alg = OPS_QUAD * i_pc + OPS_MONO * i_pp
+    achieved = alg / (force_ms * 1e-3) / 1e12
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
+    peak_max = n_sm * 128 * 2070e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "peak_basis": "FP32 lane-instructions/s = %d SMs x 128 x median SM clock %.0f MHz under load "
+                          "(at the 2070 MHz maximum: %.1f Tinst/s, frac %.3f)"
+                          % (n_sm, sm_mhz, peak_max, achieved / peak_max),
+            "kernel": "force_kernel<float,R=%d,quad,%s>, %d threads, tile %d" % (
+                stats["sinks_per_thread"], ARITH_NAMES[stats["paired"]], stats["block"], stats["tile_j"]),
+            "force_kernel_ms": force_ms}
+
+
+def equal_error(torch, qgrav, gw, thetas, flush, stream, steps, n_sample=4096):
+    """For each quadrupole theta: time quadrupole steps and measure their p99
+    of Eq. 8 against FP64 GPU direct summation on n_sample seeded sinks; find
+    the largest monopole-only theta whose p99 is no larger (theta stepped down
+    from the quadrupole's by factors of 0.8 until the p99 is met, then
+    bisected between the last two), and time monopole-only steps there (both
+    launch shapes autotuned).  Trees, groups and lists are built on the GPU
+    (gw: GpuWorkload, already built)."""
+    xs, ms = gw.sorted_positions()
+    sys_off = np.asarray(gw.ps.sys_off)
+    n = len(xs)
     rng = np.random.default_rng(12345)
-    ns = min(4096, tr.n)
-    sample = np.sort(rng.choice(tr.n, ns, replace=False))
+    ns = min(n_sample, n)
+    sample = np.sort(rng.choice(n, ns, replace=False))
     dev = torch.device("cuda")
-    xs = torch.as_tensor(tr.x[sample]).to(dev)
+    xs_d = torch.as_tensor(xs).to(dev)
+    ms_d = torch.as_tensor(ms).to(dev)
     a_d = torch.empty((ns, 3), dtype=torch.float64, device=dev)
     p_d = torch.empty(ns, dtype=torch.float64, device=dev)
-    # systems are independent: direct sums per system
-    sys_of = tr.sink_sys[sample]
+    # systems are independent (each sorted within itself): direct sums per system
+    sys_of = np.searchsorted(sys_off, sample, side="right") - 1
     a_dir = np.empty((ns, 3))
     for s in np.unique(sys_of):
         sel = np.nonzero(sys_of == s)[0]
-        b, e = tr.sys_off[s], tr.sys_off[s + 1]
-        qgrav.qg_direct_dev(xs[sel].contiguous(), torch.as_tensor(tr.x[b:e]).to(dev),
-                            torch.as_tensor(tr.m[b:e]).to(dev), eps2_all, a_d[:len(sel)], p_d[:len(sel)])
+        b, e = int(sys_off[s]), int(sys_off[s + 1])
+        qgrav.qg_direct_dev(xs_d[sample[sel]].contiguous(), xs_d[b:e], ms_d[b:e], gw.eps2_all, a_d[:len(sel)],
+                            p_d[:len(sel)])
         a_dir[sel] = a_d[:len(sel)].cpu().numpy()
 
     def p99(a):
         e = np.linalg.norm(a[sample] - a_dir, axis=1) / np.linalg.norm(a_dir, axis=1)
         return float(np.percentile(e, 99))
 
-    def timed(ctx, L):
-        load_ctx(ctx, tr, L, eps2_all, None)
-        ctx.qg_autotune(stream.cuda_stream, reps=3)
-        for _ in range(3):
-            ctx.qg_run(stream.cuda_stream)
-        torch.cuda.synchronize()
-        ms, _ = timed_steps(torch, ctx, stream, flush, steps)
+    def timed(ctx, theta):
+        gw.load(ctx, theta, stream.cuda_stream)
+        ms, _, _ = time_context(torch, ctx, stream, flush, steps, 3)
         a, _ = ctx.qg_get_forces()
         st = ctx.qg_get_stats()
         return float(ms.mean()), a, int(st["i_pp"] + st["i_pc"])
 
     rows = []
-    quad = qgrav.Context(torch.cuda.current_device())
-    mono = qgrav.Context(torch.cuda.current_device(), qgrav.Options(expansion=qgrav.QG_MONO))
+    quad = qgrav.Context(gw.dev)
+    mono = qgrav.Context(gw.dev, qgrav.Options(expansion=qgrav.QG_MONO))
     for theta_q in thetas:
-        q_ms, a_q, q_int = timed(quad, tr.walk(theta_q))
+        q_ms, a_q, q_int = timed(quad, theta_q)
         target = p99(a_q)
         cache = {}
 
         def mono_at(th):
-            th = round(th, 4)
+            th = round(th, 5)
             if th not in cache:
-                L = tr.walk(th)
-                load_ctx(mono, tr, L, eps2_all, None)
-                mono.qg_run()
+                gw.load(mono, th, stream.cuda_stream)
+                mono.qg_run(stream.cuda_stream)
                 a, _ = mono.qg_get_forces()
-                cache[th] = (p99(a), L)
+                cache[th] = p99(a)
             return cache[th]
 
-        lo, hi = max(0.1, 0.5 * theta_q), theta_q
-        if mono_at(lo)[0] > target:
-            th_m = lo
-        else:
-            for _ in range(7):
+        # step down until the monopole code is at least as accurate, then bisect
+        hi, lo = theta_q, theta_q
+        while mono_at(lo) > target and lo > 0.02:
+            hi, lo = lo, 0.8 * lo
+        if mono_at(lo) <= target:
+            for _ in range(6):
                 mid = 0.5 * (lo + hi)
-                if mono_at(mid)[0] <= target:
+                if mono_at(mid) <= target:
                     lo = mid
                 else:
                     hi = mid
-            th_m = lo
-        p_m, L_m = mono_at(th_m)
-        m_ms, _, m_int = timed(mono, L_m)
+        th_m = round(lo, 5)
+        p_m = mono_at(th_m)
+        m_ms, _, m_int = timed(mono, th_m)
         rows.append({"theta_quad": theta_q, "p99_quad": target, "quad_ms_per_step": q_ms, "quad_interactions": q_int,
                      "theta_mono": th_m, "p99_mono": p_m, "mono_ms_per_step": m_ms, "mono_interactions": m_int,
-                     "quad_over_mono_time": q_ms / m_ms})
-        cache.clear()
+                     "quad_over_mono_time": q_ms / m_ms, "mono_meets_target": p_m <= target})
     quad.close()
     mono.close()
-    return {"error_sample": "FP64 GPU direct summation on %d seeded sinks" % ns, "rows": rows}
+    return {"error_sample": "FP64 GPU direct summation on %d seeded sinks" % ns,
+            "search": "monopole theta stepped down by 0.8 from the quadrupole theta until its p99 is no larger, "
+                      "then 6 bisection steps; GPU-built trees and lists", "rows": rows}
+
+
+def config_record(torch, qgrav, name, steps, warmup, stream, flush, n_sm, local_rank=0, group_sizes=None,
+                  ee_thetas=(), batching=False):
+    """One workload measured as the main line is (GPU-built tree and lists,
+    autotuned launch shape, L2 flushed before each timed step, clocks sampled
+    during the timed region), with optional group-size tuning, quadrupole vs
+    monopole-only at equal p99 error and the one-launch-per-system
+    comparison."""
+    from paper_1812_07313_gb300 import tuning
+    t0 = time.perf_counter()
+    gw = GpuWorkload(torch, name)
+    theta = gw.wl.theta
+    rec = {"workload": "%s: %s" % (name, DESCR.get(name, "")), "theta": theta}
+    if group_sizes:
+        best, table = tuning.tune_group_size_gpu(gw.tree, gw.x, gw.m, gw.ps.sys_off, gw.wl.leaf_max, theta,
+                                                 group_sizes, gw.eps2_all, device=gw.dev, steps=3,
+                                                 stream=stream.cuda_stream)
+        gw.n_crit, gw.theta = best.n_crit, theta
+        rec["group_size"] = {"n_crit": best.n_crit, "tuned": True,
+                             "candidates": [{"n_crit": r.n_crit, "groups": r.groups, "interactions": r.interactions,
+                                             "step_ms": r.step_ms, "force_ms": r.force_ms, "launch": r.launch}
+                                            for r in table]}
+    else:
+        gw.build(gw.wl.n_crit)
+        rec["group_size"] = {"n_crit": gw.wl.n_crit, "tuned": False}
+    ctx = qgrav.Context(gw.dev)
+    gw.load(ctx, theta, stream.cuda_stream)
+    t_tune = time.perf_counter()
+    ctx.qg_autotune(stream.cuda_stream, reps=3)
+    t_tune = time.perf_counter() - t_tune
+    step_ms, force_ms, clocks = time_context(torch, ctx, stream, flush, steps, warmup, local_rank, autotune=False)
+    st = ctx.qg_get_stats()
+    i_pp, i_pc = int(st["i_pp"]), int(st["i_pc"])
+    rec.update({"value": (i_pp + i_pc) / (float(step_ms.mean()) * 1e-3), "unit": UNIT,
+                "ms_per_step": float(step_ms.mean()), "steps": steps,
+                "interactions": {"i_pp": i_pp, "i_pc": i_pc}, "groups": int(st["n_groups"]),
+                "launch": {"sinks_per_thread": st["sinks_per_thread"], "warps_per_group": st["warps_per_group"],
+                           "tile_j": st["tile_j"], "grid": st["grid"], "block": st["block"],
+                           "arith": ARITH_NAMES[st["paired"]], "autotune_s": t_tune},
+                "roofline": roofline_of(i_pp, i_pc, float(force_ms.mean()), clocks, n_sm, st),
+                "clocks": clocks})
+    if batching:
+        rec["batching"] = batching_compare(torch, qgrav, gw, stream, flush, float(step_ms.mean()))
+    ctx.close()
+    if ee_thetas:
+        rec["equal_error"] = equal_error(torch, qgrav, gw, list(ee_thetas), flush, stream, max(5, steps // 2),
+                                         n_sample=2048 if gw.ps.x.shape[0] > (1 << 23) else 4096)
+    gw.close()
+    rec["wall_s"] = time.perf_counter() - t0
+    return rec
 
 
 def run_ours(args, rank, world, local_rank):
@@ -373,7 +519,8 @@ def run_ours(args, rank, world, local_rank):
     if args.launch:
         parts = args.launch.split(",")
         R, W, T = (int(v) for v in parts[:3])
-        arith = {"x1": qgrav.QG_ARITH_SCALAR, "x2": qgrav.QG_ARITH_PAIRED}[parts[3]] if len(parts) > 3 else 0
+        arith = {"x1": qgrav.QG_ARITH_SCALAR, "x2": qgrav.QG_ARITH_PAIRED,
+                 "xe": qgrav.QG_ARITH_ENTRY_PAIRED}[parts[3]] if len(parts) > 3 else 0
         ctx.set_options(qgrav.Options(sinks_per_thread=R, warps_per_group=W, tile_j=T, arith=arith))
     else:
         ctx.qg_autotune(stream.cuda_stream, reps=3)
@@ -389,7 +536,7 @@ def run_ours(args, rank, world, local_rank):
     st = ctx.qg_get_stats()
     launch.update({"sinks_per_thread": st["sinks_per_thread"], "warps_per_group": st["warps_per_group"],
                    "tile_j": st["tile_j"], "grid": st["grid"], "block": st["block"],
-                   "arith": "paired f32x2" if st["paired"] else "scalar f32"})
+                   "arith": ARITH_NAMES[st["paired"]]})
 
     if world > 1:
         dist.barrier()
@@ -407,21 +554,8 @@ def run_ours(args, rank, world, local_rank):
                                       dist if world > 1 else None, "cuda")
 
     # roofline of the force kernel: FP32 issue bound (lane instructions, FMA = 1)
-    alg = OPS_QUAD * i_pc + OPS_MONO * i_pp
-    f_mean = float(force_ms.mean()) * 1e-3
-    achieved = alg / f_mean / 1e12
-    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    peak = n_sm * 128 * sm_mhz * 1e6 / 1e12
-    peak_max = n_sm * 128 * 2070e6 / 1e12
-    traffic = _recorded_traffic(args.workload, launch)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s", "frac": achieved / peak,
-                "traffic": traffic,
-                "peak_basis": "FP32 lane-instructions/s = %d SMs x 128 x median SM clock %.0f MHz under load "
-                              "(at the 2070 MHz maximum: %.1f Tinst/s, frac %.3f)"
-                              % (n_sm, sm_mhz, peak_max, achieved / peak_max),
-                "kernel": "force_kernel<float,R=%d,quad,%s>, %d threads, tile %d" % (
-                    launch["sinks_per_thread"], launch["arith"], launch["block"], launch["tile_j"]),
-                "force_kernel_ms": float(force_ms.mean())}
+    roofline = roofline_of(i_pp, i_pc, float(force_ms.mean()), clocks, n_sm, st,
+                           _recorded_traffic(args.workload, launch))
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -437,20 +571,24 @@ def run_ours(args, rank, world, local_rank):
            "roofline": roofline, "gpu_launches": 3 * args.steps, "clocks": clocks,
            "wall_s_timed_loop": t_wall}
 
+    gw = None
+    if rank == 0 and eps2 is None and ((not args.no_equal_error) or (args.batching_compare and ps.nsys > 1)):
+        gw = GpuWorkload(torch, args.workload, n_crit=tr_n_crit(tr, wl))
     if rank == 0 and not args.no_equal_error and eps2 is None:
         thetas = [float(v) for v in args.equal_error_thetas.split(",")]
         ee_steps = max(5, args.steps // 2)
-        out["equal_error"] = equal_error(torch, qgrav, tr, eps2_all, thetas, flush, stream, ee_steps)
-        out["gpu_launches"] += 2 * 3 * ee_steps * len(thetas)
-
-    if rank == 0 and args.batching_compare and ps.nsys > 1:
-        out["batching"] = batching_compare(torch, qgrav, tr, L, eps2_all, eps2, stream, flush,
-                                           float(np.mean(step_ms)))
+        out["equal_error"] = equal_error(torch, qgrav, gw, thetas, flush, stream, ee_steps)
+    if rank == 0 and args.batching_compare and ps.nsys > 1 and gw is not None:
+        gw.theta = None
+        gw.tree.walk(theta)
+        gw.theta = theta
+        out["batching"] = batching_compare(torch, qgrav, gw, stream, flush, float(np.mean(step_ms)))
+    if gw is not None:
+        gw.close()
     # the chosen launch shape, for the legs below
     chosen = qgrav.Options(sinks_per_thread=launch["sinks_per_thread"], warps_per_group=launch["warps_per_group"],
                            tile_j=launch["tile_j"],
-                           arith=qgrav.QG_ARITH_PAIRED if launch.get("arith", "").startswith("paired")
-                           else qgrav.QG_ARITH_SCALAR)
+                           arith=ARITH_CODES[launch.get("arith", "scalar f32")])
     if rank == 0 and not args.no_gpu_tree:
         out["gpu_tree"] = gpu_tree_step(torch, qgrav, ps, wl, tr, L, eps2_all, eps2, stream, chosen)
     if rank == 0 and args.precision_compare:
@@ -472,6 +610,18 @@ def run_ours(args, rank, world, local_rank):
                                          "kind": "oracle, groups split over host threads (OpenMP)",
                                          "cpu": cpu_model(), "sample": "the cpu_baseline sample, %.2f s" % dtp}
     ctx.close()
+
+    # the other workloads, each measured as the main line is
+    configs = args.configs
+    if configs is None:
+        configs = "none" if (args.launch or args.workload != "cube_1m") else ",".join(CONFIGS)
+    if rank == 0 and configs != "none":
+        out["configs"] = {}
+        for name in configs.split(","):
+            leg = CONFIGS.get(name, {"group_sizes": None, "ee_thetas": (), "batching": False})
+            out["configs"][name] = config_record(torch, qgrav, name, args.config_steps, max(args.warmup, 3), stream,
+                                                 flush, n_sm, local_rank, leg["group_sizes"], leg["ee_thetas"],
+                                                 leg["batching"])
     if rank == 0:
         print(json.dumps(out))
 
@@ -487,29 +637,39 @@ def aggregate_ranks(total_ms, steps, units_per_step, world, dist=None, device="c
     return total_ms, world * steps * units_per_step / (total_ms * 1e-3)
 
 
-def batching_compare(torch, qgrav, tr, L, eps2_all, eps2, stream, flush, batched_ms, steps=5):
+def batching_compare(torch, qgrav, gw, stream, flush, batched_ms, steps=5):
     """The same step as one qg_run per system (each system its own context,
     its own queue build and force launch, launched back to back on one
-    stream) against the single batched launch."""
-    sys_of_group = tr.sink_sys[tr.group_off[:-1]]
+    stream) against the single batched launch.  Each system's sinks, lists
+    and cells are cut out of the GPU-built tree (gw: GpuWorkload, built and
+    walked): its nodes gathered and the cell-list entries renumbered."""
+    t = gw.tree
+    xs, ms = gw.sorted_positions()
+    goff_all, po_all, pi_all = t.host("group_off"), t.host("plist_off"), t.host("plist_idx")
+    co_all, ci_all = t.host("clist_off"), t.host("clist_idx")
+    com, cm, cq, nr = t.host("cell_com"), t.host("cell_m"), t.host("cell_q"), t.host("node_range")
+    sys_off = np.asarray(gw.ps.sys_off)
+    sys_of_group = np.searchsorted(sys_off, goff_all[:-1], side="right") - 1
+    node_sys = np.searchsorted(sys_off, nr[:, 0], side="right") - 1
     ctxs = []
-    for s in range(len(tr.sys_off) - 1):
-        b, e = int(tr.sys_off[s]), int(tr.sys_off[s + 1])
+    for s in range(len(sys_off) - 1):
+        b, e = int(sys_off[s]), int(sys_off[s + 1])
         gsel = np.nonzero(sys_of_group == s)[0]
         if len(gsel) == 0:
             continue
         g0, g1 = int(gsel[0]), int(gsel[-1]) + 1
-        nodes = np.nonzero(tr.cell_sys == s)[0]
-        n0, n1 = int(nodes[0]), int(nodes[-1]) + 1
-        goff = tr.group_off[g0:g1 + 1] - tr.group_off[g0]
-        po = L.plist_off[g0:g1 + 1] - L.plist_off[g0]
-        co = L.clist_off[g0:g1 + 1] - L.clist_off[g0]
-        pi = L.plist_idx[L.plist_off[g0]:L.plist_off[g1]] - b
-        ci = L.clist_idx[L.clist_off[g0]:L.clist_off[g1]] - n0
-        c = qgrav.Context(torch.cuda.current_device())
-        c.qg_set_sinks(tr.x[b:e], goff, eps2_all, None if eps2 is None else eps2[b:e])
-        c.qg_set_sources(tr.x[b:e], tr.m[b:e], po, pi)
-        c.qg_set_cells(tr.cell_com[n0:n1], tr.cell_m[n0:n1], tr.cell_q[n0:n1], co, ci)
+        nodes = np.nonzero(node_sys == s)[0]
+        renum = np.full(len(nr), -1, dtype=np.int64)
+        renum[nodes] = np.arange(len(nodes))
+        goff = goff_all[g0:g1 + 1] - goff_all[g0]
+        po = po_all[g0:g1 + 1] - po_all[g0]
+        co = co_all[g0:g1 + 1] - co_all[g0]
+        pi = (pi_all[po_all[g0]:po_all[g1]] - b).astype(np.int32)
+        ci = renum[ci_all[co_all[g0]:co_all[g1]]].astype(np.int32)
+        c = qgrav.Context(gw.dev)
+        c.qg_set_sinks(xs[b:e], goff, gw.eps2_all)
+        c.qg_set_sources(xs[b:e], ms[b:e], po, pi)
+        c.qg_set_cells(com[nodes], cm[nodes], cq[nodes], co, ci)
         ctxs.append(c)
     # one launch shape for all systems: the batched step's autotuned shape would
     # favour the batched side, so each system keeps the default shape
@@ -649,8 +809,8 @@ def e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world, options=None, steps=5
             "api": "qg_evaluate_host (pinned host arrays in and out; %s), wall clock" % route}
 
 
-# the translation unit of the FP32 force kernels (its launch shape is part of the record's key)
-KERNEL_SOURCES = ("qg_force.cuh", "qg_force_f32.cu", "qg_internal.h")
+# the translation units of the FP32 force kernels (the launch shape and form are part of the record key)
+KERNEL_SOURCES = ("qg_force.cuh", "qg_force_f32.cu", "qg_force_f32ep.cu", "qg_internal.h")
 
 
 def kernel_hash():
@@ -689,7 +849,7 @@ def _recorded_traffic(workload, launch):
     if rec:
         recs.append(rec)
     shape = "%d,%d,%d,%s" % (launch["sinks_per_thread"], launch["warps_per_group"], launch["tile_j"],
-                             "x2" if launch.get("arith", "").startswith("paired") else "x1")
+                             ARITH_TAGS[launch.get("arith", "scalar f32")])
     for r in recs:
         if r.get("workload") == workload and r.get("kernel_hash") == kernel_hash() and r.get("launch") == shape:
             try:

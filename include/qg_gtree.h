@@ -43,10 +43,14 @@ extern "C" {
 
 typedef struct qg_gtree qg_gtree;
 
+/* A tree object on CUDA device `device` (no counterpart in the paper, whose
+ * tree lives in the caller's node array, List 4); destroy frees it. */
 qg_status qg_gtree_create(qg_gtree **out, int device);
 void qg_gtree_destroy(qg_gtree *t);
 
 /*
+ * List 4's create_tree: the tree, its cell moments (Eq. 2) and the groups of
+ * at most n_crit particles (Sec. 3.4); T_construct of Table 3.
  * Build from device arrays x [n][3], m [n] (n < 2^31).  sys_off [nsys+1] is a
  * HOST array: system s = particles [sys_off[s], sys_off[s+1]), sys_off[0] = 0,
  * sys_off[nsys] = n.  leaf_max >= 1, n_crit >= 1.
@@ -54,9 +58,12 @@ void qg_gtree_destroy(qg_gtree *t);
 qg_status qg_gtree_build(qg_gtree *t, int64_t n, const double *x_dev, const double *m_dev, int64_t nsys,
                          const int64_t *sys_off, int leaf_max, int n_crit, void *cuda_stream);
 
-/* Group walk with opening angle theta (theta <= 0 opens every node). */
+/* List 4's tree_traversal for every group at once (T_traverse of Table 3),
+ * with the opening test of Sec. 1: group walk with opening angle theta
+ * (theta <= 0 opens every node). */
 qg_status qg_gtree_walk(qg_gtree *t, double theta, void *cuda_stream);
 
+/* Sizes of the last build and walk (any pointer may be NULL). */
 qg_status qg_gtree_sizes(const qg_gtree *t, int64_t *n, int64_t *nnodes, int64_t *ngroups, int64_t *n_plist,
                          int64_t *n_clist);
 
@@ -75,16 +82,20 @@ qg_status qg_gtree_arrays(const qg_gtree *t, const int64_t **perm, const double 
                           const int64_t **clist_off, const int32_t **clist_idx);
 
 /*
- * Set a force context's sinks (the sorted particles), sources and cells from
+ * Hands the groups and lists to the force calls, as List 4 passes each
+ * group's i_list, j_list and j_cell to the g5_ / g5c_ calls:
+ * set a force context's sinks (the sorted particles), sources and cells from
  * the last build and walk, device to device.  eps2_all as in qg_set_sinks.
  */
 qg_status qg_gtree_attach(qg_gtree *t, qg_ctx *ctx, double eps2_all, void *cuda_stream);
 
-/* out[perm[i]] = in[i] for k values per particle (device arrays): results in
- * sorted order back to input order. */
+/* List 4's assign_force_potential / add_force_potential: the per-sink
+ * results returned to the particles.  out[perm[i]] = in[i] for k values per
+ * particle (device arrays): results in sorted order back to input order. */
 qg_status qg_gtree_unsort(const qg_gtree *t, const double *in_dev, double *out_dev, int k, void *cuda_stream);
 
-/* Device time of the last build and walk (CUDA events), milliseconds. */
+/* T_construct and T_traverse of Table 3: device time of the last build and
+ * walk (CUDA events), milliseconds. */
 qg_status qg_gtree_timing(const qg_gtree *t, float *build_ms, float *walk_ms);
 
 #ifdef __cplusplus

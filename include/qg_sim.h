@@ -60,12 +60,14 @@ typedef struct {
   int64_t groups, n_plist, n_clist, i_pp, i_pc;
 } qg_sim_times;
 
-/* force_opt may be NULL (defaults); its expansion field is overridden by
- * params->expansion. */
+/* A simulation with the parameters of Sec. 5's runs (theta, eps, n_crit,
+ * monopole or quadrupole cells).  force_opt may be NULL (defaults); its
+ * expansion field is overridden by params->expansion. */
 qg_status qg_sim_create(qg_sim **out, int device, const qg_sim_params *params, const qg_options *force_opt);
 void qg_sim_destroy(qg_sim *sim);
 
 /*
+ * The initial conditions of a run (Sec. 5: a cold homogeneous sphere).
  * Initial state from HOST arrays x [n][3], v [n][3], m [n] (n < 2^31) and
  * sys_off [nsys+1] (independent systems, each with its own tree root;
  * sys_off = {0, n} for one system).  eps2 [n] (host, may be NULL): each
@@ -75,21 +77,29 @@ void qg_sim_destroy(qg_sim *sim);
 qg_status qg_sim_set_state(qg_sim *sim, int64_t n, const double *x, const double *v, const double *m,
                            const float *eps2, int64_t nsys, const int64_t *sys_off, void *cuda_stream);
 
-/* nsteps kick-drift-kick steps of length dt (nsteps >= 0, dt finite). */
+/* The leapfrog of Sec. 5 with its fixed step: nsteps kick-drift-kick steps
+ * of length dt (nsteps >= 0, dt finite). */
 qg_status qg_sim_step(qg_sim *sim, double dt, int64_t nsteps, void *cuda_stream);
 
-/* Copy the state to HOST arrays (any pointer may be NULL); synchronises. */
+/* The particle data of List 4's particle class (positions, velocities and
+ * the accelerations and potentials of the last force evaluation): copy the
+ * state to HOST arrays (any pointer may be NULL); synchronises. */
 qg_status qg_sim_get_state(qg_sim *sim, double *x, double *v, double *a, double *phi);
 
-/* Device pointers to the state (the simulation owns them; valid until the
+/* As qg_sim_get_state, on the device.
+ * Device pointers to the state (the simulation owns them; valid until the
  * next qg_sim_set_state or qg_sim_destroy; any pointer may be NULL). */
 qg_status qg_sim_state_dev(const qg_sim *sim, const double **x, const double **v, const double **a,
                            const double **phi, const double **m);
 
-/* Kinetic and potential energy, and total momentum p [3] (may be NULL), of
- * the current state: FP64 reductions on the device in a fixed order. */
+/* The energies that check a run (Sec. 5's cold collapse starts at virial
+ * ratio 0.1): kinetic and potential energy, and total momentum p [3] (may be
+ * NULL), of the current state: FP64 reductions on the device in a fixed
+ * order. */
 qg_status qg_sim_energy(qg_sim *sim, double *kinetic, double *potential, double *momentum, void *cuda_stream);
 
+/* Seconds per step, the quantity the paper reports for its runs (Sec. 5),
+ * split into its parts. */
 qg_status qg_sim_last_times(const qg_sim *sim, qg_sim_times *out);
 
 #ifdef __cplusplus

@@ -28,6 +28,8 @@ extern "C" {
 typedef struct qgt_tree qgt_tree;
 
 /*
+ * List 4's create_tree on the host: the tree and the groups of at most
+ * n_crit particles (the modified tree algorithm, Sec. 3.4).
  * Build one oct-tree per system.  x: [n][3] positions, m: [n] masses.
  * sys_off: [nsys+1] offsets, system s = particles [sys_off[s], sys_off[s+1]).
  * leaf_max: a node with at most leaf_max particles is a leaf (>= 1).
@@ -40,6 +42,7 @@ int qgt_build(int64_t n, const double *x, const double *m,
               int64_t nsys, const int64_t *sys_off,
               int leaf_max, int n_crit, qgt_tree **out);
 
+/* Frees a tree built by qgt_build. */
 void qgt_free(qgt_tree *t);
 
 /* Sizes: particles, nodes (= cells), groups. */
@@ -60,6 +63,8 @@ int qgt_nodes(const qgt_tree *t, const double **com, const double **mass,
               const int64_t **range /* [nnodes][2] */, const int32_t **sys);
 
 /*
+ * List 4's tree_traversal for every group, with the opening test l/d < theta
+ * of Sec. 1 (theta, not theta^2 as List 4 passes it).
  * Group walk with opening angle theta.  For each group g with particle
  * bounding box B_g, a node n is accepted as a j-cell iff its cube does not
  * meet B_g, it holds none of g's particles, and side(n)^2 < theta^2 d^2
@@ -72,6 +77,8 @@ int qgt_nodes(const qgt_tree *t, const double **com, const double **mass,
  */
 int qgt_walk(qgt_tree *t, double theta, int nthreads);
 
+/* The lists of the last walk as CSR arrays: List 4's jlist (j-particles)
+ * and jcell (j-cells) of every group, concatenated. */
 int qgt_lists(const qgt_tree *t,
               const int64_t **plist_off, const int32_t **plist_idx, int64_t *np_total,
               const int64_t **clist_off, const int32_t **clist_idx, int64_t *nc_total);

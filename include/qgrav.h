@@ -52,6 +52,15 @@
  * QG_ERR_CUDA from qg_run or from the next synchronising call.
  *
  * Threading.  A context is used by one host thread at a time.
+ *
+ * Correspondence with the paper's library (Sec. 3.4, Lists 3 and 4).  The
+ * paper's tree code calls its force library once per group: g5_open and
+ * g5_set_eps_to_all once, then per group g5_set_xmjMC / g5_set_nMC /
+ * g5_calculate_force_on_xMC for the particle part of the list and
+ * g5c_set_xmjMC / g5c_set_nMC / g5c_calculate_force_on_xMC for the cell part.
+ * Here every group of a step is set at once (sinks, per-group lists as CSR
+ * offsets) and evaluated in one call; each declaration below names the
+ * paper's call or passage it stands for.
  */
 #ifndef QGRAV_H
 #define QGRAV_H
@@ -70,14 +79,24 @@ typedef enum {
   QG_ERR_CUDA = -2,    /* a CUDA call failed                               */
   QG_ERR_NOMEM = -3,   /* device or host allocation failed                 */
   QG_ERR_STATE = -4,   /* inputs missing or inconsistent (e.g. ngroups)    */
-  QG_ERR_TIMEOUT = -5, /* a bounded device-side wait gave up               */
+  QG_ERR_TIMEOUT = -5, /* reserved: no call returns it (no kernel of this
+                          library waits on another kernel or on the host) */
   QG_ERR_SIZE = -6     /* a size beyond a fixed maximum (qg_forces_noalloc) */
 } qg_status;
 
 enum { QG_FP32_CENTRED = 0, QG_FP32_RAW = 1, QG_FP64 = 2 };
 enum { QG_QUAD = 0, QG_MONO = 1 };
-enum { QG_ARITH_DEFAULT = 0, QG_ARITH_SCALAR = 1, QG_ARITH_PAIRED = 2 };
+enum { QG_ARITH_DEFAULT = 0, QG_ARITH_SCALAR = 1, QG_ARITH_PAIRED = 2, QG_ARITH_ENTRY_PAIRED = 3 };
 
+/*
+ * Options of a context.  A 0 in tile_j, warps_per_group, sinks_per_thread,
+ * flush_j or arith selects a FIXED default (tile 256, 4 warps, 4 sinks per
+ * thread, fold every 256 entries, scalar FP32), not a tuned one: the tuning
+ * call is qg_autotune, which times the supported shapes on the inputs set
+ * and stores the fastest in the context.  The paper has no counterpart (its
+ * kernel has one fixed shape, 4 i-particles x 2 j-cells per AVX2 iteration,
+ * List 2); precision and expansion select the variants compared in Secs. 4-5.
+ */
 typedef struct {
   int precision;        /* QG_FP32_CENTRED | QG_FP32_RAW | QG_FP64          */
   int expansion;        /* QG_QUAD | QG_MONO                                 */
@@ -90,8 +109,10 @@ typedef struct {
   int flush_j;          /* FP32 partials are folded into FP64 after at most
                            this many list entries per thread; 0 = 256       */
   int arith;            /* QG_FP32_CENTRED only: QG_ARITH_SCALAR (the
-                           default, 0) or QG_ARITH_PAIRED (two sinks per
-                           float2 register, f32x2 FMA instructions)          */
+                           default, 0), QG_ARITH_PAIRED (two sinks per
+                           float2 register, f32x2 FMA instructions) or
+                           QG_ARITH_ENTRY_PAIRED (two list entries per
+                           float2 register; sinks_per_thread 2 or 4)        */
 } qg_options;
 
 typedef struct {
@@ -103,17 +124,26 @@ typedef struct {
   int32_t tile_j;
   int32_t warps_per_group;
   int32_t flush_j;
-  int32_t paired;             /* 1 if the paired-FP32 form runs              */
+  int32_t paired;             /* FP32 form: 0 scalar, 1 sink-paired,
+                                 2 entry-paired                              */
   int32_t eval_in_place;      /* 1 if the last qg_evaluate_host read the
                                  lists and wrote the results in place       */
 } qg_stats;
 
-/* Create a context on CUDA device `device`.  opt may be NULL (defaults). */
+/* Create a context on CUDA device `device`.  opt may be NULL (defaults).
+ * Stands for g5_open (List 4); `device` replaces the paper's devid. */
 qg_status qg_create(qg_ctx **out, int device, const qg_options *opt);
+/* Release the context and its device memory.  Stands for g5_close (List 4). */
 void qg_destroy(qg_ctx *ctx);
+/* Change the options (see qg_options); the next qg_run uses them. */
 qg_status qg_set_options(qg_ctx *ctx, const qg_options *opt);
 
 /*
+ * The i-particles of every group (Sec. 3.4: the particles of a cell with at
+ * most n_crit particles share one interaction list; List 4's ilist holds
+ * their positions xi and count ni) and their softening (g5_set_eps_to_all in
+ * List 4 sets one eps for all; the i-particle structure of List 2 carries
+ * eps^2 per i-particle, hence the optional per-sink array).
  * Sinks, grouped: group g owns sinks [group_off[g], group_off[g+1]).
  * x: [n][3] positions.  eps2: [n] per-sink squared softening (Phantom-GRAPE
  * keeps eps^2 per i-particle) or NULL to use eps2_all for every sink.
@@ -123,6 +153,9 @@ qg_status qg_set_sinks(qg_ctx *ctx, int64_t n, const double *x, const float *eps
                        double eps2_all, int64_t ngroups, const int64_t *group_off);
 
 /*
+ * The j-particles of every group's list: what List 4 passes per group to
+ * g5_set_xmjMC (positions xj, masses mj) and g5_set_nMC (their number),
+ * evaluated as Plummer-softened point masses (the monopole term of Eq. 1).
  * Source particles and the particle part of every group's list.
  * x: [ns][3], m: [ns].  list_off: [ngroups+1] (same ngroups as the sinks),
  * list_off[0] = 0, non-decreasing; list_idx: [list_off[ngroups]] entries,
@@ -132,6 +165,10 @@ qg_status qg_set_sources(qg_ctx *ctx, int64_t ns, const double *x, const double 
                          const int64_t *list_off, const int32_t *list_idx);
 
 /*
+ * The j-cells of every group's list: what List 3's g5c_set_xmjMC (centres
+ * of mass xj, masses mj, quadrupole tensors qj[6], Eq. 2) and g5c_set_nMC
+ * (their number) pass per group, and the paper stores as floats in its
+ * j-cell structure (List 1).
  * Tree cells and the cell part of every group's list.
  * com: [nc][3] centres of mass, m: [nc] masses, q: [nc][6] quadrupole
  * tensors about the centre of mass, q00 q01 q02 q11 q12 q22, unhalved as in
@@ -155,6 +192,10 @@ qg_status qg_set_cells_dev(qg_ctx *ctx, int64_t nc, const double *com, const dou
                            int64_t n_list, void *cuda_stream);
 
 /*
+ * The force calls of every group at once: g5_calculate_force_on_xMC (the
+ * j-particles) and g5c_calculate_force_on_xMC (the j-cells, Eqs. 1, 4-7) of
+ * List 3 and the group loop of calc_force in List 4, accumulated into one
+ * acceleration and potential per sink.
  * One evaluation of every group: work-queue build (groups ordered by
  * descending cost), then one persistent launch over all groups.  The
  * sequence is captured once in a CUDA graph and replayed.  Asynchronous on
@@ -163,25 +204,35 @@ qg_status qg_set_cells_dev(qg_ctx *ctx, int64_t nc, const double *com, const dou
 qg_status qg_run(qg_ctx *ctx, void *cuda_stream);
 
 /*
+ * No counterpart in the paper (its kernel has one fixed shape, List 2).
  * Autotuner: times every supported launch shape (sinks_per_thread x
- * warps_per_group x tile_j, and scalar vs paired FP32 arithmetic for
- * QG_FP32_CENTRED) of the current precision / expansion on the
- * inputs currently set, `reps` timed runs each after one warm-up run (the
- * force kernel's device time, CUDA events), and keeps the fastest as the
- * context's options.  The sink grouping itself (n_crit) is an input and is
+ * warps_per_group x tile_j, in the scalar and the entry-paired FP32 forms for
+ * QG_FP32_CENTRED) of the current precision / expansion on the inputs
+ * currently set -- each shape once (the force kernel's device time, CUDA
+ * events), then the four fastest again with one warm-up and `reps` timed
+ * runs each -- and keeps the fastest as the context's options.  The
+ * sink-paired form (QG_ARITH_PAIRED) is not tried: it was slower at every
+ * shape measured; it stays selectable through qg_options.  The sink grouping itself (n_crit) is an input and is
  * not tuned here.  best (may be NULL) receives the chosen options,
  * best_ms the chosen shape's mean force-kernel time.  Synchronous; the
  * outputs afterwards hold a valid result of the chosen shape.
  */
 qg_status qg_autotune(qg_ctx *ctx, void *cuda_stream, int reps, qg_options *best, float *best_ms);
 
-/* Copy a [n][3] and phi [n] (either may be NULL) to the host; synchronises. */
+/* The results, as the arrays ai and pi that List 3's force call fills (the
+ * kernel's output structure in List 2 holds ax, ay, az and phi): a [n][3]
+ * and phi [n] (either may be NULL) copied to the host; synchronises.  phi is
+ * the physical potential of Eq. 1 (negative), a = -grad phi (Eq. 6). */
 qg_status qg_get_forces(qg_ctx *ctx, double *a, double *phi);
 
-/* Device-to-device copy of the results into caller buffers on `cuda_stream`. */
+/* As qg_get_forces: device-to-device copy of the results into caller
+ * buffers on `cuda_stream`. */
 qg_status qg_get_forces_dev(qg_ctx *ctx, double *a, double *phi, void *cuda_stream);
 
 /*
+ * The force part of List 4's calc_force in one call (every group's
+ * j-particle and j-cell calls, Lists 3 and 4), from host arrays as the
+ * paper's library takes them.
  * One evaluation from HOST arrays: the inputs of qg_set_sinks, qg_set_sources
  * and qg_set_cells (same meaning, layout and checks), then the forces written
  * to a [n][3] and phi [n] (host).  The sinks, sources and cells are copied
@@ -211,15 +262,21 @@ qg_status qg_evaluate_host(qg_ctx *ctx, int64_t n, const double *sink_x, const f
                            const double *cell_com, const double *cell_m, const double *cell_q,
                            const int64_t *clist_off, const int32_t *clist_idx, double *a, double *phi);
 
+/* Sizes, launch shape and interaction counts of the inputs set.  The paper
+ * reports cell interactions per second (Sec. 5.2, Fig. 4); i_pc counts those
+ * pairs and i_pp the particle pairs. */
 qg_status qg_get_stats(const qg_ctx *ctx, qg_stats *out);
 
 /*
+ * The force time of a step (T_force of Table 3, Sec. 5.1).
  * Device time of the last qg_run, from CUDA events recorded inside its
  * graph: step_ms = whole step (work-queue build + force kernel), force_ms =
  * the persistent force kernel alone.  Synchronises the run's stream.
  * Either pointer may be NULL.
  */
 qg_status qg_last_timing(qg_ctx *ctx, float *step_ms, float *force_ms);
+/* Message of the last failing call on this context (no counterpart in the
+ * paper's library, whose calls return nothing). */
 const char *qg_last_error(const qg_ctx *ctx);
 
 /*
@@ -235,6 +292,9 @@ qg_status qg_direct_dev(int device, int64_t nsink, const double *sink_x, double 
                         double *a, double *phi, void *cuda_stream);
 
 /*
+ * The double -> float conversion that the paper's g5c_set_xmjMC applies when
+ * it stores j-cells as floats (Sec. 3.4, List 1); here it is applied to
+ * positions after the FP64 group centring.
  * Self-test of the rounding the FP32 kernels apply to FP64-centred offsets:
  * double -> float, nearest with ties to even, done with integer operations
  * (IEEE 754 binary64 -> binary32).  Magnitudes below the smallest normal

@@ -125,8 +125,13 @@ __device__ __forceinline__ void quad_pair(Real dx, Real dy, Real dz, Real m,
 // two pairs, as in the scalar forms.  The 0 and 1 operands come from the
 // kernel's parameters (ForceParams::zero2, one2): as compile-time constants
 // the compiler would fold the FMA back into the half-rate add or multiply.
+// Position of the padding entry of the entry-paired form (an odd list tail):
+// far enough that rhat^-5 underflows to zero, near enough that rhat^2 stays
+// finite in FP32.
+constexpr float kPadFar = 1.0e15f;
+
 struct Pair2 {
-  float2 zero, one;
+  float2 zero, one, mone;
   __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) const { return __ffma2_rn(a, b, c); }
   __device__ __forceinline__ float2 mul2(float2 a, float2 b) const { return __ffma2_rn(a, b, zero); }
   __device__ __forceinline__ float2 add2(float2 a, float2 b) const { return __ffma2_rn(a, one, b); }
@@ -185,6 +190,65 @@ __device__ __forceinline__ void quad_pair2(const Pair2 &P, float2 jx, float2 jy,
   az = P.fma2(ri5, qz, az);
 }
 
+// Entry-paired FP32 forms: two list entries per float2 (the halves of every
+// j-value are two different entries, read as they were staged), each sink's
+// values broadcast to both halves once per group.  The offset is taken the
+// other way round, d = x_i - x_j = -r, and the staged mass is negated,
+// nm = -m: then Q d = -(Q r), d.Q.d = r.Q.r, and every sign of Eq. 7 folds
+// into an FMA with no negation in the loop.  pot accumulates the physical
+// potential, -(phi_mono + phi_quad), directly.  13 and 33 paired FMAs (and two
+// rsqrt) per two pairs, as in the scalar forms; the -1, 0 and 1 operands are
+// runtime values (see Pair2).
+template <bool GUARD>
+__device__ __forceinline__ void mono_pairE(const Pair2 &P, float2 jx, float2 jy, float2 jz, float2 nm, float2 sx,
+                                           float2 sy, float2 sz, float2 e2, float2 &ax, float2 &ay, float2 &az,
+                                           float2 &pot) {
+  const float2 dx = P.fma2(jx, P.mone, sx), dy = P.fma2(jy, P.mone, sy), dz = P.fma2(jz, P.mone, sz);  // -r
+  const float2 r2 = P.fma2(dx, dx, P.fma2(dy, dy, P.fma2(dz, dz, e2)));
+  float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+  if (GUARD) {
+    ri.x = r2.x > 0.f ? ri.x : 0.f;
+    ri.y = r2.y > 0.f ? ri.y : 0.f;
+  }
+  const float2 npm = P.mul2(nm, ri);             // -phi_mono
+  pot = P.add2(pot, npm);
+  const float2 c = P.mul2(npm, P.mul2(ri, ri));  // -m / rhat^3
+  ax = P.fma2(c, dx, ax);
+  ay = P.fma2(c, dy, ay);
+  az = P.fma2(c, dz, az);
+}
+
+template <bool GUARD>
+__device__ __forceinline__ void quad_pairE(const Pair2 &P, float2 jx, float2 jy, float2 jz, float2 nm, float2 q00,
+                                           float2 q01, float2 q02, float2 q11, float2 q12, float2 q22, float2 sx,
+                                           float2 sy, float2 sz, float2 e2, float2 &ax, float2 &ay, float2 &az,
+                                           float2 &pot) {
+  const float2 dx = P.fma2(jx, P.mone, sx), dy = P.fma2(jy, P.mone, sy), dz = P.fma2(jz, P.mone, sz);  // -r
+  const float2 r2 = P.fma2(dx, dx, P.fma2(dy, dy, P.fma2(dz, dz, e2)));
+  float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+  if (GUARD) {
+    ri.x = r2.x > 0.f ? ri.x : 0.f;
+    ri.y = r2.y > 0.f ? ri.y : 0.f;
+  }
+  const float2 ri2 = P.mul2(ri, ri);
+  const float2 npm = P.mul2(nm, ri);                                       // -phi_mono
+  const float2 qx = P.fma2(q00, dx, P.fma2(q01, dy, P.mul2(q02, dz)));    // -(Q r)_x
+  const float2 qy = P.fma2(q01, dx, P.fma2(q11, dy, P.mul2(q12, dz)));    // -(Q r)_y
+  const float2 qz = P.fma2(q02, dx, P.fma2(q12, dy, P.mul2(q22, dz)));    // -(Q r)_z
+  const float2 rqr = P.fma2(dx, qx, P.fma2(dy, qy, P.mul2(dz, qz)));       // r.Q.r
+  const float2 ri5 = P.mul2(P.mul2(ri2, ri2), ri);
+  const float2 u = P.mul2(rqr, ri5);                                       // 2 phi_quad
+  pot = P.add2(pot, npm);
+  pot = P.fma2(make_float2(-0.5f, -0.5f), u, pot);                         // - phi_quad
+  const float2 c = P.mul2(P.fma2(make_float2(-2.5f, -2.5f), u, npm), ri2); // -(phi_mono + 5 phi_quad)/rhat^2
+  ax = P.fma2(c, dx, ax);
+  ax = P.fma2(ri5, qx, ax);
+  ay = P.fma2(c, dy, ay);
+  ay = P.fma2(ri5, qy, ay);
+  az = P.fma2(c, dz, az);
+  az = P.fma2(ri5, qz, az);
+}
+
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -208,16 +272,22 @@ __device__ __forceinline__ int keep_index(int j, int lim, int32_t *keep, int *ba
   return j;
 }
 
+// Arithmetic forms of the FP32 kernel: scalar, sink-paired (two sinks per
+// float2, j-values broadcast) and entry-paired (two list entries per float2,
+// sink values broadcast).
+enum : int { kScalar = 0, kSinkPaired = 1, kEntryPaired = 2 };
+
 // Launch bounds per variant: the largest block it is launched with and the
 // CTAs per SM the register budget must allow.  Scalar R <= 4: 3 blocks of 256
 // threads leaves 80 registers a thread (72 used at R = 2), which still fits
 // the six 128-thread CTAs that shared memory allows per SM (64 registers
-// measured 2-3 % slower); the paired R = 4 form carries twice the j-entry
-// registers and gets up to 128; R = 8 keeps 8 sinks x 4 sums in registers and
-// is limited to 128 threads; the all-FP64 comparison form gets up to 128.
-template <typename Real, int R, bool PAIRED> struct Bounds {
+// measured 2-3 % slower); the paired R = 4 forms carry twice the registers per
+// sink (or per j-entry) and get up to 128; R = 8 keeps 8 sinks x 4 sums in
+// registers and is limited to 128 threads; the all-FP64 comparison form gets
+// up to 128.
+template <typename Real, int R, int FORM> struct Bounds {
   static constexpr int threads = R >= 8 ? 128 : 256;
-  static constexpr int min_blocks = (R >= 8 || sizeof(Real) == 8 || (PAIRED && R >= 4)) ? 2 : 3;
+  static constexpr int min_blocks = (R >= 8 || sizeof(Real) == 8 || (FORM != kScalar && R >= 4)) ? 2 : 3;
 };
 
 // INPLACE: the lists are read from host memory (checked and kept as they
@@ -225,12 +295,17 @@ template <typename Real, int R, bool PAIRED> struct Bounds {
 // memory (ForceParams::a_host), a[] through shared memory so that a warp
 // writes consecutive words.  A separate instantiation, so that the kernel
 // the graph replays carries none of it.
-template <typename Real, int R, bool QUAD, bool GUARD, bool CENTRED, bool PAIRED, bool INPLACE = false>
-__global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real, R, PAIRED>::min_blocks)
+template <typename Real, int R, bool QUAD, bool GUARD, bool CENTRED, int FORM, bool INPLACE = false>
+__global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R, FORM>::min_blocks)
     force_kernel(const ForceParams p) {
+  constexpr bool PAIRED = FORM == kSinkPaired;
+  constexpr bool EPAIR = FORM == kEntryPaired;
   static_assert(!PAIRED || (sizeof(Real) == 4 && R % 2 == 0), "paired arithmetic: FP32, even R");
-  constexpr int H = R / 2;  // sink pairs per thread (paired form)
-  const Pair2 P2{make_float2(p.zero, p.zero), make_float2(p.one, p.one)};
+  static_assert(!EPAIR || (sizeof(Real) == 4 && CENTRED), "entry-paired arithmetic: FP32 centred");
+  static_assert(!INPLACE || !PAIRED, "in place: scalar or entry-paired form");
+  constexpr int H = R / 2;               // sink pairs per thread (sink-paired form)
+  constexpr int NE = EPAIR ? R : 1;      // broadcast sinks per thread (entry-paired form)
+  const Pair2 P2{make_float2(p.zero, p.zero), make_float2(p.one, p.one), make_float2(-p.one, -p.one)};
   using V4 = typename RT<Real>::v4;
   using V2 = typename RT<Real>::v2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -245,8 +320,11 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
   double *acc64 = reinterpret_cast<double *>(smem_raw);
   V4 *sink_s = reinterpret_cast<V4 *>(smem_raw);
   // Staged tile.  Scalar form: A (dx dy dz m), B (q00 q01 q02 q11), C (q12 q22).
-  // Paired form: every value twice, (dx dx dy dy) (dz dz m m) and the negated
-  // quadrupole (q00 q00 q01 q01) (q02 q02 q11 q11) (q12 q12 q22 q22).
+  // Sink-paired form: every value twice, (dx dx dy dy) (dz dz m m) and the
+  // negated quadrupole (q00 q00 q01 q01) (q02 q02 q11 q11) (q12 q12 q22 q22).
+  // Entry-paired form: entries 2u and 2u+1 side by side in pair u,
+  // (dx dx' dy dy') (dz dz' -m -m') (q00 q00' q01 q01') (q02 q02' q11 q11')
+  // (q12 q12' q22 q22'): 40 bytes per entry, as in the scalar form.
   V4 *tA = reinterpret_cast<V4 *>(acc64 + 4 * R * NT);
   V4 *tB = tA + T;
   V2 *tC = reinterpret_cast<V2 *>(tB + T);
@@ -255,6 +333,11 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
   float4 *tQ0 = tP1 + T;
   float4 *tQ1 = tQ0 + T;
   float4 *tQ2 = tQ1 + T;
+  float4 *tE0 = reinterpret_cast<float4 *>(acc64 + 4 * R * NT);
+  float4 *tE1 = tE0 + T / 2;
+  float4 *tE2 = tE1 + T / 2;
+  float4 *tE3 = tE2 + T / 2;
+  float4 *tE4 = tE3 + T / 2;
 
   for (;;) {
     __syncthreads();  // the previous group is finished with shared memory
@@ -295,17 +378,22 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
       for (int i = tid; i < nch; i += NT) {
         const int64_t si = s0 + sb + i;
         const double *xi = p.sink_x + 3 * si;
-        const double e2 = p.sink_eps2 ? (double)p.sink_eps2[si] : p.eps2_all;
+        // softening: the per-sink array is float already; the global value
+        // was rounded to float on the host (FP32) or is used as given (FP64)
+        Real e2;
+        if constexpr (sizeof(Real) == 4) e2 = p.sink_eps2 ? p.sink_eps2[si] : p.eps2_all_f;
+        else e2 = p.sink_eps2 ? (double)p.sink_eps2[si] : p.eps2_all;
         sink_s[i] = RT<Real>::make4(RT<Real>::cvt(xi[0] - cx), RT<Real>::cvt(xi[1] - cy),
-                                    RT<Real>::cvt(xi[2] - cz), RT<Real>::cvt(e2));
+                                    RT<Real>::cvt(xi[2] - cz), e2);
       }
       __syncthreads();
 
       const int S = (nch + R - 1) / R;  // sink slots
       const int K = NT / S;             // list streams
       // tiles hold a whole number of passes of the K streams, so that no
-      // tile ends in a partly filled pass (only the list's last tile may)
-      const int TK = T >= K ? (T / K) * K : T;
+      // tile ends in a partly filled pass (only the list's last tile may);
+      // in the entry-paired form a stream takes two entries per pass
+      const int TK = EPAIR ? 2 * (T / 2 >= K ? (T / 2 / K) * K : T / 2) : (T >= K ? (T / K) * K : T);
       const int s = tid % S;
       const int k = tid / S;
       const bool active = k < K;
@@ -314,6 +402,7 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
       Real ax[R], ay[R], az[R], pt[R];
       float2 nx2[H > 0 ? H : 1], ny2[H > 0 ? H : 1], nz2[H > 0 ? H : 1], e22[H > 0 ? H : 1];
       float2 ax2[H > 0 ? H : 1], ay2[H > 0 ? H : 1], az2[H > 0 ? H : 1], pt2[H > 0 ? H : 1];
+      float2 bsx[NE], bsy[NE], bsz[NE], bse[NE], bax[NE], bay[NE], baz[NE], bpt[NE];
 #pragma unroll
       for (int r = 0; r < R; r++) {
         const int i = s + S * r;
@@ -329,6 +418,16 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
           nz2[h] = make_float2(-sz[2 * h], -sz[2 * h + 1]);
           e22[h] = make_float2(se[2 * h], se[2 * h + 1]);
           ax2[h] = ay2[h] = az2[h] = pt2[h] = make_float2(0.f, 0.f);
+        }
+      }
+      if constexpr (EPAIR) {
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+          bsx[r] = make_float2(sx[r], sx[r]);
+          bsy[r] = make_float2(sy[r], sy[r]);
+          bsz[r] = make_float2(sz[r], sz[r]);
+          bse[r] = make_float2(se[r], se[r]);
+          bax[r] = bay[r] = baz[r] = bpt[r] = make_float2(0.f, 0.f);
         }
       }
       __syncthreads();  // every thread holds its sinks: sink_s becomes acc64
@@ -350,6 +449,18 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
             a[6 * NT] += (double)az2[h].y;
             a[7 * NT] += (double)pt2[h].y;
             ax2[h] = ay2[h] = az2[h] = pt2[h] = make_float2(0.f, 0.f);
+          }
+        } else if constexpr (EPAIR) {
+          // both halves (even and odd entries) of each sum; the potential
+          // was accumulated with the physical sign
+#pragma unroll
+          for (int r = 0; r < R; r++) {
+            double *a = acc64 + 4 * r * NT + tid;
+            a[0] += (double)bax[r].x + (double)bax[r].y;
+            a[NT] += (double)bay[r].x + (double)bay[r].y;
+            a[2 * NT] += (double)baz[r].x + (double)baz[r].y;
+            a[3 * NT] -= (double)bpt[r].x + (double)bpt[r].y;
+            bax[r] = bay[r] = baz[r] = bpt[r] = make_float2(0.f, 0.f);
           }
         } else {
 #pragma unroll
@@ -373,18 +484,23 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
       int pf0 = -1, pf1 = -1, pf2 = -1, pf3 = -1;
       auto prefetch = [&](const int32_t *idx, int64_t b, int64_t end) {
         const int c = (int)min((int64_t)TK, end - b);
-        pf0 = tid < c ? __ldg(idx + b + tid) : -1;
-        pf1 = tid + NT < c ? __ldg(idx + b + tid + NT) : -1;
+        // the entry-paired form stages entries 2 tid and 2 tid + 1 first
+        // (then 2 tid + 2 NT and 2 tid + 2 NT + 1)
+        const int e0 = EPAIR ? 2 * tid : tid, e1 = EPAIR ? 2 * tid + 1 : tid + NT;
+        pf0 = e0 < c ? __ldg(idx + b + e0) : -1;
+        pf1 = e1 < c ? __ldg(idx + b + e1) : -1;
         if constexpr (INPLACE) {
-          pf2 = tid + 2 * NT < c ? __ldg(idx + b + tid + 2 * NT) : -1;
-          pf3 = tid + 3 * NT < c ? __ldg(idx + b + tid + 3 * NT) : -1;
+          const int e2 = EPAIR ? 2 * tid + 2 * NT : tid + 2 * NT, e3 = EPAIR ? 2 * tid + 2 * NT + 1 : tid + 3 * NT;
+          pf2 = e2 < c ? __ldg(idx + b + e2) : -1;
+          pf3 = e3 < c ? __ldg(idx + b + e3) : -1;
         }
       };
-      // in-place form: index of entry t of the tile at base, from the
+      // in-place forms: index of entry t of the tile at base, from the
       // registers loaded ahead where there is one
       auto ahead = [&](const int32_t *idx, int64_t base, int t) -> int {
-        const int u = t - tid;
-        return u == 0 ? pf0 : u == NT ? pf1 : u == 2 * NT ? pf2 : u == 3 * NT ? pf3 : idx[base + t];
+        const int u = t - (EPAIR ? 2 * tid : tid);
+        const int o1 = EPAIR ? 1 : NT, o2 = 2 * NT, o3 = EPAIR ? 2 * NT + 1 : 3 * NT;
+        return u == 0 ? pf0 : u == o1 ? pf1 : u == o2 ? pf2 : u == o3 ? pf3 : idx[base + t];
       };
       if (p0 < p1) prefetch(p.plist_idx, p0, p1);
       else if (c0 < c1) prefetch(p.clist_idx, c0, c1);
@@ -404,7 +520,38 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
             tA[t] = RT<Real>::make4(dx, dy, dz, m);
           }
         };
-        if constexpr (QG_GATHER2 != 0) {
+        if constexpr (EPAIR) {
+          // pair u = entries 2u and 2u + 1, both gathers in flight; an odd
+          // last entry is paired with a massless entry far away (it adds
+          // exactly zero: every term carries its mass, or rhat^-5 which
+          // underflows to zero there)
+          const int npair = (cnt + 1) >> 1;
+          for (int u = tid; u < npair; u += NT) {
+            const int t0 = 2 * u, t1 = t0 + 1;
+            const bool first = u == tid;
+            int j0, j1;
+            if constexpr (INPLACE) {
+              j0 = keep_index(ahead(p.plist_idx, base, t0), p.n_src, p.plist_keep + base + t0, p.bad);
+              j1 = t1 < cnt ? keep_index(ahead(p.plist_idx, base, t1), p.n_src, p.plist_keep + base + t1, p.bad) : j0;
+            } else {
+              j0 = first ? pf0 : p.plist_idx[base + t0];
+              j1 = t1 < cnt ? (first ? pf1 : p.plist_idx[base + t1]) : j0;
+            }
+            const PosMass v0 = p.src[j0];
+            const PosMass v1 = p.src[j1];
+            const float dx0 = cvt_off<float, 0>(v0.x - cx), dy0 = cvt_off<float, 1>(v0.y - cy),
+                        dz0 = cvt_off<float, 2>(v0.z - cz);
+            float dx1 = kPadFar, dy1 = kPadFar, dz1 = kPadFar, m1 = 0.f;
+            if (t1 < cnt) {
+              dx1 = cvt_off<float, 0>(v1.x - cx);
+              dy1 = cvt_off<float, 1>(v1.y - cy);
+              dz1 = cvt_off<float, 2>(v1.z - cz);
+              m1 = v1.m;
+            }
+            tE0[u] = make_float4(dx0, dx1, dy0, dy1);
+            tE1[u] = make_float4(dz0, dz1, -v0.m, -m1);
+          }
+        } else if constexpr (QG_GATHER2 != 0) {
           for (int t = tid; t < cnt; t += 2 * NT) {
             const int t1 = t + NT;
             [[maybe_unused]] const bool first = t == tid;
@@ -446,6 +593,19 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
                                   make_float2(P1.z, P1.w), nx2[h], ny2[h], nz2[h], e22[h], ax2[h], ay2[h],
                                   az2[h], pt2[h]);
             }
+            nproc += (cnt - k + K - 1) / K;
+          } else if constexpr (EPAIR) {
+            const int npair = (cnt + 1) >> 1;
+#pragma unroll 2
+            for (int uu = k; uu < npair; uu += K) {
+              const float4 E0 = tE0[uu], E1 = tE1[uu];
+#pragma unroll
+              for (int r = 0; r < R; r++)
+                mono_pairE<GUARD>(P2, make_float2(E0.x, E0.y), make_float2(E0.z, E0.w), make_float2(E1.x, E1.y),
+                                  make_float2(E1.z, E1.w), bsx[r], bsy[r], bsz[r], bse[r], bax[r], bay[r],
+                                  baz[r], bpt[r]);
+            }
+            nproc += 2 * ((npair - k + K - 1) / K);
           } else {
 #pragma unroll 2
             for (int jj = k; jj < cnt; jj += K) {
@@ -455,8 +615,8 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
                 mono_pair<Real, GUARD>(A.x - sx[r], A.y - sy[r], A.z - sz[r], A.w, se[r],
                                        ax[r], ay[r], az[r], pt[r]);
             }
+            nproc += (cnt - k + K - 1) / K;
           }
-          nproc += (cnt - k + K - 1) / K;
           if (nproc >= p.flush_j) fold();
         }
       }
@@ -492,7 +652,50 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
           }
         };
         const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        if constexpr (QG_GATHER2 != 0) {
+        if constexpr (EPAIR) {
+          // as for the particles: pair u = entries 2u and 2u + 1, an odd last
+          // entry paired with a massless, quadrupole-free entry far away
+          const int npair = (cnt + 1) >> 1;
+          for (int u = tid; u < npair; u += NT) {
+            const int t0 = 2 * u, t1 = t0 + 1;
+            const bool first = u == tid;
+            int j0, j1;
+            if constexpr (INPLACE) {
+              j0 = keep_index(ahead(p.clist_idx, base, t0), p.n_cell, p.clist_keep + base + t0, p.bad);
+              j1 = t1 < cnt ? keep_index(ahead(p.clist_idx, base, t1), p.n_cell, p.clist_keep + base + t1, p.bad) : j0;
+            } else {
+              j0 = first ? pf0 : p.clist_idx[base + t0];
+              j1 = t1 < cnt ? (first ? pf1 : p.clist_idx[base + t1]) : j0;
+            }
+            const PosMass v0 = p.cell_pm[j0];
+            const PosMass v1 = p.cell_pm[j1];
+            float4 a0 = zero4, b0 = zero4, a1 = zero4, b1 = zero4;
+            if (QUAD) {
+              a0 = p.cell_q[2 * j0];
+              b0 = p.cell_q[2 * j0 + 1];
+              a1 = p.cell_q[2 * j1];
+              b1 = p.cell_q[2 * j1 + 1];
+            }
+            const float dx0 = cvt_off<float, 0>(v0.x - cx), dy0 = cvt_off<float, 1>(v0.y - cy),
+                        dz0 = cvt_off<float, 2>(v0.z - cz);
+            float dx1 = kPadFar, dy1 = kPadFar, dz1 = kPadFar, m1 = 0.f;
+            if (t1 < cnt) {
+              dx1 = cvt_off<float, 0>(v1.x - cx);
+              dy1 = cvt_off<float, 1>(v1.y - cy);
+              dz1 = cvt_off<float, 2>(v1.z - cz);
+              m1 = v1.m;
+            } else {
+              a1 = b1 = zero4;
+            }
+            tE0[u] = make_float4(dx0, dx1, dy0, dy1);
+            tE1[u] = make_float4(dz0, dz1, -v0.m, -m1);
+            if (QUAD) {
+              tE2[u] = make_float4(a0.x, a1.x, a0.y, a1.y);
+              tE3[u] = make_float4(a0.z, a1.z, a0.w, a1.w);
+              tE4[u] = make_float4(b0.x, b1.x, b0.y, b1.y);
+            }
+          }
+        } else if constexpr (QG_GATHER2 != 0) {
           for (int t = tid; t < cnt; t += 2 * NT) {
             const int t1 = t + NT;
             [[maybe_unused]] const bool first = t == tid;
@@ -551,6 +754,31 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
                                     az2[h], pt2[h]);
               }
             }
+          } else if constexpr (EPAIR) {
+            const int npair = (cnt + 1) >> 1;
+            if (QUAD) {
+#pragma unroll 2
+              for (int uu = k; uu < npair; uu += K) {
+                const float4 E0 = tE0[uu], E1 = tE1[uu], E2 = tE2[uu], E3 = tE3[uu], E4 = tE4[uu];
+#pragma unroll
+                for (int r = 0; r < R; r++)
+                  quad_pairE<GUARD>(P2, make_float2(E0.x, E0.y), make_float2(E0.z, E0.w), make_float2(E1.x, E1.y),
+                                    make_float2(E1.z, E1.w), make_float2(E2.x, E2.y), make_float2(E2.z, E2.w),
+                                    make_float2(E3.x, E3.y), make_float2(E3.z, E3.w), make_float2(E4.x, E4.y),
+                                    make_float2(E4.z, E4.w), bsx[r], bsy[r], bsz[r], bse[r], bax[r], bay[r],
+                                    baz[r], bpt[r]);
+              }
+            } else {
+#pragma unroll 2
+              for (int uu = k; uu < npair; uu += K) {
+                const float4 E0 = tE0[uu], E1 = tE1[uu];
+#pragma unroll
+                for (int r = 0; r < R; r++)
+                  mono_pairE<GUARD>(P2, make_float2(E0.x, E0.y), make_float2(E0.z, E0.w), make_float2(E1.x, E1.y),
+                                    make_float2(E1.z, E1.w), bsx[r], bsy[r], bsz[r], bse[r], bax[r], bay[r],
+                                    baz[r], bpt[r]);
+              }
+            }
           } else if (QUAD) {
 #pragma unroll 2
             for (int jj = k; jj < cnt; jj += K) {
@@ -573,7 +801,8 @@ __global__ void __launch_bounds__(Bounds<Real, R, PAIRED>::threads, Bounds<Real,
                                        ax[r], ay[r], az[r], pt[r]);
             }
           }
-          nproc += (cnt - k + K - 1) / K;
+          // list entries this thread has added since its last fold (two per pass when entry-paired)
+          nproc += EPAIR ? 2 * ((((cnt + 1) >> 1) - k + K - 1) / K) : (cnt - k + K - 1) / K;
           if (nproc >= p.flush_j) fold();
         }
       }

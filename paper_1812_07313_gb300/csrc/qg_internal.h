@@ -15,14 +15,24 @@ struct __align__(32) PosMass {
   float pad;
 };
 
+// Largest magnitude of a position coordinate any entry point accepts (and of
+// a mass, a quadrupole component or a softening in the allocation-free
+// entry point): every value the kernels round with f64_to_f32_rn below,
+// position offsets x_j - c_g included, then stays below 2^101, inside its
+// domain.  Larger or non-finite inputs are rejected with QG_ERR_ARG.
+constexpr double kMaxInput = 0x1p100;
+
 // Round a double to the nearest float, ties to even, with integer
 // operations only (IEEE 754 binary64 -> binary32: keep the sign, rebias the
 // exponent from 1023 to 127, keep the top 23 of the 52 fraction bits and
-// round on the 29 dropped ones).  Magnitudes below the smallest normal float
-// give a signed zero (the FP32 kernels flush denormals anyway); callers only
-// pass position offsets, far below the largest float.  On this GPU the
-// hardware double->float conversion issues on the narrow FP64 pipe, which
-// this keeps free for the FP64 centring itself.
+// round on the 29 dropped ones).  Domain: finite |x| < 2^128 (a value that
+// rounds up to 2^128 gives infinity, as it should); magnitudes below the
+// smallest normal float give a signed zero (the FP32 kernels flush denormals
+// anyway).  Outside the domain (|x| >= 2^128, infinities, NaN) the exponent
+// wraps and the result is meaningless: callers pass only position offsets,
+// masses and quadrupole components of inputs checked against kMaxInput.  On
+// this GPU the hardware double->float conversion issues on the narrow FP64
+// pipe, which this keeps free for the FP64 centring itself.
 __host__ __device__ inline float f64_to_f32_rn(double x) {
 #ifdef __CUDA_ARCH__
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -61,6 +71,7 @@ struct ForceParams {
   const double *sink_x;
   const float *sink_eps2;
   double eps2_all;
+  float eps2_all_f;  // eps2_all rounded to float on the host (FP32 kernels)
   const int64_t *group_off;
   const double *gcentre;  // [G][3] centre of each group's bounding box (centred kernels)
   const PosMass *src;
@@ -108,7 +119,8 @@ inline size_t force_smem_bytes(bool fp64, bool paired, int R, int nthreads, int 
 // Returns nullptr for an unsupported combination.
 const void *force_kernel_f32(int R, bool quad, bool guard, bool centred);
 const void *force_kernel_f32x2(int R, bool quad, bool guard);
+const void *force_kernel_f32ep(int R, bool quad, bool guard);  // entry-paired FP32 centred
 const void *force_kernel_f64(int R, bool quad, bool guard);
-const void *force_kernel_inplace(int R, bool quad, bool guard);  // FP32 centred, scalar
+const void *force_kernel_inplace(int R, bool quad, bool guard, bool epaired);  // FP32 centred
 
 }  // namespace qg

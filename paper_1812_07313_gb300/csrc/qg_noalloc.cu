@@ -18,7 +18,9 @@
 // corrupt each other's queue.  The first call on a device looks the array's
 // device address up (cudaGetSymbolAddress, with that device current) and
 // caches it together with the kernels' occupancy; make that first call
-// before any stream capture.
+// before any stream capture.  Every call also waits on the host for its
+// argument check: it copies the check's flags back and synchronises the
+// caller's stream before it launches the step.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -59,7 +61,7 @@ std::mutex g_setup_mutex;
 struct Args {
   const double *sink_x;
   const float *sink_eps2;
-  double eps2_all;
+  float eps2_all;  // rounded to float on the host
   const int64_t *group_off;
   const double *src_x, *src_m;
   const int64_t *plist_off;
@@ -73,34 +75,65 @@ struct Args {
   double *a, *phi;
 };
 
-// Offsets and list indices checked before any force kernel reads them.
-// Bit 1: group offsets, 2: particle-list offsets, 4: cell-list offsets,
-// 8: a particle index outside [0, ns), 16: a cell index outside [0, nc).
+// |v| <= kMaxInput and finite (false for NaN)
+__device__ __forceinline__ bool in_range(double v) { return fabs(v) <= qg::kMaxInput; }
+
+// The inputs checked before any force kernel reads them.  Bits of *flags:
+// 1 group offsets (not starting at 0, decreasing, not ending at n, or a group
+// of more than INT32_MAX sinks), 2 particle-list offsets, 4 cell-list
+// offsets, 8 a particle index outside [0, ns), 16 a cell index outside
+// [0, nc), 32 an input value that is not finite or exceeds kMaxInput in
+// magnitude (positions, masses, quadrupole components, per-sink eps^2) or a
+// negative eps^2; kGuardBit: a per-sink eps^2 below the smallest normal
+// float (the kernel that skips rhat^2 == 0 pairs is needed).
+constexpr int kGuardBit = 64;
 __global__ void check_kernel(int64_t G, int64_t n, const int64_t *goff, const int64_t *poff, int64_t np_list,
                              const int64_t *coff, int64_t nc_list, int64_t ns, const int32_t *pidx, int64_t nc,
-                             const int32_t *cidx, int *flags) {
+                             const int32_t *cidx, const double *sink_x, const float *sink_eps2,
+                             const double *src_x, const double *src_m, const double *cell_com,
+                             const double *cell_m, const double *cell_q, int *flags) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int f = 0;
   for (int64_t g = t0; g <= G; g += stride) {
     if (g == 0) {
-      if (goff[0] != 0) atomicOr(flags, 1);
-      if (poff[0] != 0) atomicOr(flags, 2);
-      if (coff[0] != 0) atomicOr(flags, 4);
+      if (goff[0] != 0) f |= 1;
+      if (poff[0] != 0) f |= 2;
+      if (coff[0] != 0) f |= 4;
     }
     if (g == G) {
-      if (goff[G] != n) atomicOr(flags, 1);
-      if (poff[G] != np_list) atomicOr(flags, 2);
-      if (coff[G] != nc_list) atomicOr(flags, 4);
+      if (goff[G] != n) f |= 1;
+      if (poff[G] != np_list) f |= 2;
+      if (coff[G] != nc_list) f |= 4;
     } else {
-      if (goff[g + 1] < goff[g]) atomicOr(flags, 1);
-      if (poff[g + 1] < poff[g]) atomicOr(flags, 2);
-      if (coff[g + 1] < coff[g]) atomicOr(flags, 4);
+      if (goff[g + 1] < goff[g] || goff[g + 1] - goff[g] > (int64_t)INT32_MAX) f |= 1;
+      if (poff[g + 1] < poff[g]) f |= 2;
+      if (coff[g + 1] < coff[g]) f |= 4;
     }
   }
   for (int64_t i = t0; i < np_list; i += stride)
-    if (pidx[i] < 0 || (int64_t)pidx[i] >= ns) atomicOr(flags, 8);
+    if (pidx[i] < 0 || (int64_t)pidx[i] >= ns) f |= 8;
   for (int64_t i = t0; i < nc_list; i += stride)
-    if (cidx[i] < 0 || (int64_t)cidx[i] >= nc) atomicOr(flags, 16);
+    if (cidx[i] < 0 || (int64_t)cidx[i] >= nc) f |= 16;
+  for (int64_t i = t0; i < 3 * n; i += stride)
+    if (!in_range(sink_x[i])) f |= 32;
+  if (sink_eps2)
+    for (int64_t i = t0; i < n; i += stride) {
+      const float e = sink_eps2[i];
+      if (!(e >= 0.f && (double)e <= qg::kMaxInput)) f |= 32;
+      else if (e < 0x1p-126f) f |= kGuardBit;
+    }
+  for (int64_t i = t0; i < 3 * ns; i += stride)
+    if (!in_range(src_x[i])) f |= 32;
+  for (int64_t i = t0; i < ns; i += stride)
+    if (!in_range(src_m[i])) f |= 32;
+  for (int64_t i = t0; i < 3 * nc; i += stride)
+    if (!in_range(cell_com[i])) f |= 32;
+  for (int64_t i = t0; i < nc; i += stride)
+    if (!in_range(cell_m[i])) f |= 32;
+  for (int64_t i = t0; i < 6 * nc; i += stride)
+    if (!in_range(cell_q[i])) f |= 32;
+  if (f) atomicOr(flags, f);
 }
 
 // The group-force kernel of qg_force.cuh (FP32 pairwise arithmetic, FP64
@@ -168,9 +201,9 @@ __global__ void __launch_bounds__(kThreads) noalloc_force_kernel(const Args p) {
       for (int i = tid; i < nch; i += NT) {
         const int64_t si = s0 + sb + i;
         const double *xi = p.sink_x + 3 * si;
-        const double e2 = p.sink_eps2 ? (double)p.sink_eps2[si] : p.eps2_all;
+        const float e2 = p.sink_eps2 ? p.sink_eps2[si] : p.eps2_all;
         sink_s[i] = make_float4(qg::f64_to_f32_rn(xi[0] - cx), qg::f64_to_f32_rn(xi[1] - cy),
-                                qg::f64_to_f32_rn(xi[2] - cz), qg::f64_to_f32_rn(e2));
+                                qg::f64_to_f32_rn(xi[2] - cz), e2);
       }
       __syncthreads();
       const int S = (nch + kR - 1) / kR;
@@ -332,25 +365,28 @@ qg_status run(int device, int64_t n, const double *sink_x, const float *sink_eps
   int *counters = reinterpret_cast<int *>(d->scratch + kQueueBytes + kClassBytes);
   int *hist = counters, *cursor = counters + qg::kBuckets, *head = cursor + qg::kBuckets, *flags = head + 1;
   if (cudaMemsetAsync(counters, 0, kCounterInts * sizeof(int), s) != cudaSuccess) return QG_ERR_CUDA;
-  check_kernel<<<grid_for(G + 1 + n_plist + n_clist, 256), 256, 0, s>>>(G, n, group_off, plist_off, n_plist,
-                                                                         clist_off, n_clist, ns, plist_idx, nc,
-                                                                         clist_idx, flags);
+  const int64_t work = G + 1 + n_plist + n_clist + 4 * n + 4 * ns + 10 * nc;
+  check_kernel<<<grid_for(work, 256), 256, 0, s>>>(G, n, group_off, plist_off, n_plist, clist_off, n_clist, ns,
+                                                   plist_idx, nc, clist_idx, sink_x, sink_eps2, src_x, src_m,
+                                                   cell_com, cell_m, cell_q, flags);
   int h_flags = 0;
   if (cudaGetLastError() != cudaSuccess ||
       cudaMemcpyAsync(&h_flags, flags, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return QG_ERR_CUDA;
-  if (h_flags) return QG_ERR_ARG;
+  if (h_flags & ~kGuardBit) return QG_ERR_ARG;
   if (G == 0) return QG_OK;
   const bool quad = expansion == QG_QUAD;
   const double cell_ops = quad ? 33.0 : 13.0;
   qg::queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, group_off, plist_off, clist_off, cell_ops, cls, hist);
+  if (cudaGetLastError() != cudaSuccess) return QG_ERR_CUDA;
   qg::queue_scatter_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, cls, hist, cursor, queue);
-  Args p{sink_x, sink_eps2, eps2_all, group_off, src_x, src_m, plist_off, plist_idx,
+  if (cudaGetLastError() != cudaSuccess) return QG_ERR_CUDA;
+  Args p{sink_x, sink_eps2, (float)eps2_all, group_off, src_x, src_m, plist_off, plist_idx,
          cell_com, cell_m, cell_q, clist_off, clist_idx, queue, (int32_t)G, head, a, phi};
-  // zero softening anywhere (or per-sink values it cannot inspect) needs the
-  // kernel that skips coincident pairs
-  const bool guard = sink_eps2 != nullptr || !(eps2_all > 0.0);
+  // a softening that the FP32 arithmetic flushes to zero (below the smallest
+  // normal float) needs the kernel that skips coincident pairs
+  const bool guard = (h_flags & kGuardBit) != 0 || (sink_eps2 == nullptr && !(eps2_all >= 0x1p-126));
   const int64_t full = (int64_t)d->per_sm[quad][guard] * d->sms;
   const int grid = (int)(full < G ? full : G);
   void *args[] = {&p};
@@ -370,7 +406,7 @@ extern "C" qg_status qg_forces_noalloc(int device, int64_t n, const double *sink
                                        int expansion, double *a, double *phi, void *cuda_stream) {
   if (ngroups > kMaxGroups) return QG_ERR_SIZE;
   if (n < 0 || ngroups < 0 || ns < 0 || nc < 0 || n_plist < 0 || n_clist < 0 || ns >= INT32_MAX ||
-      nc >= INT32_MAX || !(eps2_all >= 0.0))
+      nc >= INT32_MAX || !(eps2_all >= 0.0 && eps2_all <= qg::kMaxInput))
     return QG_ERR_ARG;
   if (expansion != QG_QUAD && expansion != QG_MONO) return QG_ERR_ARG;
   if (!group_off || !plist_off || !clist_off) return QG_ERR_ARG;

@@ -21,7 +21,7 @@ QG_ERR_SIZE = -6
 QG_NOALLOC_MAX_GROUPS = 1 << 20
 QG_FP32_CENTRED, QG_FP32_RAW, QG_FP64 = 0, 1, 2
 QG_QUAD, QG_MONO = 0, 1
-QG_ARITH_DEFAULT, QG_ARITH_SCALAR, QG_ARITH_PAIRED = 0, 1, 2
+QG_ARITH_DEFAULT, QG_ARITH_SCALAR, QG_ARITH_PAIRED, QG_ARITH_ENTRY_PAIRED = 0, 1, 2, 3
 
 _STATUS = {0: "QG_OK", -1: "QG_ERR_ARG", -2: "QG_ERR_CUDA", -3: "QG_ERR_NOMEM", -4: "QG_ERR_STATE",
            -5: "QG_ERR_TIMEOUT", -6: "QG_ERR_SIZE"}

@@ -5,7 +5,9 @@ Larger groups open more cells (more pairs per step) but amortise each staged
 list entry over more sinks.  ``tune_group_size`` builds the tree and lists
 for each candidate n_crit, lets ``qg_autotune`` pick the launch shape for
 each, times the force step on the GPU, and returns the candidate with the
-shortest step.
+shortest step.  ``tune_group_size`` builds the trees on the host,
+``tune_group_size_gpu`` on the GPU (the same groups and lists, in
+milliseconds instead of seconds).
 """
 from __future__ import annotations
 
@@ -77,3 +79,34 @@ def tune_group_size(x, m, sys_off, leaf_max, theta, candidates, eps2_all=0.0, ep
         if best is None or r.step_ms < best.step_ms:
             best, best_tl = r, (tr, L)
     return best, results, best_tl
+
+
+def tune_group_size_gpu(gtree_obj, x, m, sys_off, leaf_max, theta, candidates, eps2_all=0.0, device=0,
+                        options=None, steps=3, stream=None):
+    """As tune_group_size, with each candidate's tree, groups and lists built
+    on the GPU (``gtree.GpuTree``; x, m are CUDA tensors, one softening for
+    every sink).  Leaves the tree of the best candidate built and walked in
+    ``gtree_obj``.  Returns (best GroupSizeResult, all results)."""
+    results, best = [], None
+    for n_crit in candidates:
+        gtree_obj.build(x, m, sys_off, leaf_max, int(n_crit), stream)
+        gtree_obj.walk(theta, stream)
+        build_ms, walk_ms = gtree_obj.timing()
+        ctx = qgrav.Context(device, options)
+        try:
+            gtree_obj.attach(ctx, eps2_all, stream)
+            ctx.qg_autotune(stream, reps=2)
+            step_ms, force_ms = _time_step(ctx, steps, stream)
+            st = ctx.qg_get_stats()
+        finally:
+            ctx.close()
+        r = GroupSizeResult(int(n_crit), int(gtree_obj.sizes()["ngroups"]), int(st["i_pp"]), int(st["i_pc"]), step_ms,
+                            force_ms, {k: st[k] for k in ("sinks_per_thread", "warps_per_group", "tile_j", "paired")},
+                            1e-3 * (build_ms + walk_ms))
+        results.append(r)
+        if best is None or r.step_ms < best.step_ms:
+            best = r
+    if best is not None and best.n_crit != results[-1].n_crit:
+        gtree_obj.build(x, m, sys_off, leaf_max, best.n_crit, stream)
+        gtree_obj.walk(theta, stream)
+    return best, results
