@@ -76,6 +76,12 @@ def parse():
                     help="other workloads measured into the line's 'configs' record (comma separated, or 'none'); "
                          "default: %s for the default workload without --launch, else none" % ",".join(CONFIGS))
     ap.add_argument("--config-steps", type=int, default=20, help="timed steps of each 'configs' workload")
+    ap.add_argument("--multi", choices=["shard", "replicas"], default="shard",
+                    help="N > 1: shard = every rank evaluates its cost-balanced range of the workload's groups "
+                         "(sources and cells replicated, no collective; total work fixed); replicas = every rank "
+                         "evaluates the whole workload")
+    ap.add_argument("--no-split-compare", action="store_true",
+                    help="skip timing the step with long lists split into work items against the unsplit step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--batching-compare", action="store_true",
@@ -88,8 +94,8 @@ def parse():
                     help="skip timing the tree build, moments, groups and walk on the GPU (whole step on the device)")
     ap.add_argument("--gpu-tree", action="store_true", help=argparse.SUPPRESS)  # the default; kept for old commands
     ap.add_argument("--launch", default=None,
-                    help="R,W,T[,x1|x2|xe]: fixed sinks/thread, warps/CTA, tile (and scalar, sink-paired or "
-                         "entry-paired FP32) instead of the autotuner (profiling)")
+                    help="R,W,T[,x1|x2|xe[,F]]: fixed sinks/thread, warps/CTA, tile (and scalar, sink-paired or "
+                         "entry-paired FP32, and entries between FP64 folds) instead of the autotuner (profiling)")
     return ap.parse_args()
 
 
@@ -432,6 +438,36 @@ def equal_error(torch, qgrav, gw, thetas, flush, stream, steps, n_sample=4096):
                       "then 6 bisection steps; GPU-built trees and lists", "rows": rows}
 
 
+def split_compare(torch, qgrav, ctx, chosen, stream, flush, steps=10):
+    """The step at the chosen launch shape with long lists split into work
+    items automatically (qg_options.split_j = -1) against the unsplit step,
+    with the largest work item's share of one CTA's average load (work =
+    the queue's cost measure; a share near 1 or above leaves the end of the
+    persistent launch to a few CTAs)."""
+    import dataclasses
+    st = ctx.qg_get_stats()
+    res = {}
+    for name, sj in (("auto", -1), ("off", 0)):  # unsplit last: ctx keeps that step's results
+        ctx.set_options(dataclasses.replace(chosen, split_j=sj))
+        ms, fms, _ = time_context(torch, ctx, stream, flush, steps, 3, autotune=False)
+        s = ctx.qg_get_stats()
+        res[name] = {"ms_per_step": float(ms.mean()), "force_ms": float(fms.mean()), "items": int(s["n_items"]),
+                     "split_groups": int(s["n_split"])}
+    ctx.set_options(chosen)
+    res["auto_over_off_time"] = res["auto"]["ms_per_step"] / res["off"]["ms_per_step"]
+    res["grid"] = int(st["grid"])
+    return res
+
+
+def item_share(tr, L, grid, cell_ops=33.0):
+    """Largest group's work (the queue's cost measure) over one CTA's average
+    share of the step's work."""
+    ni = np.diff(tr.group_off).astype(np.float64)
+    npl, ncl = np.diff(L.plist_off).astype(np.float64), np.diff(L.clist_off).astype(np.float64)
+    cost = ni * (13.0 * npl + cell_ops * ncl) + 64.0 * (npl + ncl) + 256.0
+    return float(cost.max() / (cost.sum() / max(grid, 1)))
+
+
 def config_record(torch, qgrav, name, steps, warmup, stream, flush, n_sm, local_rank=0, group_sizes=None,
                   ee_thetas=(), batching=False):
     """One workload measured as the main line is (GPU-built tree and lists,
@@ -509,7 +545,17 @@ def run_ours(args, rank, world, local_rank):
     props = torch.cuda.get_device_properties(dev)
     n_sm = props.multi_processor_count
     ctx = qgrav.Context(dev)
-    load_ctx(ctx, tr, L, eps2_all, eps2)
+    sharded = world > 1 and args.multi == "shard"
+    if sharded:
+        # this rank's cost-balanced range of groups; sources and cells replicated
+        from paper_1812_07313_gb300 import shard
+        sh = shard.shards(tr.group_off, L.plist_off, L.plist_idx, L.clist_off, L.clist_idx, world)[rank]
+        ctx.qg_set_sinks(tr.x[sh.s0:sh.s1], sh.group_off, eps2_all,
+                         None if eps2 is None else eps2[sh.s0:sh.s1])
+        ctx.qg_set_sources(tr.x, tr.m, sh.plist_off, sh.plist_idx)
+        ctx.qg_set_cells(tr.cell_com, tr.cell_m, tr.cell_q, sh.clist_off, sh.clist_idx)
+    else:
+        load_ctx(ctx, tr, L, eps2_all, eps2)
     st = ctx.qg_get_stats()
     i_pp, i_pc = int(st["i_pp"]), int(st["i_pc"])
     inter = i_pp + i_pc
@@ -521,7 +567,9 @@ def run_ours(args, rank, world, local_rank):
         R, W, T = (int(v) for v in parts[:3])
         arith = {"x1": qgrav.QG_ARITH_SCALAR, "x2": qgrav.QG_ARITH_PAIRED,
                  "xe": qgrav.QG_ARITH_ENTRY_PAIRED}[parts[3]] if len(parts) > 3 else 0
-        ctx.set_options(qgrav.Options(sinks_per_thread=R, warps_per_group=W, tile_j=T, arith=arith))
+        flush_j = int(parts[4]) if len(parts) > 4 else 0
+        ctx.set_options(qgrav.Options(sinks_per_thread=R, warps_per_group=W, tile_j=T, arith=arith,
+                                      flush_j=flush_j))
     else:
         ctx.qg_autotune(stream.cuda_stream, reps=3)
     t_tune = time.perf_counter() - t_tune
@@ -551,7 +599,7 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     clocks = sampler.stop()
     total_ms, value = aggregate_ranks(float(step_ms.sum()), args.steps, inter, world,
-                                      dist if world > 1 else None, "cuda")
+                                      dist if world > 1 else None, "cuda", summed=sharded)
 
     # roofline of the force kernel: FP32 issue bound (lane instructions, FMA = 1)
     roofline = roofline_of(i_pp, i_pc, float(force_ms.mean()), clocks, n_sm, st,
@@ -559,26 +607,29 @@ def run_ours(args, rank, world, local_rank):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "%s: %s" % (args.workload, DESCR.get(args.workload, "")),
                       "theta": theta, "expansion": "quad", "precision": "fp32, fp64 centring and merges",
                       "interactions": {"i_pp": i_pp, "i_pc": i_pc}, "groups": tr.ngroups,
                       "group_size": group_size, "launch": launch,
                       "l2": "flushed before every timed step (256 MiB device write, outside the step events)",
-                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "parallelism": ("%d cost-balanced shards of the groups, sources and cells replicated, "
+                                      "no collective" % world) if sharded else
+                                     ("%d replicas" % world if world > 1 else "single GPU"),
                       "host_tree_s": host_times},
            "paper_context": PAPER_CONTEXT,
            "roofline": roofline, "gpu_launches": 3 * args.steps, "clocks": clocks,
            "wall_s_timed_loop": t_wall}
 
     gw = None
-    if rank == 0 and eps2 is None and ((not args.no_equal_error) or (args.batching_compare and ps.nsys > 1)):
+    solo = world == 1  # the legs below measure one GPU's step; at N > 1 only the main line and e2e run
+    if solo and eps2 is None and ((not args.no_equal_error) or (args.batching_compare and ps.nsys > 1)):
         gw = GpuWorkload(torch, args.workload, n_crit=tr_n_crit(tr, wl))
-    if rank == 0 and not args.no_equal_error and eps2 is None:
+    if solo and not args.no_equal_error and eps2 is None:
         thetas = [float(v) for v in args.equal_error_thetas.split(",")]
         ee_steps = max(5, args.steps // 2)
         out["equal_error"] = equal_error(torch, qgrav, gw, thetas, flush, stream, ee_steps)
-    if rank == 0 and args.batching_compare and ps.nsys > 1 and gw is not None:
+    if solo and args.batching_compare and ps.nsys > 1 and gw is not None:
         gw.theta = None
         gw.tree.walk(theta)
         gw.theta = theta
@@ -589,13 +640,28 @@ def run_ours(args, rank, world, local_rank):
     chosen = qgrav.Options(sinks_per_thread=launch["sinks_per_thread"], warps_per_group=launch["warps_per_group"],
                            tile_j=launch["tile_j"],
                            arith=ARITH_CODES[launch.get("arith", "scalar f32")])
-    if rank == 0 and not args.no_gpu_tree:
+    if solo and not args.no_split_compare and not args.launch:
+        sc = {args.workload: dict(split_compare(torch, qgrav, ctx, chosen, stream, flush),
+                                  max_item_over_cta_share=item_share(tr, L, launch["grid"]))}
+        if args.workload != "sphere_4k":
+            # a small set: fewer groups than the GPU has CTA slots
+            _, _, tr_s, L_s, e2_s, _, _ = build_case("sphere_4k", None)
+            c_s = qgrav.Context(dev)
+            load_ctx(c_s, tr_s, L_s, e2_s, None)
+            best_s, _ = c_s.qg_autotune(stream.cuda_stream, reps=3)
+            sc["sphere_4k"] = dict(split_compare(torch, qgrav, c_s, best_s, stream, flush),
+                                   max_item_over_cta_share=item_share(tr_s, L_s, c_s.qg_get_stats()["grid"]),
+                                   groups=int(tr_s.ngroups))
+            c_s.close()
+        out["split"] = sc
+    if solo and not args.no_gpu_tree:
         out["gpu_tree"] = gpu_tree_step(torch, qgrav, ps, wl, tr, L, eps2_all, eps2, stream, chosen)
-    if rank == 0 and args.precision_compare:
+    if solo and args.precision_compare:
         out["precision"] = precision_compare(torch, qgrav, ctx, tr, L, eps2_all, eps2, stream, flush)
 
     # end to end through the C-ABI with host buffers (pinned), every step
-    out["e2e"] = e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world, chosen)
+    out["e2e"] = e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world, chosen,
+                     shard_part=sh if sharded else None, dist=dist if world > 1 else None)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         groups, work = oracle_sample(tr, L, eps2_all, eps2, args.cpu_seconds)
@@ -615,7 +681,7 @@ def run_ours(args, rank, world, local_rank):
     configs = args.configs
     if configs is None:
         configs = "none" if (args.launch or args.workload != "cube_1m") else ",".join(CONFIGS)
-    if rank == 0 and configs != "none":
+    if solo and configs != "none":
         out["configs"] = {}
         for name in configs.split(","):
             leg = CONFIGS.get(name, {"group_sizes": None, "ee_thetas": (), "batching": False})
@@ -626,15 +692,21 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(out))
 
 
-def aggregate_ranks(total_ms, steps, units_per_step, world, dist=None, device="cpu"):
-    """Whole-job throughput of replicas: every rank processed `units_per_step`
-    per step; the job took the slowest rank's time (max over ranks)."""
+def aggregate_ranks(total_ms, steps, units_per_step, world, dist=None, device="cpu", summed=False):
+    """Whole-job throughput: the job took the slowest rank's time (max over
+    ranks).  Replicas: every rank processed `units_per_step` per step;
+    summed (shards): the ranks' own units per step are added up."""
+    units = world * units_per_step
     if world > 1:
         import torch
         t = torch.tensor([total_ms], dtype=torch.float64, device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    return total_ms, world * steps * units_per_step / (total_ms * 1e-3)
+        if summed:
+            u = torch.tensor([float(units_per_step)], dtype=torch.float64, device=device)
+            dist.all_reduce(u, op=dist.ReduceOp.SUM)
+            units = float(u.item())
+    return total_ms, steps * units / (total_ms * 1e-3)
 
 
 def batching_compare(torch, qgrav, gw, stream, flush, batched_ms, steps=5):
@@ -766,14 +838,16 @@ def precision_compare(torch, qgrav, ctx, tr, L, eps2_all, eps2, stream, flush, s
     return out
 
 
-def e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world, options=None, steps=5):
+def e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world, options=None, steps=5, shard_part=None, dist=None):
     """The step through the C-ABI from pinned host arrays: qg_evaluate_host
     copies the sinks, sources and cells (the positions are one array, sinks
     and sources: copied once); on a coherent CPU-GPU link the force kernel
     then reads the lists from host memory and writes the results there,
     else the lists are copied in chunks while the kernel runs on the groups
     already there and the results copied back.  Either way every input byte
-    crosses to the device and every result byte back, each step."""
+    crosses to the device and every result byte back, each step.  With
+    shard_part (N > 1, sharded) each rank evaluates its range of groups from
+    its own host arrays; the time is the slowest rank's."""
     tdt = {np.dtype("float64"): torch.float64, np.dtype("int64"): torch.int64,
            np.dtype("int32"): torch.int32, np.dtype("float32"): torch.float32}
 
@@ -783,28 +857,49 @@ def e2e(torch, qgrav, tr, L, eps2_all, eps2, inter, world, options=None, steps=5
         v = t.numpy()
         v[...] = a
         return v
-    x, m, goff = pin(tr.x), pin(tr.m), pin(tr.group_off)
-    po, pi, co, ci = pin(L.plist_off), pin(L.plist_idx), pin(L.clist_off), pin(L.clist_idx)
+    x, m = pin(tr.x), pin(tr.m)
     com, cm, cq = pin(tr.cell_com), pin(tr.cell_m), pin(tr.cell_q)
-    e = None if eps2 is None else pin(eps2)
-    a_out, p_out = pin(np.empty((tr.n, 3))), pin(np.empty(tr.n))
-    h2d = sum(v.nbytes for v in (x, goff, m, po, pi, com, cm, cq, co, ci)) + (0 if e is None else e.nbytes)
+    if shard_part is None:
+        xs, goff = x, pin(tr.group_off)
+        po, pi, co, ci = pin(L.plist_off), pin(L.plist_idx), pin(L.clist_off), pin(L.clist_idx)
+        e = None if eps2 is None else pin(eps2)
+    else:
+        sp = shard_part
+        xs, goff = pin(tr.x[sp.s0:sp.s1]), pin(sp.group_off)
+        po, pi, co, ci = pin(sp.plist_off), pin(sp.plist_idx), pin(sp.clist_off), pin(sp.clist_idx)
+        e = None if eps2 is None else pin(eps2[sp.s0:sp.s1])
+    n = len(xs)
+    a_out, p_out = pin(np.empty((n, 3))), pin(np.empty(n))
+    arrays = (x, goff, m, po, pi, com, cm, cq, co, ci) + (() if xs is x else (xs,))
+    h2d = sum(v.nbytes for v in arrays) + (0 if e is None else e.nbytes)
     d2h = a_out.nbytes + p_out.nbytes
     ctx = qgrav.Context(torch.cuda.current_device(), options)
 
     def step():
-        ctx.qg_evaluate_host(x, goff, eps2_all, e, x, m, po, pi, com, cm, cq, co, ci, a_out, p_out)
+        ctx.qg_evaluate_host(xs, goff, eps2_all, e, x, m, po, pi, com, cm, cq, co, ci, a_out, p_out)
 
     step()
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(steps):
         step()
     dt = (time.perf_counter() - t0) / steps
     in_place = bool(ctx.qg_get_stats()["eval_in_place"])
     ctx.close()
+    units = world * inter
+    if dist is not None:
+        t = torch.tensor([dt, float(inter)], dtype=torch.float64, device="cuda")
+        tmax = t[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dt = float(tmax.item())
+        if shard_part is not None:
+            usum = t[1:].clone()
+            dist.all_reduce(usum, op=dist.ReduceOp.SUM)
+            units = float(usum.item())
     route = ("lists read and results written in place by the force kernel over the coherent CPU-GPU link"
              if in_place else "list copies overlapped with the force kernel, results copied back")
-    return {"value": world * inter / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+    return {"value": units / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": dt * 1e3, "lists_in_place": in_place,
             "api": "qg_evaluate_host (pinned host arrays in and out; %s), wall clock" % route}
 

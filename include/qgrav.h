@@ -103,7 +103,7 @@ typedef struct {
   int tile_j;           /* list entries staged per shared-memory tile;
                            0 = default (256); else 32..1024, multiple of 32 */
   int warps_per_group;  /* warps of the CTA that evaluates one group;
-                           0 = default; supported: 2, 4, 8                  */
+                           0 = default; supported: 1, 2, 4, 8               */
   int sinks_per_thread; /* sinks held in registers per thread;
                            0 = default; supported: 2, 4, 8                  */
   int flush_j;          /* FP32 partials are folded into FP64 after at most
@@ -113,6 +113,17 @@ typedef struct {
                            float2 register, f32x2 FMA instructions) or
                            QG_ARITH_ENTRY_PAIRED (two list entries per
                            float2 register; sinks_per_thread 2 or 4)        */
+  int split_j;          /* long lists cut into work items (Sec. 3.4's group x
+                           list, split for load balance): 0 = never (the
+                           default); k > 0 = every list of more than k
+                           entries is cut into parts of about k entries
+                           (at most 64 parts); -1 = automatic: a group whose
+                           FP32 work exceeds a quarter of one CTA's average
+                           share of the step is cut into parts of about an
+                           eighth of it.  Each part writes FP64 partial sums
+                           per sink; the part that completes a group adds
+                           them in a fixed order (bitwise repeatable).
+                           qg_evaluate_host never splits.                   */
 } qg_options;
 
 typedef struct {
@@ -128,6 +139,9 @@ typedef struct {
                                  2 entry-paired                              */
   int32_t eval_in_place;      /* 1 if the last qg_evaluate_host read the
                                  lists and wrote the results in place       */
+  int64_t n_items;            /* work items of the last qg_run's queue (the
+                                 groups, or groups and parts of split lists) */
+  int64_t n_split;            /* groups whose lists were split               */
 } qg_stats;
 
 /* Create a context on CUDA device `device`.  opt may be NULL (defaults).

@@ -21,6 +21,7 @@
 namespace {
 
 using qg::kBuckets;
+using qg::queue_hist_items_kernel;
 using qg::queue_hist_kernel;
 using qg::queue_scatter_kernel;
 
@@ -203,6 +204,14 @@ struct qg_ctx {
   DevBuf<int> scratch;  // hist[kBuckets], cursor[kBuckets], head, bad
   DevBuf<unsigned char> bucket;
   DevBuf<int32_t> queue;
+  // split lists (qg_options.split_j): the step's work items, the FP64
+  // partial sums of the split groups' parts, their completion counts
+  int64_t n_items = 0;  // 0: no split, one item per group
+  int n_split = 0;
+  int64_t n_slots = 0;
+  DevBuf<qg::Item> items;
+  DevBuf<double> partial;
+  DevBuf<int> done;
   bool ran = false;  // outputs hold the result of a qg_run for the current sinks
   // graph, and events recorded inside it (step start, force start/end)
   cudaGraphExec_t exec = nullptr;
@@ -269,7 +278,8 @@ bool valid_options(const qg_options &o, std::string &why) {
   if (o.precision < QG_FP32_CENTRED || o.precision > QG_FP64) { why = "precision"; return false; }
   if (o.expansion != QG_QUAD && o.expansion != QG_MONO) { why = "expansion"; return false; }
   if (o.tile_j && (o.tile_j < 32 || o.tile_j > 1024 || o.tile_j % 32)) { why = "tile_j"; return false; }
-  if (o.warps_per_group && o.warps_per_group != 2 && o.warps_per_group != 4 && o.warps_per_group != 8) {
+  if (o.warps_per_group && o.warps_per_group != 1 && o.warps_per_group != 2 && o.warps_per_group != 4 &&
+      o.warps_per_group != 8) {
     why = "warps_per_group";
     return false;
   }
@@ -279,6 +289,7 @@ bool valid_options(const qg_options &o, std::string &why) {
   }
   if (o.flush_j < 0) { why = "flush_j"; return false; }
   if (o.arith < QG_ARITH_DEFAULT || o.arith > QG_ARITH_ENTRY_PAIRED) { why = "arith"; return false; }
+  if (o.split_j < -1) { why = "split_j"; return false; }
   return true;
 }
 
@@ -407,6 +418,81 @@ qg::ForceParams force_params(qg_ctx *c, int64_t g0, int64_t G, int *head) {
   return p;
 }
 
+// Work items of a step with split lists (qg_options.split_j != 0): every
+// group whose list is long (split_j > 0: more than split_j entries) or
+// expensive (split_j = -1: more than a quarter of one CTA's average share of
+// the step) is cut into parts of about equal FP32 work (particle entries
+// weigh 13, cells 33 or 13), at most 64; the other groups stay one item.
+// Host work O(groups), done when the step's graph is (re)built.
+qg_status build_items(qg_ctx *c) {
+  c->n_items = 0;
+  c->n_split = 0;
+  c->n_slots = 0;
+  const int split = c->opt.split_j;
+  const int64_t G = c->G;
+  if (split == 0 || G <= 0) return QG_OK;
+  const double cell_ops = c->opt.expansion == QG_QUAD ? 33.0 : 13.0;
+  const std::vector<int64_t> &go = c->h_goff, &po = c->h_poff, &co = c->h_coff;
+  double share = 0.0;
+  if (split < 0) {
+    for (int64_t g = 0; g < G; g++) {
+      const double ni = (double)(go[g + 1] - go[g]), np = (double)(po[g + 1] - po[g]),
+                   nc = (double)(co[g + 1] - co[g]);
+      share += ni * (13.0 * np + cell_ops * nc) + 64.0 * (np + nc) + 256.0;
+    }
+    share /= std::max(c->grid, 1);
+  }
+  std::vector<qg::Item> it;
+  it.reserve((size_t)G);
+  int64_t slot = 0;
+  int ctr = 0;
+  for (int64_t g = 0; g < G; g++) {
+    const int64_t ni = go[g + 1] - go[g], np = po[g + 1] - po[g], nc = co[g + 1] - co[g], ne = np + nc;
+    int64_t P = 1;
+    if (ni > 0 && ne > 1) {
+      if (split > 0) {
+        P = (ne + split - 1) / split;
+      } else {
+        const double cost = (double)ni * (13.0 * np + cell_ops * nc) + 64.0 * ne + 256.0;
+        if (cost > 0.25 * share) P = (int64_t)std::ceil(cost / (0.125 * share));
+      }
+      P = std::min<int64_t>(std::min<int64_t>(P, 64), ne);
+    }
+    if (P <= 1) {
+      it.push_back(qg::Item{(int32_t)g, -1, 1, 0, 0, ne, 0});
+      continue;
+    }
+    // cut points at equal FP32 work
+    const double W = 13.0 * np + cell_ops * nc;
+    int64_t prev = 0;
+    for (int64_t k = 0; k < P; k++) {
+      int64_t e = ne;
+      if (k < P - 1) {
+        const double target = W * (double)(k + 1) / (double)P;
+        e = target <= 13.0 * np ? (int64_t)std::ceil(target / 13.0)
+                                : np + (int64_t)std::ceil((target - 13.0 * np) / cell_ops);
+        e = std::max(e, prev + 1);
+        e = std::min(e, ne - (P - 1 - k));
+      }
+      it.push_back(qg::Item{(int32_t)g, (int32_t)k, (int32_t)P, ctr, prev, e, slot + k * ni});
+      prev = e;
+    }
+    slot += P * ni;
+    ctr++;
+  }
+  if (ctr == 0) return QG_OK;  // nothing long enough to split: one item per group
+  if (it.size() >= (size_t)INT32_MAX) return fail(c, QG_ERR_SIZE, "too many work items (%zu)", it.size());
+  cudaError_t e;
+  if ((e = c->items.reserve(it.size())) != cudaSuccess || (e = c->partial.reserve(4 * slot)) != cudaSuccess ||
+      (e = c->done.reserve(ctr)) != cudaSuccess)
+    return fail(c, QG_ERR_NOMEM, "work item allocation: %s", cudaGetErrorString(e));
+  QG_CUDA(c, cudaMemcpy(c->items.p, it.data(), it.size() * sizeof(qg::Item), cudaMemcpyHostToDevice));
+  c->n_items = (int64_t)it.size();
+  c->n_split = ctr;
+  c->n_slots = slot;
+  return QG_OK;
+}
+
 // Record the queue build and the persistent force launch on stream s.
 qg_status record_step(qg_ctx *c, cudaStream_t s) {
   const int64_t G = c->G;
@@ -414,13 +500,28 @@ qg_status record_step(qg_ctx *c, cudaStream_t s) {
   QG_CUDA(c, cudaEventRecordWithFlags(c->ev[0], s, cudaEventRecordExternal));
   QG_CUDA(c, cudaMemsetAsync(hist, 0, (2 * kBuckets + 2) * sizeof(int), s));
   const double cell_ops = c->opt.expansion == QG_QUAD ? 33.0 : 13.0;
-  queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->goff.p, c->poff.p, c->coff.p, cell_ops,
-                                                      c->bucket.p, hist);
+  const int64_t NI = c->n_items ? c->n_items : G;  // work items: groups, or groups and parts of split lists
+  if (c->n_items) {
+    QG_CUDA(c, cudaMemsetAsync(c->done.p, 0, std::max(c->n_split, 1) * sizeof(int), s));
+    queue_hist_items_kernel<<<grid_for(NI, 256), 256, 0, s>>>(NI, c->items.p, c->goff.p, c->poff.p, cell_ops,
+                                                               c->bucket.p, hist);
+  } else {
+    queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->goff.p, c->poff.p, c->coff.p, cell_ops,
+                                                        c->bucket.p, hist);
+  }
   QG_CUDA(c, cudaGetLastError());
-  queue_scatter_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->bucket.p, hist, cursor, c->queue.p);
+  queue_scatter_kernel<<<grid_for(NI, 256), 256, 0, s>>>(NI, c->bucket.p, hist, cursor, c->queue.p);
   QG_CUDA(c, cudaGetLastError());
   qg::ForceParams p = force_params(c, 0, G, head);
-  const int grid = (int)std::min<int64_t>(c->grid, std::max<int64_t>(G, 1));
+  if (c->n_items) {
+    p.items = c->items.p;
+    p.partial = c->partial.p;
+    p.done = c->done.p;
+    p.nitems = (int32_t)NI;
+  }
+  const int grid = (int)std::min<int64_t>(c->grid, std::max<int64_t>(NI, 1));
+  c->stats.n_items = NI;
+  c->stats.n_split = c->n_split;
   c->stats.grid = grid;
   void *args[] = {&p};
   QG_CUDA(c, cudaEventRecordWithFlags(c->ev[1], s, cudaEventRecordExternal));
@@ -434,11 +535,13 @@ qg_status ensure_graph(qg_ctx *c) {
   invalidate(c);
   qg_status st = choose_kernel(c);
   if (st != QG_OK) return st;
+  if ((st = build_items(c)) != QG_OK) return st;
   const int64_t G = c->G;
+  const int64_t NI = std::max(G, c->n_items);
   {
     cudaError_t e;
     if ((e = c->scratch.reserve(kScratchInts)) != cudaSuccess ||
-        (e = c->bucket.reserve(G)) != cudaSuccess || (e = c->queue.reserve(G)) != cudaSuccess ||
+        (e = c->bucket.reserve(NI)) != cudaSuccess || (e = c->queue.reserve(NI)) != cudaSuccess ||
         (e = c->a.reserve(3 * std::max<int64_t>(c->n, 1))) != cudaSuccess ||
         (e = c->phi.reserve(std::max<int64_t>(c->n, 1))) != cudaSuccess)
       return fail(c, QG_ERR_NOMEM, "device allocation: %s", cudaGetErrorString(e));

@@ -54,13 +54,20 @@ template <> struct RT<double> {
 //              the first QG_CVT_HW coordinates (it issues on the narrow FP64
 //              pipe), by integer operations for the rest (ALU pipe);
 //   QG_GATHER2 each thread keeps two list entries' gathers in flight before
-//              converting either.
+//              converting either;
+//   QG_EP_UNROLL unroll of the entry-paired pair loops.
 #ifndef QG_CVT_HW
 #define QG_CVT_HW 0
 #endif
 #ifndef QG_GATHER2
 #define QG_GATHER2 1
 #endif
+#ifndef QG_EP_UNROLL
+#define QG_EP_UNROLL 1
+#endif
+// #pragma unroll does not expand macros: the unroll count goes through _Pragma
+#define QG_PRAGMA_(x) _Pragma(#x)
+#define QG_UNROLL(n) QG_PRAGMA_(unroll n)
 
 template <typename Real, int K>
 __device__ __forceinline__ Real cvt_off(double v) {
@@ -310,6 +317,7 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
   using V2 = typename RT<Real>::v2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_item;
+  __shared__ int s_last;  // split lists: this item completed its group's parts
 
   const int NT = blockDim.x;
   const int tid = threadIdx.x;
@@ -345,7 +353,21 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
     __syncthreads();
     const int item = s_item;
     if (item >= p.nitems) break;
-    const int g = p.queue[item];
+    const int q = p.queue[item];
+    // the work item: a whole group, or one part of a split group's list
+    // (entries [e0, e1) of its particle entries followed by its cell entries)
+    int g = q, part = -1, nparts = 1, ctr = 0;
+    int64_t e0 = 0, e1 = -1, slot = 0;
+    if (p.items) {
+      const Item it = p.items[q];
+      g = it.g;
+      part = it.part;
+      nparts = it.nparts;
+      ctr = it.ctr;
+      e0 = it.e0;
+      e1 = it.e1;
+      slot = it.slot;
+    }
     const int64_t s0 = p.group_off[g];
     const int ni = (int)(p.group_off[g + 1] - s0);
     constexpr bool keep = INPLACE;
@@ -368,8 +390,11 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
       cz = p.gcentre[3 * g + 2];
     }
 
-    const int64_t p0 = p.plist_off[g], p1 = p.plist_off[g + 1];
-    const int64_t c0 = p.clist_off[g], c1 = p.clist_off[g + 1];
+    const int64_t gp0 = p.plist_off[g], np_g = p.plist_off[g + 1] - gp0;
+    const int64_t gc0 = p.clist_off[g], nc_g = p.clist_off[g + 1] - gc0;
+    if (e1 < 0) e1 = np_g + nc_g;
+    const int64_t p0 = gp0 + min(e0, np_g), p1 = gp0 + min(e1, np_g);
+    const int64_t c0 = gc0 + max(e0 - np_g, (int64_t)0), c1 = gc0 + max(e1 - np_g, (int64_t)0);
 
     // ---- sink chunks of at most R * NT sinks --------------------------------
     for (int sb = 0; sb < ni; sb += R * NT) {
@@ -451,15 +476,17 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
             ax2[h] = ay2[h] = az2[h] = pt2[h] = make_float2(0.f, 0.f);
           }
         } else if constexpr (EPAIR) {
-          // both halves (even and odd entries) of each sum; the potential
-          // was accumulated with the physical sign
+          // the two halves (even and odd entries) of each sum added in FP32
+          // -- together they cover at most flush_j entries, as one scalar
+          // FP32 sum does -- then folded; the potential was accumulated with
+          // the physical sign
 #pragma unroll
           for (int r = 0; r < R; r++) {
             double *a = acc64 + 4 * r * NT + tid;
-            a[0] += (double)bax[r].x + (double)bax[r].y;
-            a[NT] += (double)bay[r].x + (double)bay[r].y;
-            a[2 * NT] += (double)baz[r].x + (double)baz[r].y;
-            a[3 * NT] -= (double)bpt[r].x + (double)bpt[r].y;
+            a[0] += (double)(bax[r].x + bax[r].y);
+            a[NT] += (double)(bay[r].x + bay[r].y);
+            a[2 * NT] += (double)(baz[r].x + baz[r].y);
+            a[3 * NT] -= (double)(bpt[r].x + bpt[r].y);
             bax[r] = bay[r] = baz[r] = bpt[r] = make_float2(0.f, 0.f);
           }
         } else {
@@ -596,7 +623,7 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
             nproc += (cnt - k + K - 1) / K;
           } else if constexpr (EPAIR) {
             const int npair = (cnt + 1) >> 1;
-#pragma unroll 2
+QG_UNROLL(QG_EP_UNROLL)
             for (int uu = k; uu < npair; uu += K) {
               const float4 E0 = tE0[uu], E1 = tE1[uu];
 #pragma unroll
@@ -757,7 +784,7 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
           } else if constexpr (EPAIR) {
             const int npair = (cnt + 1) >> 1;
             if (QUAD) {
-#pragma unroll 2
+QG_UNROLL(QG_EP_UNROLL)
               for (int uu = k; uu < npair; uu += K) {
                 const float4 E0 = tE0[uu], E1 = tE1[uu], E2 = tE2[uu], E3 = tE3[uu], E4 = tE4[uu];
 #pragma unroll
@@ -769,7 +796,7 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
                                     baz[r], bpt[r]);
               }
             } else {
-#pragma unroll 2
+QG_UNROLL(QG_EP_UNROLL)
               for (int uu = k; uu < npair; uu += K) {
                 const float4 E0 = tE0[uu], E1 = tE1[uu];
 #pragma unroll
@@ -819,10 +846,18 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
             m0 += a[0]; m1 += a[NT]; m2 += a[2 * NT]; m3 += a[3 * NT];
           }
           const int64_t o = s0 + sb + i;
-          p.a[3 * o] = m0;
-          p.a[3 * o + 1] = m1;
-          p.a[3 * o + 2] = m2;
-          p.phi[o] = -m3;  // physical potential, Eq. 1
+          if (part < 0) {
+            p.a[3 * o] = m0;
+            p.a[3 * o + 1] = m1;
+            p.a[3 * o + 2] = m2;
+            p.phi[o] = -m3;  // physical potential, Eq. 1
+          } else {            // this part's sums, merged below by the group's last part
+            double *w = p.partial + 4 * (slot + sb + i);
+            w[0] = m0;
+            w[1] = m1;
+            w[2] = m2;
+            w[3] = m3;
+          }
         }
       } else {
         // the same sums, written to the device and to host memory
@@ -863,6 +898,38 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
           const double v = out[t];
           ag[t] = v;
           ah[t] = v;
+        }
+      }
+    }
+
+    // ---- a6. split lists: the part that completes its group's count adds
+    // the parts' sums of every sink in the fixed order k = 0, 1, ... (no
+    // part waits for another; the partial sums of other CTAs are read past
+    // the L1, after the count that follows their writes)
+    if constexpr (!INPLACE) {
+      if (part >= 0) {
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_last = atomicAdd(p.done + ctr, 1) == nparts - 1;
+        __syncthreads();
+        if (s_last) {
+          __threadfence();
+          const int64_t base = slot - (int64_t)part * ni;  // the group's first slot
+          for (int i = tid; i < ni; i += NT) {
+            double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+            for (int k = 0; k < nparts; k++) {
+              const double *w = p.partial + 4 * (base + (int64_t)k * ni + i);
+              m0 += __ldcg(w);
+              m1 += __ldcg(w + 1);
+              m2 += __ldcg(w + 2);
+              m3 += __ldcg(w + 3);
+            }
+            const int64_t o = s0 + i;
+            p.a[3 * o] = m0;
+            p.a[3 * o + 1] = m1;
+            p.a[3 * o + 2] = m2;
+            p.phi[o] = -m3;
+          }
         }
       }
     }

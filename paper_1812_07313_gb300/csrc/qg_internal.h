@@ -56,6 +56,24 @@ __host__ __device__ inline float f64_to_f32_rn(double x) {
 #endif
 }
 
+// One work item of a step whose long lists are split (the modified tree
+// algorithm's group x list, Sec. 3.4, cut into parts): group g, entries
+// [e0, e1) of its list taken as its particle entries followed by its cell
+// entries.  part = -1: the whole list (the group's results are written
+// directly).  part = k of nparts: the item writes FP64 partial sums of its
+// range for every sink of g to partial[slot + i] (slot = the group's first
+// slot + k n_i), counts itself in done[ctr], and the item that completes the
+// count adds the parts of every sink in the order k = 0, 1, ... and writes
+// the results (bitwise repeatable whichever part finishes last).
+struct Item {
+  int32_t g;
+  int32_t part;
+  int32_t nparts;
+  int32_t ctr;
+  int64_t e0, e1;
+  int64_t slot;
+};
+
 // Device pointers and sizes one force launch reads.  Layouts:
 //   sink_x    [n][3] double           sink_eps2 [n] float or null
 //   group_off [G+1]                   queue     [nitems] group ids
@@ -87,6 +105,12 @@ struct ForceParams {
   const int32_t *queue;
   int32_t nitems;
   int32_t *head;
+  // Split lists (null: every queue entry is a group id, whole lists): the
+  // queue holds indices into items; partial [slots][4] FP64 (a, phi) per
+  // sink and part; done [split groups] completion counts (zero at launch).
+  const Item *items;
+  double *partial;
+  int *done;
   double *a;
   double *phi;
   // In-place kernels only (lists read from host memory): every index is

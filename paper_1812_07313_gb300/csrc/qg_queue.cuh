@@ -7,6 +7,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "qg_internal.h"
+
 namespace qg {
 
 constexpr int kBuckets = 128;  // cost classes of the work queue (4 per octave)
@@ -39,7 +41,32 @@ static __global__ void queue_hist_kernel(int64_t G, const int64_t *__restrict__ 
     if (h[b]) atomicAdd(&hist[b], h[b]);
 }
 
-// Work queue, pass 2: groups scattered in descending cost class.
+// Work queue, pass 1 when lists are split: the same cost classes for work
+// items (a group's list, or one part of it: its entries [e0, e1) of the
+// particle entries followed by the cell entries).
+static __global__ void queue_hist_items_kernel(int64_t n, const Item *__restrict__ items,
+                                               const int64_t *__restrict__ goff, const int64_t *__restrict__ poff,
+                                               double cell_ops, unsigned char *bucket, int *hist) {
+  __shared__ int h[kBuckets];
+  for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) h[b] = 0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const Item it = items[i];
+    const double ni = (double)(goff[it.g + 1] - goff[it.g]);
+    const int64_t npg = poff[it.g + 1] - poff[it.g];
+    const double np = (double)(min(it.e1, npg) - min(it.e0, npg));
+    const double nc = (double)(max(it.e1 - npg, (int64_t)0) - max(it.e0 - npg, (int64_t)0));
+    const double cost = ni * (13.0 * np + cell_ops * nc) + 64.0 * (np + nc) + 256.0;
+    const int b = cost_bucket(cost);
+    bucket[i] = (unsigned char)b;
+    atomicAdd(&h[b], 1);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kBuckets; b += blockDim.x)
+    if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+// Work queue, pass 2: groups (or work items) scattered in descending cost class.
 static __global__ void queue_scatter_kernel(int64_t G, const unsigned char *__restrict__ bucket,
                                      const int *__restrict__ hist, int *cursor, int32_t *queue) {
   __shared__ int start[kBuckets];

@@ -101,8 +101,9 @@ class GpuTree:
         self._ok(self._L.qg_gtree_arrays(self._h, *[ctypes.addressof(p) for p in ptrs]), "qg_gtree_arrays")
         return {k: p.value for k, p in zip(ARRAYS, ptrs)}
 
-    def host(self, name):
-        """A device array of the last build / walk, copied to numpy."""
+    def host(self, name, start=None, stop=None):
+        """A device array of the last build / walk, copied to numpy (rows
+        [start, stop) of it when given)."""
         sz = self.sizes()
         n, nn, G = sz["n"], sz["nnodes"], sz["ngroups"]
         shapes = {"perm": ((n,), np.int64), "xs": ((n, 3), np.float64), "ms": ((n,), np.float64),
@@ -113,12 +114,16 @@ class GpuTree:
                   "clist_off": ((G + 1,), np.int64), "plist_idx": ((sz["n_plist"],), np.int32),
                   "clist_idx": ((sz["n_clist"],), np.int32)}
         shape, dt = shapes[name]
-        out = np.empty(shape, dtype=dt)
+        rows = shape[0]
+        lo = 0 if start is None else max(0, min(int(start), rows))
+        hi = rows if stop is None else max(lo, min(int(stop), rows))
+        out = np.empty((hi - lo,) + shape[1:], dtype=dt)
+        row_bytes = int(np.prod(shape[1:], dtype=np.int64)) * np.dtype(dt).itemsize
         ptr = self.pointers()[name]
         if out.nbytes:
             if not ptr:
                 raise qgrav.QGError(qgrav.QG_ERR_STATE, "%s is not available" % name)
-            rc = self._L.cudaMemcpy(out.ctypes.data, ptr, out.nbytes, 2)  # device -> host
+            rc = self._L.cudaMemcpy(out.ctypes.data, ptr + lo * row_bytes, out.nbytes, 2)  # device -> host
             if rc != 0:
                 raise qgrav.QGError(qgrav.QG_ERR_CUDA, "cudaMemcpy of %s failed (%d)" % (name, rc))
         return out

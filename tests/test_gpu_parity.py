@@ -525,6 +525,109 @@ def test_invalid_lists_are_rejected_before_any_kernel_reads_them():
     assert np.all(np.isfinite(a))
 
 
+@pytest.mark.parametrize("arith", [qgrav.QG_ARITH_SCALAR, qgrav.QG_ARITH_ENTRY_PAIRED])
+@pytest.mark.parametrize("split", [7, 64, 500, -1])
+def test_split_lists_are_repeatable_and_keep_parity(sphere4k, split, arith):
+    """Long lists cut into work items (group, entry range): each part's FP64
+    partial sums merged by the group's last part in a fixed order.  Results
+    are bitwise repeatable (twice in one context and in a fresh one), match
+    the oracle at the stated tolerance, and agree with the unsplit step to
+    FP32 rounding.  split 7 cuts every list (up to the maximum of 64 parts);
+    -1 is the automatic mode (on this small set nearly every group is above a
+    quarter of its share of the persistent grid's CTAs, so nearly every list
+    is cut)."""
+    o = qgrav.Options(arith=arith, split_j=split)
+    ctx = qgrav.Context(0, o)
+    a1, p1, st = sphere4k.gpu(ctx=ctx)
+    ctx.qg_run()
+    a2, p2 = ctx.qg_get_forces()
+    ctx.close()
+    a3, p3, st3 = sphere4k.gpu(o)
+    assert np.array_equal(a1, a2) and np.array_equal(p1, p2)
+    assert np.array_equal(a1, a3) and np.array_equal(p1, p3)
+    G = sphere4k.tree.ngroups
+    assert st["n_split"] > 0 and st["n_items"] > G, st
+    if split == 7:
+        assert st["n_split"] == G, st        # every list has more than 7 entries
+    if split == -1:
+        assert st["n_split"] >= 0.9 * G, st  # all but the cheapest groups
+    a_ref, phi_ref = sphere4k.oracle()
+    assert_parity(a1, p1, a_ref, phi_ref, label="split %d form %d" % (split, arith))
+    a0, p0, st0 = sphere4k.gpu(qgrav.Options(arith=arith))
+    assert st0["n_split"] == 0 and st0["n_items"] == G
+    assert np.max(rel_err(a1, a0)) < 1e-5 and np.max(rel_err(p1, p0)) < 1e-5
+
+
+def test_split_lists_with_empty_and_single_entry_lists():
+    """Splitting leaves groups with no list entries, one entry or no sinks
+    alone, and cuts lists that end in ragged tails; every part of a group of
+    more sinks than one CTA pass holds (sink chunks) adds up too."""
+    rng = np.random.default_rng(8)
+    G = 40
+    sizes = rng.integers(0, 6, G)
+    sizes[3] = 0
+    sizes[11] = 2
+    sizes[7] = 700   # more sinks than one pass of 128 threads x 4 sinks
+    group_off = np.concatenate([[0], np.cumsum(sizes)])
+    n = int(group_off[-1])
+    sink_x = rng.uniform(-1, 1, (n, 3))
+    src_x = rng.uniform(-5, 5, (400, 3))
+    src_m = rng.uniform(0.1, 1, 400)
+    com, cm, cq = _random_cells(rng, 120, np.array([10.0, 0, 0]), 3.0)
+    plen = (np.arange(G) * 13) % 97
+    clen = (np.arange(G) * 7) % 89
+    plen[5], clen[5] = 1, 0
+    plen[9], clen[9] = 0, 1
+    plen[11], clen[11] = 0, 0
+    plist_off = np.concatenate([[0], np.cumsum(plen)])
+    clist_off = np.concatenate([[0], np.cumsum(clen)])
+    plist_idx = rng.integers(0, 400, plist_off[-1]).astype(np.int32)
+    clist_idx = rng.integers(0, 120, clist_off[-1]).astype(np.int32)
+    for arith in (qgrav.QG_ARITH_SCALAR, qgrav.QG_ARITH_ENTRY_PAIRED):
+        a, phi, a_ref, phi_ref = _explicit(sink_x, group_off, src_x, src_m, plist_off, plist_idx, com, cm, cq,
+                                           clist_off, clist_idx, 1e-3,
+                                           options=qgrav.Options(tile_j=32, split_j=5, arith=arith))
+        empty = np.concatenate([np.arange(group_off[g], group_off[g + 1]) for g in (11,)])
+        assert np.all(a[empty] == 0.0) and np.all(phi[empty] == 0.0)
+        live = np.setdiff1d(np.arange(n), empty)
+        assert_parity(a[live], phi[live], a_ref[live], phi_ref[live], label="split edges form %d" % arith)
+
+
+def test_split_option_is_checked():
+    ctx = qgrav.Context(0)
+    with pytest.raises(qgrav.QGError) as e:
+        ctx.set_options(qgrav.Options(split_j=-2))
+    assert e.value.status == qgrav.QG_ERR_ARG
+    ctx.close()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_contexts_concatenate_to_the_unsharded_step(sphere4k, world):
+    """The multi-GPU split of a step (contiguous cost-balanced ranges of
+    groups, sources and cells replicated, no collective), run as one context
+    per shard on one GPU: the shards' results, concatenated, are the
+    unsharded step's bit for bit (same launch shape)."""
+    from paper_1812_07313_gb300 import shard
+    t, L = sphere4k.tree, sphere4k.lists
+    for opt in (qgrav.Options(sinks_per_thread=4, warps_per_group=2, tile_j=256, arith=qgrav.QG_ARITH_ENTRY_PAIRED),
+                qgrav.Options(sinks_per_thread=2, warps_per_group=4, tile_j=128, arith=qgrav.QG_ARITH_SCALAR)):
+        a0, p0, _ = sphere4k.gpu(opt)
+        parts = shard.shards(t.group_off, L.plist_off, L.plist_idx, L.clist_off, L.clist_idx, world)
+        assert len(parts) == world and parts[0].s0 == 0 and parts[-1].s1 == t.n
+        a_parts, p_parts = [], []
+        for sh in parts:
+            ctx = qgrav.Context(0, opt)
+            ctx.qg_set_sinks(t.x[sh.s0:sh.s1], sh.group_off, sphere4k.eps2_all)
+            ctx.qg_set_sources(t.x, t.m, sh.plist_off, sh.plist_idx)
+            ctx.qg_set_cells(t.cell_com, t.cell_m, t.cell_q, sh.clist_off, sh.clist_idx)
+            ctx.qg_run()
+            a, phi = ctx.qg_get_forces()
+            ctx.close()
+            a_parts.append(a)
+            p_parts.append(phi)
+        assert np.array_equal(np.concatenate(a_parts), a0) and np.array_equal(np.concatenate(p_parts), p0)
+
+
 def test_non_finite_or_out_of_range_inputs_are_rejected():
     """A position, mass, quadrupole component or softening that is not finite,
     or beyond 2^100 in magnitude, is refused (QG_ERR_ARG) by every entry point
@@ -637,6 +740,72 @@ def test_full_size_sampled(name, theta, k):
     s = case.sinks_of(groups)
     assert_parity(a[s], phi[s], a_ref[s], phi_ref[s], label="%s theta=%.2f" % (name, theta))
     assert np.all(np.isfinite(a)) and np.all(np.isfinite(phi))
+
+
+def test_batched_512_all_sinks_against_the_oracle():
+    """The batched configuration (512 systems, 8.8 million sinks, n_crit 64,
+    theta 0.5) at the autotuned launch shape, checked against the oracle on
+    every sink (the oracle's groups split over the host cores)."""
+    import os
+    case = Case.workload("batched_512")
+    a, phi, st = case.gpu(autotune=True)
+    oracle.set_threads(os.cpu_count() or 1)
+    try:
+        a_ref, phi_ref = case.oracle()
+    finally:
+        oracle.set_threads(1)
+    assert len(a_ref) == case.tree.n == 8826172
+    assert_parity(a, phi, a_ref, phi_ref, label="batched_512, all %d sinks, launch %s" % (
+        case.tree.n, {k: st[k] for k in ("sinks_per_thread", "warps_per_group", "tile_j", "paired")}))
+
+
+def test_plummer_4m_theta_sweep_fp32_centred_vs_fp64_and_oracle():
+    """The clustered configuration over theta 0.3 ... 0.8 (GPU-built tree and
+    lists): the FP32 kernel with FP64 centring against the all-FP64 kernel on
+    every sink, and both against the oracle on sampled groups (the largest
+    group and the longest list included)."""
+    import torch
+    from paper_1812_07313_gb300 import gtree
+    wl = workloads.WORKLOADS["plummer_4m"]
+    ps = wl.particles()
+    eps2 = float(ps.eps[0]) ** 2
+    t = gtree.GpuTree(0)
+    t.build(torch.as_tensor(ps.x).cuda(), torch.as_tensor(ps.m).cuda(), ps.sys_off, wl.leaf_max, wl.n_crit)
+    xs, ms = t.host("xs"), t.host("ms")
+    com, cm, cq = t.host("cell_com"), t.host("cell_m"), t.host("cell_q")
+    goff = t.host("group_off")
+    rng = np.random.default_rng(33)
+    for theta in (0.3, 0.4, 0.5, 0.6, 0.7, 0.8):
+        t.walk(theta)
+        res = {}
+        for name, opt in (("fp32", None), ("fp64", qgrav.Options(precision=qgrav.QG_FP64))):
+            ctx = qgrav.Context(0, opt)
+            t.attach(ctx, eps2)
+            ctx.qg_run()
+            res[name] = ctx.qg_get_forces()
+            ctx.close()
+        (a32, p32), (a64, p64) = res["fp32"], res["fp64"]
+        sa, sp = assert_parity(a32, p32, a64, p64, label="theta %.1f fp32 vs fp64, every sink" % theta)
+        # the oracle on sampled groups: their lists cut out of the device arrays
+        po, co = t.host("plist_off"), t.host("clist_off")
+        ni, nl = np.diff(goff), np.diff(po) + np.diff(co)
+        groups = np.unique(np.concatenate([rng.choice(len(ni), 20, replace=False), [np.argmax(ni), np.argmax(nl)]]))
+        s_goff, s_po, s_co, s_pi, s_ci, sinks = [0], [0], [0], [], [], []
+        for g in groups:
+            s_pi.append(t.host("plist_idx", po[g], po[g + 1]))
+            s_ci.append(t.host("clist_idx", co[g], co[g + 1]))
+            sinks.append(np.arange(goff[g], goff[g + 1]))
+            s_goff.append(s_goff[-1] + len(sinks[-1]))
+            s_po.append(s_po[-1] + len(s_pi[-1]))
+            s_co.append(s_co[-1] + len(s_ci[-1]))
+        sinks = np.concatenate(sinks)
+        a_or, p_or = oracle.expansion_forces(np.array(s_goff), xs[sinks], xs, ms, np.array(s_po),
+                                             np.concatenate(s_pi), com, cm, cq, np.array(s_co), np.concatenate(s_ci),
+                                             eps2_all=eps2)
+        assert_parity(a64[sinks], p64[sinks], a_or, p_or, med=TOL_FP64, p99=TOL_FP64,
+                      label="theta %.1f fp64 vs oracle" % theta)
+        assert_parity(a32[sinks], p32[sinks], a_or, p_or, label="theta %.1f fp32 vs oracle" % theta)
+    t.close()
 
 
 def test_plummer_4m_fp64_kernel_sampled():

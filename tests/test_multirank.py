@@ -1,7 +1,8 @@
 """The N > 1 path on the CPU with gloo, world size 2: the group split that
 shards a step across ranks (each rank evaluates its range of groups; the
 gathered result equals the unsharded one) and the benchmark's aggregation of
-replica timings (max over ranks)."""
+the ranks' timings (max over ranks; replicas' units times the ranks, shards'
+units added up)."""
 import os
 import socket
 
@@ -87,7 +88,10 @@ def _worker_aggregate(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         total_ms, value = bench.aggregate_ranks(100.0 + 50.0 * rank, 10, 1e9, world, dist, "cpu")
-        q.put((rank, total_ms, value))
+        # shards: each rank's own units, added up, over the slowest rank's time
+        _, value_s = bench.aggregate_ranks(100.0 + 50.0 * rank, 10, 1e9 * (1 + rank), world, dist, "cpu",
+                                           summed=True)
+        q.put((rank, total_ms, value, value_s))
     finally:
         dist.destroy_process_group()
 
@@ -103,9 +107,10 @@ def test_replica_timing_is_max_over_ranks():
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
-    for rank, total_ms, value in got:
+    for rank, total_ms, value, value_s in got:
         assert total_ms == 150.0
         assert value == pytest.approx(2 * 10 * 1e9 / 0.150)
+        assert value_s == pytest.approx(10 * 3e9 / 0.150)
 
 
 def test_split_ranges_edge_cases():
