@@ -666,7 +666,8 @@ void qg_destroy(qg_ctx *c) {
   if (c->last_stream) cudaStreamSynchronize(c->last_stream);
   if (c->stream) cudaStreamSynchronize(c->stream);
   invalidate(c);
-  c->sink_x.release(); c->sink_eps2.release(); c->goff.release();
+  c->sink_x.release(); c->sink_eps2.release(); c->goff.release(); c->gcentre.release();
+  c->items.release(); c->partial.release(); c->done.release();
   c->src.release(); c->src_m64.release(); c->stage_x.release();
   c->poff.release(); c->pidx.release();
   c->cell_pm.release(); c->cell_m64.release(); c->cell_q.release(); c->cell_q64.release(); c->coff.release(); c->cidx.release();
