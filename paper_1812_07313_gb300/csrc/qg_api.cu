@@ -34,7 +34,7 @@ __device__ __forceinline__ bool in_range(double v) { return fabs(v) <= qg::kMaxI
 // stay in their own array (m is that array).  A position or mass that is not
 // finite or exceeds kMaxInput in magnitude sets *bad.
 __global__ void pack_src_kernel(int64_t ns, const double *__restrict__ x, const double *__restrict__ m,
-                                qg::PosMass *__restrict__ out, int *bad) {
+                                qg::PosMass *__restrict__ out, qg::PosMassF *__restrict__ outf, int *bad) {
   bool ok = true;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ns; i += (int64_t)gridDim.x * blockDim.x) {
     qg::PosMass v;
@@ -44,6 +44,7 @@ __global__ void pack_src_kernel(int64_t ns, const double *__restrict__ x, const 
     v.m = (float)m[i];
     v.pad = 0.f;
     out[i] = v;
+    outf[i] = qg::make_posmassf(v.x, v.y, v.z, v.m);
     ok = ok && in_range(v.x) && in_range(v.y) && in_range(v.z) && in_range(m[i]);
   }
   if (!ok) atomicOr(bad, 1);
@@ -53,7 +54,7 @@ __global__ void pack_src_kernel(int64_t ns, const double *__restrict__ x, const 
 // dense FP64 copy of Q for the all-FP64 kernel (skipped when q already is it).
 // A value that is not finite or exceeds kMaxInput in magnitude sets *bad.
 __global__ void pack_cells_kernel(int64_t nc, const double *__restrict__ com, const double *__restrict__ m,
-                                  const double *q, qg::PosMass *__restrict__ pm,
+                                  const double *q, qg::PosMass *__restrict__ pm, qg::PosMassF *__restrict__ pmf,
                                   float4 *__restrict__ qf, double *q64, int *bad) {
   bool ok = true;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nc; i += (int64_t)gridDim.x * blockDim.x) {
@@ -64,6 +65,7 @@ __global__ void pack_cells_kernel(int64_t nc, const double *__restrict__ com, co
     v.m = (float)m[i];
     v.pad = 0.f;
     pm[i] = v;
+    pmf[i] = qg::make_posmassf(v.x, v.y, v.z, v.m);
     const double *qi = q + 6 * i;
     qf[2 * i] = make_float4((float)qi[0], (float)qi[1], (float)qi[2], (float)qi[3]);
     qf[2 * i + 1] = make_float4((float)qi[4], (float)qi[5], 0.f, 0.f);
@@ -87,7 +89,9 @@ constexpr int kZeroEps2 = 4;     // a per-sink eps^2 below the smallest normal f
 // entries on it.  Every sink's position (and per-sink eps^2, when given) is
 // checked on the way (the kBad* / kZeroEps2 bits of *flags).
 __global__ void group_centre_kernel(int64_t G, const int64_t *__restrict__ goff, const double *__restrict__ x,
-                                    const float *__restrict__ eps2, double *__restrict__ centre, int *flags) {
+                                    const float *__restrict__ eps2, double *__restrict__ centre,
+                                    qg::PosMassF *__restrict__ centre_f, qg::PosMassF *__restrict__ sink_f,
+                                    int *flags) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (gridDim.x * (int64_t)blockDim.x) >> 5;
   int f = 0;
@@ -99,6 +103,7 @@ __global__ void group_centre_kernel(int64_t G, const int64_t *__restrict__ goff,
       float mn0 = 0.f, mn1 = 0.f, mn2 = 0.f, mx0 = 0.f, mx1 = 0.f, mx2 = 0.f;
       for (int64_t i = lane; i < ni; i += 32) {
         const double *xi = x + 3 * (s0 + i);
+        sink_f[s0 + i] = qg::make_posmassf(xi[0], xi[1], xi[2], 0.f);
         if (!(in_range(xi[0]) && in_range(xi[1]) && in_range(xi[2]))) f |= kBadPosition;
         if (eps2) {
           const float e = eps2[s0 + i];
@@ -124,6 +129,10 @@ __global__ void group_centre_kernel(int64_t G, const int64_t *__restrict__ goff,
       c = base + 0.5 * ((double)lo + (double)hi);
     }
     if (lane < 3) centre[3 * g + lane] = c;
+    // the centre as float pairs, for the centred FP32 kernels
+    const double c0 = __shfl_sync(0xffffffffu, c, 0), c1 = __shfl_sync(0xffffffffu, c, 1),
+                 c2 = __shfl_sync(0xffffffffu, c, 2);
+    if (lane == 0) centre_f[g] = qg::make_posmassf(c0, c1, c2, 0.f);
   }
   if (f) atomicOr(flags, f);
 }
@@ -179,11 +188,13 @@ struct qg_ctx {
   DevBuf<float> sink_eps2;
   DevBuf<int64_t> goff;
   DevBuf<double> gcentre;  // [G][3] bounding-box centre of each group
+  DevBuf<qg::PosMassF> gcentre_f, sink_f;  // the centres and sinks as float pairs
   std::vector<int64_t> h_goff;
   // sources
   int64_t ns = 0, G_src = -1, np_list = 0;
   bool src_ok = false;
   DevBuf<qg::PosMass> src;
+  DevBuf<qg::PosMassF> src_f;
   DevBuf<double> src_m64;
   DevBuf<double> stage_x;  // device staging of host positions
   DevBuf<int64_t> poff;
@@ -193,6 +204,7 @@ struct qg_ctx {
   int64_t nc = 0, G_cell = -1, nc_list = 0;
   bool cells_ok = false;
   DevBuf<qg::PosMass> cell_pm;
+  DevBuf<qg::PosMassF> cell_f;
   DevBuf<double> cell_m64;
   DevBuf<float4> cell_q;
   DevBuf<double> cell_q64;
@@ -396,6 +408,10 @@ qg::ForceParams force_params(qg_ctx *c, int64_t g0, int64_t G, int *head) {
   p.eps2_all_f = (float)c->eps2_all;
   p.group_off = c->goff.p + g0;
   p.gcentre = c->gcentre.p + 3 * g0;
+  p.gcentre_f = c->gcentre_f.p + g0;
+  p.sink_f = c->sink_f.p;
+  p.src_f = c->src_f.p;
+  p.cell_f = c->cell_f.p;
   p.src = c->src.p;
   p.src_m64 = c->src_m64.p;
   p.plist_off = c->poff.p + g0;
@@ -666,11 +682,12 @@ void qg_destroy(qg_ctx *c) {
   if (c->last_stream) cudaStreamSynchronize(c->last_stream);
   if (c->stream) cudaStreamSynchronize(c->stream);
   invalidate(c);
-  c->sink_x.release(); c->sink_eps2.release(); c->goff.release(); c->gcentre.release();
+  c->sink_x.release(); c->sink_eps2.release(); c->goff.release();
+  c->gcentre.release(); c->gcentre_f.release(); c->sink_f.release();
   c->items.release(); c->partial.release(); c->done.release();
-  c->src.release(); c->src_m64.release(); c->stage_x.release();
+  c->src.release(); c->src_f.release(); c->src_m64.release(); c->stage_x.release();
   c->poff.release(); c->pidx.release();
-  c->cell_pm.release(); c->cell_m64.release(); c->cell_q.release(); c->cell_q64.release(); c->coff.release(); c->cidx.release();
+  c->cell_pm.release(); c->cell_f.release(); c->cell_m64.release(); c->cell_q.release(); c->cell_q64.release(); c->coff.release(); c->cidx.release();
   c->a.release(); c->phi.release(); c->scratch.release(); c->bucket.release(); c->queue.release();
   for (auto &e : c->ev)
     if (e) cudaEventDestroy(e);
@@ -704,12 +721,14 @@ qg_status qg_set_options(qg_ctx *c, const qg_options *opt) {
 // Group centres of the sinks now on the device (sink_x, goff), on stream s;
 // the sinks' positions (and eps2, a device array or null) are checked into
 // *flags on the way.
-static qg_status group_centres(qg_ctx *c, int64_t G, const float *eps2, int *flags, cudaStream_t s) {
+static qg_status group_centres(qg_ctx *c, int64_t n, int64_t G, const float *eps2, int *flags, cudaStream_t s) {
   cudaError_t e = c->gcentre.reserve(3 * std::max<int64_t>(G, 1));
+  if (e == cudaSuccess) e = c->gcentre_f.reserve(std::max<int64_t>(G, 1));
+  if (e == cudaSuccess) e = c->sink_f.reserve(std::max<int64_t>(n, 1));
   if (e != cudaSuccess) return fail(c, QG_ERR_NOMEM, "group centre allocation");
   if (G > 0) {
     group_centre_kernel<<<grid_for(32 * G, 256), 256, 0, s>>>(G, c->goff.p, c->sink_x.p, eps2, c->gcentre.p,
-                                                               flags);
+                                                               c->gcentre_f.p, c->sink_f.p, flags);
     QG_CUDA(c, cudaGetLastError());
   }
   return QG_OK;
@@ -760,7 +779,7 @@ static qg_status set_sinks_common(qg_ctx *c, int64_t n, const double *x, const f
   }
   int *flags = nullptr, fl = 0;
   if ((st = value_flags_begin(c, s, &flags)) != QG_OK) return st;
-  if ((st = group_centres(c, ngroups, dev && eps2 ? c->sink_eps2.p : nullptr, flags, s)) != QG_OK) return st;
+  if ((st = group_centres(c, n, ngroups, dev && eps2 ? c->sink_eps2.p : nullptr, flags, s)) != QG_OK) return st;
   if ((st = value_flags_end(c, s, flags, &fl)) != QG_OK) return st;
   if (fl & kBadPosition) return fail(c, QG_ERR_ARG, "qg_set_sinks: a position is not finite or exceeds 2^100");
   if (fl & kBadEps2) return fail(c, QG_ERR_ARG, "qg_set_sinks: an eps2 is negative, not finite or exceeds 2^100");
@@ -821,9 +840,10 @@ static qg_status set_sources_common(qg_ctx *c, int64_t ns, const double *x, cons
     if ((st = copy_d2d(c, c->pidx, list_idx, cnt, s)) != QG_OK) return st;
     if ((st = copy_d2d(c, c->src_m64, m, ns, s)) != QG_OK) return st;
     cudaError_t e = c->src.reserve(ns);
+    if (e == cudaSuccess) e = c->src_f.reserve(ns);
     if (e != cudaSuccess) return fail(c, QG_ERR_NOMEM, "source allocation");
     if ((st = value_flags_begin(c, s, &flags)) != QG_OK) return st;
-    if (ns) pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, x, c->src_m64.p, c->src.p, flags);
+    if (ns) pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, x, c->src_m64.p, c->src.p, c->src_f.p, flags);
   } else {
     if ((st = upload(c, c->poff, list_off, G + 1, s)) != QG_OK) return st;
     if ((st = upload(c, c->pidx, list_idx, cnt, s)) != QG_OK) return st;
@@ -832,9 +852,11 @@ static qg_status set_sources_common(qg_ctx *c, int64_t ns, const double *x, cons
     if ((st = upload(c, c->stage_x, x, 3 * ns, s)) != QG_OK) return st;
     if ((st = upload(c, c->src_m64, m, ns, s)) != QG_OK) return st;
     cudaError_t e = c->src.reserve(ns);
+    if (e == cudaSuccess) e = c->src_f.reserve(ns);
     if (e != cudaSuccess) return fail(c, QG_ERR_NOMEM, "source allocation");
     if ((st = value_flags_begin(c, s, &flags)) != QG_OK) return st;
-    if (ns) pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, c->stage_x.p, c->src_m64.p, c->src.p, flags);
+    if (ns)
+      pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, c->stage_x.p, c->src_m64.p, c->src.p, c->src_f.p, flags);
   }
   int fl = 0;
   if ((st = value_flags_end(c, s, flags, &fl)) != QG_OK) return st;
@@ -887,8 +909,8 @@ static qg_status set_cells_common(qg_ctx *c, int64_t nc, const double *com, cons
     if (h[G] > 0 && !list_idx) return fail(c, QG_ERR_ARG, "qg_set_cells: list_idx is NULL");
   }
   const int64_t cnt = h[G];
-  if (c->cell_pm.reserve(nc) != cudaSuccess || c->cell_q.reserve(2 * nc) != cudaSuccess ||
-      c->cell_q64.reserve(6 * nc) != cudaSuccess)
+  if (c->cell_pm.reserve(nc) != cudaSuccess || c->cell_f.reserve(nc) != cudaSuccess ||
+      c->cell_q.reserve(2 * nc) != cudaSuccess || c->cell_q64.reserve(6 * nc) != cudaSuccess)
     return fail(c, QG_ERR_NOMEM, "cell allocation");
   if (dev) {
     if ((st = copy_d2d(c, c->coff, list_off, G + 1, s)) != QG_OK) return st;
@@ -896,8 +918,8 @@ static qg_status set_cells_common(qg_ctx *c, int64_t nc, const double *com, cons
     if ((st = copy_d2d(c, c->cell_m64, m, nc, s)) != QG_OK) return st;
     if ((st = value_flags_begin(c, s, &flags)) != QG_OK) return st;
     if (nc)
-      pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, com, c->cell_m64.p, q, c->cell_pm.p, c->cell_q.p,
-                                                           c->cell_q64.p, flags);
+      pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, com, c->cell_m64.p, q, c->cell_pm.p, c->cell_f.p,
+                                                           c->cell_q.p, c->cell_q64.p, flags);
   } else {
     if ((st = upload(c, c->coff, list_off, G + 1, s)) != QG_OK) return st;
     if ((st = upload(c, c->cidx, list_idx, cnt, s)) != QG_OK) return st;
@@ -909,7 +931,8 @@ static qg_status set_cells_common(qg_ctx *c, int64_t nc, const double *com, cons
     if ((st = value_flags_begin(c, s, &flags)) != QG_OK) return st;
     if (nc)
       pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, c->stage_x.p, c->cell_m64.p, c->cell_q64.p,
-                                                           c->cell_pm.p, c->cell_q.p, c->cell_q64.p, flags);
+                                                           c->cell_pm.p, c->cell_f.p, c->cell_q.p, c->cell_q64.p,
+                                                           flags);
   }
   int fl = 0;
   if ((st = value_flags_end(c, s, flags, &fl)) != QG_OK) return st;
@@ -1205,7 +1228,8 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
   if ((st = upload(c, c->stage_x, cell_com, 3 * nc, ci_s)) != QG_OK) return st;
   if ((st = upload(c, c->cell_m64, cell_m, nc, ci_s)) != QG_OK) return st;
   if (c->cell_pm.reserve(nc) != cudaSuccess || c->cell_q.reserve(2 * nc) != cudaSuccess ||
-      c->cell_q64.reserve(6 * nc) != cudaSuccess || c->src.reserve(ns) != cudaSuccess)
+      c->cell_q64.reserve(6 * nc) != cudaSuccess || c->src.reserve(ns) != cudaSuccess ||
+      c->src_f.reserve(ns) != cudaSuccess || c->cell_f.reserve(nc) != cudaSuccess)
     return fail(c, QG_ERR_NOMEM, "source or cell allocation");
   if ((st = upload(c, c->cell_q64, cell_q, 6 * nc, ci_s)) != QG_OK) return st;
   QG_CUDA(c, cudaEventRecord(c->inputs_ready, ci_s));
@@ -1237,16 +1261,17 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
   // input values are checked into the first chunk's flag (the kernels below
   // still run on them, reading nothing out of bounds; the call then fails)
   int *vflags = c->scratch.p + 2 * kBuckets + 1;
-  if ((st = group_centres(c, G, nullptr, vflags, s)) != QG_OK) {
+  if ((st = group_centres(c, n, G, nullptr, vflags, s)) != QG_OK) {
     cudaStreamSynchronize(ci_s);
     return st;
   }
   if (ns)
     pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, same_x ? c->sink_x.p : c->stage_src.p, c->src_m64.p,
-                                                      c->src.p, vflags);
+                                                      c->src.p, c->src_f.p, vflags);
   if (nc)
     pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, c->stage_x.p, c->cell_m64.p, c->cell_q64.p,
-                                                         c->cell_pm.p, c->cell_q.p, c->cell_q64.p, vflags);
+                                                         c->cell_pm.p, c->cell_f.p, c->cell_q.p, c->cell_q64.p,
+                                                         vflags);
   QG_CUDA(c, cudaGetLastError());
   QG_CUDA(c, cudaEventRecord(c->ev[0], s));
   // ---- in place: lists and results in page-locked memory the device reads

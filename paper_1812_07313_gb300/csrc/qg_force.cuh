@@ -79,6 +79,29 @@ __device__ __forceinline__ Real cvt_off(double v) {
   }
 }
 
+// Group centre for the staging: FP64 (x, y, z) and, for the centred FP32
+// kernels, the same centre as float pairs.
+struct Centre {
+  double x, y, z;
+  float hx, hy, hz, lx, ly, lz;
+};
+
+// Centred offset of an entry: FP64 subtraction, then rounded to Real ...
+template <typename Real>
+__device__ __forceinline__ void centred(const PosMass &v, const Centre &c, Real &dx, Real &dy, Real &dz) {
+  dx = cvt_off<Real, 0>(v.x - c.x);
+  dy = cvt_off<Real, 1>(v.y - c.y);
+  dz = cvt_off<Real, 2>(v.z - c.z);
+}
+// ... or from float pairs: (hi - hi_c) + (lo - lo_c), the same operations for
+// a sink and for its own list entry, so that its self pair has offset 0
+template <typename Real>
+__device__ __forceinline__ void centred(const PosMassF &v, const Centre &c, Real &dx, Real &dy, Real &dz) {
+  dx = (v.hx - c.hx) + (v.lx - c.lx);
+  dy = (v.hy - c.hy) + (v.ly - c.ly);
+  dz = (v.hz - c.hz) + (v.lz - c.lz);
+}
+
 // One source particle on one sink: Eq. 4 and its gradient.  13 Real ops + 1 rsqrt.
 template <typename Real, bool GUARD>
 __device__ __forceinline__ void mono_pair(Real dx, Real dy, Real dz, Real m, Real e2,
@@ -307,6 +330,9 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
     force_kernel(const ForceParams p) {
   constexpr bool PAIRED = FORM == kSinkPaired;
   constexpr bool EPAIR = FORM == kEntryPaired;
+  // centred FP32 kernels centre sinks and entries from their float-pair
+  // records; the all-FP64 kernel from the FP64 positions
+  constexpr bool FF = sizeof(Real) == 4 && CENTRED;
   static_assert(!PAIRED || (sizeof(Real) == 4 && R % 2 == 0), "paired arithmetic: FP32, even R");
   static_assert(!EPAIR || (sizeof(Real) == 4 && CENTRED), "entry-paired arithmetic: FP32 centred");
   static_assert(!INPLACE || !PAIRED, "in place: scalar or entry-paired form");
@@ -383,11 +409,15 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
 
     // ---- 1. group centre: the bounding-box centre of the sinks, computed
     // once when the sinks were set (group_centre_kernel)
-    double cx = 0.0, cy = 0.0, cz = 0.0;
-    if (CENTRED) {
-      cx = p.gcentre[3 * g];
-      cy = p.gcentre[3 * g + 1];
-      cz = p.gcentre[3 * g + 2];
+    Centre cc{};
+    if constexpr (FF) {
+      const PosMassF cf = p.gcentre_f[g];
+      cc.hx = cf.hx; cc.hy = cf.hy; cc.hz = cf.hz;
+      cc.lx = cf.lx; cc.ly = cf.ly; cc.lz = cf.lz;
+    } else if (CENTRED) {
+      cc.x = p.gcentre[3 * g];
+      cc.y = p.gcentre[3 * g + 1];
+      cc.z = p.gcentre[3 * g + 2];
     }
 
     const int64_t gp0 = p.plist_off[g], np_g = p.plist_off[g + 1] - gp0;
@@ -402,14 +432,21 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
       __syncthreads();  // previous chunk's readers of sink_s / acc64 are done
       for (int i = tid; i < nch; i += NT) {
         const int64_t si = s0 + sb + i;
-        const double *xi = p.sink_x + 3 * si;
         // softening: the per-sink array is float already; the global value
         // was rounded to float on the host (FP32) or is used as given (FP64)
         Real e2;
         if constexpr (sizeof(Real) == 4) e2 = p.sink_eps2 ? p.sink_eps2[si] : p.eps2_all_f;
         else e2 = p.sink_eps2 ? (double)p.sink_eps2[si] : p.eps2_all;
-        sink_s[i] = RT<Real>::make4(RT<Real>::cvt(xi[0] - cx), RT<Real>::cvt(xi[1] - cy),
-                                    RT<Real>::cvt(xi[2] - cz), e2);
+        Real dx, dy, dz;
+        if constexpr (FF) {
+          centred<Real>(p.sink_f[si], cc, dx, dy, dz);
+        } else {
+          const double *xi = p.sink_x + 3 * si;
+          dx = RT<Real>::cvt(xi[0] - cc.x);
+          dy = RT<Real>::cvt(xi[1] - cc.y);
+          dz = RT<Real>::cvt(xi[2] - cc.z);
+        }
+        sink_s[i] = RT<Real>::make4(dx, dy, dz, e2);
       }
       __syncthreads();
 
@@ -536,10 +573,10 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
       for (int64_t base = p0; base < p1; base += TK) {
         const int cnt = (int)min((int64_t)TK, p1 - base);
         __syncthreads();  // the previous tile's readers are done
-        auto put_p = [&](int t, const PosMass &v, int j) {
+        auto put_p = [&](int t, const auto &v, int j) {
           const Real m = sizeof(Real) == 4 ? (Real)v.m : (Real)p.src_m64[j];
-          const Real dx = cvt_off<Real, 0>(v.x - cx), dy = cvt_off<Real, 1>(v.y - cy),
-                     dz = cvt_off<Real, 2>(v.z - cz);
+          Real dx, dy, dz;
+          centred<Real>(v, cc, dx, dy, dz);
           if constexpr (PAIRED) {
             tP0[t] = make_float4(dx, dx, dy, dy);
             tP1[t] = make_float4(dz, dz, m, m);
@@ -564,15 +601,13 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
               j0 = first ? pf0 : p.plist_idx[base + t0];
               j1 = t1 < cnt ? (first ? pf1 : p.plist_idx[base + t1]) : j0;
             }
-            const PosMass v0 = p.src[j0];
-            const PosMass v1 = p.src[j1];
-            const float dx0 = cvt_off<float, 0>(v0.x - cx), dy0 = cvt_off<float, 1>(v0.y - cy),
-                        dz0 = cvt_off<float, 2>(v0.z - cz);
+            const PosMassF v0 = p.src_f[j0];
+            const PosMassF v1 = p.src_f[j1];
+            float dx0, dy0, dz0;
+            centred<float>(v0, cc, dx0, dy0, dz0);
             float dx1 = kPadFar, dy1 = kPadFar, dz1 = kPadFar, m1 = 0.f;
             if (t1 < cnt) {
-              dx1 = cvt_off<float, 0>(v1.x - cx);
-              dy1 = cvt_off<float, 1>(v1.y - cy);
-              dz1 = cvt_off<float, 2>(v1.z - cz);
+              centred<float>(v1, cc, dx1, dy1, dz1);
               m1 = v1.m;
             }
             tE0[u] = make_float4(dx0, dx1, dy0, dy1);
@@ -594,16 +629,24 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
               j0 = keep_index(j0, p.n_src, p.plist_keep + base + t, p.bad);
               j1 = t1 < cnt ? keep_index(j1, p.n_src, p.plist_keep + base + t1, p.bad) : j0;
             }
-            const PosMass v0 = p.src[j0];
-            const PosMass v1 = p.src[j1];
-            put_p(t, v0, j0);
-            if (t1 < cnt) put_p(t1, v1, j1);
+            if constexpr (FF) {
+              const PosMassF v0 = p.src_f[j0];
+              const PosMassF v1 = p.src_f[j1];
+              put_p(t, v0, j0);
+              if (t1 < cnt) put_p(t1, v1, j1);
+            } else {
+              const PosMass v0 = p.src[j0];
+              const PosMass v1 = p.src[j1];
+              put_p(t, v0, j0);
+              if (t1 < cnt) put_p(t1, v1, j1);
+            }
           }
         } else {
           for (int t = tid; t < cnt; t += NT) {
             int j = INPLACE ? ahead(p.plist_idx, base, t) : t == tid ? pf0 : (t == tid + NT ? pf1 : p.plist_idx[base + t]);
             if (keep) j = keep_index(j, p.n_src, p.plist_keep + base + t, p.bad);
-            put_p(t, p.src[j], j);
+            if constexpr (FF) put_p(t, p.src_f[j], j);
+            else put_p(t, p.src[j], j);
           }
         }
         if (base + TK < p1) prefetch(p.plist_idx, base + TK, p1);
@@ -652,10 +695,10 @@ QG_UNROLL(QG_EP_UNROLL)
       for (int64_t base = c0; base < c1; base += TK) {
         const int cnt = (int)min((int64_t)TK, c1 - base);
         __syncthreads();  // the previous tile's readers are done
-        auto put_c = [&](int t, const PosMass &v, int j, float4 q0, float4 q1) {
+        auto put_c = [&](int t, const auto &v, int j, float4 q0, float4 q1) {
           const Real m = sizeof(Real) == 4 ? (Real)v.m : (Real)p.cell_m64[j];
-          const Real dx = cvt_off<Real, 0>(v.x - cx), dy = cvt_off<Real, 1>(v.y - cy),
-                     dz = cvt_off<Real, 2>(v.z - cz);
+          Real dx, dy, dz;
+          centred<Real>(v, cc, dx, dy, dz);
           if constexpr (PAIRED) {
             tP0[t] = make_float4(dx, dx, dy, dy);
             tP1[t] = make_float4(dz, dz, m, m);
@@ -694,8 +737,8 @@ QG_UNROLL(QG_EP_UNROLL)
               j0 = first ? pf0 : p.clist_idx[base + t0];
               j1 = t1 < cnt ? (first ? pf1 : p.clist_idx[base + t1]) : j0;
             }
-            const PosMass v0 = p.cell_pm[j0];
-            const PosMass v1 = p.cell_pm[j1];
+            const PosMassF v0 = p.cell_f[j0];
+            const PosMassF v1 = p.cell_f[j1];
             float4 a0 = zero4, b0 = zero4, a1 = zero4, b1 = zero4;
             if (QUAD) {
               a0 = p.cell_q[2 * j0];
@@ -703,13 +746,11 @@ QG_UNROLL(QG_EP_UNROLL)
               a1 = p.cell_q[2 * j1];
               b1 = p.cell_q[2 * j1 + 1];
             }
-            const float dx0 = cvt_off<float, 0>(v0.x - cx), dy0 = cvt_off<float, 1>(v0.y - cy),
-                        dz0 = cvt_off<float, 2>(v0.z - cz);
+            float dx0, dy0, dz0;
+            centred<float>(v0, cc, dx0, dy0, dz0);
             float dx1 = kPadFar, dy1 = kPadFar, dz1 = kPadFar, m1 = 0.f;
             if (t1 < cnt) {
-              dx1 = cvt_off<float, 0>(v1.x - cx);
-              dy1 = cvt_off<float, 1>(v1.y - cy);
-              dz1 = cvt_off<float, 2>(v1.z - cz);
+              centred<float>(v1, cc, dx1, dy1, dz1);
               m1 = v1.m;
             } else {
               a1 = b1 = zero4;
@@ -738,20 +779,29 @@ QG_UNROLL(QG_EP_UNROLL)
               j0 = keep_index(j0, p.n_cell, p.clist_keep + base + t, p.bad);
               j1 = t1 < cnt ? keep_index(j1, p.n_cell, p.clist_keep + base + t1, p.bad) : j0;
             }
-            const PosMass v0 = p.cell_pm[j0];
-            const PosMass v1 = p.cell_pm[j1];
             const bool fq = QUAD && sizeof(Real) == 4;
             const float4 a0 = fq ? p.cell_q[2 * j0] : zero4, b0 = fq ? p.cell_q[2 * j0 + 1] : zero4;
             const float4 a1 = fq ? p.cell_q[2 * j1] : zero4, b1 = fq ? p.cell_q[2 * j1 + 1] : zero4;
-            put_c(t, v0, j0, a0, b0);
-            if (t1 < cnt) put_c(t1, v1, j1, a1, b1);
+            if constexpr (FF) {
+              const PosMassF v0 = p.cell_f[j0];
+              const PosMassF v1 = p.cell_f[j1];
+              put_c(t, v0, j0, a0, b0);
+              if (t1 < cnt) put_c(t1, v1, j1, a1, b1);
+            } else {
+              const PosMass v0 = p.cell_pm[j0];
+              const PosMass v1 = p.cell_pm[j1];
+              put_c(t, v0, j0, a0, b0);
+              if (t1 < cnt) put_c(t1, v1, j1, a1, b1);
+            }
           }
         } else {
           for (int t = tid; t < cnt; t += NT) {
             int j = INPLACE ? ahead(p.clist_idx, base, t) : t == tid ? pf0 : (t == tid + NT ? pf1 : p.clist_idx[base + t]);
             if (keep) j = keep_index(j, p.n_cell, p.clist_keep + base + t, p.bad);
             const bool fq = QUAD && sizeof(Real) == 4;
-            put_c(t, p.cell_pm[j], j, fq ? p.cell_q[2 * j] : zero4, fq ? p.cell_q[2 * j + 1] : zero4);
+            const float4 qa = fq ? p.cell_q[2 * j] : zero4, qb = fq ? p.cell_q[2 * j + 1] : zero4;
+            if constexpr (FF) put_c(t, p.cell_f[j], j, qa, qb);
+            else put_c(t, p.cell_pm[j], j, qa, qb);
           }
         }
         if (base + TK < c1) prefetch(p.clist_idx, base + TK, c1);

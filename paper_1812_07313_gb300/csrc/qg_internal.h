@@ -15,6 +15,32 @@ struct __align__(32) PosMass {
   float pad;
 };
 
+// The same entry for the centred FP32 kernels: every coordinate as a pair of
+// floats, hi = the float nearest x and lo = the float nearest x - hi (about
+// 48 bits of x together), and the mass as float: one aligned 32-byte sector.
+// Centring on c = (hi_c, lo_c) is then (hi - hi_c) + (lo - lo_c): three FP32
+// adds, exact in its first step wherever the entry is near the centre.
+struct __align__(32) PosMassF {
+  float hx, hy, hz, m;
+  float lx, ly, lz, pad;
+};
+
+// x as hi + lo (round to nearest, both on the host and on the GPU).
+__host__ __device__ inline void split_f32x2(double x, float &hi, float &lo) {
+  hi = (float)x;
+  lo = (float)(x - (double)hi);
+}
+
+__host__ __device__ inline PosMassF make_posmassf(double x, double y, double z, float m) {
+  PosMassF r;
+  split_f32x2(x, r.hx, r.lx);
+  split_f32x2(y, r.hy, r.ly);
+  split_f32x2(z, r.hz, r.lz);
+  r.m = m;
+  r.pad = 0.f;
+  return r;
+}
+
 // Largest magnitude of a position coordinate any entry point accepts (and of
 // a mass, a quadrupole component or a softening in the allocation-free
 // entry point): every value the kernels round with f64_to_f32_rn below,
@@ -92,6 +118,11 @@ struct ForceParams {
   float eps2_all_f;  // eps2_all rounded to float on the host (FP32 kernels)
   const int64_t *group_off;
   const double *gcentre;  // [G][3] centre of each group's bounding box (centred kernels)
+  // the same centres, sinks, sources and cells as float pairs (centred FP32 kernels)
+  const PosMassF *gcentre_f;
+  const PosMassF *sink_f;
+  const PosMassF *src_f;
+  const PosMassF *cell_f;
   const PosMass *src;
   const double *src_m64;
   const int64_t *plist_off;
