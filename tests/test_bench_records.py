@@ -11,7 +11,13 @@ if ROOT not in sys.path:
 
 import bench  # noqa: E402
 
-LAUNCH = {"sinks_per_thread": 4, "warps_per_group": 4, "tile_j": 512, "arith": "scalar f32"}
+FORMS = {"x1": "scalar f32", "x2": "paired f32x2", "xe": "entry-paired f32x2"}
+
+
+def _launch(shape):
+    """The bench line's launch record for a record's 'R,W,T,form' key."""
+    R, W, T, form = shape.split(",")
+    return {"sinks_per_thread": int(R), "warps_per_group": int(W), "tile_j": int(T), "arith": FORMS[form]}
 
 
 def _records():
@@ -33,14 +39,16 @@ def _records():
 def test_a_record_is_used_only_for_its_workload_shape_and_sources(monkeypatch):
     recs = _records()
     assert recs and all({"workload", "launch", "kernel_hash", "bytes_per_launch"} <= set(r) for r in recs)
-    r = next(r for r in recs if r["launch"] == "4,4,512,x1")
+    r = recs[0]
+    launch = _launch(r["launch"])
+    other_form = "scalar f32" if launch["arith"] != "scalar f32" else "entry-paired f32x2"
     monkeypatch.setattr(bench, "kernel_hash", lambda: r["kernel_hash"])
-    assert bench._recorded_traffic(r["workload"], LAUNCH) == float(r["bytes_per_launch"])
-    assert bench._recorded_traffic("plummer_4m", LAUNCH) is None            # another workload
-    assert bench._recorded_traffic(r["workload"], dict(LAUNCH, tile_j=1024)) is None   # another shape
-    assert bench._recorded_traffic(r["workload"], dict(LAUNCH, arith="paired f32x2")) is None
+    assert bench._recorded_traffic(r["workload"], launch) == float(r["bytes_per_launch"])
+    assert bench._recorded_traffic("plummer_4m", launch) is None            # another workload
+    assert bench._recorded_traffic(r["workload"], dict(launch, tile_j=1024)) is None   # another shape
+    assert bench._recorded_traffic(r["workload"], dict(launch, arith=other_form)) is None   # another form
     monkeypatch.setattr(bench, "kernel_hash", lambda: "0" * 12)
-    assert bench._recorded_traffic(r["workload"], LAUNCH) is None            # other sources
+    assert bench._recorded_traffic(r["workload"], launch) is None            # other sources
 
 
 def test_the_source_hash_ignores_comments_but_not_code(tmp_path, monkeypatch):
