@@ -94,8 +94,9 @@ def parse():
                     help="skip timing the tree build, moments, groups and walk on the GPU (whole step on the device)")
     ap.add_argument("--gpu-tree", action="store_true", help=argparse.SUPPRESS)  # the default; kept for old commands
     ap.add_argument("--launch", default=None,
-                    help="R,W,T[,x1|x2|xe[,F]]: fixed sinks/thread, warps/CTA, tile (and scalar, sink-paired or "
-                         "entry-paired FP32, and entries between FP64 folds) instead of the autotuner (profiling)")
+                    help="R,W,T[,x1|x2|xe[,F]]: fixed sinks/thread (4a: chosen per item up to 4), warps/CTA, tile "
+                         "(and scalar, sink-paired or entry-paired FP32, and entries between FP64 folds) instead of "
+                         "the autotuner (profiling)")
     return ap.parse_args()
 
 
@@ -352,8 +353,9 @@ def roofline_of(i_pp, i_pc, force_ms, clocks, n_sm, stats, traffic=None):
             "peak_basis": "FP32 lane-instructions/s = %d SMs x 128 x median SM clock %.0f MHz under load "
                           "(at the 2070 MHz maximum: %.1f Tinst/s, frac %.3f)"
                           % (n_sm, sm_mhz, peak_max, achieved / peak_max),
-            "kernel": "force_kernel<float,R=%d,quad,%s>, %d threads, tile %d" % (
-                stats["sinks_per_thread"], ARITH_NAMES[stats["paired"]], stats["block"], stats["tile_j"]),
+            "kernel": "force_kernel<float,R=%s,quad,%s>, %d threads, tile %d" % (
+                ("1..%d per item" if stats.get("sinks_adaptive") else "%d") % stats["sinks_per_thread"],
+                ARITH_NAMES[stats["paired"]], stats["block"], stats["tile_j"]),
             "force_kernel_ms": force_ms}
 
 
@@ -505,7 +507,8 @@ def config_record(torch, qgrav, name, steps, warmup, stream, flush, n_sm, local_
                 "interactions": {"i_pp": i_pp, "i_pc": i_pc}, "groups": int(st["n_groups"]),
                 "launch": {"sinks_per_thread": st["sinks_per_thread"], "warps_per_group": st["warps_per_group"],
                            "tile_j": st["tile_j"], "grid": st["grid"], "block": st["block"],
-                           "arith": ARITH_NAMES[st["paired"]], "autotune_s": t_tune},
+                           "arith": ARITH_NAMES[st["paired"]], "sinks_adaptive": st["sinks_adaptive"],
+                           "autotune_s": t_tune},
                 "roofline": roofline_of(i_pp, i_pc, float(force_ms.mean()), clocks, n_sm, st),
                 "clocks": clocks})
     if batching:
@@ -564,12 +567,13 @@ def run_ours(args, rank, world, local_rank):
     t_tune = time.perf_counter()
     if args.launch:
         parts = args.launch.split(",")
-        R, W, T = (int(v) for v in parts[:3])
+        adapt = parts[0].endswith("a")  # e.g. 4a: sinks per thread chosen per item, up to 4
+        R, W, T = int(parts[0].rstrip("a")), int(parts[1]), int(parts[2])
         arith = {"x1": qgrav.QG_ARITH_SCALAR, "x2": qgrav.QG_ARITH_PAIRED,
                  "xe": qgrav.QG_ARITH_ENTRY_PAIRED}[parts[3]] if len(parts) > 3 else 0
         flush_j = int(parts[4]) if len(parts) > 4 else 0
         ctx.set_options(qgrav.Options(sinks_per_thread=R, warps_per_group=W, tile_j=T, arith=arith,
-                                      flush_j=flush_j))
+                                      flush_j=flush_j, sinks_adaptive=int(adapt)))
     else:
         ctx.qg_autotune(stream.cuda_stream, reps=3)
     t_tune = time.perf_counter() - t_tune
@@ -584,7 +588,7 @@ def run_ours(args, rank, world, local_rank):
     st = ctx.qg_get_stats()
     launch.update({"sinks_per_thread": st["sinks_per_thread"], "warps_per_group": st["warps_per_group"],
                    "tile_j": st["tile_j"], "grid": st["grid"], "block": st["block"],
-                   "arith": ARITH_NAMES[st["paired"]]})
+                   "arith": ARITH_NAMES[st["paired"]], "sinks_adaptive": st["sinks_adaptive"]})
 
     if world > 1:
         dist.barrier()
@@ -639,7 +643,8 @@ def run_ours(args, rank, world, local_rank):
     # the chosen launch shape, for the legs below
     chosen = qgrav.Options(sinks_per_thread=launch["sinks_per_thread"], warps_per_group=launch["warps_per_group"],
                            tile_j=launch["tile_j"],
-                           arith=ARITH_CODES[launch.get("arith", "scalar f32")])
+                           arith=ARITH_CODES[launch.get("arith", "scalar f32")],
+                           sinks_adaptive=launch.get("sinks_adaptive", 0))
     if solo and not args.no_split_compare and not args.launch:
         sc = {args.workload: dict(split_compare(torch, qgrav, ctx, chosen, stream, flush),
                                   max_item_over_cta_share=item_share(tr, L, launch["grid"]))}
@@ -943,8 +948,8 @@ def _recorded_traffic(workload, launch):
                 rec[k.strip()] = v.strip()
     if rec:
         recs.append(rec)
-    shape = "%d,%d,%d,%s" % (launch["sinks_per_thread"], launch["warps_per_group"], launch["tile_j"],
-                             ARITH_TAGS[launch.get("arith", "scalar f32")])
+    shape = "%d%s,%d,%d,%s" % (launch["sinks_per_thread"], "a" if launch.get("sinks_adaptive") else "",
+                               launch["warps_per_group"], launch["tile_j"], ARITH_TAGS[launch.get("arith", "scalar f32")])
     for r in recs:
         if r.get("workload") == workload and r.get("kernel_hash") == kernel_hash() and r.get("launch") == shape:
             try:

@@ -48,7 +48,10 @@ typedef struct {
   int n_crit;     /* sink group size bound (>= 1) */
   int leaf_max;   /* tree leaf size bound (>= 1) */
   int expansion;  /* QG_QUAD or QG_MONO */
-  int autotune;   /* nonzero: qg_autotune the force launch on the first force evaluation */
+  int autotune;   /* nonzero: qg_autotune the force launch on the first force
+                     evaluation, and again whenever the step's list entries
+                     differ from those it was last tuned on by more than a
+                     quarter */
 } qg_sim_params;
 
 /* Device time (CUDA events) of the parts of the last step, milliseconds,
@@ -58,6 +61,7 @@ typedef struct {
   float build_ms, walk_ms, force_ms, integrate_ms;
   double wall_ms;
   int64_t groups, n_plist, n_clist, i_pp, i_pc;
+  int64_t retunes;  /* force-launch tunings so far (autotune) */
 } qg_sim_times;
 
 /* A simulation with the parameters of Sec. 5's runs (theta, eps, n_crit,

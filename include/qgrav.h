@@ -90,10 +90,13 @@ enum { QG_ARITH_DEFAULT = 0, QG_ARITH_SCALAR = 1, QG_ARITH_PAIRED = 2, QG_ARITH_
 
 /*
  * Options of a context.  A 0 in tile_j, warps_per_group, sinks_per_thread,
- * flush_j or arith selects a FIXED default (tile 256, 4 warps, 4 sinks per
- * thread, fold every 256 entries, scalar FP32), not a tuned one: the tuning
- * call is qg_autotune, which times the supported shapes on the inputs set
- * and stores the fastest in the context.  The paper has no counterpart (its
+ * flush_j or arith selects a FIXED default, not a tuned one: tile 256, 4
+ * sinks per thread, fold every 256 entries, and for QG_FP32_CENTRED the
+ * entry-paired form with 2 warps (with 8 sinks per thread, and for the other
+ * precisions, the scalar form with 4 warps) -- the shape the autotuner picks
+ * on most of the workloads measured.  The tuning call is qg_autotune, which
+ * times the supported shapes on the inputs set and stores the fastest in the
+ * context.  The paper has no counterpart (its
  * kernel has one fixed shape, 4 i-particles x 2 j-cells per AVX2 iteration,
  * List 2); precision and expansion select the variants compared in Secs. 4-5.
  */
@@ -108,11 +111,12 @@ typedef struct {
                            0 = default; supported: 2, 4, 8                  */
   int flush_j;          /* FP32 partials are folded into FP64 after at most
                            this many list entries per thread; 0 = 256       */
-  int arith;            /* QG_FP32_CENTRED only: QG_ARITH_SCALAR (the
-                           default, 0), QG_ARITH_PAIRED (two sinks per
-                           float2 register, f32x2 FMA instructions) or
-                           QG_ARITH_ENTRY_PAIRED (two list entries per
-                           float2 register; sinks_per_thread 2 or 4)        */
+  int arith;            /* QG_FP32_CENTRED only: QG_ARITH_SCALAR,
+                           QG_ARITH_PAIRED (two sinks per float2 register,
+                           f32x2 FMA instructions) or QG_ARITH_ENTRY_PAIRED
+                           (two list entries per float2 register;
+                           sinks_per_thread 2 or 4; the default, 0, up to 4
+                           sinks per thread)                                 */
   int split_j;          /* long lists cut into work items (Sec. 3.4's group x
                            list, split for load balance): 0 = never (the
                            default); k > 0 = every list of more than k
@@ -124,6 +128,11 @@ typedef struct {
                            per sink; the part that completes a group adds
                            them in a fixed order (bitwise repeatable).
                            qg_evaluate_host never splits.                   */
+  int sinks_adaptive;   /* QG_FP32_CENTRED, scalar or entry-paired form: 1 =
+                           every work item runs at the number of sinks per
+                           thread from 1 to 4 that suits its group's size and
+                           list length (sinks_per_thread then 0 or 4); 0 =
+                           sinks_per_thread for every item (the default)   */
 } qg_options;
 
 typedef struct {
@@ -142,6 +151,8 @@ typedef struct {
   int64_t n_items;            /* work items of the last qg_run's queue (the
                                  groups, or groups and parts of split lists) */
   int64_t n_split;            /* groups whose lists were split               */
+  int32_t sinks_adaptive;     /* 1 if sinks per thread are chosen per item   */
+  int32_t reserved;
 } qg_stats;
 
 /* Create a context on CUDA device `device`.  opt may be NULL (defaults).
@@ -221,7 +232,8 @@ qg_status qg_run(qg_ctx *ctx, void *cuda_stream);
  * No counterpart in the paper (its kernel has one fixed shape, List 2).
  * Autotuner: times every supported launch shape (sinks_per_thread x
  * warps_per_group x tile_j, in the scalar and the entry-paired FP32 forms for
- * QG_FP32_CENTRED) of the current precision / expansion on the inputs
+ * QG_FP32_CENTRED, each at 4 sinks per thread also with sinks_adaptive) of
+ * the current precision / expansion on the inputs
  * currently set -- each shape once (the force kernel's device time, CUDA
  * events), then the four fastest again with one warm-up and `reps` timed
  * runs each -- and keeps the fastest as the context's options.  The

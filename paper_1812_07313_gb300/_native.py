@@ -31,6 +31,7 @@ CUDA_ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # denormals (one SFU instruction per reciprocal square root, no fix-up path).
 CUDA_FLAGS = {"qg_force_f32.cu": ["-ftz=true"], "qg_force_f32x2.cu": ["-ftz=true"],
               "qg_force_f32ep.cu": ["-ftz=true"], "qg_noalloc.cu": ["-ftz=true"],
+              "qg_force_adapt.cu": ["-ftz=true"], "qg_force_inplace_adapt.cu": ["-ftz=true"],
               "qg_force_inplace.cu": ["-ftz=true"],
               # the GPU tree reproduces the host builder bit for bit: no FMA
               # contraction on either side

@@ -302,6 +302,12 @@ bool valid_options(const qg_options &o, std::string &why) {
   if (o.flush_j < 0) { why = "flush_j"; return false; }
   if (o.arith < QG_ARITH_DEFAULT || o.arith > QG_ARITH_ENTRY_PAIRED) { why = "arith"; return false; }
   if (o.split_j < -1) { why = "split_j"; return false; }
+  if (o.sinks_adaptive != 0 && o.sinks_adaptive != 1) { why = "sinks_adaptive"; return false; }
+  if (o.sinks_adaptive &&
+      (o.precision != QG_FP32_CENTRED || o.arith == QG_ARITH_PAIRED || (o.sinks_per_thread && o.sinks_per_thread != 4))) {
+    why = "sinks_adaptive (FP32 centred, scalar or entry-paired, up to 4 sinks per thread)";
+    return false;
+  }
   return true;
 }
 
@@ -352,12 +358,17 @@ qg_status choose_kernel(qg_ctx *c) {
   const bool guard = !c->eps_positive;
   int R = o.sinks_per_thread ? o.sinks_per_thread : 4;
   if (fp64) R = 2;
-  int warps = o.warps_per_group ? o.warps_per_group : 4;
+  const bool paired = o.precision == QG_FP32_CENTRED && o.arith == QG_ARITH_PAIRED;
+  // the entry-paired form is the default of the centred FP32 precision (up to
+  // 4 sinks per thread), the scalar form otherwise
+  const bool epaired = o.precision == QG_FP32_CENTRED &&
+                       (o.arith == QG_ARITH_ENTRY_PAIRED || (o.arith == QG_ARITH_DEFAULT && R <= 4));
+  int warps = o.warps_per_group ? o.warps_per_group : (epaired ? 2 : 4);
   if (R >= 8 && warps > 4) warps = 4;
   const int nt = 32 * warps;
-  const bool paired = o.precision == QG_FP32_CENTRED && o.arith == QG_ARITH_PAIRED;
-  const bool epaired = o.precision == QG_FP32_CENTRED && o.arith == QG_ARITH_ENTRY_PAIRED;
+  const bool adapt = o.sinks_adaptive != 0;
   const void *k = fp64 ? qg::force_kernel_f64(R, quad, guard)
+                  : adapt ? qg::force_kernel_adapt(epaired, quad, guard)
                   : paired ? qg::force_kernel_f32x2(R, quad, guard)
                   : epaired ? qg::force_kernel_f32ep(R, quad, guard)
                             : qg::force_kernel_f32(R, quad, guard, o.precision == QG_FP32_CENTRED);
@@ -371,7 +382,8 @@ qg_status choose_kernel(qg_ctx *c) {
   c->kernel = k;
   c->kernel_inplace = nullptr;
   if (o.precision == QG_FP32_CENTRED && !paired) {
-    const void *ki = qg::force_kernel_inplace(R, quad, guard, epaired);
+    const void *ki = adapt ? qg::force_kernel_inplace_adapt(epaired, quad, guard)
+                           : qg::force_kernel_inplace(R, quad, guard, epaired);
     int per_sm_i = 0;
     if (ki) {
       QG_CUDA(c, cudaFuncSetAttribute(ki, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -394,6 +406,7 @@ qg_status choose_kernel(qg_ctx *c) {
   c->stats.warps_per_group = warps;
   c->stats.flush_j = c->flush;
   c->stats.paired = paired ? 1 : epaired ? 2 : 0;
+  c->stats.sinks_adaptive = adapt ? 1 : 0;
   return QG_OK;
 }
 
@@ -1036,11 +1049,16 @@ qg_status qg_autotune(qg_ctx *c, void *stream, int reps, qg_options *best, float
             o.sinks_per_thread = R;
             o.warps_per_group = W;
             o.tile_j = T;
+            o.sinks_adaptive = 0;
             if (fp32c) o.arith = ai == 0 ? QG_ARITH_ENTRY_PAIRED : QG_ARITH_SCALAR;
             if (base.precision == QG_FP64 && R != 2) continue;
             if (R >= 8 && W > 4) continue;
             if (o.arith == QG_ARITH_ENTRY_PAIRED && R > 4) continue;
             cand.push_back(o);
+            if (fp32c && R == 4) {  // the same shape with sinks per thread chosen per item
+              o.sinks_adaptive = 1;
+              cand.push_back(o);
+            }
           }
     // mean force-kernel time of `runs` graph replays at options o (after
     // `warm` untimed ones); < 0 if the shape does not fit this device

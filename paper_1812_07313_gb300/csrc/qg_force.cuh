@@ -160,6 +160,12 @@ __device__ __forceinline__ void quad_pair(Real dx, Real dy, Real dz, Real m,
 // finite in FP32.
 constexpr float kPadFar = 1.0e15f;
 
+// Throughput of the pair loop at r = 1 ... 4 sinks per thread relative to the
+// FP32 peak, measured on this GPU with the loop alone over a shared-memory
+// tile (quadrupole, entry-paired, 64-thread CTAs, 8 per SM as for the R = 4
+// kernel): the weights of choose_sinks_per_thread.
+constexpr float kLoopEff1 = 0.746f, kLoopEff2 = 0.807f, kLoopEff3 = 0.824f, kLoopEff4 = 0.844f;
+
 struct Pair2 {
   float2 zero, one, mone;
   __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) const { return __ffma2_rn(a, b, c); }
@@ -320,31 +326,26 @@ template <typename Real, int R, int FORM> struct Bounds {
   static constexpr int min_blocks = (R >= 8 || sizeof(Real) == 8 || (FORM != kScalar && R >= 4)) ? 2 : 3;
 };
 
-// INPLACE: the lists are read from host memory (checked and kept as they
-// are read, ForceParams::plist_keep) and the results also written to host
-// memory (ForceParams::a_host), a[] through shared memory so that a warp
-// writes consecutive words.  A separate instantiation, so that the kernel
-// the graph replays carries none of it.
-template <typename Real, int R, bool QUAD, bool GUARD, bool CENTRED, int FORM, bool INPLACE = false>
-__global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R, FORM>::min_blocks)
-    force_kernel(const ForceParams p) {
+// The sink chunks of one work item (group g's sinks [s0, s0 + ni), its list
+// entries [p0, p1) and [c0, c1)) at R sinks per thread: sink staging, list
+// tiles, pair loops, folds, the FP64 merge of the K streams and the outputs
+// (or, for a part of a split list, its partial sums at slot).  Rtile is the R
+// the shared memory was laid out for (the tile follows the FP64 accumulators
+// of Rtile sinks per thread).
+template <typename Real, int R, bool QUAD, bool GUARD, bool CENTRED, int FORM, bool INPLACE>
+__device__ __forceinline__ void evaluate_chunks(const ForceParams &p, unsigned char *smem_raw, const int Rtile,
+                                                const Centre &cc, const int64_t s0, const int ni, const int64_t p0,
+                                                const int64_t p1, const int64_t c0, const int64_t c1, const int part,
+                                                const int64_t slot) {
   constexpr bool PAIRED = FORM == kSinkPaired;
   constexpr bool EPAIR = FORM == kEntryPaired;
-  // centred FP32 kernels centre sinks and entries from their float-pair
-  // records; the all-FP64 kernel from the FP64 positions
   constexpr bool FF = sizeof(Real) == 4 && CENTRED;
-  static_assert(!PAIRED || (sizeof(Real) == 4 && R % 2 == 0), "paired arithmetic: FP32, even R");
-  static_assert(!EPAIR || (sizeof(Real) == 4 && CENTRED), "entry-paired arithmetic: FP32 centred");
-  static_assert(!INPLACE || !PAIRED, "in place: scalar or entry-paired form");
   constexpr int H = R / 2;               // sink pairs per thread (sink-paired form)
   constexpr int NE = EPAIR ? R : 1;      // broadcast sinks per thread (entry-paired form)
+  constexpr bool keep = INPLACE;
   const Pair2 P2{make_float2(p.zero, p.zero), make_float2(p.one, p.one), make_float2(-p.one, -p.one)};
   using V4 = typename RT<Real>::v4;
   using V2 = typename RT<Real>::v2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_item;
-  __shared__ int s_last;  // split lists: this item completed its group's parts
-
   const int NT = blockDim.x;
   const int tid = threadIdx.x;
   const int T = p.tile;
@@ -359,72 +360,20 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
   // Entry-paired form: entries 2u and 2u+1 side by side in pair u,
   // (dx dx' dy dy') (dz dz' -m -m') (q00 q00' q01 q01') (q02 q02' q11 q11')
   // (q12 q12' q22 q22'): 40 bytes per entry, as in the scalar form.
-  V4 *tA = reinterpret_cast<V4 *>(acc64 + 4 * R * NT);
+  double *tile = acc64 + 4 * Rtile * NT;
+  V4 *tA = reinterpret_cast<V4 *>(tile);
   V4 *tB = tA + T;
   V2 *tC = reinterpret_cast<V2 *>(tB + T);
-  float4 *tP0 = reinterpret_cast<float4 *>(acc64 + 4 * R * NT);
+  float4 *tP0 = reinterpret_cast<float4 *>(tile);
   float4 *tP1 = tP0 + T;
   float4 *tQ0 = tP1 + T;
   float4 *tQ1 = tQ0 + T;
   float4 *tQ2 = tQ1 + T;
-  float4 *tE0 = reinterpret_cast<float4 *>(acc64 + 4 * R * NT);
+  float4 *tE0 = reinterpret_cast<float4 *>(tile);
   float4 *tE1 = tE0 + T / 2;
   float4 *tE2 = tE1 + T / 2;
   float4 *tE3 = tE2 + T / 2;
   float4 *tE4 = tE3 + T / 2;
-
-  for (;;) {
-    __syncthreads();  // the previous group is finished with shared memory
-    if (tid == 0) s_item = atomicAdd(p.head, 1);
-    __syncthreads();
-    const int item = s_item;
-    if (item >= p.nitems) break;
-    const int q = p.queue[item];
-    // the work item: a whole group, or one part of a split group's list
-    // (entries [e0, e1) of its particle entries followed by its cell entries)
-    int g = q, part = -1, nparts = 1, ctr = 0;
-    int64_t e0 = 0, e1 = -1, slot = 0;
-    if (p.items) {
-      const Item it = p.items[q];
-      g = it.g;
-      part = it.part;
-      nparts = it.nparts;
-      ctr = it.ctr;
-      e0 = it.e0;
-      e1 = it.e1;
-      slot = it.slot;
-    }
-    const int64_t s0 = p.group_off[g];
-    const int ni = (int)(p.group_off[g + 1] - s0);
-    constexpr bool keep = INPLACE;
-    if (ni <= 0) {
-      if (keep) {  // no sinks: the lists are only checked and kept
-        for (int64_t e = p.plist_off[g] + tid; e < p.plist_off[g + 1]; e += NT)
-          keep_index(p.plist_idx[e], p.n_src, p.plist_keep + e, p.bad);
-        for (int64_t e = p.clist_off[g] + tid; e < p.clist_off[g + 1]; e += NT)
-          keep_index(p.clist_idx[e], p.n_cell, p.clist_keep + e, p.bad);
-      }
-      continue;
-    }
-
-    // ---- 1. group centre: the bounding-box centre of the sinks, computed
-    // once when the sinks were set (group_centre_kernel)
-    Centre cc{};
-    if constexpr (FF) {
-      const PosMassF cf = p.gcentre_f[g];
-      cc.hx = cf.hx; cc.hy = cf.hy; cc.hz = cf.hz;
-      cc.lx = cf.lx; cc.ly = cf.ly; cc.lz = cf.lz;
-    } else if (CENTRED) {
-      cc.x = p.gcentre[3 * g];
-      cc.y = p.gcentre[3 * g + 1];
-      cc.z = p.gcentre[3 * g + 2];
-    }
-
-    const int64_t gp0 = p.plist_off[g], np_g = p.plist_off[g + 1] - gp0;
-    const int64_t gc0 = p.clist_off[g], nc_g = p.clist_off[g + 1] - gc0;
-    if (e1 < 0) e1 = np_g + nc_g;
-    const int64_t p0 = gp0 + min(e0, np_g), p1 = gp0 + min(e1, np_g);
-    const int64_t c0 = gc0 + max(e0 - np_g, (int64_t)0), c1 = gc0 + max(e1 - np_g, (int64_t)0);
 
     // ---- sink chunks of at most R * NT sinks --------------------------------
     for (int sb = 0; sb < ni; sb += R * NT) {
@@ -950,6 +899,139 @@ QG_UNROLL(QG_EP_UNROLL)
           ah[t] = v;
         }
       }
+    }
+
+}
+
+// Sinks per thread for a work item when the kernel chooses it per item (1 to
+// RMAX): the choice that keeps the FMA pipe busiest with useful pairs.  For
+// each r, S = ceil(n/r) sink slots and K = NT/S streams leave S K threads
+// active (whole warps of them issue), each running ceil(L/K) list entries
+// (rounded up to pairs in the entry-paired form) of r sinks; the lane-cycles
+// spent are weighed by the pair loop's throughput at r sinks per thread
+// (isolated-loop measurements on this GPU).  Uniform across the CTA.
+template <int RMAX, bool EPAIR>
+__device__ __forceinline__ int choose_sinks_per_thread(int n, int64_t L, int NT) {
+  constexpr float eff[5] = {1.f, kLoopEff1, kLoopEff2, kLoopEff3, kLoopEff4};
+  int best = RMAX;
+  float best_cost = 0.f;
+  for (int r = RMAX; r >= 1; r--) {
+    const int S = (n + r - 1) / r;
+    if (S > NT && r < RMAX) continue;  // would need more sink chunks than the largest r
+    const int Sc = min(S, NT);
+    const int K = max(NT / Sc, 1);
+    int64_t it = (L + K - 1) / K;
+    if (EPAIR) it = (it + 1) & ~(int64_t)1;
+    const int warps = (min(Sc * K, NT) + 31) / 32;
+    const int chunks = (S + NT - 1) / NT;
+    const float cost = (float)chunks * (float)warps * 32.f * (float)r * (float)it / eff[r];
+    if (r == RMAX || cost < best_cost) {  // ties keep the larger r
+      best = r;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+
+// INPLACE: the lists are read from host memory (checked and kept as they
+// are read, ForceParams::plist_keep) and the results also written to host
+// memory (ForceParams::a_host), a[] through shared memory so that a warp
+// writes consecutive words.  A separate instantiation, so that the kernel
+// the graph replays carries none of it.
+// ADAPT: R is the largest number of sinks per thread, and every work item
+// runs at the number from 1 to R that suits its group's size and list length
+// (choose_sinks_per_thread); shared memory is laid out for R.
+template <typename Real, int R, bool QUAD, bool GUARD, bool CENTRED, int FORM, bool INPLACE = false,
+          bool ADAPT = false>
+__global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R, FORM>::min_blocks)
+    force_kernel(const ForceParams p) {
+  constexpr bool PAIRED = FORM == kSinkPaired;
+  constexpr bool EPAIR = FORM == kEntryPaired;
+  // centred FP32 kernels centre sinks and entries from their float-pair
+  // records; the all-FP64 kernel from the FP64 positions
+  constexpr bool FF = sizeof(Real) == 4 && CENTRED;
+  static_assert(!PAIRED || (sizeof(Real) == 4 && R % 2 == 0), "paired arithmetic: FP32, even R");
+  static_assert(!EPAIR || (sizeof(Real) == 4 && CENTRED), "entry-paired arithmetic: FP32 centred");
+  static_assert(!INPLACE || !PAIRED, "in place: scalar or entry-paired form");
+  static_assert(!ADAPT || (!PAIRED && R == 4), "sinks per thread chosen per item: up to 4, not sink-paired");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  __shared__ int s_last;  // split lists: this item completed its group's parts
+
+  const int NT = blockDim.x;
+  const int tid = threadIdx.x;
+
+  for (;;) {
+    __syncthreads();  // the previous group is finished with shared memory
+    if (tid == 0) s_item = atomicAdd(p.head, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= p.nitems) break;
+    const int q = p.queue[item];
+    // the work item: a whole group, or one part of a split group's list
+    // (entries [e0, e1) of its particle entries followed by its cell entries)
+    int g = q, part = -1, nparts = 1, ctr = 0;
+    int64_t e0 = 0, e1 = -1, slot = 0;
+    if (p.items) {
+      const Item it = p.items[q];
+      g = it.g;
+      part = it.part;
+      nparts = it.nparts;
+      ctr = it.ctr;
+      e0 = it.e0;
+      e1 = it.e1;
+      slot = it.slot;
+    }
+    const int64_t s0 = p.group_off[g];
+    const int ni = (int)(p.group_off[g + 1] - s0);
+    constexpr bool keep = INPLACE;
+    if (ni <= 0) {
+      if (keep) {  // no sinks: the lists are only checked and kept
+        for (int64_t e = p.plist_off[g] + tid; e < p.plist_off[g + 1]; e += NT)
+          keep_index(p.plist_idx[e], p.n_src, p.plist_keep + e, p.bad);
+        for (int64_t e = p.clist_off[g] + tid; e < p.clist_off[g + 1]; e += NT)
+          keep_index(p.clist_idx[e], p.n_cell, p.clist_keep + e, p.bad);
+      }
+      continue;
+    }
+
+    // ---- 1. group centre: the bounding-box centre of the sinks, computed
+    // once when the sinks were set (group_centre_kernel)
+    Centre cc{};
+    if constexpr (FF) {
+      const PosMassF cf = p.gcentre_f[g];
+      cc.hx = cf.hx; cc.hy = cf.hy; cc.hz = cf.hz;
+      cc.lx = cf.lx; cc.ly = cf.ly; cc.lz = cf.lz;
+    } else if (CENTRED) {
+      cc.x = p.gcentre[3 * g];
+      cc.y = p.gcentre[3 * g + 1];
+      cc.z = p.gcentre[3 * g + 2];
+    }
+
+    const int64_t gp0 = p.plist_off[g], np_g = p.plist_off[g + 1] - gp0;
+    const int64_t gc0 = p.clist_off[g], nc_g = p.clist_off[g + 1] - gc0;
+    if (e1 < 0) e1 = np_g + nc_g;
+    const int64_t p0 = gp0 + min(e0, np_g), p1 = gp0 + min(e1, np_g);
+    const int64_t c0 = gc0 + max(e0 - np_g, (int64_t)0), c1 = gc0 + max(e1 - np_g, (int64_t)0);
+
+    // ---- sink chunks: the staging, pair loops, folds, merges and outputs
+    if constexpr (ADAPT) {
+      const int r = choose_sinks_per_thread<R, EPAIR>(ni, (p1 - p0) + (c1 - c0), NT);
+      if (r == 1)
+        evaluate_chunks<Real, 1, QUAD, GUARD, CENTRED, FORM, INPLACE>(p, smem_raw, R, cc, s0, ni, p0, p1, c0, c1,
+                                                                      part, slot);
+      else if (r == 2)
+        evaluate_chunks<Real, 2, QUAD, GUARD, CENTRED, FORM, INPLACE>(p, smem_raw, R, cc, s0, ni, p0, p1, c0, c1,
+                                                                      part, slot);
+      else if (r == 3)
+        evaluate_chunks<Real, 3, QUAD, GUARD, CENTRED, FORM, INPLACE>(p, smem_raw, R, cc, s0, ni, p0, p1, c0, c1,
+                                                                      part, slot);
+      else
+        evaluate_chunks<Real, R, QUAD, GUARD, CENTRED, FORM, INPLACE>(p, smem_raw, R, cc, s0, ni, p0, p1, c0, c1,
+                                                                      part, slot);
+    } else {
+      evaluate_chunks<Real, R, QUAD, GUARD, CENTRED, FORM, INPLACE>(p, smem_raw, R, cc, s0, ni, p0, p1, c0, c1, part,
+                                                                    slot);
     }
 
     // ---- a6. split lists: the part that completes its group's count adds

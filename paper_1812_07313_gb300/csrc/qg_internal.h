@@ -177,5 +177,8 @@ const void *force_kernel_f32x2(int R, bool quad, bool guard);
 const void *force_kernel_f32ep(int R, bool quad, bool guard);  // entry-paired FP32 centred
 const void *force_kernel_f64(int R, bool quad, bool guard);
 const void *force_kernel_inplace(int R, bool quad, bool guard, bool epaired);  // FP32 centred
+// FP32 centred, sinks per thread chosen per work item (1 to 4); scalar or entry-paired
+const void *force_kernel_adapt(bool epaired, bool quad, bool guard);
+const void *force_kernel_inplace_adapt(bool epaired, bool quad, bool guard);
 
 }  // namespace qg

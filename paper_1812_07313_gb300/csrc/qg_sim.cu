@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -120,6 +121,7 @@ struct qg_sim {
   Buf<float> eps2, eps2_s;  // per-particle softening (caller order, sorted order)
   bool per_particle_eps = false;
   bool has_state = false, tuned = false;
+  int64_t tuned_entries = 0;  // list entries of the step the launch shape was last tuned on
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t stream = nullptr;  // used when the caller passes no stream
   qg_sim_times times{};
@@ -177,9 +179,19 @@ qg_status evaluate(qg_sim *s, cudaStream_t st, bool kick, double h) {
   } else {
     SIM_OK(qg_gtree_attach(s->tree, s->ctx, s->prm.eps2, st));
   }
-  if (s->prm.autotune && !s->tuned) {
-    SIM_OK(qg_autotune(s->ctx, st, 2, nullptr, nullptr));
-    s->tuned = true;
+  if (s->prm.autotune) {
+    // tune at the first force evaluation, and again whenever the lists have
+    // grown or shrunk by more than a quarter since (a collapsing system
+    // changes its groups' lists several-fold)
+    int64_t np = 0, nc = 0;
+    SIM_OK(qg_gtree_sizes(s->tree, nullptr, nullptr, nullptr, &np, &nc));
+    const int64_t entries = np + nc;
+    if (!s->tuned || 4 * std::llabs(entries - s->tuned_entries) > s->tuned_entries) {
+      SIM_OK(qg_autotune(s->ctx, st, 2, nullptr, nullptr));
+      s->tuned = true;
+      s->tuned_entries = entries;
+      s->times.retunes++;
+    }
   }
   SIM_OK(qg_run(s->ctx, st));
   SIM_OK(qg_get_forces_dev(s->ctx, s->a_s.p, s->phi_s.p, st));

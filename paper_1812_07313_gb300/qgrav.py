@@ -63,7 +63,7 @@ SIGNATURES = {
 class qg_options(ctypes.Structure):
     _fields_ = [("precision", _int), ("expansion", _int), ("tile_j", _int),
                 ("warps_per_group", _int), ("sinks_per_thread", _int), ("flush_j", _int), ("arith", _int),
-                ("split_j", _int)]
+                ("split_j", _int), ("sinks_adaptive", _int)]
 
 
 class qg_stats(ctypes.Structure):
@@ -73,7 +73,7 @@ class qg_stats(ctypes.Structure):
                 ("sinks_per_thread", ctypes.c_int32), ("tile_j", ctypes.c_int32),
                 ("warps_per_group", ctypes.c_int32), ("flush_j", ctypes.c_int32),
                 ("paired", ctypes.c_int32), ("eval_in_place", ctypes.c_int32), ("n_items", _i64),
-                ("n_split", _i64)]
+                ("n_split", _i64), ("sinks_adaptive", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -135,10 +135,11 @@ class Options:
     flush_j: int = 0
     arith: int = QG_ARITH_DEFAULT
     split_j: int = 0
+    sinks_adaptive: int = 0
 
     def c(self):
         return qg_options(self.precision, self.expansion, self.tile_j, self.warps_per_group,
-                          self.sinks_per_thread, self.flush_j, self.arith, self.split_j)
+                          self.sinks_per_thread, self.flush_j, self.arith, self.split_j, self.sinks_adaptive)
 
 
 class Context:
@@ -301,7 +302,7 @@ class Context:
         self._ok(self._L.qg_autotune(self._h, stream, int(reps), ctypes.addressof(o), ctypes.addressof(ms)),
                  "qg_autotune")
         return (Options(o.precision, o.expansion, o.tile_j, o.warps_per_group, o.sinks_per_thread, o.flush_j,
-                        o.arith, o.split_j), ms.value)
+                        o.arith, o.split_j, o.sinks_adaptive), ms.value)
 
     def qg_last_timing(self):
         """(step_ms, force_ms) of the last run, from events inside its graph."""

@@ -73,7 +73,7 @@ def tune_group_size(x, m, sys_off, leaf_max, theta, candidates, eps2_all=0.0, ep
         finally:
             ctx.close()
         r = GroupSizeResult(int(n_crit), tr.ngroups, int(st["i_pp"]), int(st["i_pc"]), step_ms, force_ms,
-                            {k: st[k] for k in ("sinks_per_thread", "warps_per_group", "tile_j", "paired")},
+                            {k: st[k] for k in ("sinks_per_thread", "sinks_adaptive", "warps_per_group", "tile_j", "paired")},
                             host_s)
         results.append(r)
         if best is None or r.step_ms < best.step_ms:
@@ -101,7 +101,7 @@ def tune_group_size_gpu(gtree_obj, x, m, sys_off, leaf_max, theta, candidates, e
         finally:
             ctx.close()
         r = GroupSizeResult(int(n_crit), int(gtree_obj.sizes()["ngroups"]), int(st["i_pp"]), int(st["i_pc"]), step_ms,
-                            force_ms, {k: st[k] for k in ("sinks_per_thread", "warps_per_group", "tile_j", "paired")},
+                            force_ms, {k: st[k] for k in ("sinks_per_thread", "sinks_adaptive", "warps_per_group", "tile_j", "paired")},
                             1e-3 * (build_ms + walk_ms))
         results.append(r)
         if best is None or r.step_ms < best.step_ms:

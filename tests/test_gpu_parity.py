@@ -418,10 +418,11 @@ def test_zero_softening_skips_coincident_pairs():
         assert_parity(a, phi, a_ref, phi_ref, label="eps=0 form %d" % arith)
 
 
+@pytest.mark.parametrize("adaptive", [0, 1])
 @pytest.mark.parametrize("arith", [qgrav.QG_ARITH_SCALAR, qgrav.QG_ARITH_ENTRY_PAIRED])
 @pytest.mark.parametrize("n", [96, 97])
 @pytest.mark.parametrize("origin", [0.0, 3000.0])
-def test_self_pair_adds_no_force_at_tiny_softening(origin, n, arith):
+def test_self_pair_adds_no_force_at_tiny_softening(origin, n, arith, adaptive):
     """Every sink is also an entry of its own group's list.  With eps = 1e-9
     its own pair must give dx = 0 exactly (sink and entry offsets rounded by
     the same operations), else it adds a force of order m dx / eps^3; the
@@ -435,7 +436,7 @@ def test_self_pair_adds_no_force_at_tiny_softening(origin, n, arith):
     off = np.array([0, n, 2 * n], dtype=np.int64)
     idx = np.concatenate([np.arange(n), np.arange(n)]).astype(np.int32)
     eps2 = 1e-18
-    ctx = qgrav.Context(0, qgrav.Options(arith=arith))
+    ctx = qgrav.Context(0, qgrav.Options(arith=arith, sinks_adaptive=adaptive))
     ctx.qg_set_sinks(x, goff, eps2)
     ctx.qg_set_sources(x, m, off, idx)
     ctx.qg_set_cells(np.zeros((0, 3)), np.zeros(0), np.zeros((0, 6)), np.zeros(3, dtype=np.int64),
@@ -628,6 +629,62 @@ def test_sharded_contexts_concatenate_to_the_unsharded_step(sphere4k, world):
             a_parts.append(a)
             p_parts.append(phi)
         assert np.array_equal(np.concatenate(a_parts), a0) and np.array_equal(np.concatenate(p_parts), p0)
+
+
+@pytest.mark.parametrize("arith", [qgrav.QG_ARITH_SCALAR, qgrav.QG_ARITH_ENTRY_PAIRED])
+@pytest.mark.parametrize("warps,tile", [(2, 256), (4, 128), (8, 1024)])
+def test_sinks_per_thread_chosen_per_item(arith, warps, tile):
+    """The kernels that choose 1 to 4 sinks per thread for every work item:
+    on groups of 1 to 1500 sinks (several passes of the CTA's sink slots)
+    with lists of 0 to ~3000 entries, every choice is taken; the results
+    match the oracle, are bitwise repeatable, and agree with the fixed R = 4
+    kernel to FP32 rounding."""
+    rng = np.random.default_rng(61)
+    ps = workloads.small_set("cube", 6000, 8, 2e-3)
+    case = Case(ps, 0.5, leaf_max=8, n_crit=1500)
+    small = Case(workloads.small_set("plummer", 5000, 9, 0.01), 0.5, leaf_max=8, n_crit=24)
+    o = qgrav.Options(arith=arith, warps_per_group=warps, tile_j=tile, sinks_per_thread=4, sinks_adaptive=1)
+    for c in (case, small):
+        a1, p1, st = c.gpu(o)
+        assert st["sinks_adaptive"] == 1 and st["sinks_per_thread"] == 4
+        a2, p2, _ = c.gpu(o)
+        assert np.array_equal(a1, a2) and np.array_equal(p1, p2)
+        a_ref, phi_ref = c.oracle()
+        assert_parity(a1, p1, a_ref, phi_ref, label="adaptive R form %d, %d warps, tile %d" % (arith, warps, tile))
+        a4, p4, _ = c.gpu(qgrav.Options(arith=arith, warps_per_group=warps, tile_j=tile, sinks_per_thread=4))
+        assert np.max(rel_err(a1, a4)) < 1e-5 and np.max(rel_err(p1, p4)) < 1e-5
+
+
+def test_sinks_per_thread_chosen_per_item_edges():
+    """Empty and ragged lists, tiny softening with self pairs, zero softening
+    (the guarded kernel) and the one-call path by both routes, bit for bit
+    the separate calls."""
+    for arith in (qgrav.QG_ARITH_SCALAR, qgrav.QG_ARITH_ENTRY_PAIRED):
+        o = qgrav.Options(arith=arith, sinks_adaptive=1, tile_j=32)
+        # zero softening: coincident self pairs skipped
+        c0 = Case(workloads.small_set("sphere", 2000, 12, 0.0), 0.5)
+        a, phi, _ = c0.gpu(o)
+        a_ref, phi_ref = c0.oracle()
+        assert_parity(a, phi, a_ref, phi_ref, label="adaptive eps=0 form %d" % arith)
+        # one call from host arrays, copied and in place: the separate calls' results
+        c1 = Case(workloads.batched_systems(nsys=6, seed=17, n_lo=800, n_hi=4000), 0.5)
+        ctx = qgrav.Context(0, o)
+        a_ref1, p_ref1, _ = c1.gpu(ctx=ctx)
+        for pinned in (False, True):
+            a2, p2 = _evaluate_host(c1, ctx, pinned=pinned)
+            assert ctx.qg_get_stats()["eval_in_place"] == (1 if pinned else 0)
+            assert np.array_equal(a2, a_ref1) and np.array_equal(p2, p_ref1)
+        ctx.close()
+    # the option is checked: up to 4 sinks per thread, not with the sink-paired form
+    ctx = qgrav.Context(0)
+    for bad in (qgrav.Options(sinks_adaptive=1, sinks_per_thread=2),
+                qgrav.Options(sinks_adaptive=1, arith=qgrav.QG_ARITH_PAIRED),
+                qgrav.Options(sinks_adaptive=1, precision=qgrav.QG_FP64),
+                qgrav.Options(sinks_adaptive=2)):
+        with pytest.raises(qgrav.QGError) as e:
+            ctx.set_options(bad)
+        assert e.value.status == qgrav.QG_ERR_ARG
+    ctx.close()
 
 
 def test_non_finite_or_out_of_range_inputs_are_rejected():

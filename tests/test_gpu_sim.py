@@ -182,3 +182,30 @@ def test_batched_systems_step_like_each_system_alone():
     s.close()
     with pytest.raises(qgrav.QGError):
         sim.Simulation(sim.Params(theta=0.0))
+
+
+def test_autotuning_follows_the_lists():
+    """With autotune on, the force launch is tuned at the first force
+    evaluation and again only when the step's list entries have changed by
+    more than a quarter since the last tuning: steps that hardly move the
+    particles keep the tuning; a new state with much longer lists (a
+    centrally concentrated sphere after a uniform one) is re-tuned."""
+    n = 20000
+    ps = workloads.small_set("sphere", n, 7, 0.01)
+    s = sim.Simulation(sim.Params(theta=0.5, eps2=1e-4, n_crit=64, autotune=True))
+    s.set_state(ps.x, np.zeros((n, 3)), ps.m)
+    t0 = s.last_times()
+    assert t0["retunes"] == 1
+    s.step(1e-3, 3)   # hardly moves: the same lists, no tuning
+    t1 = s.last_times()
+    assert t1["retunes"] == 1
+    assert abs((t1["n_plist"] + t1["n_clist"]) / (t0["n_plist"] + t0["n_clist"]) - 1) < 0.25
+    pl = workloads.small_set("plummer", n, 8, 0.01)
+    s.set_state(pl.x, np.zeros((n, 3)), pl.m)
+    t2 = s.last_times()
+    ratio = (t2["n_plist"] + t2["n_clist"]) / (t1["n_plist"] + t1["n_clist"])
+    print("list entries, Plummer over uniform: %.2fx; %d tunings" % (ratio, t2["retunes"]))
+    assert abs(ratio - 1) > 0.25 and t2["retunes"] == 2
+    x, v, a, phi = s.state()
+    assert np.all(np.isfinite(a)) and np.all(np.isfinite(phi))
+    s.close()
