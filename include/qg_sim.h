@@ -49,9 +49,13 @@ typedef struct {
   int leaf_max;   /* tree leaf size bound (>= 1) */
   int expansion;  /* QG_QUAD or QG_MONO */
   int autotune;   /* nonzero: qg_autotune the force launch on the first force
-                     evaluation, and again whenever the step's list entries
+                     evaluation; afterwards, whenever the step's list entries
                      differ from those it was last tuned on by more than a
-                     quarter */
+                     quarter, an online trial: each of the next (at most 6)
+                     force evaluations runs one launch shape near the current
+                     one (2, 4 or 8 warps per CTA; at 4 sinks per thread, fixed
+                     or chosen per work item), timed by its own force kernel,
+                     and the fastest is kept.  A trial adds no evaluations. */
 } qg_sim_params;
 
 /* Device time (CUDA events) of the parts of the last step, milliseconds,
@@ -61,7 +65,12 @@ typedef struct {
   float build_ms, walk_ms, force_ms, integrate_ms;
   double wall_ms;
   int64_t groups, n_plist, n_clist, i_pp, i_pc;
-  int64_t retunes;  /* force-launch tunings so far (autotune) */
+  int64_t retunes;  /* force-launch tunings so far (autotune): the first
+                       qg_autotune and every online trial started since */
+  /* the force launch of the last step (qg_stats): sinks per thread (and 1
+   * if chosen per item), warps per CTA, tile, FP32 form; trial_left: force
+   * evaluations still to run in the current online trial (0 = none) */
+  int32_t sinks_per_thread, sinks_adaptive, warps_per_group, tile_j, form, trial_left;
 } qg_sim_times;
 
 /* A simulation with the parameters of Sec. 5's runs (theta, eps, n_crit,

@@ -66,6 +66,7 @@ def run(label, n=1 << 22, t_end=10.0, dt=2.0 ** -8, eps=2.0 ** -8, n_crit=256, s
     K0, W0, _ = s.energy()
     nsteps = int(round(t_end / dt))
     wall, build, walk, force, integ, ipp, ipc = [], [], [], [], [], [], []
+    launches = {}  # force launch (R, chosen per item, warps, tile, form) -> steps run with it
     track = [{"t": 0.0, "K": K0, "W": W0}]
     t0 = time.perf_counter()
     for k in range(1, nsteps + 1):
@@ -78,6 +79,9 @@ def run(label, n=1 << 22, t_end=10.0, dt=2.0 ** -8, eps=2.0 ** -8, n_crit=256, s
         integ.append(tt["integrate_ms"])
         ipp.append(tt["i_pp"])
         ipc.append(tt["i_pc"])
+        key = "%d%s,%d,%d,%s" % (tt["sinks_per_thread"], "a" if tt["sinks_adaptive"] else "", tt["warps_per_group"],
+                                 tt["tile_j"], ("x1", "x2", "xe")[tt["form"]])
+        launches[key] = launches.get(key, 0) + 1
         if k % sample_every == 0 or k == nsteps:
             K, W, _ = s.energy()
             track.append({"t": k * dt, "K": K, "W": W})
@@ -85,6 +89,7 @@ def run(label, n=1 << 22, t_end=10.0, dt=2.0 ** -8, eps=2.0 ** -8, n_crit=256, s
                 log("%s t=%.3f K=%.5f W=%.5f E=%.6f  %.1f ms/step" % (label, k * dt, K, W, K + W,
                                                                         np.mean(wall[-sample_every:])))
     total_s = time.perf_counter() - t0
+    tunings = s.last_times()["retunes"]
     x, v, a, phi = s.state()
     s.close()
     edges, rho, count = density_profile(x, m)
@@ -97,6 +102,7 @@ def run(label, n=1 << 22, t_end=10.0, dt=2.0 ** -8, eps=2.0 ** -8, n_crit=256, s
         "ms_per_step_device": {"build": float(np.mean(build)), "walk": float(np.mean(walk)),
                                "force": float(np.mean(force)), "integrate": float(np.mean(integ))},
         "interactions_per_step": {"pp": float(np.mean(ipp)), "pc": float(np.mean(ipc))},
+        "force_launch": {"tunings": int(tunings), "steps_per_shape": launches},
         "paper_s_per_step": PAPER_S_PER_STEP[label],
         "energy": {"E0": E0, "E_end": E, "rel_change": (E - E0) / abs(E0),
                    "max_rel_change": max(abs((p["K"] + p["W"] - E0) / E0) for p in track)},

@@ -15,32 +15,6 @@ struct __align__(32) PosMass {
   float pad;
 };
 
-// The same entry for the centred FP32 kernels: every coordinate as a pair of
-// floats, hi = the float nearest x and lo = the float nearest x - hi (about
-// 48 bits of x together), and the mass as float: one aligned 32-byte sector.
-// Centring on c = (hi_c, lo_c) is then (hi - hi_c) + (lo - lo_c): three FP32
-// adds, exact in its first step wherever the entry is near the centre.
-struct __align__(32) PosMassF {
-  float hx, hy, hz, m;
-  float lx, ly, lz, pad;
-};
-
-// x as hi + lo (round to nearest, both on the host and on the GPU).
-__host__ __device__ inline void split_f32x2(double x, float &hi, float &lo) {
-  hi = (float)x;
-  lo = (float)(x - (double)hi);
-}
-
-__host__ __device__ inline PosMassF make_posmassf(double x, double y, double z, float m) {
-  PosMassF r;
-  split_f32x2(x, r.hx, r.lx);
-  split_f32x2(y, r.hy, r.ly);
-  split_f32x2(z, r.hz, r.lz);
-  r.m = m;
-  r.pad = 0.f;
-  return r;
-}
-
 // Largest magnitude of a position coordinate any entry point accepts (and of
 // a mass, a quadrupole component or a softening in the allocation-free
 // entry point): every value the kernels round with f64_to_f32_rn below,
@@ -55,8 +29,10 @@ constexpr double kMaxInput = 0x1p100;
 // rounds up to 2^128 gives infinity, as it should); magnitudes below the
 // smallest normal float give a signed zero (the FP32 kernels flush denormals
 // anyway).  Outside the domain (|x| >= 2^128, infinities, NaN) the exponent
-// wraps and the result is meaningless: callers pass only position offsets,
-// masses and quadrupole components of inputs checked against kMaxInput.  On
+// wraps and the result is meaningless: callers pass only positions, position
+// offsets, masses and quadrupole components of inputs checked against
+// kMaxInput (a rejected input's values are rounded all the same, harmlessly,
+// before the call reports it).  On
 // this GPU the hardware double->float conversion issues on the narrow FP64
 // pipe, which this keeps free for the FP64 centring itself.
 __host__ __device__ inline float f64_to_f32_rn(double x) {
@@ -80,6 +56,36 @@ __host__ __device__ inline float f64_to_f32_rn(double x) {
   __builtin_memcpy(&f, &t, sizeof f);
   return f;
 #endif
+}
+
+// The same entry for the centred FP32 kernels: every coordinate as a pair of
+// floats, hi = the float nearest x and lo = the float nearest x - hi (about
+// 48 bits of x together), and the mass as float: one aligned 32-byte sector.
+// Centring on c = (hi_c, lo_c) is then (hi - hi_c) + (lo - lo_c): three FP32
+// adds, exact in its first step wherever the entry is near the centre.
+struct __align__(32) PosMassF {
+  float hx, hy, hz, m;
+  float lx, ly, lz, pad;
+};
+
+// x as hi + lo, both rounded to nearest with the integer rounding above (on
+// the GPU the hardware double -> float conversion issues on the narrow FP64
+// pipe; this needs one FP64 subtraction).  A result below the smallest normal
+// float becomes 0, which the FP32 kernels (built to flush denormals) would
+// make of it anyway.
+__host__ __device__ inline void split_f32x2(double x, float &hi, float &lo) {
+  hi = f64_to_f32_rn(x);
+  lo = f64_to_f32_rn(x - (double)hi);
+}
+
+__host__ __device__ inline PosMassF make_posmassf(double x, double y, double z, float m) {
+  PosMassF r;
+  split_f32x2(x, r.hx, r.lx);
+  split_f32x2(y, r.hy, r.ly);
+  split_f32x2(z, r.hz, r.lz);
+  r.m = m;
+  r.pad = 0.f;
+  return r;
 }
 
 // One work item of a step whose long lists are split (the modified tree

@@ -122,6 +122,11 @@ struct qg_sim {
   bool per_particle_eps = false;
   bool has_state = false, tuned = false;
   int64_t tuned_entries = 0;  // list entries of the step the launch shape was last tuned on
+  qg_options best{};          // the force launch in use outside trials
+  // online re-tuning: launch shapes near `best`, one per force evaluation,
+  // each timed by that evaluation's own force kernel
+  std::vector<qg_options> trial;
+  std::vector<float> trial_ms;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaStream_t stream = nullptr;  // used when the caller passes no stream
   qg_sim_times times{};
@@ -157,6 +162,30 @@ struct DeviceGuard {
   }
 };
 
+// The shapes an online trial runs: the current one and its neighbours --
+// 2, 4 or 8 warps per CTA at the same list entries staged per warp and, at 4
+// sinks per thread in an FP32 centred form, sinks per thread fixed or chosen
+// per work item.  These are the dimensions along which the full tuner's
+// choice moved as a collapsing sphere's lists grew.
+std::vector<qg_options> neighbour_shapes(const qg_options &best) {
+  std::vector<qg_options> out;
+  const int W0 = best.warps_per_group > 0 ? best.warps_per_group : 4;
+  const int T0 = best.tile_j > 0 ? best.tile_j : 256;
+  const bool adapt = best.precision == QG_FP32_CENTRED && best.sinks_per_thread == 4 &&
+                     best.arith != QG_ARITH_PAIRED;
+  for (int W : {2, 4, 8}) {
+    if (best.sinks_per_thread >= 8 && W > 4) continue;
+    qg_options o = best;
+    o.warps_per_group = W;
+    o.tile_j = std::min(1024, std::max(128, T0 * W / W0 / 32 * 32));
+    for (int a = 0; a < (adapt ? 2 : 1); a++) {
+      o.sinks_adaptive = adapt ? a : best.sinks_adaptive;
+      out.push_back(o);
+    }
+  }
+  return out;
+}
+
 // forces(x) -> a, phi in the caller's order; with kick, also v += a h.
 qg_status evaluate(qg_sim *s, cudaStream_t st, bool kick, double h) {
   SIM_OK(qg_gtree_build(s->tree, s->n, s->x.p, s->m.p, (int64_t)s->sys_off.size() - 1, s->sys_off.data(),
@@ -180,20 +209,36 @@ qg_status evaluate(qg_sim *s, cudaStream_t st, bool kick, double h) {
     SIM_OK(qg_gtree_attach(s->tree, s->ctx, s->prm.eps2, st));
   }
   if (s->prm.autotune) {
-    // tune at the first force evaluation, and again whenever the lists have
-    // grown or shrunk by more than a quarter since (a collapsing system
-    // changes its groups' lists several-fold)
+    // a full qg_autotune at the first force evaluation; afterwards, whenever
+    // the lists have grown or shrunk by more than a quarter since the last
+    // tuning (a collapsing system changes its groups' lists several-fold),
+    // an online trial: the next few evaluations each run one shape near the
+    // current one, and the fastest of them is kept
     int64_t np = 0, nc = 0;
     SIM_OK(qg_gtree_sizes(s->tree, nullptr, nullptr, nullptr, &np, &nc));
     const int64_t entries = np + nc;
-    if (!s->tuned || 4 * std::llabs(entries - s->tuned_entries) > s->tuned_entries) {
-      SIM_OK(qg_autotune(s->ctx, st, 2, nullptr, nullptr));
+    if (!s->tuned) {
+      SIM_OK(qg_autotune(s->ctx, st, 2, &s->best, nullptr));
       s->tuned = true;
       s->tuned_entries = entries;
       s->times.retunes++;
+    } else if (s->trial.empty() && 4 * std::llabs(entries - s->tuned_entries) > s->tuned_entries) {
+      s->trial = neighbour_shapes(s->best);
+      s->trial_ms.clear();
+      s->tuned_entries = entries;
+      s->times.retunes++;
     }
+    if (!s->trial.empty()) SIM_OK(qg_set_options(s->ctx, &s->trial[s->trial_ms.size()]));
   }
-  SIM_OK(qg_run(s->ctx, st));
+  qg_status run = qg_run(s->ctx, st);
+  bool misfit = false;
+  if (run == QG_ERR_ARG && !s->trial.empty()) {
+    // the trial shape does not fit this device: run the current one instead
+    misfit = true;
+    SIM_OK(qg_set_options(s->ctx, &s->best));
+    run = qg_run(s->ctx, st);
+  }
+  SIM_OK(run);
   SIM_OK(qg_get_forces_dev(s->ctx, s->a_s.p, s->phi_s.p, st));
   const int64_t *perm = nullptr;
   SIM_OK(qg_gtree_arrays(s->tree, &perm, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
@@ -217,6 +262,24 @@ qg_status evaluate(qg_sim *s, cudaStream_t st, bool kick, double h) {
   s->times.n_clist = stt.n_clist;
   s->times.i_pp = stt.i_pp;
   s->times.i_pc = stt.i_pc;
+  s->times.sinks_per_thread = stt.sinks_per_thread;
+  s->times.sinks_adaptive = stt.sinks_adaptive;
+  s->times.warps_per_group = stt.warps_per_group;
+  s->times.tile_j = stt.tile_j;
+  s->times.form = stt.paired;
+  // the times above are of the shape this evaluation ran; a trial that has
+  // now run all its shapes keeps the fastest for the evaluations after it
+  if (!s->trial.empty()) {
+    s->trial_ms.push_back(misfit ? INFINITY : f);
+    if (s->trial_ms.size() == s->trial.size()) {
+      const size_t k = std::min_element(s->trial_ms.begin(), s->trial_ms.end()) - s->trial_ms.begin();
+      if (std::isfinite(s->trial_ms[k])) s->best = s->trial[k];
+      s->trial.clear();
+      s->trial_ms.clear();
+      SIM_OK(qg_set_options(s->ctx, &s->best));
+    }
+  }
+  s->times.trial_left = (int32_t)(s->trial.size() - s->trial_ms.size());
   return QG_OK;
 }
 

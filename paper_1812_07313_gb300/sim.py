@@ -27,7 +27,10 @@ class qg_sim_params(ctypes.Structure):
 class qg_sim_times(ctypes.Structure):
     _fields_ = [("build_ms", ctypes.c_float), ("walk_ms", ctypes.c_float), ("force_ms", ctypes.c_float),
                 ("integrate_ms", ctypes.c_float), ("wall_ms", _dbl), ("groups", _i64), ("n_plist", _i64),
-                ("n_clist", _i64), ("i_pp", _i64), ("i_pc", _i64), ("retunes", _i64)]
+                ("n_clist", _i64), ("i_pp", _i64), ("i_pc", _i64), ("retunes", _i64),
+                ("sinks_per_thread", ctypes.c_int32), ("sinks_adaptive", ctypes.c_int32),
+                ("warps_per_group", ctypes.c_int32), ("tile_j", ctypes.c_int32), ("form", ctypes.c_int32),
+                ("trial_left", ctypes.c_int32)]
 
 
 SIGNATURES = {

@@ -189,16 +189,18 @@ def test_autotuning_follows_the_lists():
     evaluation and again only when the step's list entries have changed by
     more than a quarter since the last tuning: steps that hardly move the
     particles keep the tuning; a new state with much longer lists (a
-    centrally concentrated sphere after a uniform one) is re-tuned."""
+    centrally concentrated sphere after a uniform one) starts an online
+    trial, whose evaluations each run one neighbouring launch shape, after
+    which the fastest shape stays."""
     n = 20000
     ps = workloads.small_set("sphere", n, 7, 0.01)
     s = sim.Simulation(sim.Params(theta=0.5, eps2=1e-4, n_crit=64, autotune=True))
     s.set_state(ps.x, np.zeros((n, 3)), ps.m)
     t0 = s.last_times()
-    assert t0["retunes"] == 1
+    assert t0["retunes"] == 1 and t0["trial_left"] == 0
     s.step(1e-3, 3)   # hardly moves: the same lists, no tuning
     t1 = s.last_times()
-    assert t1["retunes"] == 1
+    assert t1["retunes"] == 1 and t1["trial_left"] == 0
     assert abs((t1["n_plist"] + t1["n_clist"]) / (t0["n_plist"] + t0["n_clist"]) - 1) < 0.25
     pl = workloads.small_set("plummer", n, 8, 0.01)
     s.set_state(pl.x, np.zeros((n, 3)), pl.m)
@@ -206,6 +208,21 @@ def test_autotuning_follows_the_lists():
     ratio = (t2["n_plist"] + t2["n_clist"]) / (t1["n_plist"] + t1["n_clist"])
     print("list entries, Plummer over uniform: %.2fx; %d tunings" % (ratio, t2["retunes"]))
     assert abs(ratio - 1) > 0.25 and t2["retunes"] == 2
+    shape = lambda t: (t["sinks_per_thread"], t["sinks_adaptive"], t["warps_per_group"], t["tile_j"], t["form"])
+    tried, left = [shape(t2)], t2["trial_left"]
+    assert 1 <= left <= 5
+    while left:
+        s.step(1e-4, 1)
+        t = s.last_times()
+        assert t["trial_left"] == left - 1 and t["retunes"] == 2
+        left = t["trial_left"]
+        tried.append(shape(t))
+    assert len(set(tried)) == len(tried) >= 2
+    s.step(1e-4, 1)   # the trial is over: one of its shapes stays
+    kept = shape(s.last_times())
+    assert kept in tried
+    s.step(1e-4, 3)
+    assert shape(s.last_times()) == kept and s.last_times()["retunes"] == 2
     x, v, a, phi = s.state()
     assert np.all(np.isfinite(a)) and np.all(np.isfinite(phi))
     s.close()
