@@ -25,9 +25,11 @@
  * the GPU each group's centre c_g (centre of the bounding box of its sinks)
  * is subtracted in FP64 from every sink and every staged list entry, and only
  * then is the offset cast to FP32.  The pairwise arithmetic is FP32 with the
- * SFU reciprocal square root; each thread's FP32 partial sums are folded into
- * FP64 after a bounded number of list entries, and the partials of all
- * threads of a group are merged in FP64.  QG_FP32_RAW skips the centring
+ * SFU reciprocal square root; each thread's FP32 partial sums are folded,
+ * after a bounded number of list entries, into float-float sums (an FP32
+ * hi + lo pair, about 48 significant bits; FP64 sums in the sink-paired
+ * form), and the partials of all threads of a group are merged the same way
+ * in a fixed order and converted to FP64.  QG_FP32_RAW skips the centring
  * (absolute coordinates cast to FP32; an ablation).  QG_FP64 does everything
  * in FP64 (a comparison kernel, about 70x slower on this GPU).
  *
@@ -109,8 +111,9 @@ typedef struct {
                            0 = default; supported: 1, 2, 4, 8               */
   int sinks_per_thread; /* sinks held in registers per thread;
                            0 = default; supported: 2, 4, 8                  */
-  int flush_j;          /* FP32 partials are folded into FP64 after at most
-                           this many list entries per thread; 0 = 256       */
+  int flush_j;          /* FP32 partials are folded into the float-float
+                           (or FP64) sums after at most this many list
+                           entries per thread; 0 = 256                      */
   int arith;            /* QG_FP32_CENTRED only: QG_ARITH_SCALAR,
                            QG_ARITH_PAIRED (two sinks per float2 register,
                            f32x2 FMA instructions) or QG_ARITH_ENTRY_PAIRED

@@ -5,19 +5,23 @@
 // device work queue (ordered by descending cost) with an atomic counter.
 // Inside the CTA:
 //   1. c_g = centre of the bounding box of the group's sinks (FP64, computed
-//      once per set of sinks by group_centre_kernel).
-//   2. sink offsets x_i - c_g are formed in FP64, cast to Real, kept in
-//      shared memory; each thread holds R sinks in registers.
+//      once per set of sinks by group_centre_kernel, and stored also as a
+//      float-pair record).
+//   2. sink offsets x_i - c_g are formed from the float-pair records (FP32
+//      kernels) or in FP64 (the all-FP64 kernel), kept in shared memory;
+//      each thread holds R sinks in registers.
 //   3. the group's list is staged tile by tile into shared memory:
 //      particles (x_j - c_g, m) and cells (x_j - c_g, m, Q) gathered through
-//      the CSR index list, centred in FP64, cast to Real.
+//      the CSR index list and centred the same way.
 //   4. the threads form S sink slots x K list streams (S = ceil(n_i / R),
 //      K = blockDim / S); stream k walks entries k, k+K, ... of each tile,
 //      so every staged entry is read from shared memory once per thread and
 //      used for R sinks.
-//   5. Real partial sums are folded into FP64 accumulators (shared memory)
-//      after at most flush_j entries per thread; at the end the K streams of
-//      each sink are merged in FP64 in a fixed order (deterministic).
+//   5. Real partial sums are folded into accumulators in shared memory
+//      (float-float in the FP32 scalar and entry-paired forms, FP64 in the
+//      others) after at most flush_j entries per thread; at the end the K
+//      streams of each sink are merged in a fixed order (deterministic) and
+//      written in FP64.
 //
 // Real = float is the production path; Real = double is the all-FP64
 // comparison kernel (same structure, no casts).
@@ -165,6 +169,28 @@ constexpr float kPadFar = 1.0e15f;
 // tile (quadrupole, entry-paired, 64-thread CTAs, 8 per SM as for the R = 4
 // kernel): the weights of choose_sinks_per_thread.
 constexpr float kLoopEff1 = 0.746f, kLoopEff2 = 0.807f, kLoopEff3 = 0.824f, kLoopEff4 = 0.844f;
+
+// Float-float running sums (hi, lo): hi holds the rounded sum and lo the
+// rounding errors of every addition, each found exactly by Knuth's TwoSum
+// (The Art of Computer Programming, vol. 2, 4.2.2), so hi + lo carries
+// about 48 significant bits.  The FP32 kernels fold their partial sums into
+// these instead of FP64 accumulators: six FP32 adds in place of a conversion
+// and an add on the FP64 pipe, which issues at about 1/64 of the FP32 rate
+// on this GPU.  The kernels are built with FTZ, so a sum below 2^-126 keeps
+// FP32 precision only.
+__device__ __forceinline__ float2 ff_add(float2 v, float x) {
+  const float s = v.x + x;
+  const float b = s - v.x;
+  const float e = (v.x - (s - b)) + (x - b);
+  return make_float2(s, v.y + e);
+}
+__device__ __forceinline__ float2 ff_add(float2 v, float2 w) {
+  const float s = v.x + w.x;
+  const float b = s - v.x;
+  const float e = (v.x - (s - b)) + (w.x - b);
+  return make_float2(s, (v.y + w.y) + e);
+}
+__device__ __forceinline__ double ff_value(float2 v) { return (double)v.x + (double)v.y; }
 
 struct Pair2 {
   float2 zero, one, mone;
@@ -328,10 +354,10 @@ template <typename Real, int R, int FORM> struct Bounds {
 
 // The sink chunks of one work item (group g's sinks [s0, s0 + ni), its list
 // entries [p0, p1) and [c0, c1)) at R sinks per thread: sink staging, list
-// tiles, pair loops, folds, the FP64 merge of the K streams and the outputs
+// tiles, pair loops, folds, the fixed-order merge of the K streams and the outputs
 // (or, for a part of a split list, its partial sums at slot).  Rtile is the R
-// the shared memory was laid out for (the tile follows the FP64 accumulators
-// of Rtile sinks per thread).
+// the shared memory was laid out for (the tile follows the 8-byte
+// accumulators of Rtile sinks per thread).
 template <typename Real, int R, bool QUAD, bool GUARD, bool CENTRED, int FORM, bool INPLACE>
 __device__ __forceinline__ void evaluate_chunks(const ForceParams &p, unsigned char *smem_raw, const int Rtile,
                                                 const Centre &cc, const int64_t s0, const int ni, const int64_t p0,
@@ -351,8 +377,12 @@ __device__ __forceinline__ void evaluate_chunks(const ForceParams &p, unsigned c
   const int T = p.tile;
   // acc64 [4R][NT] (value-major, so that a warp's accesses are consecutive);
   // sink_s aliases it: the sink offsets are read into registers before the
-  // accumulators are zeroed.
+  // accumulators are zeroed.  The FP32 scalar and entry-paired forms keep
+  // float-float sums there (accF, 8 bytes each like a double); the
+  // sink-paired and all-FP64 forms keep FP64 sums.
+  constexpr bool FFACC = sizeof(Real) == 4 && !PAIRED;
   double *acc64 = reinterpret_cast<double *>(smem_raw);
+  float2 *accF = reinterpret_cast<float2 *>(smem_raw);
   V4 *sink_s = reinterpret_cast<V4 *>(smem_raw);
   // Staged tile.  Scalar form: A (dx dy dz m), B (q00 q01 q02 q11), C (q12 q22).
   // Sink-paired form: every value twice, (dx dx dy dy) (dz dz m m) and the
@@ -443,7 +473,10 @@ __device__ __forceinline__ void evaluate_chunks(const ForceParams &p, unsigned c
       }
       __syncthreads();  // every thread holds its sinks: sink_s becomes acc64
 #pragma unroll
-      for (int v = 0; v < 4 * R; v++) acc64[v * NT + tid] = 0.0;
+      for (int v = 0; v < 4 * R; v++) {
+        if constexpr (FFACC) accF[v * NT + tid] = make_float2(0.f, 0.f);
+        else acc64[v * NT + tid] = 0.0;
+      }
       int nproc = 0;
 
       auto fold = [&]() {
@@ -468,12 +501,22 @@ __device__ __forceinline__ void evaluate_chunks(const ForceParams &p, unsigned c
           // the physical sign
 #pragma unroll
           for (int r = 0; r < R; r++) {
-            double *a = acc64 + 4 * r * NT + tid;
-            a[0] += (double)(bax[r].x + bax[r].y);
-            a[NT] += (double)(bay[r].x + bay[r].y);
-            a[2 * NT] += (double)(baz[r].x + baz[r].y);
-            a[3 * NT] -= (double)(bpt[r].x + bpt[r].y);
+            float2 *a = accF + 4 * r * NT + tid;
+            a[0] = ff_add(a[0], bax[r].x + bax[r].y);
+            a[NT] = ff_add(a[NT], bay[r].x + bay[r].y);
+            a[2 * NT] = ff_add(a[2 * NT], baz[r].x + baz[r].y);
+            a[3 * NT] = ff_add(a[3 * NT], -(bpt[r].x + bpt[r].y));
             bax[r] = bay[r] = baz[r] = bpt[r] = make_float2(0.f, 0.f);
+          }
+        } else if constexpr (FFACC) {
+#pragma unroll
+          for (int r = 0; r < R; r++) {
+            float2 *a = accF + 4 * r * NT + tid;
+            a[0] = ff_add(a[0], ax[r]);
+            a[NT] = ff_add(a[NT], ay[r]);
+            a[2 * NT] = ff_add(a[2 * NT], az[r]);
+            a[3 * NT] = ff_add(a[3 * NT], pt[r]);
+            ax[r] = ay[r] = az[r] = pt[r] = Real(0);
           }
         } else {
 #pragma unroll
@@ -833,17 +876,32 @@ QG_UNROLL(QG_EP_UNROLL)
         }
       }
 
-      // ---- 5. FP64 merge of the K streams, fixed order ----------------------
+      // ---- 5. merge of the K streams, fixed order --------------------------
+      // (float-float in the FP32 scalar and entry-paired forms, then one
+      // conversion to FP64; FP64 in the others)
       if (active) fold();
       __syncthreads();
-      if constexpr (!INPLACE) {
-        for (int i = tid; i < nch; i += NT) {
-          const int si = i % S, ri = i / S;
-          double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+      auto merged = [&](int si, int ri, double &m0, double &m1, double &m2, double &m3) {
+        if constexpr (FFACC) {
+          float2 f0 = make_float2(0.f, 0.f), f1 = f0, f2 = f0, f3 = f0;
+          for (int kk = 0; kk < K; kk++) {
+            const float2 *a = accF + 4 * ri * NT + kk * S + si;
+            f0 = ff_add(f0, a[0]); f1 = ff_add(f1, a[NT]); f2 = ff_add(f2, a[2 * NT]); f3 = ff_add(f3, a[3 * NT]);
+          }
+          m0 = ff_value(f0); m1 = ff_value(f1); m2 = ff_value(f2); m3 = ff_value(f3);
+        } else {
+          m0 = m1 = m2 = m3 = 0.0;
           for (int kk = 0; kk < K; kk++) {
             const double *a = acc64 + 4 * ri * NT + kk * S + si;
             m0 += a[0]; m1 += a[NT]; m2 += a[2 * NT]; m3 += a[3 * NT];
           }
+        }
+      };
+      if constexpr (!INPLACE) {
+        for (int i = tid; i < nch; i += NT) {
+          const int si = i % S, ri = i / S;
+          double m0, m1, m2, m3;
+          merged(si, ri, m0, m1, m2, m3);
           const int64_t o = s0 + sb + i;
           if (part < 0) {
             p.a[3 * o] = m0;
@@ -867,11 +925,8 @@ QG_UNROLL(QG_EP_UNROLL)
           m[r][0] = m[r][1] = m[r][2] = 0.0;
           if (i < nch) {
             const int si = i % S, ri = i / S;
-            double m3 = 0.0;
-            for (int kk = 0; kk < K; kk++) {
-              const double *a = acc64 + 4 * ri * NT + kk * S + si;
-              m[r][0] += a[0]; m[r][1] += a[NT]; m[r][2] += a[2 * NT]; m3 += a[3 * NT];
-            }
+            double m3;
+            merged(si, ri, m[r][0], m[r][1], m[r][2], m3);
             const int64_t o = s0 + sb + i;
             p.phi[o] = -m3;
             p.phi_host[o] = -m3;
