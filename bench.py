@@ -488,8 +488,11 @@ def config_record(torch, qgrav, name, steps, warmup, stream, flush, n_sm, local_
                                                  stream=stream.cuda_stream)
         gw.n_crit, gw.theta = best.n_crit, theta
         rec["group_size"] = {"n_crit": best.n_crit, "tuned": True,
+                             "chosen_by": "shortest whole GPU step: tree build + walk + force step",
                              "candidates": [{"n_crit": r.n_crit, "groups": r.groups, "interactions": r.interactions,
-                                             "step_ms": r.step_ms, "force_ms": r.force_ms, "launch": r.launch}
+                                             "step_ms": r.step_ms, "force_ms": r.force_ms,
+                                             "tree_build_walk_ms": r.tree_ms,
+                                             "whole_step_ms": r.step_ms + r.tree_ms, "launch": r.launch}
                                             for r in table]}
     else:
         gw.build(gw.wl.n_crit)

@@ -5,9 +5,12 @@ Larger groups open more cells (more pairs per step) but amortise each staged
 list entry over more sinks.  ``tune_group_size`` builds the tree and lists
 for each candidate n_crit, lets ``qg_autotune`` pick the launch shape for
 each, times the force step on the GPU, and returns the candidate with the
-shortest step.  ``tune_group_size`` builds the trees on the host,
-``tune_group_size_gpu`` on the GPU (the same groups and lists, in
-milliseconds instead of seconds).
+shortest step.  ``tune_group_size`` builds the trees on the host and ranks
+the candidates by the force step alone; ``tune_group_size_gpu`` builds the
+same groups and lists on the GPU and ranks them by the whole GPU step, tree
+build + group walk + force (T_construct + T_traverse + T_force of the
+paper's timing tables): smaller groups shorten the lists but lengthen the
+walk, which visits the tree once per group.
 """
 from __future__ import annotations
 
@@ -29,7 +32,8 @@ class GroupSizeResult:
     step_ms: float
     force_ms: float
     launch: dict = field(default_factory=dict)
-    host_s: float = 0.0
+    host_s: float = 0.0   # host tree build + walk (tune_group_size), seconds
+    tree_ms: float = 0.0  # GPU tree build + walk (tune_group_size_gpu), device milliseconds
 
     @property
     def interactions(self) -> int:
@@ -85,8 +89,10 @@ def tune_group_size_gpu(gtree_obj, x, m, sys_off, leaf_max, theta, candidates, e
                         options=None, steps=3, stream=None):
     """As tune_group_size, with each candidate's tree, groups and lists built
     on the GPU (``gtree.GpuTree``; x, m are CUDA tensors, one softening for
-    every sink).  Leaves the tree of the best candidate built and walked in
-    ``gtree_obj``.  Returns (best GroupSizeResult, all results)."""
+    every sink), and the best candidate the one with the shortest whole step
+    (tree build + walk + force step, device times).  Leaves the tree of the
+    best candidate built and walked in ``gtree_obj``.  Returns (best
+    GroupSizeResult, all results)."""
     results, best = [], None
     for n_crit in candidates:
         gtree_obj.build(x, m, sys_off, leaf_max, int(n_crit), stream)
@@ -102,9 +108,9 @@ def tune_group_size_gpu(gtree_obj, x, m, sys_off, leaf_max, theta, candidates, e
             ctx.close()
         r = GroupSizeResult(int(n_crit), int(gtree_obj.sizes()["ngroups"]), int(st["i_pp"]), int(st["i_pc"]), step_ms,
                             force_ms, {k: st[k] for k in ("sinks_per_thread", "sinks_adaptive", "warps_per_group", "tile_j", "paired")},
-                            1e-3 * (build_ms + walk_ms))
+                            tree_ms=build_ms + walk_ms)
         results.append(r)
-        if best is None or r.step_ms < best.step_ms:
+        if best is None or r.step_ms + r.tree_ms < best.step_ms + best.tree_ms:
             best = r
     if best is not None and best.n_crit != results[-1].n_crit:
         gtree_obj.build(x, m, sys_off, leaf_max, best.n_crit, stream)
