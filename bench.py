@@ -616,7 +616,9 @@ def run_ours(args, rank, world, local_rank):
            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
            "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "%s: %s" % (args.workload, DESCR.get(args.workload, "")),
-                      "theta": theta, "expansion": "quad", "precision": "fp32, fp64 centring and merges",
+                      "theta": theta, "expansion": "quad",
+                      "precision": "fp32 pair arithmetic, offsets centred from float-pair records, "
+                                   "float-float folds and stream merges, fp64 outputs",
                       "interactions": {"i_pp": i_pp, "i_pc": i_pc}, "groups": tr.ngroups,
                       "group_size": group_size, "launch": launch,
                       "l2": "flushed before every timed step (256 MiB device write, outside the step events)",

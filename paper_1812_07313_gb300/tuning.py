@@ -95,8 +95,11 @@ def tune_group_size_gpu(gtree_obj, x, m, sys_off, leaf_max, theta, candidates, e
     GroupSizeResult, all results)."""
     results, best = [], None
     for n_crit in candidates:
-        gtree_obj.build(x, m, sys_off, leaf_max, int(n_crit), stream)
-        gtree_obj.walk(theta, stream)
+        # built and walked twice, the second timed: the first pass of a size
+        # grows the tree's buffers and may walk twice to size the lists
+        for _ in range(2):
+            gtree_obj.build(x, m, sys_off, leaf_max, int(n_crit), stream)
+            gtree_obj.walk(theta, stream)
         build_ms, walk_ms = gtree_obj.timing()
         ctx = qgrav.Context(device, options)
         try:
