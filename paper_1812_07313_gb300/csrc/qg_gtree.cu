@@ -708,13 +708,16 @@ __global__ void walk_data_kernel(int32_t nn, const int32_t *__restrict__ nsysid,
 
 
 // Group walk, one warp per group (a persistent grid; each warp owns a stack in
-// global memory).  Per iteration the lanes take up to 32 nodes off the top
-// segment of the stack and test them at once; accepted cells, opened leaves'
-// particles and opened nodes' children are emitted / pushed through warp
-// prefix sums.  The children of one iteration form a new segment one level
+// global memory).  Per iteration the lanes take up to kWalkPop = 64 nodes off
+// the top segment of the stack, two per lane (both nodes' records requested
+// before either is tested: the walk waits on load latency, and two loads in
+// flight per lane halve the waits of wide segments), and test them;
+// accepted cells, opened leaves' particles and opened nodes' children are
+// emitted / pushed through warp prefix sums, the lanes' first nodes before
+// their second.  The children of one iteration form a new segment one level
 // deeper, and pops never cross a segment boundary, so segment d holds nodes of
-// level d only: at most 21 segments left behind with <= 224 entries each
-// (256 children of 32 nodes, less the 32 popped) plus the top one (<= 256)
+// level d only: at most 21 segments left behind with <= 448 entries each
+// (512 children of 64 nodes, less the 64 popped) plus the top one (<= 512)
 // ever sit on the stack.  The lists hold the same entries as a depth-first
 // walk, in this walk's own fixed order.  walk_group walks one group;
 // walk_single_kernel (one pass, groups taken from a counter, lists staged per
@@ -729,9 +732,10 @@ __global__ void walk_data_kernel(int32_t nn, const int32_t *__restrict__ nsysid,
 // is taken in FP32 only when the compared quantities are apart by more than
 // their error bounds.  Otherwise (ties and near-ties) the FP64 test decides.
 // Scaling both sides of side^2 < theta^2 d^2 by 1/S^2 does not change it.
-constexpr int kWarpStack = kMaxLevel * 224 + 256;
+constexpr int kWalkPop = 64;  // nodes taken off the stack per walk iteration (two per lane)
+constexpr int kWarpStack = kMaxLevel * (8 * kWalkPop - kWalkPop) + 8 * kWalkPop;
 constexpr int kWalkBlock = 128;       // threads per block of the walk kernels
-constexpr int kWalkBlocksPerSM = 10;  // the single-pass walk's register bound (48): 40 warps per SM
+constexpr int kWalkBlocksPerSM = 9;   // the single-pass walk's register bound (56): 36 warps per SM
 
 __device__ __forceinline__ int warp_excl(int v, int lane, int *total) {
   int x = v;
@@ -846,51 +850,84 @@ __device__ bool walk_group(const WalkTree &T, int64_t g, double theta2, float th
   int seg = 0;  // lane d: first stack slot of the segment at depth d
   np = 0;
   nc = 0;
+  // kind of a popped node: 1 = accepted cell, 2 = opened leaf (its
+  // particles), 3 = opened internal node (its children); 0 = no node
+  auto classify = [&](int32_t k, const int4 &tp, const float4 &ga, const float4 &gb2) -> int {
+    bool open = true;
+    if (theta2 > 0.0 && !(tp.x < ge && tp.y > gb)) {
+      const int dec = node_opens32(ga, gb2, th2, dl, lo, hi);
+      open = dec == 2 ? node_opens64(k, theta2, T.centre, T.side, T.com, box64, box64 + 3) : dec == 1;
+    }
+    return !open ? 1 : (tp.w == 0 ? 2 : 3);
+  };
   while (sp > 0) {
     const int base = __shfl_sync(0xffffffffu, seg, depth);
     if (sp == base) {  // this level's segment is used up: back to the one below
       depth--;
       continue;
     }
-    const int take = sp - base < 32 ? sp - base : 32;
+    const int take = sp - base < kWalkPop ? sp - base : kWalkPop;
     sp -= take;
-    const bool have = lane < take;
-    const int32_t k = have ? stack[sp + lane] : -1;
-    __syncwarp();  // every lane has read its entry before the stack is written again
-    int kind = 0;  // 1: cell, 2: leaf particles, 3: open (children)
-    int4 tp = make_int4(0, 0, 0, 0);
-    if (have) {
-      tp = T.topo[k];
-      bool open = true;
-      if (theta2 > 0.0 && !(tp.x < ge && tp.y > gb)) {
-        const int dec = node_opens32(T.geom[2 * k], T.geom[2 * k + 1], th2, dl, lo, hi);
-        open = dec == 2 ? node_opens64(k, theta2, T.centre, T.side, T.com, box64, box64 + 3) : dec == 1;
+    const bool haveA = lane < take, haveB = lane + 32 < take;
+    const int32_t kA = haveA ? stack[sp + lane] : -1;
+    const int32_t kB = haveB ? stack[sp + 32 + lane] : -1;
+    __syncwarp();  // every lane has read its entries before the stack is written again
+    int4 tpA = make_int4(0, 0, 0, 0), tpB = make_int4(0, 0, 0, 0);
+    float4 gA0 = make_float4(0.f, 0.f, 0.f, 0.f), gA1 = gA0, gB0 = gA0, gB1 = gA0;
+    if (haveA) {  // both nodes' records requested before either is tested
+      tpA = T.topo[kA];
+      gA0 = T.geom[2 * kA];
+      gA1 = T.geom[2 * kA + 1];
+    }
+    if (haveB) {
+      tpB = T.topo[kB];
+      gB0 = T.geom[2 * kB];
+      gB1 = T.geom[2 * kB + 1];
+    }
+    const int kindA = haveA ? classify(kA, tpA, gA0, gA1) : 0;
+    const int kindB = haveB ? classify(kB, tpB, gB0, gB1) : 0;
+    // accepted cells: the lanes' first nodes, then their second
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned cellsA = __ballot_sync(0xffffffffu, kindA == 1), cellsB = __ballot_sync(0xffffffffu, kindB == 1);
+    if (out.c) {
+      if (kindA == 1) {
+        const int64_t at = nc + __popc(cellsA & lt);
+        if (at < out.cap_c) out.c[at] = kA;
       }
-      kind = !open ? 1 : (tp.w == 0 ? 2 : 3);
+      if (kindB == 1) {
+        const int64_t at = nc + __popc(cellsA) + __popc(cellsB & lt);
+        if (at < out.cap_c) out.c[at] = kB;
+      }
     }
-    // accepted cells
-    const unsigned cells = __ballot_sync(0xffffffffu, kind == 1);
-    if (kind == 1 && out.c) {
-      const int64_t at = nc + __popc(cells & ((1u << lane) - 1u));
-      if (at < out.cap_c) out.c[at] = k;
-    }
-    nc += __popc(cells);
+    nc += __popc(cellsA) + __popc(cellsB);
     // particles of opened leaves
-    int ptotal = 0;
-    const int pofs = warp_excl(kind == 2 ? tp.y - tp.x : 0, lane, &ptotal);
-    if (kind == 2 && out.p)
-      for (int32_t i = tp.x; i < tp.y; i++) {
-        const int64_t at = np + pofs + (i - tp.x);
-        if (at < out.cap_p) out.p[at] = i;
-      }
-    np += ptotal;
-    // children of opened internal nodes: a new segment one level deeper
-    int ctotal = 0;
-    const int cofs = warp_excl(kind == 3 ? tp.w : 0, lane, &ctotal);
+    int ptA = 0, ptB = 0;
+    const int pofsA = warp_excl(kindA == 2 ? tpA.y - tpA.x : 0, lane, &ptA);
+    const int pofsB = warp_excl(kindB == 2 ? tpB.y - tpB.x : 0, lane, &ptB);
+    if (out.p) {
+      if (kindA == 2)
+        for (int32_t i = tpA.x; i < tpA.y; i++) {
+          const int64_t at = np + pofsA + (i - tpA.x);
+          if (at < out.cap_p) out.p[at] = i;
+        }
+      if (kindB == 2)
+        for (int32_t i = tpB.x; i < tpB.y; i++) {
+          const int64_t at = np + ptA + pofsB + (i - tpB.x);
+          if (at < out.cap_p) out.p[at] = i;
+        }
+    }
+    np += ptA + ptB;
+    // children of opened internal nodes: one new segment one level deeper
+    int ctA = 0, ctB = 0;
+    const int cofsA = warp_excl(kindA == 3 ? tpA.w : 0, lane, &ctA);
+    const int cofsB = warp_excl(kindB == 3 ? tpB.w : 0, lane, &ctB);
+    const int ctotal = ctA + ctB;
     if (ctotal > 0) {
       if (depth + 1 > kMaxLevel || sp + ctotal > kWarpStack) return false;  // not reachable for 21 levels
-      if (kind == 3)
-        for (int c = 0; c < tp.w; c++) stack[sp + cofs + c] = tp.z + c;
+      if (kindA == 3)
+        for (int c = 0; c < tpA.w; c++) stack[sp + cofsA + c] = tpA.z + c;
+      if (kindB == 3)
+        for (int c = 0; c < tpB.w; c++) stack[sp + ctA + cofsB + c] = tpB.z + c;
       depth++;
       if (lane == depth) seg = sp;
       sp += ctotal;
