@@ -89,6 +89,20 @@ qg_status qg_gtree_arrays(const qg_gtree *t, const int64_t **perm, const double 
  */
 qg_status qg_gtree_attach(qg_gtree *t, qg_ctx *ctx, double eps2_all, void *cuda_stream);
 
+/*
+ * As qg_gtree_attach, without copies: the lists of the last walk move into
+ * the context (its former list buffers move into the tree, to be reused by
+ * the next walk), their indices are not checked again (the walk produced
+ * them), and the call synchronises `cuda_stream` once instead of once per
+ * input set.  Positions, masses and moments are checked as qg_set_*_dev
+ * check them.  Afterwards, until the next qg_gtree_walk, the tree holds no
+ * lists: qg_gtree_arrays returns NULL for them and qg_gtree_attach /
+ * qg_gtree_attach_move return QG_ERR_STATE (also after a failed call).  The
+ * tree and the context must be on the same device (else QG_ERR_ARG).  The
+ * time integrator (qg_sim.h) attaches this way every step.
+ */
+qg_status qg_gtree_attach_move(qg_gtree *t, qg_ctx *ctx, double eps2_all, void *cuda_stream);
+
 /* List 4's assign_force_potential / add_force_potential: the per-sink
  * results returned to the particles.  out[perm[i]] = in[i] for k values per
  * particle (device arrays): results in sorted order back to input order. */

@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "qg_attach.h"
 #include "qg_devbuf.h"
 #include "qg_internal.h"
 #include "qg_queue.cuh"
@@ -1428,3 +1429,76 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
 const char *qg_last_error(const qg_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
 }  // extern "C"
+
+// qg_gtree_attach_move: the three qg_set_*_dev calls in one, for a tree the
+// library built and walked itself.  The list buffers are exchanged rather
+// than copied and their indices are not checked (the walk produced them);
+// positions, masses and moments are checked by the same kernels, and one
+// synchronisation reads the checks and the host copies of the offsets.
+qg_status qg::attach_tree_lists(qg_ctx *c, qg::TreeLists &t, double eps2_all, cudaStream_t s) {
+  if (!c) return QG_ERR_ARG;
+  // inputs must not change under a step that is still running
+  if (c->last_stream) cudaStreamSynchronize(c->last_stream);
+  c->sinks_ok = c->src_ok = c->cells_ok = false;
+  invalidate(c);
+  if (t.n < 0 || t.n >= INT32_MAX || t.G < 0 || t.G >= INT32_MAX || t.nn < 0 || t.nn >= INT32_MAX ||
+      !t.poff || !t.coff || !t.pidx || !t.cidx || !t.goff || (t.n > 0 && (!t.xs || !t.ms)) ||
+      (t.nn > 0 && (!t.com || !t.mass || !t.q)))
+    return fail(c, QG_ERR_ARG, "attach: bad sizes or NULL pointer");
+  if (t.device != c->device) return fail(c, QG_ERR_ARG, "attach: the tree and the context are on different devices");
+  if (!(eps2_all >= 0 && eps2_all <= qg::kMaxInput))
+    return fail(c, QG_ERR_ARG, "attach: eps2_all must be finite, >= 0 and at most 2^100");
+  DeviceGuard dg(c->device);
+  const int64_t n = t.n, G = t.G, nc = t.nn;
+  qg_status st;
+  if ((st = copy_d2d(c, c->sink_x, t.xs, 3 * n, s)) != QG_OK) return st;
+  if ((st = copy_d2d(c, c->goff, t.goff, G + 1, s)) != QG_OK) return st;
+  std::swap(c->poff, *t.poff);
+  std::swap(c->pidx, *t.pidx);
+  std::swap(c->coff, *t.coff);
+  std::swap(c->cidx, *t.cidx);
+  if ((st = copy_d2d(c, c->src_m64, t.ms, n, s)) != QG_OK) return st;
+  if ((st = copy_d2d(c, c->cell_m64, t.mass, nc, s)) != QG_OK) return st;
+  if (c->src.reserve(n) != cudaSuccess || c->src_f.reserve(n) != cudaSuccess || c->cell_pm.reserve(nc) != cudaSuccess ||
+      c->cell_f.reserve(nc) != cudaSuccess || c->cell_q.reserve(2 * nc) != cudaSuccess ||
+      c->cell_q64.reserve(6 * nc) != cudaSuccess)
+    return fail(c, QG_ERR_NOMEM, "attach: source and cell allocation");
+  int *flags = nullptr;
+  if ((st = value_flags_begin(c, s, &flags)) != QG_OK) return st;
+  if ((st = group_centres(c, n, G, nullptr, flags, s)) != QG_OK) return st;
+  if (n) pack_src_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, t.xs, c->src_m64.p, c->src.p, c->src_f.p, flags);
+  if (nc)
+    pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, t.com, c->cell_m64.p, t.q, c->cell_pm.p, c->cell_f.p,
+                                                         c->cell_q.p, c->cell_q64.p, flags);
+  QG_CUDA(c, cudaGetLastError());
+  std::vector<int64_t> hg(G + 1), hp(G + 1), hc(G + 1);
+  QG_CUDA(c, cudaMemcpyAsync(hg.data(), c->goff.p, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  QG_CUDA(c, cudaMemcpyAsync(hp.data(), c->poff.p, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  QG_CUDA(c, cudaMemcpyAsync(hc.data(), c->coff.p, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  int fl = 0;
+  if ((st = value_flags_end(c, s, flags, &fl)) != QG_OK) return st;
+  if (fl & kBadPosition)
+    return fail(c, QG_ERR_ARG, "attach: a position, mass or quadrupole component is not finite or exceeds 2^100");
+  if (hp[G] != t.np_list || hc[G] != t.nc_list || hg[G] != n)
+    return fail(c, QG_ERR_STATE, "attach: the tree's list sizes do not match its offsets");
+  c->n = n;
+  c->G = G;
+  c->has_eps2 = false;
+  c->eps2_all = eps2_all;
+  c->eps_positive = eps2_all >= 0x1p-126;
+  c->h_goff.swap(hg);
+  c->sinks_ok = true;
+  c->ran = false;
+  c->ns = n;
+  c->G_src = G;
+  c->np_list = t.np_list;
+  c->h_poff.swap(hp);
+  c->src_ok = true;
+  c->nc = nc;
+  c->G_cell = G;
+  c->nc_list = t.nc_list;
+  c->h_coff.swap(hc);
+  c->cells_ok = true;
+  update_counts(c);
+  return QG_OK;
+}

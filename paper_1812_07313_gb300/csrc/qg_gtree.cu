@@ -8,12 +8,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <new>
 #include <vector>
 
+#include "qg_attach.h"
 #include "qg_devbuf.h"
 #include "qg_gtree.h"
 #include "qgrav.h"
@@ -115,6 +117,7 @@ struct qg_gtree {
   int64_t n = 0, nsys = 0, nnodes = 0, G = 0, np_list = 0, nc_list = 0;
   int leaf_max = 8, n_crit = 64;
   bool built = false, walked = false;
+  bool lists_moved = false;  // the last walk's lists went to a force context (qg_gtree_attach_move)
   std::vector<int64_t> h_sys_off;
   // particles
   DBuf<int64_t> perm;
@@ -792,6 +795,18 @@ __device__ __forceinline__ int node_opens32(float4 ga, float4 gb, float th2, flo
   return 2;
 }
 
+// Finite doubles as signed 64-bit integers in the same order: a negative
+// value's magnitude bits are flipped (-0 then sorts just below +0, which
+// changes no comparison made with the result).  A group's box is reduced on
+// these keys and turned back into the exact FP64 extremes.
+__device__ __forceinline__ long long order_key(double v) {
+  const long long b = __double_as_longlong(v);
+  return b < 0 ? b ^ 0x7fffffffffffffffLL : b;
+}
+__device__ __forceinline__ double key_value(long long k) {
+  return __longlong_as_double(k < 0 ? k ^ 0x7fffffffffffffffLL : k);
+}
+
 // Where one group's list entries go: particle entries at p[0, cap_p), cell
 // entries at c[0, cap_c); entries past a capacity (or with a null pointer)
 // are counted but not written.
@@ -815,18 +830,23 @@ __device__ bool walk_group(const WalkTree &T, int64_t g, double theta2, float th
                            int64_t &np, int64_t &nc, double *box64) {
   const int lane = threadIdx.x & 31;
   const int32_t gb = (int32_t)T.group_off[g], ge = (int32_t)T.group_off[g + 1];
-  double bmin[3] = {INFINITY, INFINITY, INFINITY}, bmax[3] = {-INFINITY, -INFINITY, -INFINITY};
+  // the group's box, reduced on ordered integer keys of the coordinates (the
+  // integer pipes; the FP64 pipe is the scarcest one on this GPU)
+  long long kmin[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX}, kmax[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
   for (int64_t i = gb + lane; i < ge; i += 32)
     for (int d = 0; d < 3; d++) {
-      bmin[d] = fmin(bmin[d], T.xs[3 * i + d]);
-      bmax[d] = fmax(bmax[d], T.xs[3 * i + d]);
+      const long long k = order_key(T.xs[3 * i + d]);
+      kmin[d] = min(kmin[d], k);
+      kmax[d] = max(kmax[d], k);
     }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
     for (int d = 0; d < 3; d++) {
-      bmin[d] = fmin(bmin[d], __shfl_xor_sync(0xffffffffu, bmin[d], o));
-      bmax[d] = fmax(bmax[d], __shfl_xor_sync(0xffffffffu, bmax[d], o));
+      kmin[d] = min(kmin[d], __shfl_xor_sync(0xffffffffu, kmin[d], o));
+      kmax[d] = max(kmax[d], __shfl_xor_sync(0xffffffffu, kmax[d], o));
     }
+  const double bmin[3] = {key_value(kmin[0]), key_value(kmin[1]), key_value(kmin[2])};
+  const double bmax[3] = {key_value(kmax[0]), key_value(kmax[1]), key_value(kmax[2])};
   const int32_t root = T.sys_root[T.nsysid[T.group_node[g]]];
   const double o0 = T.centre[3 * root], o1 = T.centre[3 * root + 1], o2 = T.centre[3 * root + 2], S = T.side[root];
   const double u = 1.0 / S, omax = fmax(fabs(o0), fmax(fabs(o1), fabs(o2)));
@@ -1483,6 +1503,7 @@ static qg_status walk_impl(qg_gtree *t, double theta, cudaStream_t s) {
   t->np_list = tot[0];
   t->nc_list = tot[1];
   t->walked = true;
+  t->lists_moved = false;
   return QG_OK;
 }
 
@@ -1524,22 +1545,47 @@ qg_status qg_gtree_arrays(const qg_gtree *t, const int64_t **perm, const double 
   if (cell_q) *cell_q = t->q.p;
   if (cell_side) *cell_side = t->side.p;
   if (group_off) *group_off = t->group_off.p;
-  if (plist_off) *plist_off = t->walked ? t->plist_off.p : nullptr;
-  if (plist_idx) *plist_idx = t->walked ? t->plist_idx.p : nullptr;
-  if (clist_off) *clist_off = t->walked ? t->clist_off.p : nullptr;
-  if (clist_idx) *clist_idx = t->walked ? t->clist_idx.p : nullptr;
+  const bool lists = t->walked && !t->lists_moved;
+  if (plist_off) *plist_off = lists ? t->plist_off.p : nullptr;
+  if (plist_idx) *plist_idx = lists ? t->plist_idx.p : nullptr;
+  if (clist_off) *clist_off = lists ? t->clist_off.p : nullptr;
+  if (clist_idx) *clist_idx = lists ? t->clist_idx.p : nullptr;
   return QG_OK;
 }
 
 qg_status qg_gtree_attach(qg_gtree *t, qg_ctx *ctx, double eps2_all, void *stream) {
   if (!t || !ctx) return QG_ERR_ARG;
-  if (!t->built || !t->walked) return QG_ERR_STATE;
+  if (!t->built || !t->walked || t->lists_moved) return QG_ERR_STATE;
   qg_status st = qg_set_sinks_dev(ctx, t->n, t->xs.p, nullptr, eps2_all, t->G, t->group_off.p, stream);
   if (st != QG_OK) return st;
   st = qg_set_sources_dev(ctx, t->n, t->xs.p, t->ms.p, t->plist_off.p, t->plist_idx.p, t->np_list, stream);
   if (st != QG_OK) return st;
   return qg_set_cells_dev(ctx, t->nnodes, t->com.p, t->mass.p, t->q.p, t->clist_off.p, t->clist_idx.p, t->nc_list,
                           stream);
+}
+
+qg_status qg_gtree_attach_move(qg_gtree *t, qg_ctx *ctx, double eps2_all, void *stream) {
+  if (!t || !ctx) return QG_ERR_ARG;
+  if (!t->built || !t->walked || t->lists_moved) return QG_ERR_STATE;
+  qg::TreeLists L;
+  L.device = t->device;
+  L.n = t->n;
+  L.G = t->G;
+  L.nn = t->nnodes;
+  L.np_list = t->np_list;
+  L.nc_list = t->nc_list;
+  L.xs = t->xs.p;
+  L.ms = t->ms.p;
+  L.com = t->com.p;
+  L.mass = t->mass.p;
+  L.q = t->q.p;
+  L.goff = t->group_off.p;
+  L.poff = &t->plist_off;
+  L.coff = &t->clist_off;
+  L.pidx = &t->plist_idx;
+  L.cidx = &t->clist_idx;
+  t->lists_moved = true;  // from here on the list buffers may be the context's former ones
+  return qg::attach_tree_lists(ctx, L, eps2_all, (cudaStream_t)stream);
 }
 
 qg_status qg_gtree_unsort(const qg_gtree *t, const double *in, double *out, int k, void *stream) {

@@ -206,7 +206,7 @@ qg_status evaluate(qg_sim *s, cudaStream_t st, bool kick, double h) {
     SIM_OK(qg_set_sources_dev(s->ctx, s->n, xs, ms, poff, pidx, np, st));
     SIM_OK(qg_set_cells_dev(s->ctx, nn, ccom, cm, cq, coff, cidx, nc, st));
   } else {
-    SIM_OK(qg_gtree_attach(s->tree, s->ctx, s->prm.eps2, st));
+    SIM_OK(qg_gtree_attach_move(s->tree, s->ctx, s->prm.eps2, st));
   }
   if (s->prm.autotune) {
     // a full qg_autotune at the first force evaluation; afterwards, whenever

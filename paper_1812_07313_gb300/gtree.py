@@ -29,6 +29,7 @@ SIGNATURES = {
     "qg_gtree_sizes": ([_vp, _vp, _vp, _vp, _vp, _vp], _int),
     "qg_gtree_arrays": ([_vp] + [_vp] * 14, _int),
     "qg_gtree_attach": ([_vp, _vp, _dbl, _vp], _int),
+    "qg_gtree_attach_move": ([_vp, _vp, _dbl, _vp], _int),
     "qg_gtree_unsort": ([_vp, _vp, _vp, _int, _vp], _int),
     "qg_gtree_timing": ([_vp, _vp, _vp], _int),
 }
@@ -131,6 +132,13 @@ class GpuTree:
     def attach(self, ctx, eps2_all, stream=None):
         """Set a qgrav.Context's sinks, sources and cells from this tree (device to device)."""
         self._ok(self._L.qg_gtree_attach(self._h, ctx._h, float(eps2_all), stream), "qg_gtree_attach")
+        sz = self.sizes()
+        ctx.n, ctx.G = sz["n"], sz["ngroups"]
+
+    def attach_move(self, ctx, eps2_all, stream=None):
+        """As attach, with the lists moved into the context instead of copied:
+        the tree holds no lists until its next walk."""
+        self._ok(self._L.qg_gtree_attach_move(self._h, ctx._h, float(eps2_all), stream), "qg_gtree_attach_move")
         sz = self.sizes()
         ctx.n, ctx.G = sz["n"], sz["ngroups"]
 

@@ -202,6 +202,58 @@ def test_gpu_built_step_matches_oracle_and_host_lists():
     t.close()
 
 
+def test_attach_move_equals_attach():
+    """qg_gtree_attach_move hands the walk's lists to a context without copies:
+    the step equals the one from the copying attach bit for bit; the tree then
+    holds no lists (NULL pointers, QG_ERR_STATE on a second attach) until its
+    next walk; the buffers it got back serve that walk; and a context that
+    takes lists twice in a row (as the integrator does every step) keeps
+    giving the copying attach's results."""
+    import torch
+    ps = workloads.small_set("plummer", 30000, 11, 1e-2)
+    eps2 = 1e-4
+    t = _gpu_tree(ps, 8, 64, 0.5)
+    ctx_copy, ctx_move = qgrav.Context(0), qgrav.Context(0)
+    t.attach(ctx_copy, eps2)
+    ctx_copy.qg_run()
+    a0, p0 = ctx_copy.qg_get_forces()
+    st0 = ctx_copy.qg_get_stats()
+    t.attach_move(ctx_move, eps2)
+    assert t.pointers()["plist_idx"] is None and t.pointers()["clist_off"] is None
+    for attach in (t.attach, t.attach_move):
+        with pytest.raises(qgrav.QGError) as e:
+            attach(qgrav.Context(0), eps2)
+        assert e.value.status == qgrav.QG_ERR_STATE
+    ctx_move.qg_run()
+    a1, p1 = ctx_move.qg_get_forces()
+    st1 = ctx_move.qg_get_stats()
+    assert np.array_equal(a1, a0) and np.array_equal(p1, p0)
+    for k in ("n_sinks", "n_groups", "n_plist", "n_clist", "i_pp", "i_pc"):
+        assert st1[k] == st0[k], k
+    # a second system through the same tree and the same two contexts
+    ps2 = workloads.small_set("sphere", 12000, 3, 1e-2)
+    t.build(torch.as_tensor(ps2.x).cuda(), torch.as_tensor(ps2.m).cuda(), ps2.sys_off, 8, 32)
+    t.walk(0.6)
+    t.attach(ctx_copy, eps2)
+    ctx_copy.qg_run()
+    a2, p2 = ctx_copy.qg_get_forces()
+    t.attach_move(ctx_move, eps2)
+    ctx_move.qg_run()
+    a3, p3 = ctx_move.qg_get_forces()
+    assert np.array_equal(a3, a2) and np.array_equal(p3, p2)
+    # and the first system again: the walk refills the buffers the tree got back
+    t.build(torch.as_tensor(ps.x).cuda(), torch.as_tensor(ps.m).cuda(), ps.sys_off, 8, 64)
+    t.walk(0.5)
+    assert t.pointers()["plist_idx"] is not None
+    t.attach_move(ctx_move, eps2)
+    ctx_move.qg_run()
+    a4, p4 = ctx_move.qg_get_forces()
+    assert np.array_equal(a4, a0) and np.array_equal(p4, p0)
+    for c in (ctx_copy, ctx_move):
+        c.close()
+    t.close()
+
+
 @pytest.mark.parametrize("name", ["cube_1m", "plummer_4m"])
 def test_full_size_gpu_built_step_sampled(name):
     """The whole step on the GPU at full size (tree, moments, groups, walk,
