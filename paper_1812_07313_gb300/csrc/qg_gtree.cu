@@ -567,10 +567,11 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
         c1 += ms[i] * xs[3 * i + 1];
         c2 += ms[i] * xs[3 * i + 2];
       }
-      if (M > 0) {
-        c0 /= M;
-        c1 /= M;
-        c2 /= M;
+      if (M > 0) {  // one FP64 division, the host builder's expressions
+        const double inv = 1.0 / M;
+        c0 *= inv;
+        c1 *= inv;
+        c2 *= inv;
       }
       // Q = 3 S - tr(S) I with S = sum m r r^T, the host builder's expressions
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
@@ -601,10 +602,11 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
         c1 += mass[cj] * com[3 * cj + 1];
         c2 += mass[cj] * com[3 * cj + 2];
       }
-      if (M > 0) {
-        c0 /= M;
-        c1 /= M;
-        c2 /= M;
+      if (M > 0) {  // one FP64 division, the host builder's expressions
+        const double inv = 1.0 / M;
+        c0 *= inv;
+        c1 *= inv;
+        c2 *= inv;
       }
       // parallel-axis shift: Q = sum Q_c + 3 S - tr(S) I with S = sum m_c d d^T
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
@@ -872,9 +874,10 @@ __device__ bool walk_group(const WalkTree &T, int64_t g, double theta2, float th
   nc = 0;
   // kind of a popped node: 1 = accepted cell, 2 = opened leaf (its
   // particles), 3 = opened internal node (its children); 0 = no node
+  const bool test = theta2 > 0.0;  // theta = 0 opens every node
   auto classify = [&](int32_t k, const int4 &tp, const float4 &ga, const float4 &gb2) -> int {
     bool open = true;
-    if (theta2 > 0.0 && !(tp.x < ge && tp.y > gb)) {
+    if (test && !(tp.x < ge && tp.y > gb)) {
       const int dec = node_opens32(ga, gb2, th2, dl, lo, hi);
       open = dec == 2 ? node_opens64(k, theta2, T.centre, T.side, T.com, box64, box64 + 3) : dec == 1;
     }

@@ -266,7 +266,10 @@ extern "C" int qgt_build(int64_t n, const double *x, const double *m, int64_t ns
             M += t->ms[i];
             for (int d = 0; d < 3; d++) c[d] += t->ms[i] * t->xs[3 * i + d];
           }
-          if (M > 0) for (int d = 0; d < 3; d++) c[d] /= M;
+          if (M > 0) {  // one division (the GPU builder evaluates the same expressions)
+            const double inv = 1.0 / M;
+            for (int d = 0; d < 3; d++) c[d] *= inv;
+          }
           // Eq. 2 as Q = 3 S - tr(S) I with S = sum m r r^T (the same sum,
           // fewer operations; the GPU builder evaluates the same expressions)
           double sm[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -294,7 +297,10 @@ extern "C" int qgt_build(int64_t n, const double *x, const double *m, int64_t ns
             M += t->mass[cj];
             for (int d = 0; d < 3; d++) c[d] += t->mass[cj] * t->com[3 * cj + d];
           }
-          if (M > 0) for (int d = 0; d < 3; d++) c[d] /= M;
+          if (M > 0) {  // one division (the GPU builder evaluates the same expressions)
+            const double inv = 1.0 / M;
+            for (int d = 0; d < 3; d++) c[d] *= inv;
+          }
           // parallel-axis shift of each child's tensor to the parent's COM:
           // Q = sum Q_c + 3 S - tr(S) I with S = sum m_c d d^T
           double sm[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, qs[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
