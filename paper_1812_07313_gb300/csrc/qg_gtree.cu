@@ -548,6 +548,8 @@ __global__ void emit_children_kernel(int32_t lb, int32_t le, int32_t base, int l
 
 // ------------------------------------------------------------------ moments (Eq. 2)
 
+constexpr int kMomentBatch = 8;  // leaves of up to this many particles load them all first
+
 __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64_t *__restrict__ nbeg,
                                const int64_t *__restrict__ nend, const int32_t *__restrict__ nfirst,
                                const int32_t *__restrict__ nnchild, const double *__restrict__ xs,
@@ -559,14 +561,29 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
     double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0, q4 = 0.0, q5 = 0.0;
     const int nc = nnchild[j];
     if ((nc != 0) != (internal != 0)) continue;
-    if (nc == 0) {
-      const int64_t b = nbeg[j], e = nend[j];
-      for (int64_t i = b; i < e; i++) {
-        M += ms[i];
-        c0 += ms[i] * xs[3 * i];
-        c1 += ms[i] * xs[3 * i + 1];
-        c2 += ms[i] * xs[3 * i + 2];
+    if (nc == 0 && nend[j] - nbeg[j] <= kMomentBatch) {
+      // a leaf of at most kMomentBatch particles: every particle's position
+      // and mass requested before the sums start (the sums themselves run in
+      // particle order, the host builder's expressions)
+      const int64_t b = nbeg[j];
+      const int cnt = (int)(nend[j] - b);
+      double px[kMomentBatch], py[kMomentBatch], pz[kMomentBatch], pm[kMomentBatch];
+#pragma unroll
+      for (int k = 0; k < kMomentBatch; k++) {
+        const bool in = k < cnt;
+        px[k] = in ? xs[3 * (b + k)] : 0.0;
+        py[k] = in ? xs[3 * (b + k) + 1] : 0.0;
+        pz[k] = in ? xs[3 * (b + k) + 2] : 0.0;
+        pm[k] = in ? ms[b + k] : 0.0;
       }
+#pragma unroll
+      for (int k = 0; k < kMomentBatch; k++)
+        if (k < cnt) {
+          M += pm[k];
+          c0 += pm[k] * px[k];
+          c1 += pm[k] * py[k];
+          c2 += pm[k] * pz[k];
+        }
       if (M > 0) {  // one FP64 division, the host builder's expressions
         const double inv = 1.0 / M;
         c0 *= inv;
@@ -574,6 +591,40 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
         c2 *= inv;
       }
       // Q = 3 S - tr(S) I with S = sum m r r^T, the host builder's expressions
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
+#pragma unroll
+      for (int k = 0; k < kMomentBatch; k++)
+        if (k < cnt) {
+          const double r0 = px[k] - c0, r1 = py[k] - c1, r2c = pz[k] - c2;
+          const double m0 = pm[k] * r0, m1 = pm[k] * r1, m2 = pm[k] * r2c;
+          s0 += m0 * r0;
+          s1 += m0 * r1;
+          s2 += m0 * r2c;
+          s3 += m1 * r1;
+          s4 += m1 * r2c;
+          s5 += m2 * r2c;
+        }
+      const double tr = s0 + s3 + s5;
+      q0 = 3 * s0 - tr;
+      q1 = 3 * s1;
+      q2 = 3 * s2;
+      q3 = 3 * s3 - tr;
+      q4 = 3 * s4;
+      q5 = 3 * s5 - tr;
+    } else if (nc == 0) {  // a larger leaf (coincident particles at the deepest level)
+      const int64_t b = nbeg[j], e = nend[j];
+      for (int64_t i = b; i < e; i++) {
+        M += ms[i];
+        c0 += ms[i] * xs[3 * i];
+        c1 += ms[i] * xs[3 * i + 1];
+        c2 += ms[i] * xs[3 * i + 2];
+      }
+      if (M > 0) {
+        const double inv = 1.0 / M;
+        c0 *= inv;
+        c1 *= inv;
+        c2 *= inv;
+      }
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
       for (int64_t i = b; i < e; i++) {
         const double r0 = xs[3 * i] - c0, r1 = xs[3 * i + 1] - c1, r2c = xs[3 * i + 2] - c2;
@@ -594,14 +645,27 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
       q4 = 3 * s4;
       q5 = 3 * s5 - tr;
     } else {
+      // an internal node (at most 8 children): the children's masses and
+      // centres requested before the sums start, then their tensors; every
+      // sum runs in child order, the host builder's expressions
       const int f = nfirst[j];
-      for (int ch = 0; ch < nc; ch++) {
-        const int cj = f + ch;
-        M += mass[cj];
-        c0 += mass[cj] * com[3 * cj];
-        c1 += mass[cj] * com[3 * cj + 1];
-        c2 += mass[cj] * com[3 * cj + 2];
+      double cm[8], cx[8], cy[8], cz[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        const bool in = k < nc;
+        cm[k] = in ? mass[f + k] : 0.0;
+        cx[k] = in ? com[3 * (f + k)] : 0.0;
+        cy[k] = in ? com[3 * (f + k) + 1] : 0.0;
+        cz[k] = in ? com[3 * (f + k) + 2] : 0.0;
       }
+#pragma unroll
+      for (int k = 0; k < 8; k++)
+        if (k < nc) {
+          M += cm[k];
+          c0 += cm[k] * cx[k];
+          c1 += cm[k] * cy[k];
+          c2 += cm[k] * cz[k];
+        }
       if (M > 0) {  // one FP64 division, the host builder's expressions
         const double inv = 1.0 / M;
         c0 *= inv;
@@ -610,25 +674,29 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
       }
       // parallel-axis shift: Q = sum Q_c + 3 S - tr(S) I with S = sum m_c d d^T
       double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
-      for (int ch = 0; ch < nc; ch++) {
-        const int cj = f + ch;
-        const double mc = mass[cj];
-        const double r0 = com[3 * cj] - c0, r1 = com[3 * cj + 1] - c1, r2c = com[3 * cj + 2] - c2;
-        const double m0 = mc * r0, m1 = mc * r1, m2 = mc * r2c;
-        s0 += m0 * r0;
-        s1 += m0 * r1;
-        s2 += m0 * r2c;
-        s3 += m1 * r1;
-        s4 += m1 * r2c;
-        s5 += m2 * r2c;
-        const double *qc = q + 6 * cj;
-        q0 += qc[0];
-        q1 += qc[1];
-        q2 += qc[2];
-        q3 += qc[3];
-        q4 += qc[4];
-        q5 += qc[5];
-      }
+#pragma unroll
+      for (int k = 0; k < 8; k++)
+        if (k < nc) {
+          const double r0 = cx[k] - c0, r1 = cy[k] - c1, r2c = cz[k] - c2;
+          const double m0 = cm[k] * r0, m1 = cm[k] * r1, m2 = cm[k] * r2c;
+          s0 += m0 * r0;
+          s1 += m0 * r1;
+          s2 += m0 * r2c;
+          s3 += m1 * r1;
+          s4 += m1 * r2c;
+          s5 += m2 * r2c;
+        }
+#pragma unroll
+      for (int k = 0; k < 8; k++)
+        if (k < nc) {
+          const double *qc = q + 6 * (f + k);
+          q0 += qc[0];
+          q1 += qc[1];
+          q2 += qc[2];
+          q3 += qc[3];
+          q4 += qc[4];
+          q5 += qc[5];
+        }
       const double tr = s0 + s3 + s5;
       q0 = q0 + (3 * s0 - tr);
       q1 = q1 + 3 * s1;
