@@ -25,6 +25,8 @@ namespace {
 constexpr int kMaxLevel = 21;   // 21 bits per axis -> 63-bit Morton keys
 constexpr int kScanThreads = 256, kScanItems = 4, kScanTile = kScanThreads * kScanItems;
 constexpr int kSortThreads = 256, kSortItems = 8, kSortTile = kSortThreads * kSortItems;
+// the digit histograms give each thread of a block one of the 256 digits
+static_assert(kSortThreads == 256, "radix sort blocks have one thread per digit");
 
 template <typename T>
 using DBuf = qg::DevBuf<T>;
