@@ -357,8 +357,8 @@ qg_status qg_round_f32_dev(int64_t n, const double *in, float *out, float *out_h
  * call's contents (each call clears what it needs zeroed): calls whose work
  * overlaps on the GPU -- on different streams, or from racing host threads
  * -- corrupt each other.  The first call on a device looks up the array's
- * device address and caches it (make that first call before any stream
- * capture).  The call waits for the argument check on `cuda_stream`, then
+ * device address and caches it.  The call waits for the argument check on
+ * `cuda_stream` (a device-to-host copy and a stream synchronisation), then
  * launches the step and returns; a and phi are complete when the stream
  * reaches that point.
  */

@@ -17,10 +17,9 @@
 // work overlaps on the GPU (different streams, or host threads racing)
 // corrupt each other's queue.  The first call on a device looks the array's
 // device address up (cudaGetSymbolAddress, with that device current) and
-// caches it together with the kernels' occupancy; make that first call
-// before any stream capture.  Every call also waits on the host for its
-// argument check: it copies the check's flags back and synchronises the
-// caller's stream before it launches the step.
+// caches it together with the kernels' occupancy.  Every call also waits on
+// the host for its argument check: it copies the check's flags back and
+// synchronises the caller's stream before it launches the step.
 #include <cuda_runtime.h>
 
 #include <cstdint>
