@@ -17,7 +17,7 @@
  *     particles, and side^2 < theta^2 d^2 (d: distance from the node's centre
  *     of mass to the box; the test l/d < theta of Sec. 1); otherwise a leaf's
  *     particles join the j-particle list and an internal node is opened.
- *     One warp walks one group, testing up to 32 nodes at once; each group's
+ *     One warp walks one group, testing up to 64 nodes at once; each group's
  *     lists hold the same entries as the host's depth-first walk, in the
  *     walk's own fixed order (deterministic from run to run).
  * Node numbering differs from the host builder's (level by level here); the
@@ -74,6 +74,9 @@ qg_status qg_gtree_sizes(const qg_gtree *t, int64_t *n, int64_t *nnodes, int64_t
  *   int32, cell_com [nnodes][3], cell_m [nnodes], cell_q [nnodes][6] (q00 q01
  *   q02 q11 q12 q22), cell_side [nnodes]; group_off [ngroups+1] int64;
  *   plist_off / clist_off [ngroups+1] int64, plist_idx / clist_idx int32.
+ * The walk leaves each group's lists where it finished them; the first call
+ * that asks for a list array puts the lists in group (CSR) order, on the
+ * walk's stream, and waits for it.
  */
 qg_status qg_gtree_arrays(const qg_gtree *t, const int64_t **perm, const double **xs, const double **ms,
                           const int64_t **node_range, const int32_t **node_level, const double **cell_com,
@@ -85,16 +88,19 @@ qg_status qg_gtree_arrays(const qg_gtree *t, const int64_t **perm, const double 
  * Hands the groups and lists to the force calls, as List 4 passes each
  * group's i_list, j_list and j_cell to the g5_ / g5c_ calls:
  * set a force context's sinks (the sorted particles), sources and cells from
- * the last build and walk, device to device.  eps2_all as in qg_set_sinks.
+ * the last build and walk, device to device (the lists in CSR order, made
+ * first if need be).  eps2_all as in qg_set_sinks.
  */
 qg_status qg_gtree_attach(qg_gtree *t, qg_ctx *ctx, double eps2_all, void *cuda_stream);
 
 /*
  * As qg_gtree_attach, without copies: the lists of the last walk move into
- * the context (its former list buffers move into the tree, to be reused by
- * the next walk), their indices are not checked again (the walk produced
- * them), and the call synchronises `cuda_stream` once instead of once per
- * input set.  Positions, masses and moments are checked as qg_set_*_dev
+ * the context as the walk left them (each group's entries where the walk
+ * finished them, with per-group begin / end offsets, so no CSR pass runs),
+ * the context's former list buffers move into the tree, to be reused by the
+ * next walk, their indices are not checked again (the walk produced them),
+ * and the call synchronises `cuda_stream` once instead of once per input
+ * set.  Positions, masses and moments are checked as qg_set_*_dev
  * check them.  Afterwards, until the next qg_gtree_walk, the tree holds no
  * lists: qg_gtree_arrays returns NULL for them and qg_gtree_attach /
  * qg_gtree_attach_move return QG_ERR_STATE (also after a failed call).  The

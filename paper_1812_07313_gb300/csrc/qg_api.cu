@@ -198,9 +198,13 @@ struct qg_ctx {
   DevBuf<qg::PosMassF> src_f;
   DevBuf<double> src_m64;
   DevBuf<double> stage_x;  // device staging of host positions
-  DevBuf<int64_t> poff;
+  // group g's list: pidx[poff[g] .. poff[g + 1]) (CSR, the qg_set_* layout)
+  // or, when p_ranges, pidx[poff[g] .. pend[g]) (a GPU tree's lists in the
+  // order its walk produced them, qg_gtree_attach_move)
+  DevBuf<int64_t> poff, pend;
   DevBuf<int32_t> pidx;
-  std::vector<int64_t> h_poff;
+  std::vector<int64_t> h_poff, h_pend;
+  bool p_ranges = false;
   // cells
   int64_t nc = 0, G_cell = -1, nc_list = 0;
   bool cells_ok = false;
@@ -209,9 +213,10 @@ struct qg_ctx {
   DevBuf<double> cell_m64;
   DevBuf<float4> cell_q;
   DevBuf<double> cell_q64;
-  DevBuf<int64_t> coff;
+  DevBuf<int64_t> coff, cend;  // as poff / pend
   DevBuf<int32_t> cidx;
-  std::vector<int64_t> h_coff;
+  std::vector<int64_t> h_coff, h_cend;
+  bool c_ranges = false;
   // outputs and queue
   DevBuf<double> a, phi;
   DevBuf<int> scratch;  // hist[kBuckets], cursor[kBuckets], head, bad
@@ -332,6 +337,17 @@ int grid_for(int64_t n, int block) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 4096));
 }
 
+// Host-side list lengths and device-side list ends of group g (CSR offsets
+// or begin / end ranges).
+int64_t plen(const qg_ctx *c, int64_t g) {
+  return c->p_ranges ? c->h_pend[g] - c->h_poff[g] : c->h_poff[g + 1] - c->h_poff[g];
+}
+int64_t clen(const qg_ctx *c, int64_t g) {
+  return c->c_ranges ? c->h_cend[g] - c->h_coff[g] : c->h_coff[g + 1] - c->h_coff[g];
+}
+const int64_t *pend_dev(const qg_ctx *c) { return c->p_ranges ? c->pend.p : c->poff.p + 1; }
+const int64_t *cend_dev(const qg_ctx *c) { return c->c_ranges ? c->cend.p : c->coff.p + 1; }
+
 // Stats that depend on every input.
 void update_counts(qg_ctx *c) {
   c->stats.n_sinks = c->n;
@@ -344,8 +360,8 @@ void update_counts(qg_ctx *c) {
   if (c->sinks_ok && (int64_t)c->h_goff.size() == c->G + 1) {
     for (int64_t g = 0; g < c->G; g++) {
       const int64_t ni = c->h_goff[g + 1] - c->h_goff[g];
-      if (c->src_ok && c->G_src == c->G) ipp += ni * (c->h_poff[g + 1] - c->h_poff[g]);
-      if (c->cells_ok && c->G_cell == c->G) ipc += ni * (c->h_coff[g + 1] - c->h_coff[g]);
+      if (c->src_ok && c->G_src == c->G) ipp += ni * plen(c, g);
+      if (c->cells_ok && c->G_cell == c->G) ipc += ni * clen(c, g);
     }
   }
   c->stats.i_pp = ipp;
@@ -429,12 +445,14 @@ qg::ForceParams force_params(qg_ctx *c, int64_t g0, int64_t G, int *head) {
   p.src = c->src.p;
   p.src_m64 = c->src_m64.p;
   p.plist_off = c->poff.p + g0;
+  p.plist_end = pend_dev(c) + g0;
   p.plist_idx = c->pidx.p;
   p.cell_pm = c->cell_pm.p;
   p.cell_m64 = c->cell_m64.p;
   p.cell_q = c->cell_q.p;
   p.cell_q64 = c->cell_q64.p;
   p.clist_off = c->coff.p + g0;
+  p.clist_end = cend_dev(c) + g0;
   p.clist_idx = c->cidx.p;
   p.queue = c->queue.p + g0;
   p.nitems = (int32_t)G;
@@ -462,12 +480,11 @@ qg_status build_items(qg_ctx *c) {
   const int64_t G = c->G;
   if (split == 0 || G <= 0) return QG_OK;
   const double cell_ops = c->opt.expansion == QG_QUAD ? 33.0 : 13.0;
-  const std::vector<int64_t> &go = c->h_goff, &po = c->h_poff, &co = c->h_coff;
+  const std::vector<int64_t> &go = c->h_goff;
   double share = 0.0;
   if (split < 0) {
     for (int64_t g = 0; g < G; g++) {
-      const double ni = (double)(go[g + 1] - go[g]), np = (double)(po[g + 1] - po[g]),
-                   nc = (double)(co[g + 1] - co[g]);
+      const double ni = (double)(go[g + 1] - go[g]), np = (double)plen(c, g), nc = (double)clen(c, g);
       share += ni * (13.0 * np + cell_ops * nc) + 64.0 * (np + nc) + 256.0;
     }
     share /= std::max(c->grid, 1);
@@ -477,7 +494,7 @@ qg_status build_items(qg_ctx *c) {
   int64_t slot = 0;
   int ctr = 0;
   for (int64_t g = 0; g < G; g++) {
-    const int64_t ni = go[g + 1] - go[g], np = po[g + 1] - po[g], nc = co[g + 1] - co[g], ne = np + nc;
+    const int64_t ni = go[g + 1] - go[g], np = plen(c, g), nc = clen(c, g), ne = np + nc;
     int64_t P = 1;
     if (ni > 0 && ne > 1) {
       if (split > 0) {
@@ -533,11 +550,11 @@ qg_status record_step(qg_ctx *c, cudaStream_t s) {
   const int64_t NI = c->n_items ? c->n_items : G;  // work items: groups, or groups and parts of split lists
   if (c->n_items) {
     QG_CUDA(c, cudaMemsetAsync(c->done.p, 0, std::max(c->n_split, 1) * sizeof(int), s));
-    queue_hist_items_kernel<<<grid_for(NI, 256), 256, 0, s>>>(NI, c->items.p, c->goff.p, c->poff.p, cell_ops,
-                                                               c->bucket.p, hist);
+    queue_hist_items_kernel<<<grid_for(NI, 256), 256, 0, s>>>(NI, c->items.p, c->goff.p, c->poff.p, pend_dev(c),
+                                                               cell_ops, c->bucket.p, hist);
   } else {
-    queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->goff.p, c->poff.p, c->coff.p, cell_ops,
-                                                        c->bucket.p, hist);
+    queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->goff.p, c->poff.p, pend_dev(c), c->coff.p,
+                                                        cend_dev(c), cell_ops, c->bucket.p, hist);
   }
   QG_CUDA(c, cudaGetLastError());
   queue_scatter_kernel<<<grid_for(NI, 256), 256, 0, s>>>(NI, c->bucket.p, hist, cursor, c->queue.p);
@@ -700,7 +717,7 @@ void qg_destroy(qg_ctx *c) {
   c->gcentre.release(); c->gcentre_f.release(); c->sink_f.release();
   c->items.release(); c->partial.release(); c->done.release();
   c->src.release(); c->src_f.release(); c->src_m64.release(); c->stage_x.release();
-  c->poff.release(); c->pidx.release();
+  c->poff.release(); c->pend.release(); c->pidx.release(); c->cend.release();
   c->cell_pm.release(); c->cell_f.release(); c->cell_m64.release(); c->cell_q.release(); c->cell_q64.release(); c->coff.release(); c->cidx.release();
   c->a.release(); c->phi.release(); c->scratch.release(); c->bucket.release(); c->queue.release();
   for (auto &e : c->ev)
@@ -879,6 +896,7 @@ static qg_status set_sources_common(qg_ctx *c, int64_t ns, const double *x, cons
   c->G_src = G;
   c->np_list = cnt;
   c->h_poff.swap(h);
+  c->p_ranges = false;
   c->src_ok = true;
   update_counts(c);
   return QG_OK;
@@ -955,6 +973,7 @@ static qg_status set_cells_common(qg_ctx *c, int64_t nc, const double *com, cons
   c->G_cell = G;
   c->nc_list = cnt;
   c->h_coff.swap(h);
+  c->c_ranges = false;
   c->cells_ok = true;
   update_counts(c);
   return QG_OK;
@@ -1241,6 +1260,7 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
   if ((st = upload(c, c->goff, group_off, G + 1, ci_s)) != QG_OK) return st;
   if ((st = upload(c, c->poff, plist_off, G + 1, ci_s)) != QG_OK) return st;
   if ((st = upload(c, c->coff, clist_off, G + 1, ci_s)) != QG_OK) return st;
+  c->p_ranges = c->c_ranges = false;  // CSR lists
   if ((st = upload(c, c->src_m64, src_m, ns, ci_s)) != QG_OK) return st;
   const bool same_x = src_x == sink_x && ns == n;
   if (!same_x && (st = upload(c, c->stage_src, src_x, 3 * ns, ci_s)) != QG_OK) return st;
@@ -1307,8 +1327,8 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
   if (direct) {
     int *hist = c->scratch.p, *cursor = hist + kBuckets, *head = cursor + kBuckets, *bad = head + 1;
     const double cell_ops = c->opt.expansion == QG_QUAD ? 33.0 : 13.0;
-    queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->goff.p, c->poff.p, c->coff.p, cell_ops, c->bucket.p,
-                                                        hist);
+    queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->goff.p, c->poff.p, pend_dev(c), c->coff.p,
+                                                        cend_dev(c), cell_ops, c->bucket.p, hist);
     queue_scatter_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->bucket.p, hist, cursor, c->queue.p);
     QG_CUDA(c, cudaGetLastError());
     qg::ForceParams fp = force_params(c, 0, G, head);
@@ -1369,8 +1389,9 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
         const int64_t p0 = plist_off[g0], p1 = plist_off[g1], c0 = clist_off[g0], c1 = clist_off[g1];
         if (p1 > p0) sanitize_index_kernel<<<grid_for(p1 - p0, 256), 256, 0, sk>>>(p1 - p0, c->pidx.p + p0, ns, bad);
         if (c1 > c0) sanitize_index_kernel<<<grid_for(c1 - c0, 256), 256, 0, sk>>>(c1 - c0, c->cidx.p + c0, nc, bad);
-        queue_hist_kernel<<<grid_for(Gk, 256), 256, 0, sk>>>(Gk, c->goff.p + g0, c->poff.p + g0, c->coff.p + g0,
-                                                             cell_ops, c->bucket.p + g0, hist);
+        queue_hist_kernel<<<grid_for(Gk, 256), 256, 0, sk>>>(Gk, c->goff.p + g0, c->poff.p + g0, pend_dev(c) + g0,
+                                                             c->coff.p + g0, cend_dev(c) + g0, cell_ops,
+                                                             c->bucket.p + g0, hist);
         queue_scatter_kernel<<<grid_for(Gk, 256), 256, 0, sk>>>(Gk, c->bucket.p + g0, hist, cursor, c->queue.p + g0);
         QG_CUDA(c, cudaGetLastError());
         qg::ForceParams fp = force_params(c, g0, Gk, head);
@@ -1442,7 +1463,8 @@ qg_status qg::attach_tree_lists(qg_ctx *c, qg::TreeLists &t, double eps2_all, cu
   c->sinks_ok = c->src_ok = c->cells_ok = false;
   invalidate(c);
   if (t.n < 0 || t.n >= INT32_MAX || t.G < 0 || t.G >= INT32_MAX || t.nn < 0 || t.nn >= INT32_MAX ||
-      !t.poff || !t.coff || !t.pidx || !t.cidx || !t.goff || (t.n > 0 && (!t.xs || !t.ms)) ||
+      !t.poff || !t.coff || !t.pidx || !t.cidx || (t.ranges && (!t.pend || !t.cend)) || !t.goff ||
+      (t.n > 0 && (!t.xs || !t.ms)) ||
       (t.nn > 0 && (!t.com || !t.mass || !t.q)))
     return fail(c, QG_ERR_ARG, "attach: bad sizes or NULL pointer");
   if (t.device != c->device) return fail(c, QG_ERR_ARG, "attach: the tree and the context are on different devices");
@@ -1457,6 +1479,11 @@ qg_status qg::attach_tree_lists(qg_ctx *c, qg::TreeLists &t, double eps2_all, cu
   std::swap(c->pidx, *t.pidx);
   std::swap(c->coff, *t.coff);
   std::swap(c->cidx, *t.cidx);
+  if (t.ranges) {
+    std::swap(c->pend, *t.pend);
+    std::swap(c->cend, *t.cend);
+  }
+  c->p_ranges = c->c_ranges = t.ranges;
   if ((st = copy_d2d(c, c->src_m64, t.ms, n, s)) != QG_OK) return st;
   if ((st = copy_d2d(c, c->cell_m64, t.mass, nc, s)) != QG_OK) return st;
   if (c->src.reserve(n) != cudaSuccess || c->src_f.reserve(n) != cudaSuccess || c->cell_pm.reserve(nc) != cudaSuccess ||
@@ -1471,15 +1498,34 @@ qg_status qg::attach_tree_lists(qg_ctx *c, qg::TreeLists &t, double eps2_all, cu
     pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, t.com, c->cell_m64.p, t.q, c->cell_pm.p, c->cell_f.p,
                                                          c->cell_q.p, c->cell_q64.p, flags);
   QG_CUDA(c, cudaGetLastError());
-  std::vector<int64_t> hg(G + 1), hp(G + 1), hc(G + 1);
+  // host copies of the offsets (CSR: G + 1 of them; ranges: G begins and
+  // G ends per list) and the value checks, with one synchronisation
+  const int64_t nb = t.ranges ? G : G + 1;
+  std::vector<int64_t> hg(G + 1), hp(nb), hc(nb), hpe(t.ranges ? G : 0), hce(t.ranges ? G : 0);
   QG_CUDA(c, cudaMemcpyAsync(hg.data(), c->goff.p, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  QG_CUDA(c, cudaMemcpyAsync(hp.data(), c->poff.p, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-  QG_CUDA(c, cudaMemcpyAsync(hc.data(), c->coff.p, (G + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  if (nb > 0) {
+    QG_CUDA(c, cudaMemcpyAsync(hp.data(), c->poff.p, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    QG_CUDA(c, cudaMemcpyAsync(hc.data(), c->coff.p, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  }
+  if (t.ranges && G > 0) {
+    QG_CUDA(c, cudaMemcpyAsync(hpe.data(), c->pend.p, G * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    QG_CUDA(c, cudaMemcpyAsync(hce.data(), c->cend.p, G * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  }
   int fl = 0;
   if ((st = value_flags_end(c, s, flags, &fl)) != QG_OK) return st;
   if (fl & kBadPosition)
     return fail(c, QG_ERR_ARG, "attach: a position, mass or quadrupole component is not finite or exceeds 2^100");
-  if (hp[G] != t.np_list || hc[G] != t.nc_list || hg[G] != n)
+  int64_t tp = 0, tc = 0;
+  if (t.ranges) {
+    for (int64_t g = 0; g < G; g++) {
+      tp += hpe[g] - hp[g];
+      tc += hce[g] - hc[g];
+    }
+  } else {
+    tp = hp[G];
+    tc = hc[G];
+  }
+  if (tp != t.np_list || tc != t.nc_list || hg[G] != n)
     return fail(c, QG_ERR_STATE, "attach: the tree's list sizes do not match its offsets");
   c->n = n;
   c->G = G;
@@ -1493,11 +1539,13 @@ qg_status qg::attach_tree_lists(qg_ctx *c, qg::TreeLists &t, double eps2_all, cu
   c->G_src = G;
   c->np_list = t.np_list;
   c->h_poff.swap(hp);
+  c->h_pend.swap(hpe);
   c->src_ok = true;
   c->nc = nc;
   c->G_cell = G;
   c->nc_list = t.nc_list;
   c->h_coff.swap(hc);
+  c->h_cend.swap(hce);
   c->cells_ok = true;
   update_counts(c);
   return QG_OK;

@@ -22,8 +22,13 @@ struct TreeLists {
   const double *xs = nullptr, *ms = nullptr;                // sorted positions [n][3] and masses [n]
   const double *com = nullptr, *mass = nullptr, *q = nullptr;  // node moments (Eq. 2)
   const int64_t *goff = nullptr;                            // group offsets [G + 1]
-  DevBuf<int64_t> *poff = nullptr, *coff = nullptr;         // list offsets [G + 1]
-  DevBuf<int32_t> *pidx = nullptr, *cidx = nullptr;         // list indices
+  // the lists: CSR (poff, coff: offsets [G + 1]) or, when ranges, group g's
+  // entries at [poff[g], pend[g]) of pidx (the walk's own order; likewise
+  // for the cells)
+  bool ranges = false;
+  DevBuf<int64_t> *poff = nullptr, *coff = nullptr;
+  DevBuf<int64_t> *pend = nullptr, *cend = nullptr;
+  DevBuf<int32_t> *pidx = nullptr, *cidx = nullptr;
 };
 
 // Sets the context's sinks, sources and cells from t (eps2_all as in

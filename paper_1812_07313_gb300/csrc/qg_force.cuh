@@ -1042,9 +1042,9 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
     constexpr bool keep = INPLACE;
     if (ni <= 0) {
       if (keep) {  // no sinks: the lists are only checked and kept
-        for (int64_t e = p.plist_off[g] + tid; e < p.plist_off[g + 1]; e += NT)
+        for (int64_t e = p.plist_off[g] + tid; e < p.plist_end[g]; e += NT)
           keep_index(p.plist_idx[e], p.n_src, p.plist_keep + e, p.bad);
-        for (int64_t e = p.clist_off[g] + tid; e < p.clist_off[g + 1]; e += NT)
+        for (int64_t e = p.clist_off[g] + tid; e < p.clist_end[g]; e += NT)
           keep_index(p.clist_idx[e], p.n_cell, p.clist_keep + e, p.bad);
       }
       continue;
@@ -1063,8 +1063,8 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
       cc.z = p.gcentre[3 * g + 2];
     }
 
-    const int64_t gp0 = p.plist_off[g], np_g = p.plist_off[g + 1] - gp0;
-    const int64_t gc0 = p.clist_off[g], nc_g = p.clist_off[g + 1] - gc0;
+    const int64_t gp0 = p.plist_off[g], np_g = p.plist_end[g] - gp0;
+    const int64_t gc0 = p.clist_off[g], nc_g = p.clist_end[g] - gc0;
     if (e1 < 0) e1 = np_g + nc_g;
     const int64_t p0 = gp0 + min(e0, np_g), p1 = gp0 + min(e1, np_g);
     const int64_t c0 = gc0 + max(e0 - np_g, (int64_t)0), c1 = gc0 + max(e1 - np_g, (int64_t)0);

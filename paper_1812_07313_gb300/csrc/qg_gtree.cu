@@ -120,6 +120,11 @@ struct qg_gtree {
   int leaf_max = 8, n_crit = 64;
   bool built = false, walked = false;
   bool lists_moved = false;  // the last walk's lists went to a force context (qg_gtree_attach_move)
+  // the single-pass walk leaves each group's lists in the scratch arrays, in
+  // the order the groups finished; the CSR lists (plist_off / plist_idx ...)
+  // are made from them on the first request (csr_ready)
+  bool lists_scratch = false, csr_ready = false;
+  cudaStream_t walk_stream = nullptr;
   std::vector<int64_t> h_sys_off;
   // particles
   DBuf<int64_t> perm;
@@ -148,7 +153,7 @@ struct qg_gtree {
   DBuf<int32_t> stacks;  // per-warp walk stacks
   // single-pass walk: per-warp staging areas, scratch lists in completion order
   DBuf<int32_t> stage_p, stage_c, scratch_p, scratch_c;
-  DBuf<int64_t> gstart_p, gstart_c;
+  DBuf<int64_t> gstart_p, gstart_c, gend_p, gend_c;  // each group's scratch list range
   DBuf<unsigned long long> cursor;
   int64_t stage_cap_p = int64_t(1) << 15, stage_cap_c = int64_t(1) << 14;
   DBuf<float4> geom;     // per node: (com - o, side) / S, ((centre - o) / S, 0) in FP32; o, S: system root cube
@@ -1072,6 +1077,7 @@ __global__ void __launch_bounds__(kWalkBlock, kWalkBlocksPerSM) walk_single_kern
                                    int32_t *__restrict__ scratch_p, int32_t *__restrict__ scratch_c, int64_t cap_p,
                                    int64_t cap_c, unsigned long long *__restrict__ cursor,
                                    int64_t *__restrict__ gstart_p, int64_t *__restrict__ gstart_c,
+                                   int64_t *__restrict__ gend_p, int64_t *__restrict__ gend_c,
                                    int32_t *__restrict__ cnt_p, int32_t *__restrict__ cnt_c,
                                    int32_t *__restrict__ stacks, int *err) {
   const int lane = threadIdx.x & 31;
@@ -1109,6 +1115,8 @@ __global__ void __launch_bounds__(kWalkBlock, kWalkBlocksPerSM) walk_single_kern
     if (lane == 0) {
       gstart_p[g] = (int64_t)bp;
       gstart_c[g] = (int64_t)bc;
+      gend_p[g] = (int64_t)bp + np;
+      gend_c[g] = (int64_t)bc + nc;
       cnt_p[g] = (int32_t)(np < INT32_MAX ? np : INT32_MAX);
       cnt_c[g] = (int32_t)(nc < INT32_MAX ? nc : INT32_MAX);
     }
@@ -1209,6 +1217,8 @@ void qg_gtree_destroy(qg_gtree *t) {
   for (DBuf<int32_t> *b : {&t->stage_p, &t->stage_c, &t->scratch_p, &t->scratch_c}) b->release();
   t->gstart_p.release();
   t->gstart_c.release();
+  t->gend_p.release();
+  t->gend_c.release();
   t->cursor.release();
   t->geom.release();
   t->topo.release();
@@ -1479,6 +1489,33 @@ static qg_status walk_two_pass(qg_gtree *t, double theta2, const WalkTree &T, un
                                              t->plist_idx.p, t->clist_idx.p, t->stacks.p, t->err.p);
     GT_CUDA(cudaGetLastError());
   }
+  t->lists_scratch = false;
+  t->csr_ready = true;
+  return QG_OK;
+}
+
+// The last walk's lists in group (CSR) order, made on the first request after
+// a single-pass walk from its scratch lists (a scan of the list lengths and a
+// copy), on stream s, which it synchronises so that the arrays are complete
+// on return.
+static qg_status ensure_csr(qg_gtree *t, cudaStream_t s) {
+  if (!t->walked || t->lists_moved || t->csr_ready || !t->lists_scratch) return QG_OK;
+  const int64_t G = t->G;
+  qg_status st = scan_excl(t, G, t->cnt_p.p, t->plist_off.p, s);
+  if (st != QG_OK) return st;
+  st = scan_excl(t, G, t->cnt_c.p, t->clist_off.p, s);
+  if (st != QG_OK) return st;
+  GT_CUDA(t->plist_idx.reserve(t->np_list));
+  GT_CUDA(t->clist_idx.reserve(t->nc_list));
+  if (G > 0) {
+    lists_to_csr_kernel<<<grid1(32 * G), 256, 0, s>>>(G, t->gstart_p.p, t->plist_off.p, t->scratch_p.p,
+                                                       t->plist_idx.p);
+    lists_to_csr_kernel<<<grid1(32 * G), 256, 0, s>>>(G, t->gstart_c.p, t->clist_off.p, t->scratch_c.p,
+                                                       t->clist_idx.p);
+    GT_CUDA(cudaGetLastError());
+  }
+  GT_CUDA(cudaStreamSynchronize(s));
+  t->csr_ready = true;
   return QG_OK;
 }
 
@@ -1493,6 +1530,8 @@ static qg_status walk_single_pass(qg_gtree *t, double theta2, const WalkTree &T,
   GT_CUDA(t->stage_c.reserve((size_t)(nw * t->stage_cap_c)));
   GT_CUDA(t->gstart_p.reserve(G));
   GT_CUDA(t->gstart_c.reserve(G));
+  GT_CUDA(t->gend_p.reserve(G));
+  GT_CUDA(t->gend_c.reserve(G));
   GT_CUDA(t->cursor.reserve(3));
   int64_t want_p = std::max<int64_t>(1024, 48 * t->n), want_c = std::max<int64_t>(1024, 24 * t->n);
   for (int attempt = 0; attempt < 2; attempt++) {
@@ -1503,7 +1542,7 @@ static qg_status walk_single_pass(qg_gtree *t, double theta2, const WalkTree &T,
     walk_single_kernel<<<wg, wb, 0, s>>>(G, theta2, T, t->stage_p.p, t->stage_c.p, t->stage_cap_p, t->stage_cap_c,
                                          t->scratch_p.p, t->scratch_c.p, (int64_t)t->scratch_p.cap,
                                          (int64_t)t->scratch_c.cap, t->cursor.p, t->gstart_p.p, t->gstart_c.p,
-                                         t->cnt_p.p, t->cnt_c.p, t->stacks.p, t->err.p);
+                                         t->gend_p.p, t->gend_c.p, t->cnt_p.p, t->cnt_c.p, t->stacks.p, t->err.p);
     GT_CUDA(cudaGetLastError());
     unsigned long long cur[3] = {0, 0, 0};
     int herr = 0;
@@ -1523,15 +1562,9 @@ static qg_status walk_single_pass(qg_gtree *t, double theta2, const WalkTree &T,
       want_c = tot[1] + tot[1] / 8 + 1024;
       continue;
     }
-    qg_status st = scan_excl(t, G, t->cnt_p.p, t->plist_off.p, s);
-    if (st != QG_OK) return st;
-    st = scan_excl(t, G, t->cnt_c.p, t->clist_off.p, s);
-    if (st != QG_OK) return st;
-    GT_CUDA(t->plist_idx.reserve(tot[0]));
-    GT_CUDA(t->clist_idx.reserve(tot[1]));
-    lists_to_csr_kernel<<<wg, wb, 0, s>>>(G, t->gstart_p.p, t->plist_off.p, t->scratch_p.p, t->plist_idx.p);
-    lists_to_csr_kernel<<<wg, wb, 0, s>>>(G, t->gstart_c.p, t->clist_off.p, t->scratch_c.p, t->clist_idx.p);
-    GT_CUDA(cudaGetLastError());
+    // the lists stay in the scratch arrays; CSR on request (ensure_csr)
+    t->lists_scratch = true;
+    t->csr_ready = false;
     *done = true;
     return QG_OK;
   }
@@ -1540,6 +1573,8 @@ static qg_status walk_single_pass(qg_gtree *t, double theta2, const WalkTree &T,
 
 static qg_status walk_impl(qg_gtree *t, double theta, cudaStream_t s) {
   t->walked = false;
+  t->lists_scratch = t->csr_ready = false;
+  t->walk_stream = s;
   const int64_t G = t->G;
   const double theta2 = theta > 0 ? theta * theta : 0.0;
   GT_CUDA(cudaEventRecord(t->ev[2], s));
@@ -1608,6 +1643,16 @@ qg_status qg_gtree_arrays(const qg_gtree *t, const int64_t **perm, const double 
                           const int64_t **group_off, const int64_t **plist_off, const int32_t **plist_idx,
                           const int64_t **clist_off, const int32_t **clist_idx) {
   if (!t || !t->built) return QG_ERR_STATE;
+  if (plist_off || plist_idx || clist_off || clist_idx) {
+    // CSR lists on request (the tree's state, not its content, changes)
+    qg_gtree *mt = const_cast<qg_gtree *>(t);
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != t->device) cudaSetDevice(t->device);
+    const qg_status st = ensure_csr(mt, t->walk_stream);
+    if (prev >= 0 && prev != t->device) cudaSetDevice(prev);
+    if (st != QG_OK) return st;
+  }
   if (perm) *perm = t->perm.p;
   if (xs) *xs = t->xs.p;
   if (ms) *ms = t->ms.p;
@@ -1629,6 +1674,14 @@ qg_status qg_gtree_arrays(const qg_gtree *t, const int64_t **perm, const double 
 qg_status qg_gtree_attach(qg_gtree *t, qg_ctx *ctx, double eps2_all, void *stream) {
   if (!t || !ctx) return QG_ERR_ARG;
   if (!t->built || !t->walked || t->lists_moved) return QG_ERR_STATE;
+  {
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != t->device) cudaSetDevice(t->device);
+    const qg_status st = ensure_csr(t, (cudaStream_t)stream);
+    if (prev >= 0 && prev != t->device) cudaSetDevice(prev);
+    if (st != QG_OK) return st;
+  }
   qg_status st = qg_set_sinks_dev(ctx, t->n, t->xs.p, nullptr, eps2_all, t->G, t->group_off.p, stream);
   if (st != QG_OK) return st;
   st = qg_set_sources_dev(ctx, t->n, t->xs.p, t->ms.p, t->plist_off.p, t->plist_idx.p, t->np_list, stream);
@@ -1653,10 +1706,20 @@ qg_status qg_gtree_attach_move(qg_gtree *t, qg_ctx *ctx, double eps2_all, void *
   L.mass = t->mass.p;
   L.q = t->q.p;
   L.goff = t->group_off.p;
-  L.poff = &t->plist_off;
-  L.coff = &t->clist_off;
-  L.pidx = &t->plist_idx;
-  L.cidx = &t->clist_idx;
+  L.ranges = t->lists_scratch;  // the walk's own order: no CSR pass
+  if (L.ranges) {
+    L.poff = &t->gstart_p;
+    L.pend = &t->gend_p;
+    L.pidx = &t->scratch_p;
+    L.coff = &t->gstart_c;
+    L.cend = &t->gend_c;
+    L.cidx = &t->scratch_c;
+  } else {
+    L.poff = &t->plist_off;
+    L.coff = &t->clist_off;
+    L.pidx = &t->plist_idx;
+    L.cidx = &t->clist_idx;
+  }
   t->lists_moved = true;  // from here on the list buffers may be the context's former ones
   return qg::attach_tree_lists(ctx, L, eps2_all, (cudaStream_t)stream);
 }

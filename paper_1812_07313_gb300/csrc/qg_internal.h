@@ -131,13 +131,17 @@ struct ForceParams {
   const PosMassF *cell_f;
   const PosMass *src;
   const double *src_m64;
+  // group g's particle list is plist_idx[plist_off[g] .. plist_end[g]) (CSR
+  // lists: plist_end = plist_off + 1); the same for its cell list
   const int64_t *plist_off;
+  const int64_t *plist_end;
   const int32_t *plist_idx;
   const PosMass *cell_pm;
   const double *cell_m64;
   const float4 *cell_q;
   const double *cell_q64;
   const int64_t *clist_off;
+  const int64_t *clist_end;
   const int32_t *clist_idx;
   const int32_t *queue;
   int32_t nitems;

@@ -377,7 +377,8 @@ qg_status run(int device, int64_t n, const double *sink_x, const float *sink_eps
   if (G == 0) return QG_OK;
   const bool quad = expansion == QG_QUAD;
   const double cell_ops = quad ? 33.0 : 13.0;
-  qg::queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, group_off, plist_off, clist_off, cell_ops, cls, hist);
+  qg::queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, group_off, plist_off, plist_off + 1, clist_off,
+                                                          clist_off + 1, cell_ops, cls, hist);
   if (cudaGetLastError() != cudaSuccess) return QG_ERR_CUDA;
   qg::queue_scatter_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, cls, hist, cursor, queue);
   if (cudaGetLastError() != cudaSuccess) return QG_ERR_CUDA;

@@ -21,16 +21,19 @@ __device__ __forceinline__ int cost_bucket(double cost) {
 
 // Work queue, pass 1: cost class of every group and a histogram of classes.
 // cost = n_i * (13 n_p + c_cell n_c) FP32 ops + staging of the list entries.
-static __global__ void queue_hist_kernel(int64_t G, const int64_t *__restrict__ goff, const int64_t *__restrict__ poff,
-                                  const int64_t *__restrict__ coff, double cell_ops, unsigned char *bucket,
+// Group g's lists are [pbeg[g], pend[g]) and [cbeg[g], cend[g]) (CSR lists:
+// pend = pbeg + 1).
+static __global__ void queue_hist_kernel(int64_t G, const int64_t *__restrict__ goff, const int64_t *__restrict__ pbeg,
+                                  const int64_t *__restrict__ pend, const int64_t *__restrict__ cbeg,
+                                  const int64_t *__restrict__ cend, double cell_ops, unsigned char *bucket,
                                   int *hist) {
   __shared__ int h[kBuckets];
   for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) h[b] = 0;
   __syncthreads();
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
     const double ni = (double)(goff[g + 1] - goff[g]);
-    const double np = (double)(poff[g + 1] - poff[g]);
-    const double nc = (double)(coff[g + 1] - coff[g]);
+    const double np = (double)(pend[g] - pbeg[g]);
+    const double nc = (double)(cend[g] - cbeg[g]);
     const double cost = ni * (13.0 * np + cell_ops * nc) + 64.0 * (np + nc) + 256.0;
     const int b = cost_bucket(cost);
     bucket[g] = (unsigned char)b;
@@ -45,15 +48,16 @@ static __global__ void queue_hist_kernel(int64_t G, const int64_t *__restrict__ 
 // items (a group's list, or one part of it: its entries [e0, e1) of the
 // particle entries followed by the cell entries).
 static __global__ void queue_hist_items_kernel(int64_t n, const Item *__restrict__ items,
-                                               const int64_t *__restrict__ goff, const int64_t *__restrict__ poff,
-                                               double cell_ops, unsigned char *bucket, int *hist) {
+                                               const int64_t *__restrict__ goff, const int64_t *__restrict__ pbeg,
+                                               const int64_t *__restrict__ pend, double cell_ops,
+                                               unsigned char *bucket, int *hist) {
   __shared__ int h[kBuckets];
   for (int b = threadIdx.x; b < kBuckets; b += blockDim.x) h[b] = 0;
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const Item it = items[i];
     const double ni = (double)(goff[it.g + 1] - goff[it.g]);
-    const int64_t npg = poff[it.g + 1] - poff[it.g];
+    const int64_t npg = pend[it.g] - pbeg[it.g];
     const double np = (double)(min(it.e1, npg) - min(it.e0, npg));
     const double nc = (double)(max(it.e1 - npg, (int64_t)0) - max(it.e0 - npg, (int64_t)0));
     const double cost = ni * (13.0 * np + cell_ops * nc) + 64.0 * (np + nc) + 256.0;
