@@ -587,9 +587,9 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
       for (int k = 0; k < kMomentBatch; k++)
         if (k < cnt) {
           M += pm[k];
-          c0 += pm[k] * px[k];
-          c1 += pm[k] * py[k];
-          c2 += pm[k] * pz[k];
+          c0 = fma(pm[k], px[k], c0);
+          c1 = fma(pm[k], py[k], c1);
+          c2 = fma(pm[k], pz[k], c2);
         }
       if (M > 0) {  // one FP64 division, the host builder's expressions
         const double inv = 1.0 / M;
@@ -604,12 +604,12 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
         if (k < cnt) {
           const double r0 = px[k] - c0, r1 = py[k] - c1, r2c = pz[k] - c2;
           const double m0 = pm[k] * r0, m1 = pm[k] * r1, m2 = pm[k] * r2c;
-          s0 += m0 * r0;
-          s1 += m0 * r1;
-          s2 += m0 * r2c;
-          s3 += m1 * r1;
-          s4 += m1 * r2c;
-          s5 += m2 * r2c;
+          s0 = fma(m0, r0, s0);
+          s1 = fma(m0, r1, s1);
+          s2 = fma(m0, r2c, s2);
+          s3 = fma(m1, r1, s3);
+          s4 = fma(m1, r2c, s4);
+          s5 = fma(m2, r2c, s5);
         }
       const double tr = s0 + s3 + s5;
       q0 = 3 * s0 - tr;
@@ -622,9 +622,9 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
       const int64_t b = nbeg[j], e = nend[j];
       for (int64_t i = b; i < e; i++) {
         M += ms[i];
-        c0 += ms[i] * xs[3 * i];
-        c1 += ms[i] * xs[3 * i + 1];
-        c2 += ms[i] * xs[3 * i + 2];
+        c0 = fma(ms[i], xs[3 * i], c0);
+        c1 = fma(ms[i], xs[3 * i + 1], c1);
+        c2 = fma(ms[i], xs[3 * i + 2], c2);
       }
       if (M > 0) {
         const double inv = 1.0 / M;
@@ -637,12 +637,12 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
         const double r0 = xs[3 * i] - c0, r1 = xs[3 * i + 1] - c1, r2c = xs[3 * i + 2] - c2;
         const double mi = ms[i];
         const double m0 = mi * r0, m1 = mi * r1, m2 = mi * r2c;
-        s0 += m0 * r0;
-        s1 += m0 * r1;
-        s2 += m0 * r2c;
-        s3 += m1 * r1;
-        s4 += m1 * r2c;
-        s5 += m2 * r2c;
+        s0 = fma(m0, r0, s0);
+        s1 = fma(m0, r1, s1);
+        s2 = fma(m0, r2c, s2);
+        s3 = fma(m1, r1, s3);
+        s4 = fma(m1, r2c, s4);
+        s5 = fma(m2, r2c, s5);
       }
       const double tr = s0 + s3 + s5;
       q0 = 3 * s0 - tr;
@@ -669,9 +669,9 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
       for (int k = 0; k < 8; k++)
         if (k < nc) {
           M += cm[k];
-          c0 += cm[k] * cx[k];
-          c1 += cm[k] * cy[k];
-          c2 += cm[k] * cz[k];
+          c0 = fma(cm[k], cx[k], c0);
+          c1 = fma(cm[k], cy[k], c1);
+          c2 = fma(cm[k], cz[k], c2);
         }
       if (M > 0) {  // one FP64 division, the host builder's expressions
         const double inv = 1.0 / M;
@@ -686,12 +686,12 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
         if (k < nc) {
           const double r0 = cx[k] - c0, r1 = cy[k] - c1, r2c = cz[k] - c2;
           const double m0 = cm[k] * r0, m1 = cm[k] * r1, m2 = cm[k] * r2c;
-          s0 += m0 * r0;
-          s1 += m0 * r1;
-          s2 += m0 * r2c;
-          s3 += m1 * r1;
-          s4 += m1 * r2c;
-          s5 += m2 * r2c;
+          s0 = fma(m0, r0, s0);
+          s1 = fma(m0, r1, s1);
+          s2 = fma(m0, r2c, s2);
+          s3 = fma(m1, r1, s3);
+          s4 = fma(m1, r2c, s4);
+          s5 = fma(m2, r2c, s5);
         }
 #pragma unroll
       for (int k = 0; k < 8; k++)

@@ -264,25 +264,26 @@ extern "C" int qgt_build(int64_t n, const double *x, const double *m, int64_t ns
           // Eq. 2 directly over the leaf's particles
           for (int64_t i = nd.begin; i < nd.end; i++) {
             M += t->ms[i];
-            for (int d = 0; d < 3; d++) c[d] += t->ms[i] * t->xs[3 * i + d];
+            for (int d = 0; d < 3; d++) c[d] = std::fma(t->ms[i], t->xs[3 * i + d], c[d]);
           }
           if (M > 0) {  // one division (the GPU builder evaluates the same expressions)
             const double inv = 1.0 / M;
             for (int d = 0; d < 3; d++) c[d] *= inv;
           }
           // Eq. 2 as Q = 3 S - tr(S) I with S = sum m r r^T (the same sum,
-          // fewer operations; the GPU builder evaluates the same expressions)
+          // fewer operations; the GPU builder evaluates the same expressions,
+          // with the same explicit fused multiply-adds)
           double sm[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
           for (int64_t i = nd.begin; i < nd.end; i++) {
             const double r[3] = {t->xs[3 * i] - c[0], t->xs[3 * i + 1] - c[1], t->xs[3 * i + 2] - c[2]};
             const double mi = t->ms[i];
             const double m0 = mi * r[0], m1 = mi * r[1], m2 = mi * r[2];
-            sm[0] += m0 * r[0];
-            sm[1] += m0 * r[1];
-            sm[2] += m0 * r[2];
-            sm[3] += m1 * r[1];
-            sm[4] += m1 * r[2];
-            sm[5] += m2 * r[2];
+            sm[0] = std::fma(m0, r[0], sm[0]);
+            sm[1] = std::fma(m0, r[1], sm[1]);
+            sm[2] = std::fma(m0, r[2], sm[2]);
+            sm[3] = std::fma(m1, r[1], sm[3]);
+            sm[4] = std::fma(m1, r[2], sm[4]);
+            sm[5] = std::fma(m2, r[2], sm[5]);
           }
           const double tr = sm[0] + sm[3] + sm[5];
           qq[0] = 3 * sm[0] - tr;
@@ -295,7 +296,7 @@ extern "C" int qgt_build(int64_t n, const double *x, const double *m, int64_t ns
           for (int ch = 0; ch < nd.nchild; ch++) {
             const int64_t cj = nd.first_child + ch;
             M += t->mass[cj];
-            for (int d = 0; d < 3; d++) c[d] += t->mass[cj] * t->com[3 * cj + d];
+            for (int d = 0; d < 3; d++) c[d] = std::fma(t->mass[cj], t->com[3 * cj + d], c[d]);
           }
           if (M > 0) {  // one division (the GPU builder evaluates the same expressions)
             const double inv = 1.0 / M;
@@ -309,12 +310,12 @@ extern "C" int qgt_build(int64_t n, const double *x, const double *m, int64_t ns
             const double mc = t->mass[cj];
             const double r[3] = {t->com[3 * cj] - c[0], t->com[3 * cj + 1] - c[1], t->com[3 * cj + 2] - c[2]};
             const double m0 = mc * r[0], m1 = mc * r[1], m2 = mc * r[2];
-            sm[0] += m0 * r[0];
-            sm[1] += m0 * r[1];
-            sm[2] += m0 * r[2];
-            sm[3] += m1 * r[1];
-            sm[4] += m1 * r[2];
-            sm[5] += m2 * r[2];
+            sm[0] = std::fma(m0, r[0], sm[0]);
+            sm[1] = std::fma(m0, r[1], sm[1]);
+            sm[2] = std::fma(m0, r[2], sm[2]);
+            sm[3] = std::fma(m1, r[1], sm[3]);
+            sm[4] = std::fma(m1, r[2], sm[4]);
+            sm[5] = std::fma(m2, r[2], sm[5]);
             const double *qc = &t->q[6 * cj];
             for (int k = 0; k < 6; k++) qs[k] += qc[k];
           }
