@@ -311,6 +311,12 @@ __device__ __forceinline__ void quad_pairE(const Pair2 &P, float2 jx, float2 jy,
   az = P.fma2(ri5, qz, az);
 }
 
+// A list index is read once per launch: the streaming (evict-first) load keeps
+// the index stream from pushing the gathered records out of L2.  Likewise the
+// results, written once, go out with streaming stores.
+__device__ __forceinline__ int ld_index(const int32_t *q) { return __ldcs(q); }
+__device__ __forceinline__ void st_result(double *q, double v) { __stcs(q, v); }
+
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -543,8 +549,8 @@ __device__ __forceinline__ void evaluate_chunks(const ForceParams &p, unsigned c
         // the entry-paired form stages entries 2 tid and 2 tid + 1 first
         // (then 2 tid + 2 NT and 2 tid + 2 NT + 1)
         const int e0 = EPAIR ? 2 * tid : tid, e1 = EPAIR ? 2 * tid + 1 : tid + NT;
-        pf0 = e0 < c ? __ldg(idx + b + e0) : -1;
-        pf1 = e1 < c ? __ldg(idx + b + e1) : -1;
+        pf0 = e0 < c ? (INPLACE ? __ldg(idx + b + e0) : ld_index(idx + b + e0)) : -1;
+        pf1 = e1 < c ? (INPLACE ? __ldg(idx + b + e1) : ld_index(idx + b + e1)) : -1;
         if constexpr (INPLACE) {
           const int e2 = EPAIR ? 2 * tid + 2 * NT : tid + 2 * NT, e3 = EPAIR ? 2 * tid + 2 * NT + 1 : tid + 3 * NT;
           pf2 = e2 < c ? __ldg(idx + b + e2) : -1;
@@ -590,8 +596,8 @@ __device__ __forceinline__ void evaluate_chunks(const ForceParams &p, unsigned c
               j0 = keep_index(ahead(p.plist_idx, base, t0), p.n_src, p.plist_keep + base + t0, p.bad);
               j1 = t1 < cnt ? keep_index(ahead(p.plist_idx, base, t1), p.n_src, p.plist_keep + base + t1, p.bad) : j0;
             } else {
-              j0 = first ? pf0 : p.plist_idx[base + t0];
-              j1 = t1 < cnt ? (first ? pf1 : p.plist_idx[base + t1]) : j0;
+              j0 = first ? pf0 : ld_index(p.plist_idx + base + t0);
+              j1 = t1 < cnt ? (first ? pf1 : ld_index(p.plist_idx + base + t1)) : j0;
             }
             const PosMassF v0 = p.src_f[j0];
             const PosMassF v1 = p.src_f[j1];
@@ -614,8 +620,8 @@ __device__ __forceinline__ void evaluate_chunks(const ForceParams &p, unsigned c
               j0 = ahead(p.plist_idx, base, t);
               j1 = t1 < cnt ? ahead(p.plist_idx, base, t1) : j0;
             } else {
-              j0 = first ? pf0 : p.plist_idx[base + t];
-              j1 = t1 < cnt ? (first ? pf1 : p.plist_idx[base + t1]) : j0;
+              j0 = first ? pf0 : ld_index(p.plist_idx + base + t);
+              j1 = t1 < cnt ? (first ? pf1 : ld_index(p.plist_idx + base + t1)) : j0;
             }
             if (keep) {
               j0 = keep_index(j0, p.n_src, p.plist_keep + base + t, p.bad);
@@ -635,7 +641,7 @@ __device__ __forceinline__ void evaluate_chunks(const ForceParams &p, unsigned c
           }
         } else {
           for (int t = tid; t < cnt; t += NT) {
-            int j = INPLACE ? ahead(p.plist_idx, base, t) : t == tid ? pf0 : (t == tid + NT ? pf1 : p.plist_idx[base + t]);
+            int j = INPLACE ? ahead(p.plist_idx, base, t) : t == tid ? pf0 : (t == tid + NT ? pf1 : ld_index(p.plist_idx + base + t));
             if (keep) j = keep_index(j, p.n_src, p.plist_keep + base + t, p.bad);
             if constexpr (FF) put_p(t, p.src_f[j], j);
             else put_p(t, p.src[j], j);
@@ -726,8 +732,8 @@ QG_UNROLL(QG_EP_UNROLL)
               j0 = keep_index(ahead(p.clist_idx, base, t0), p.n_cell, p.clist_keep + base + t0, p.bad);
               j1 = t1 < cnt ? keep_index(ahead(p.clist_idx, base, t1), p.n_cell, p.clist_keep + base + t1, p.bad) : j0;
             } else {
-              j0 = first ? pf0 : p.clist_idx[base + t0];
-              j1 = t1 < cnt ? (first ? pf1 : p.clist_idx[base + t1]) : j0;
+              j0 = first ? pf0 : ld_index(p.clist_idx + base + t0);
+              j1 = t1 < cnt ? (first ? pf1 : ld_index(p.clist_idx + base + t1)) : j0;
             }
             const PosMassF v0 = p.cell_f[j0];
             const PosMassF v1 = p.cell_f[j1];
@@ -764,8 +770,8 @@ QG_UNROLL(QG_EP_UNROLL)
               j0 = ahead(p.clist_idx, base, t);
               j1 = t1 < cnt ? ahead(p.clist_idx, base, t1) : j0;
             } else {
-              j0 = first ? pf0 : p.clist_idx[base + t];
-              j1 = t1 < cnt ? (first ? pf1 : p.clist_idx[base + t1]) : j0;
+              j0 = first ? pf0 : ld_index(p.clist_idx + base + t);
+              j1 = t1 < cnt ? (first ? pf1 : ld_index(p.clist_idx + base + t1)) : j0;
             }
             if (keep) {
               j0 = keep_index(j0, p.n_cell, p.clist_keep + base + t, p.bad);
@@ -788,7 +794,7 @@ QG_UNROLL(QG_EP_UNROLL)
           }
         } else {
           for (int t = tid; t < cnt; t += NT) {
-            int j = INPLACE ? ahead(p.clist_idx, base, t) : t == tid ? pf0 : (t == tid + NT ? pf1 : p.clist_idx[base + t]);
+            int j = INPLACE ? ahead(p.clist_idx, base, t) : t == tid ? pf0 : (t == tid + NT ? pf1 : ld_index(p.clist_idx + base + t));
             if (keep) j = keep_index(j, p.n_cell, p.clist_keep + base + t, p.bad);
             const bool fq = QUAD && sizeof(Real) == 4;
             const float4 qa = fq ? p.cell_q[2 * j] : zero4, qb = fq ? p.cell_q[2 * j + 1] : zero4;
@@ -904,10 +910,10 @@ QG_UNROLL(QG_EP_UNROLL)
           merged(si, ri, m0, m1, m2, m3);
           const int64_t o = s0 + sb + i;
           if (part < 0) {
-            p.a[3 * o] = m0;
-            p.a[3 * o + 1] = m1;
-            p.a[3 * o + 2] = m2;
-            p.phi[o] = -m3;  // physical potential, Eq. 1
+            st_result(p.a + 3 * o, m0);
+            st_result(p.a + 3 * o + 1, m1);
+            st_result(p.a + 3 * o + 2, m2);
+            st_result(p.phi + o, -m3);  // physical potential, Eq. 1
           } else {            // this part's sums, merged below by the group's last part
             double *w = p.partial + 4 * (slot + sb + i);
             w[0] = m0;
@@ -1112,10 +1118,10 @@ __global__ void __launch_bounds__(Bounds<Real, R, FORM>::threads, Bounds<Real, R
               m3 += __ldcg(w + 3);
             }
             const int64_t o = s0 + i;
-            p.a[3 * o] = m0;
-            p.a[3 * o + 1] = m1;
-            p.a[3 * o + 2] = m2;
-            p.phi[o] = -m3;
+            st_result(p.a + 3 * o, m0);
+            st_result(p.a + 3 * o + 1, m1);
+            st_result(p.a + 3 * o + 2, m2);
+            st_result(p.phi + o, -m3);
           }
         }
       }
