@@ -239,6 +239,7 @@ struct qg_ctx {
   // qg_evaluate_host: streams for the copies in and out, events per chunk
   cudaStream_t copy_in = nullptr, copy_out = nullptr, chunk_stream[4] = {};
   cudaEvent_t chunk_in[8] = {}, chunk_done[8] = {}, inputs_ready = nullptr, packed = nullptr;
+  cudaEvent_t offsets_ready = nullptr, sinks_ready = nullptr;  // the first two groups of input copies
   DevBuf<double> stage_src;  // source positions when they are not the sinks' array
   int coherent_host = -1;    // device reads host memory through the host's page tables (-1: not asked yet)
   int *hbad = nullptr;       // page-locked [4]: bad-entry flags read back per chunk
@@ -727,6 +728,8 @@ void qg_destroy(qg_ctx *c) {
     if (c->chunk_done[k]) cudaEventDestroy(c->chunk_done[k]);
   }
   if (c->inputs_ready) cudaEventDestroy(c->inputs_ready);
+  if (c->offsets_ready) cudaEventDestroy(c->offsets_ready);
+  if (c->sinks_ready) cudaEventDestroy(c->sinks_ready);
   if (c->packed) cudaEventDestroy(c->packed);
   c->stage_src.release();
   for (cudaStream_t t : {c->copy_in, c->copy_out, c->chunk_stream[0], c->chunk_stream[1], c->chunk_stream[2],
@@ -1229,6 +1232,8 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
   if (!c->copy_in) QG_CUDA(c, cudaStreamCreateWithFlags(&c->copy_in, cudaStreamNonBlocking));
   if (!c->copy_out) QG_CUDA(c, cudaStreamCreateWithFlags(&c->copy_out, cudaStreamNonBlocking));
   if (!c->inputs_ready) QG_CUDA(c, cudaEventCreateWithFlags(&c->inputs_ready, cudaEventDisableTiming));
+  if (!c->offsets_ready) QG_CUDA(c, cudaEventCreateWithFlags(&c->offsets_ready, cudaEventDisableTiming));
+  if (!c->sinks_ready) QG_CUDA(c, cudaEventCreateWithFlags(&c->sinks_ready, cudaEventDisableTiming));
   if (!c->packed) QG_CUDA(c, cudaEventCreateWithFlags(&c->packed, cudaEventDisableTiming));
   if (!c->hbad) QG_CUDA(c, cudaMallocHost(&c->hbad, kChunks * sizeof(int)));
   for (int k = 0; k < kChunks; k++) {
@@ -1250,20 +1255,24 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
       (e = c->phi.reserve(std::max<int64_t>(n, 1))) != cudaSuccess || (e = c->pidx.reserve(np_tot)) != cudaSuccess ||
       (e = c->cidx.reserve(nc_tot)) != cudaSuccess)
     return fail(c, QG_ERR_NOMEM, "device allocation: %s", cudaGetErrorString(e));
-  // ---- sinks, sources and cells: every host-to-device copy goes on one
-  // stream (copy_in), these first and the list chunks after them, so the
-  // copy engine takes them in that order; the packing waits for them on s.
-  // One copy of x when the sinks are the sources.
+  // ---- offsets, sinks and sources, cells: every host-to-device copy goes
+  // on one stream (copy_in), in that order and the list chunks after them, so
+  // the copy engine takes them in that order.  On s, the queue waits for the
+  // offsets, the group centres and the source packing for the sinks and
+  // sources (while the cells are still being copied), the cell packing for
+  // the cells.  One copy of x when the sinks are the sources.
   cudaStream_t ci_s = c->copy_in;
-  if ((st = upload(c, c->sink_x, sink_x, 3 * n, ci_s)) != QG_OK) return st;
-  if (sink_eps2 && (st = upload(c, c->sink_eps2, sink_eps2, n, ci_s)) != QG_OK) return st;
   if ((st = upload(c, c->goff, group_off, G + 1, ci_s)) != QG_OK) return st;
   if ((st = upload(c, c->poff, plist_off, G + 1, ci_s)) != QG_OK) return st;
   if ((st = upload(c, c->coff, clist_off, G + 1, ci_s)) != QG_OK) return st;
   c->p_ranges = c->c_ranges = false;  // CSR lists
+  QG_CUDA(c, cudaEventRecord(c->offsets_ready, ci_s));
+  if ((st = upload(c, c->sink_x, sink_x, 3 * n, ci_s)) != QG_OK) return st;
+  if (sink_eps2 && (st = upload(c, c->sink_eps2, sink_eps2, n, ci_s)) != QG_OK) return st;
   if ((st = upload(c, c->src_m64, src_m, ns, ci_s)) != QG_OK) return st;
   const bool same_x = src_x == sink_x && ns == n;
   if (!same_x && (st = upload(c, c->stage_src, src_x, 3 * ns, ci_s)) != QG_OK) return st;
+  QG_CUDA(c, cudaEventRecord(c->sinks_ready, ci_s));
   if ((st = upload(c, c->stage_x, cell_com, 3 * nc, ci_s)) != QG_OK) return st;
   if ((st = upload(c, c->cell_m64, cell_m, nc, ci_s)) != QG_OK) return st;
   if (c->cell_pm.reserve(nc) != cudaSuccess || c->cell_q.reserve(2 * nc) != cudaSuccess ||
@@ -1295,11 +1304,31 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
     cudaStreamSynchronize(ci_s);
     return st;
   }
-  QG_CUDA(c, cudaStreamWaitEvent(s, c->inputs_ready, 0));
+  // ---- in place: lists and results in page-locked memory the device reads
+  // and writes over a coherent link (FP32 centred, scalar or entry-paired
+  // form).  One queue and one persistent launch over all groups; the kernel
+  // reads each list index from the host, checks it and keeps it in the
+  // device lists, and writes the results both to the device buffers and to
+  // a / phi.  No list copy, no copy back.
+  const void *pi_h = np_tot > 0 ? in_place(c, plist_idx) : nullptr, *ci_h = nc_tot > 0 ? in_place(c, clist_idx) : nullptr;
+  const void *a_h = n > 0 ? in_place(c, a) : nullptr, *phi_h = n > 0 ? in_place(c, phi) : nullptr;
+  const bool direct = c->kernel_inplace && n > 0 && G > 0 && (np_tot == 0 || pi_h) && (nc_tot == 0 || ci_h) && a_h &&
+                      phi_h;
+  c->stats.eval_in_place = direct ? 1 : 0;
+  QG_CUDA(c, cudaStreamWaitEvent(s, c->offsets_ready, 0));
   QG_CUDA(c, cudaMemsetAsync(c->scratch.p, 0, kChunks * kScr * sizeof(int), s));
+  if (direct) {  // the queue needs the offsets only
+    int *hist = c->scratch.p, *cursor = hist + kBuckets;
+    const double cell_ops = c->opt.expansion == QG_QUAD ? 33.0 : 13.0;
+    queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->goff.p, c->poff.p, pend_dev(c), c->coff.p,
+                                                        cend_dev(c), cell_ops, c->bucket.p, hist);
+    queue_scatter_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->bucket.p, hist, cursor, c->queue.p);
+    QG_CUDA(c, cudaGetLastError());
+  }
   // input values are checked into the first chunk's flag (the kernels below
   // still run on them, reading nothing out of bounds; the call then fails)
   int *vflags = c->scratch.p + 2 * kBuckets + 1;
+  QG_CUDA(c, cudaStreamWaitEvent(s, c->sinks_ready, 0));
   if ((st = group_centres(c, n, G, nullptr, vflags, s)) != QG_OK) {
     cudaStreamSynchronize(ci_s);
     return st;
@@ -1307,30 +1336,15 @@ qg_status qg_evaluate_host(qg_ctx *c, int64_t n, const double *sink_x, const flo
   if (ns)
     pack_src_kernel<<<grid_for(ns, 256), 256, 0, s>>>(ns, same_x ? c->sink_x.p : c->stage_src.p, c->src_m64.p,
                                                       c->src.p, c->src_f.p, vflags);
+  QG_CUDA(c, cudaStreamWaitEvent(s, c->inputs_ready, 0));
   if (nc)
     pack_cells_kernel<<<grid_for(nc, 256), 256, 0, s>>>(nc, c->stage_x.p, c->cell_m64.p, c->cell_q64.p,
                                                          c->cell_pm.p, c->cell_f.p, c->cell_q.p, c->cell_q64.p,
                                                          vflags);
   QG_CUDA(c, cudaGetLastError());
   QG_CUDA(c, cudaEventRecord(c->ev[0], s));
-  // ---- in place: lists and results in page-locked memory the device reads
-  // and writes over a coherent link (FP32 centred, scalar form).  One queue
-  // and one persistent launch over all groups; the kernel reads each list
-  // index from the host, checks it and keeps it in the device lists, and
-  // writes the results both to the device buffers and to a / phi.  No list
-  // copy, no copy back.
-  const void *pi_h = np_tot > 0 ? in_place(c, plist_idx) : nullptr, *ci_h = nc_tot > 0 ? in_place(c, clist_idx) : nullptr;
-  const void *a_h = n > 0 ? in_place(c, a) : nullptr, *phi_h = n > 0 ? in_place(c, phi) : nullptr;
-  const bool direct = c->kernel_inplace && n > 0 && G > 0 && (np_tot == 0 || pi_h) && (nc_tot == 0 || ci_h) && a_h &&
-                      phi_h;
-  c->stats.eval_in_place = direct ? 1 : 0;
   if (direct) {
-    int *hist = c->scratch.p, *cursor = hist + kBuckets, *head = cursor + kBuckets, *bad = head + 1;
-    const double cell_ops = c->opt.expansion == QG_QUAD ? 33.0 : 13.0;
-    queue_hist_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->goff.p, c->poff.p, pend_dev(c), c->coff.p,
-                                                        cend_dev(c), cell_ops, c->bucket.p, hist);
-    queue_scatter_kernel<<<grid_for(G, 256), 256, 0, s>>>(G, c->bucket.p, hist, cursor, c->queue.p);
-    QG_CUDA(c, cudaGetLastError());
+    int *head = c->scratch.p + 2 * kBuckets, *bad = head + 1;
     qg::ForceParams fp = force_params(c, 0, G, head);
     fp.plist_idx = static_cast<const int32_t *>(pi_h);
     fp.clist_idx = static_cast<const int32_t *>(ci_h);
