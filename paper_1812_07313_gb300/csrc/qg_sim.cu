@@ -41,13 +41,22 @@ __global__ void kick_drift_kernel(int64_t n3, double *__restrict__ x, double *__
   }
 }
 
+// Sorted position of every particle of the caller's order: rank[perm[i]] = i
+// (perm is the tree's permutation of 0 .. n-1, n < 2^31).
+__global__ void rank_kernel(int64_t n, const int64_t *__restrict__ perm, int32_t *__restrict__ rank) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    rank[perm[i]] = (int32_t)i;
+}
+
 // Forces from the tree's sorted order back to the caller's order, and the
-// second kick (h = 0: store only).
-__global__ void unsort_kick_kernel(int64_t n, const int64_t *__restrict__ perm, const double *__restrict__ a_s,
+// second kick (h = 0: store only).  Threads run over the caller's order and
+// gather through rank: the writes (and the read-modify-write of v) stay
+// coalesced, and only the 4-byte ranks are scattered, by rank_kernel.
+__global__ void unsort_kick_kernel(int64_t n, const int32_t *__restrict__ rank, const double *__restrict__ a_s,
                                    const double *__restrict__ phi_s, double *__restrict__ a,
                                    double *__restrict__ phi, double *__restrict__ v, double h, int kick) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = perm[i];
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = rank[j];
     phi[j] = phi_s[i];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
@@ -118,6 +127,7 @@ struct qg_sim {
   int64_t n = 0;
   std::vector<int64_t> sys_off;
   Buf<double> x, v, m, a, phi, a_s, phi_s, red;
+  Buf<int32_t> rank;        // sorted position of each particle of the caller's order
   Buf<float> eps2, eps2_s;  // per-particle softening (caller order, sorted order)
   bool per_particle_eps = false;
   bool has_state = false, tuned = false;
@@ -244,7 +254,8 @@ qg_status evaluate(qg_sim *s, cudaStream_t st, bool kick, double h) {
   SIM_OK(qg_gtree_arrays(s->tree, &perm, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                          nullptr, nullptr, nullptr, nullptr, nullptr));
   SIM_CUDA(cudaEventRecord(s->ev[2], st));
-  unsort_kick_kernel<<<blocks_for(s->n), kThreads, 0, st>>>(s->n, perm, s->a_s.p, s->phi_s.p, s->a.p, s->phi.p,
+  rank_kernel<<<blocks_for(s->n), kThreads, 0, st>>>(s->n, perm, s->rank.p);
+  unsort_kick_kernel<<<blocks_for(s->n), kThreads, 0, st>>>(s->n, s->rank.p, s->a_s.p, s->phi_s.p, s->a.p, s->phi.p,
                                                             s->v.p, h, kick ? 1 : 0);
   SIM_CUDA(cudaGetLastError());
   SIM_CUDA(cudaEventRecord(s->ev[3], st));
@@ -330,6 +341,7 @@ void qg_sim_destroy(qg_sim *s) {
   for (Buf<double> *b : {&s->x, &s->v, &s->m, &s->a, &s->phi, &s->a_s, &s->phi_s, &s->red}) b->release();
   s->eps2.release();
   s->eps2_s.release();
+  s->rank.release();
   delete s;
 }
 
@@ -354,6 +366,7 @@ qg_status qg_sim_set_state(qg_sim *s, int64_t n, const double *x, const double *
   SIM_CUDA(s->m.reserve(n));
   SIM_CUDA(s->phi.reserve(n));
   SIM_CUDA(s->phi_s.reserve(n));
+  SIM_CUDA(s->rank.reserve(n));
   SIM_CUDA(cudaMemcpyAsync(s->x.p, x, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
   SIM_CUDA(cudaMemcpyAsync(s->v.p, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
   SIM_CUDA(cudaMemcpyAsync(s->m.p, m, n * sizeof(double), cudaMemcpyHostToDevice, st));
