@@ -264,14 +264,16 @@ qg_status qg_get_forces_dev(qg_ctx *ctx, double *a, double *phi, void *cuda_stre
  * paper's library takes them.
  * One evaluation from HOST arrays: the inputs of qg_set_sinks, qg_set_sources
  * and qg_set_cells (same meaning, layout and checks), then the forces written
- * to a [n][3] and phi [n] (host).  The sinks, sources and cells are copied
- * first (one copy of x when src_x is the same array as sink_x and ns == n).
- * The lists then take one of two routes:
+ * to a [n][3] and phi [n] (host).  The offsets, then the sinks and
+ * sources, then the cells are copied first, in that order (one copy of x
+ * when src_x is the same array as sink_x and ns == n); each set-up kernel
+ * (work queue, group centres, packing) starts once the copies it reads
+ * are done.  The lists then take one of two routes:
  *   - in place, when plist_idx, clist_idx, a and phi are all page-locked
  *     (cudaHostAlloc / cudaHostRegister), the GPU reads host memory
  *     through the host's page tables (a coherent CPU-GPU link, as on
  *     Grace-Blackwell) and the options select the FP32 centred precision in
- *     the scalar form: one persistent force launch reads every list index
+ *     the scalar or entry-paired form: one persistent force launch reads every list index
  *     from host memory, checks it and keeps it in the context's device
  *     lists, and writes the results to the device and to a / phi; nothing
  *     is copied back;

@@ -1188,8 +1188,9 @@ const void *in_place(qg_ctx *c, const void *h) {
   return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
-// One evaluation from host arrays.  The sinks, sources and cells are copied
-// (and packed) first.  The lists are then either read in place by one
+// One evaluation from host arrays.  The offsets, sinks, sources and cells
+// are copied first, and each is packed as soon as it is there.  The lists
+// are then either read in place by one
 // persistent launch (page-locked host memory on a coherent link) or copied
 // in chunks of groups on a second stream while the force kernel runs on the
 // chunks already there, each chunk's results copied back on a third stream
