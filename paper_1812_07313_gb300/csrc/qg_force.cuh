@@ -12,7 +12,8 @@
 //      each thread holds R sinks in registers.
 //   3. the group's list is staged tile by tile into shared memory:
 //      particles (x_j - c_g, m) and cells (x_j - c_g, m, Q) gathered through
-//      the CSR index list and centred the same way.
+//      the group's index range [off[g], end[g]) (CSR lists have end = off + 1)
+//      and centred the same way.
 //   4. the threads form S sink slots x K list streams (S = ceil(n_i / R),
 //      K = blockDim / S); stream k walks entries k, k+K, ... of each tile,
 //      so every staged entry is read from shared memory once per thread and
