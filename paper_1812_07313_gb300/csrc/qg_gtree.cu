@@ -1109,8 +1109,11 @@ __global__ void __launch_bounds__(kWalkBlock, kWalkBlocksPerSM) walk_single_kern
     } else if ((int64_t)bp + np > cap_p || (int64_t)bc + nc > cap_c) {
       if (lane == 0) atomicOr(err, 4);
     } else {
-      for (int64_t i = lane; i < np; i += 32) scratch_p[bp + i] = mp[i];
-      for (int64_t i = lane; i < nc; i += 32) scratch_c[bc + i] = mc[i];
+      // streaming stores: the lists are read by the next kernel, not by this
+      // one, so they should not push the tree's node records and the staging
+      // areas out of L2
+      for (int64_t i = lane; i < np; i += 32) __stcs(scratch_p + bp + i, mp[i]);
+      for (int64_t i = lane; i < nc; i += 32) __stcs(scratch_c + bc + i, mc[i]);
     }
     if (lane == 0) {
       gstart_p[g] = (int64_t)bp;
