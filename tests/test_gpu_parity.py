@@ -77,19 +77,24 @@ def _evaluate_host(case, ctx, same_x=True, idx_fix=None, pinned=False):
     return out
 
 
+@pytest.mark.parametrize("form", ["entry-paired", "entry-paired, R per item", "scalar, R per item"])
 @pytest.mark.parametrize("pinned", [False, True])
 @pytest.mark.parametrize("name", ["sphere", "batched"])
-def test_pipelined_host_evaluation_equals_the_separate_calls(name, pinned):
+def test_pipelined_host_evaluation_equals_the_separate_calls(name, pinned, form):
     """qg_evaluate_host gives bit for bit the results of qg_set_* + qg_run at
     the same options, with the positions copied once or twice, and leaves
     the context holding the inputs: by both routes, list copies overlapped
     with the kernel in four chunks of groups (pageable lists) and lists read
-    in place by the kernel (page-locked lists and outputs)."""
+    in place by the kernel (page-locked lists and outputs), for each FP32
+    form with an in-place variant (sinks per thread fixed or chosen per
+    work item)."""
     if name == "sphere":
         case = Case(workloads.small_set("sphere", 6000, 31, 1e-2), 0.5, 8, 64)
     else:
         case = Case(workloads.batched_systems(nsys=6, seed=9, n_lo=300, n_hi=5000), 0.5, 8, 64)
-    opts = qgrav.Options(sinks_per_thread=4, warps_per_group=2, tile_j=128)
+    arith = qgrav.QG_ARITH_SCALAR if form.startswith("scalar") else qgrav.QG_ARITH_ENTRY_PAIRED
+    opts = qgrav.Options(sinks_per_thread=4, warps_per_group=2, tile_j=128, arith=arith,
+                         sinks_adaptive=1 if "per item" in form else 0)
     a_ref, phi_ref, st_ref = case.gpu(opts)
     ctx = qgrav.Context(0, opts)
     for same in (True, False):
@@ -98,6 +103,7 @@ def test_pipelined_host_evaluation_equals_the_separate_calls(name, pinned):
     st = ctx.qg_get_stats()
     assert st["i_pp"] == st_ref["i_pp"] and st["i_pc"] == st_ref["i_pc"]
     assert st["eval_in_place"] == (1 if pinned else 0)
+    assert st["sinks_adaptive"] == opts.sinks_adaptive
     a_d, phi_d = ctx.qg_get_forces()  # the device holds the same results
     assert np.array_equal(a_d, a_ref) and np.array_equal(phi_d, phi_ref)
     ctx.qg_run()  # the context holds the inputs: a graph step on them
