@@ -143,6 +143,8 @@ struct qg_gtree {
   DBuf<int64_t> cstart;  // per level: the eight octant starts of each node
   DBuf<int64_t> excl;
   DBuf<double> centre, half, side, com, mass, q;
+  DBuf<int32_t> leaves;  // leaf node indices by particle count (the leaf moments pass)
+  DBuf<int> leaf_hist;   // bucket sizes, then bucket cursors
   std::vector<int64_t> level_begin;
   DBuf<int32_t> sys_root;
   // groups and lists
@@ -557,7 +559,201 @@ __global__ void emit_children_kernel(int32_t lb, int32_t le, int32_t base, int l
 
 constexpr int kMomentBatch = 8;  // leaves of up to this many particles load them all first
 
-__global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64_t *__restrict__ nbeg,
+// Leaves by particle count: bucket c - 1 holds the leaves of c <= kMomentBatch
+// particles, the last bucket the larger ones (coincident particles at the
+// deepest level).  The leaf pass runs the leaves bucket by bucket, so that the
+// lanes of a warp sum the same number of particles: the pass is bound by the
+// FP64 pipe, and a warp of mixed leaves would issue every particle slot of its
+// largest one.
+constexpr int kLeafBuckets = kMomentBatch + 1;
+static_assert(kMomentBatch == 8, "leaf_moments_kernel dispatches leaves of 1 to 8 particles");
+
+__device__ __forceinline__ int leaf_bucket(int64_t cnt) {
+  return cnt >= 1 && cnt <= kMomentBatch ? (int)cnt - 1 : kMomentBatch;
+}
+
+// hist[b] += leaves in bucket b (hist zeroed before)
+__global__ void leaf_hist_kernel(int32_t nn, const int32_t *__restrict__ nnchild, const int64_t *__restrict__ nbeg,
+                                 const int64_t *__restrict__ nend, int *__restrict__ hist) {
+  __shared__ int h[kLeafBuckets];
+  if (threadIdx.x < kLeafBuckets) h[threadIdx.x] = 0;
+  __syncthreads();
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nn; j += (int64_t)gridDim.x * blockDim.x)
+    if (nnchild[j] == 0) atomicAdd(&h[leaf_bucket(nend[j] - nbeg[j])], 1);
+  __syncthreads();
+  if (threadIdx.x < kLeafBuckets && h[threadIdx.x] > 0) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+}
+
+// Every leaf's node index into its bucket of leaves[] (buckets in order, from
+// hist; cursor zeroed before).  A block places its share of each bucket with
+// one atomic add per bucket; the order inside a bucket does not matter, since
+// every leaf is summed on its own.
+__global__ void leaf_fill_kernel(int32_t nn, const int32_t *__restrict__ nnchild, const int64_t *__restrict__ nbeg,
+                                 const int64_t *__restrict__ nend, const int *__restrict__ hist,
+                                 int *__restrict__ cursor, int32_t *__restrict__ leaves) {
+  __shared__ int pre[kLeafBuckets], h[kLeafBuckets], off[kLeafBuckets];
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int b = 0; b < kLeafBuckets; b++) {
+      pre[b] = acc;
+      acc += hist[b];
+    }
+  }
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nn; base += (int64_t)gridDim.x * blockDim.x) {
+    if (threadIdx.x < kLeafBuckets) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t j = base + threadIdx.x;
+    int b = -1, r = 0;
+    if (j < nn && nnchild[j] == 0) {
+      b = leaf_bucket(nend[j] - nbeg[j]);
+      r = atomicAdd(&h[b], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x < kLeafBuckets)
+      off[threadIdx.x] = h[threadIdx.x] > 0 ? atomicAdd(&cursor[threadIdx.x], h[threadIdx.x]) : 0;
+    __syncthreads();
+    if (b >= 0) leaves[pre[b] + off[b] + r] = (int32_t)j;
+  }
+}
+
+// Mass, centre of mass and Q of a leaf of CNT particles from [b, b + CNT):
+// every position and mass requested before the sums start; the sums run in
+// particle order, the host builder's expressions.
+template <int CNT>
+__device__ __forceinline__ void leaf_sums(int64_t b, const double *__restrict__ xs, const double *__restrict__ ms,
+                                          double &M, double (&c)[3], double (&qq)[6]) {
+  double px[CNT], py[CNT], pz[CNT], pm[CNT];
+#pragma unroll
+  for (int k = 0; k < CNT; k++) {
+    px[k] = xs[3 * (b + k)];
+    py[k] = xs[3 * (b + k) + 1];
+    pz[k] = xs[3 * (b + k) + 2];
+    pm[k] = ms[b + k];
+  }
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+  M = 0.0;
+#pragma unroll
+  for (int k = 0; k < CNT; k++) {
+    M += pm[k];
+    c0 = fma(pm[k], px[k], c0);
+    c1 = fma(pm[k], py[k], c1);
+    c2 = fma(pm[k], pz[k], c2);
+  }
+  if (M > 0) {  // one FP64 division, the host builder's expressions
+    const double inv = 1.0 / M;
+    c0 *= inv;
+    c1 *= inv;
+    c2 *= inv;
+  }
+  // Q = 3 S - tr(S) I with S = sum m r r^T
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
+#pragma unroll
+  for (int k = 0; k < CNT; k++) {
+    const double r0 = px[k] - c0, r1 = py[k] - c1, r2c = pz[k] - c2;
+    const double m0 = pm[k] * r0, m1 = pm[k] * r1, m2 = pm[k] * r2c;
+    s0 = fma(m0, r0, s0);
+    s1 = fma(m0, r1, s1);
+    s2 = fma(m0, r2c, s2);
+    s3 = fma(m1, r1, s3);
+    s4 = fma(m1, r2c, s4);
+    s5 = fma(m2, r2c, s5);
+  }
+  const double tr = s0 + s3 + s5;
+  c[0] = c0;
+  c[1] = c1;
+  c[2] = c2;
+  qq[0] = 3 * s0 - tr;
+  qq[1] = 3 * s1;
+  qq[2] = 3 * s2;
+  qq[3] = 3 * s3 - tr;
+  qq[4] = 3 * s4;
+  qq[5] = 3 * s5 - tr;
+}
+
+// The same for a leaf of any size (coincident particles at the deepest level
+// can exceed kMomentBatch), reading its particles as it sums them.
+__device__ __forceinline__ void leaf_sums_any(int64_t b, int64_t e, const double *__restrict__ xs,
+                                              const double *__restrict__ ms, double &M, double (&c)[3],
+                                              double (&qq)[6]) {
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+  M = 0.0;
+  for (int64_t i = b; i < e; i++) {
+    M += ms[i];
+    c0 = fma(ms[i], xs[3 * i], c0);
+    c1 = fma(ms[i], xs[3 * i + 1], c1);
+    c2 = fma(ms[i], xs[3 * i + 2], c2);
+  }
+  if (M > 0) {
+    const double inv = 1.0 / M;
+    c0 *= inv;
+    c1 *= inv;
+    c2 *= inv;
+  }
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
+  for (int64_t i = b; i < e; i++) {
+    const double r0 = xs[3 * i] - c0, r1 = xs[3 * i + 1] - c1, r2c = xs[3 * i + 2] - c2;
+    const double mi = ms[i];
+    const double m0 = mi * r0, m1 = mi * r1, m2 = mi * r2c;
+    s0 = fma(m0, r0, s0);
+    s1 = fma(m0, r1, s1);
+    s2 = fma(m0, r2c, s2);
+    s3 = fma(m1, r1, s3);
+    s4 = fma(m1, r2c, s4);
+    s5 = fma(m2, r2c, s5);
+  }
+  const double tr = s0 + s3 + s5;
+  c[0] = c0;
+  c[1] = c1;
+  c[2] = c2;
+  qq[0] = 3 * s0 - tr;
+  qq[1] = 3 * s1;
+  qq[2] = 3 * s2;
+  qq[3] = 3 * s3 - tr;
+  qq[4] = 3 * s4;
+  qq[5] = 3 * s5 - tr;
+}
+
+// Moments (Eq. 2) of every leaf, bucket by bucket (leaves[] from
+// leaf_fill_kernel, hist[] its bucket sizes).
+__global__ void leaf_moments_kernel(const int *__restrict__ hist, const int32_t *__restrict__ leaves,
+                                    const int64_t *__restrict__ nbeg, const int64_t *__restrict__ nend,
+                                    const double *__restrict__ xs, const double *__restrict__ ms,
+                                    double *__restrict__ com, double *__restrict__ mass, double *__restrict__ q,
+                                    double *__restrict__ side, const double *__restrict__ half,
+                                    int64_t *__restrict__ range) {
+  int total = 0;
+#pragma unroll
+  for (int k = 0; k < kLeafBuckets; k++) total += hist[k];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = leaves[i];
+    const int64_t b = nbeg[j], e = nend[j];
+    double M, c[3], qq[6];
+    switch (e - b) {
+      case 1: leaf_sums<1>(b, xs, ms, M, c, qq); break;
+      case 2: leaf_sums<2>(b, xs, ms, M, c, qq); break;
+      case 3: leaf_sums<3>(b, xs, ms, M, c, qq); break;
+      case 4: leaf_sums<4>(b, xs, ms, M, c, qq); break;
+      case 5: leaf_sums<5>(b, xs, ms, M, c, qq); break;
+      case 6: leaf_sums<6>(b, xs, ms, M, c, qq); break;
+      case 7: leaf_sums<7>(b, xs, ms, M, c, qq); break;
+      case 8: leaf_sums<8>(b, xs, ms, M, c, qq); break;
+      default: leaf_sums_any(b, e, xs, ms, M, c, qq);
+    }
+    mass[j] = M;
+    com[3 * j] = c[0];
+    com[3 * j + 1] = c[1];
+    com[3 * j + 2] = c[2];
+#pragma unroll
+    for (int k = 0; k < 6; k++) q[6 * j + k] = qq[k];
+    side[j] = 2.0 * half[j];
+    range[2 * j] = b;
+    range[2 * j + 1] = e;
+  }
+}
+
+// Moments (Eq. 2) of the internal nodes in [lo, hi) from their children's
+// (leaves are done by leaf_moments_kernel).
+__global__ void moments_kernel(int32_t lo, int32_t hi, const int64_t *__restrict__ nbeg,
                                const int64_t *__restrict__ nend, const int32_t *__restrict__ nfirst,
                                const int32_t *__restrict__ nnchild, const double *__restrict__ xs,
                                const double *__restrict__ ms, double *__restrict__ com, double *__restrict__ mass,
@@ -567,91 +763,8 @@ __global__ void moments_kernel(int32_t lo, int32_t hi, int internal, const int64
     double M = 0.0, c0 = 0.0, c1 = 0.0, c2 = 0.0;
     double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0, q4 = 0.0, q5 = 0.0;
     const int nc = nnchild[j];
-    if ((nc != 0) != (internal != 0)) continue;
-    if (nc == 0 && nend[j] - nbeg[j] <= kMomentBatch) {
-      // a leaf of at most kMomentBatch particles: every particle's position
-      // and mass requested before the sums start (the sums themselves run in
-      // particle order, the host builder's expressions)
-      const int64_t b = nbeg[j];
-      const int cnt = (int)(nend[j] - b);
-      double px[kMomentBatch], py[kMomentBatch], pz[kMomentBatch], pm[kMomentBatch];
-#pragma unroll
-      for (int k = 0; k < kMomentBatch; k++) {
-        const bool in = k < cnt;
-        px[k] = in ? xs[3 * (b + k)] : 0.0;
-        py[k] = in ? xs[3 * (b + k) + 1] : 0.0;
-        pz[k] = in ? xs[3 * (b + k) + 2] : 0.0;
-        pm[k] = in ? ms[b + k] : 0.0;
-      }
-#pragma unroll
-      for (int k = 0; k < kMomentBatch; k++)
-        if (k < cnt) {
-          M += pm[k];
-          c0 = fma(pm[k], px[k], c0);
-          c1 = fma(pm[k], py[k], c1);
-          c2 = fma(pm[k], pz[k], c2);
-        }
-      if (M > 0) {  // one FP64 division, the host builder's expressions
-        const double inv = 1.0 / M;
-        c0 *= inv;
-        c1 *= inv;
-        c2 *= inv;
-      }
-      // Q = 3 S - tr(S) I with S = sum m r r^T, the host builder's expressions
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
-#pragma unroll
-      for (int k = 0; k < kMomentBatch; k++)
-        if (k < cnt) {
-          const double r0 = px[k] - c0, r1 = py[k] - c1, r2c = pz[k] - c2;
-          const double m0 = pm[k] * r0, m1 = pm[k] * r1, m2 = pm[k] * r2c;
-          s0 = fma(m0, r0, s0);
-          s1 = fma(m0, r1, s1);
-          s2 = fma(m0, r2c, s2);
-          s3 = fma(m1, r1, s3);
-          s4 = fma(m1, r2c, s4);
-          s5 = fma(m2, r2c, s5);
-        }
-      const double tr = s0 + s3 + s5;
-      q0 = 3 * s0 - tr;
-      q1 = 3 * s1;
-      q2 = 3 * s2;
-      q3 = 3 * s3 - tr;
-      q4 = 3 * s4;
-      q5 = 3 * s5 - tr;
-    } else if (nc == 0) {  // a larger leaf (coincident particles at the deepest level)
-      const int64_t b = nbeg[j], e = nend[j];
-      for (int64_t i = b; i < e; i++) {
-        M += ms[i];
-        c0 = fma(ms[i], xs[3 * i], c0);
-        c1 = fma(ms[i], xs[3 * i + 1], c1);
-        c2 = fma(ms[i], xs[3 * i + 2], c2);
-      }
-      if (M > 0) {
-        const double inv = 1.0 / M;
-        c0 *= inv;
-        c1 *= inv;
-        c2 *= inv;
-      }
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
-      for (int64_t i = b; i < e; i++) {
-        const double r0 = xs[3 * i] - c0, r1 = xs[3 * i + 1] - c1, r2c = xs[3 * i + 2] - c2;
-        const double mi = ms[i];
-        const double m0 = mi * r0, m1 = mi * r1, m2 = mi * r2c;
-        s0 = fma(m0, r0, s0);
-        s1 = fma(m0, r1, s1);
-        s2 = fma(m0, r2c, s2);
-        s3 = fma(m1, r1, s3);
-        s4 = fma(m1, r2c, s4);
-        s5 = fma(m2, r2c, s5);
-      }
-      const double tr = s0 + s3 + s5;
-      q0 = 3 * s0 - tr;
-      q1 = 3 * s1;
-      q2 = 3 * s2;
-      q3 = 3 * s3 - tr;
-      q4 = 3 * s4;
-      q5 = 3 * s5 - tr;
-    } else {
+    if (nc == 0) continue;  // leaves: leaf_moments_kernel
+    {
       // an internal node (at most 8 children): the children's masses and
       // centres requested before the sums start, then their tensors; every
       // sum runs in child order, the host builder's expressions
@@ -1212,7 +1325,7 @@ void qg_gtree_destroy(qg_gtree *t) {
   t->nbeg.release(); t->nend.release(); t->range.release(); t->nlevel.release(); t->nparent.release();
   t->nfirst.release(); t->nnchild.release(); t->nsysid.release(); t->cstart.release(); t->flag.release();
   t->excl.release(); t->centre.release(); t->half.release(); t->side.release(); t->com.release();
-  t->mass.release(); t->q.release(); t->sys_root.release(); t->gflag.release(); t->gnode_at.release();
+  t->mass.release(); t->q.release(); t->leaves.release(); t->leaf_hist.release(); t->sys_root.release(); t->gflag.release(); t->gnode_at.release();
   t->group_node.release(); t->cnt_p.release(); t->cnt_c.release(); t->gidx.release(); t->group_off.release();
   t->plist_off.release(); t->clist_off.release(); t->plist_idx.release(); t->clist_idx.release();
   for (auto &b : t->scan_tmp) b.release();
@@ -1400,17 +1513,24 @@ static qg_status build_impl(qg_gtree *t, int64_t n, const double *x, const doubl
   GT_CUDA(t->q.reserve(6 * nn));
   GT_CUDA(t->side.reserve(nn));
   GT_CUDA(t->range.reserve(2 * nn));
-  // every leaf at once (their moments come from particles only), then the
-  // internal nodes level by level, deepest first
-  if (nn > 0)
-    moments_kernel<<<grid1(nn), 256, 0, s>>>(0, (int32_t)nn, 0, t->nbeg.p, t->nend.p, t->nfirst.p, t->nnchild.p,
-                                             t->xs.p, t->ms.p, t->com.p, t->mass.p, t->q.p, t->side.p, t->half.p,
-                                             t->range.p);
+  // every leaf at once (their moments come from particles only), grouped by
+  // particle count, then the internal nodes level by level, deepest first
+  GT_CUDA(t->leaves.reserve(std::max<int64_t>(nn, 1)));
+  GT_CUDA(t->leaf_hist.reserve(2 * kLeafBuckets));
+  GT_CUDA(cudaMemsetAsync(t->leaf_hist.p, 0, 2 * kLeafBuckets * sizeof(int), s));
+  if (nn > 0) {
+    int *hist = t->leaf_hist.p, *cursor = t->leaf_hist.p + kLeafBuckets;
+    leaf_hist_kernel<<<grid1(nn), 256, 0, s>>>((int32_t)nn, t->nnchild.p, t->nbeg.p, t->nend.p, hist);
+    leaf_fill_kernel<<<grid1(nn), 256, 0, s>>>((int32_t)nn, t->nnchild.p, t->nbeg.p, t->nend.p, hist, cursor,
+                                               t->leaves.p);
+    leaf_moments_kernel<<<grid1(nn), 256, 0, s>>>(hist, t->leaves.p, t->nbeg.p, t->nend.p, t->xs.p, t->ms.p,
+                                                  t->com.p, t->mass.p, t->q.p, t->side.p, t->half.p, t->range.p);
+  }
   GT_CUDA(cudaGetLastError());
   for (int l = (int)t->level_begin.size() - 2; l >= 0; l--) {
     const int64_t a = t->level_begin[l], b = t->level_begin[l + 1];
     if (b > a && l + 2 < (int)t->level_begin.size())  // the deepest level holds leaves only
-      moments_kernel<<<grid1(b - a), 256, 0, s>>>((int32_t)a, (int32_t)b, 1, t->nbeg.p, t->nend.p, t->nfirst.p,
+      moments_kernel<<<grid1(b - a), 256, 0, s>>>((int32_t)a, (int32_t)b, t->nbeg.p, t->nend.p, t->nfirst.p,
                                                   t->nnchild.p, t->xs.p, t->ms.p, t->com.p, t->mass.p, t->q.p,
                                                   t->side.p, t->half.p, t->range.p);
     GT_CUDA(cudaGetLastError());
