@@ -143,8 +143,8 @@ struct qg_gtree {
   DBuf<int64_t> cstart;  // per level: the eight octant starts of each node
   DBuf<int64_t> excl;
   DBuf<double> centre, half, side, com, mass, q;
-  DBuf<int32_t> leaves;  // leaf node indices by particle count (the leaf moments pass)
-  DBuf<int> leaf_hist;   // bucket sizes, then bucket cursors
+  DBuf<int32_t> morder;  // node indices grouped for the moments passes (node_bucket)
+  DBuf<int> mbuckets;    // bucket sizes, cursors and starts
   std::vector<int64_t> level_begin;
   DBuf<int32_t> sys_root;
   // groups and lists
@@ -559,60 +559,72 @@ __global__ void emit_children_kernel(int32_t lb, int32_t le, int32_t base, int l
 
 constexpr int kMomentBatch = 8;  // leaves of up to this many particles load them all first
 
-// Leaves by particle count: bucket c - 1 holds the leaves of c <= kMomentBatch
-// particles, the last bucket the larger ones (coincident particles at the
-// deepest level).  The leaf pass runs the leaves bucket by bucket, so that the
-// lanes of a warp sum the same number of particles: the pass is bound by the
-// FP64 pipe, and a warp of mixed leaves would issue every particle slot of its
-// largest one.
+// Nodes grouped for the moments passes: a leaf of c <= kMomentBatch particles
+// goes to bucket c - 1, a larger one (coincident particles at the deepest
+// level) to bucket kMomentBatch; an internal node of level l with k children
+// to bucket kLeafBuckets + 8 l + k - 1.  The leaf pass runs the leaf buckets,
+// each internal level its eight buckets, so that the lanes of a warp sum the
+// same number of particles or children: these passes are bound by the FP64
+// pipe, and a warp of mixed nodes would issue every slot of its largest node
+// (and idle the lanes of the other kind).
 constexpr int kLeafBuckets = kMomentBatch + 1;
-static_assert(kMomentBatch == 8, "leaf_moments_kernel dispatches leaves of 1 to 8 particles");
+constexpr int kNodeBuckets = kLeafBuckets + 8 * kMaxLevel;
+static_assert(kMomentBatch == 8, "the moments passes dispatch nodes of 1 to 8 particles or children");
 
-__device__ __forceinline__ int leaf_bucket(int64_t cnt) {
-  return cnt >= 1 && cnt <= kMomentBatch ? (int)cnt - 1 : kMomentBatch;
+__device__ __forceinline__ int node_bucket(int64_t cnt, int nc, int level) {
+  if (nc == 0) return cnt >= 1 && cnt <= kMomentBatch ? (int)cnt - 1 : kMomentBatch;
+  // an open node has a level below kMaxLevel and 1 to 8 children; the clamps
+  // only keep the index inside the table
+  level = level < 0 ? 0 : (level >= kMaxLevel ? kMaxLevel - 1 : level);
+  nc = nc > 8 ? 8 : nc;
+  return kLeafBuckets + 8 * level + nc - 1;
 }
 
-// hist[b] += leaves in bucket b (hist zeroed before)
-__global__ void leaf_hist_kernel(int32_t nn, const int32_t *__restrict__ nnchild, const int64_t *__restrict__ nbeg,
-                                 const int64_t *__restrict__ nend, int *__restrict__ hist) {
-  __shared__ int h[kLeafBuckets];
-  if (threadIdx.x < kLeafBuckets) h[threadIdx.x] = 0;
+// hist[b] += nodes in bucket b (hist zeroed before)
+__global__ void node_hist_kernel(int32_t nn, const int32_t *__restrict__ nnchild, const int64_t *__restrict__ nbeg,
+                                 const int64_t *__restrict__ nend, const int32_t *__restrict__ nlevel,
+                                 int *__restrict__ hist) {
+  __shared__ int h[kNodeBuckets];
+  for (int k = threadIdx.x; k < kNodeBuckets; k += blockDim.x) h[k] = 0;
   __syncthreads();
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nn; j += (int64_t)gridDim.x * blockDim.x)
-    if (nnchild[j] == 0) atomicAdd(&h[leaf_bucket(nend[j] - nbeg[j])], 1);
+    atomicAdd(&h[node_bucket(nend[j] - nbeg[j], nnchild[j], nlevel[j])], 1);
   __syncthreads();
-  if (threadIdx.x < kLeafBuckets && h[threadIdx.x] > 0) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+  for (int k = threadIdx.x; k < kNodeBuckets; k += blockDim.x)
+    if (h[k] > 0) atomicAdd(&hist[k], h[k]);
 }
 
-// Every leaf's node index into its bucket of leaves[] (buckets in order, from
-// hist; cursor zeroed before).  A block places its share of each bucket with
-// one atomic add per bucket; the order inside a bucket does not matter, since
-// every leaf is summed on its own.
-__global__ void leaf_fill_kernel(int32_t nn, const int32_t *__restrict__ nnchild, const int64_t *__restrict__ nbeg,
-                                 const int64_t *__restrict__ nend, const int *__restrict__ hist,
-                                 int *__restrict__ cursor, int32_t *__restrict__ leaves) {
-  __shared__ int pre[kLeafBuckets], h[kLeafBuckets], off[kLeafBuckets];
-  if (threadIdx.x == 0) {
-    int acc = 0;
-    for (int b = 0; b < kLeafBuckets; b++) {
-      pre[b] = acc;
-      acc += hist[b];
-    }
+// pre[b] = nodes in the buckets before b (pre[kNodeBuckets] = all); one thread
+__global__ void bucket_scan_kernel(const int *__restrict__ hist, int *__restrict__ pre) {
+  int acc = 0;
+  for (int k = 0; k < kNodeBuckets; k++) {
+    pre[k] = acc;
+    acc += hist[k];
   }
+  pre[kNodeBuckets] = acc;
+}
+
+// Every node's index into its bucket of order[] (cursor zeroed before).  A
+// block places its share of each bucket with one atomic add per bucket; the
+// order inside a bucket does not matter, since every node is summed on its own.
+__global__ void node_fill_kernel(int32_t nn, const int32_t *__restrict__ nnchild, const int64_t *__restrict__ nbeg,
+                                 const int64_t *__restrict__ nend, const int32_t *__restrict__ nlevel,
+                                 const int *__restrict__ pre, int *__restrict__ cursor, int32_t *__restrict__ order) {
+  __shared__ int h[kNodeBuckets], off[kNodeBuckets];
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nn; base += (int64_t)gridDim.x * blockDim.x) {
-    if (threadIdx.x < kLeafBuckets) h[threadIdx.x] = 0;
+    for (int k = threadIdx.x; k < kNodeBuckets; k += blockDim.x) h[k] = 0;
     __syncthreads();
     const int64_t j = base + threadIdx.x;
     int b = -1, r = 0;
-    if (j < nn && nnchild[j] == 0) {
-      b = leaf_bucket(nend[j] - nbeg[j]);
+    if (j < nn) {
+      b = node_bucket(nend[j] - nbeg[j], nnchild[j], nlevel[j]);
       r = atomicAdd(&h[b], 1);
     }
     __syncthreads();
-    if (threadIdx.x < kLeafBuckets)
-      off[threadIdx.x] = h[threadIdx.x] > 0 ? atomicAdd(&cursor[threadIdx.x], h[threadIdx.x]) : 0;
+    for (int k = threadIdx.x; k < kNodeBuckets; k += blockDim.x)
+      off[k] = h[k] > 0 ? atomicAdd(&cursor[k], h[k]) : 0;
     __syncthreads();
-    if (b >= 0) leaves[pre[b] + off[b] + r] = (int32_t)j;
+    if (b >= 0) order[pre[b] + off[b] + r] = (int32_t)j;
   }
 }
 
@@ -713,19 +725,17 @@ __device__ __forceinline__ void leaf_sums_any(int64_t b, int64_t e, const double
   qq[5] = 3 * s5 - tr;
 }
 
-// Moments (Eq. 2) of every leaf, bucket by bucket (leaves[] from
-// leaf_fill_kernel, hist[] its bucket sizes).
-__global__ void leaf_moments_kernel(const int *__restrict__ hist, const int32_t *__restrict__ leaves,
+// Moments (Eq. 2) of every leaf, bucket by bucket (order[] and pre[] from
+// node_fill_kernel and bucket_scan_kernel).
+__global__ void leaf_moments_kernel(const int *__restrict__ pre, const int32_t *__restrict__ order,
                                     const int64_t *__restrict__ nbeg, const int64_t *__restrict__ nend,
                                     const double *__restrict__ xs, const double *__restrict__ ms,
                                     double *__restrict__ com, double *__restrict__ mass, double *__restrict__ q,
                                     double *__restrict__ side, const double *__restrict__ half,
                                     int64_t *__restrict__ range) {
-  int total = 0;
-#pragma unroll
-  for (int k = 0; k < kLeafBuckets; k++) total += hist[k];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = leaves[i];
+  const int64_t lo = pre[0], hi = pre[kLeafBuckets];
+  for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = order[i];
     const int64_t b = nbeg[j], e = nend[j];
     double M, c[3], qq[6];
     switch (e - b) {
@@ -751,90 +761,101 @@ __global__ void leaf_moments_kernel(const int *__restrict__ hist, const int32_t 
   }
 }
 
-// Moments (Eq. 2) of the internal nodes in [lo, hi) from their children's
-// (leaves are done by leaf_moments_kernel).
-__global__ void moments_kernel(int32_t lo, int32_t hi, const int64_t *__restrict__ nbeg,
-                               const int64_t *__restrict__ nend, const int32_t *__restrict__ nfirst,
-                               const int32_t *__restrict__ nnchild, const double *__restrict__ xs,
-                               const double *__restrict__ ms, double *__restrict__ com, double *__restrict__ mass,
-                               double *__restrict__ q, double *__restrict__ side, const double *__restrict__ half,
-                               int64_t *__restrict__ range) {
-  for (int64_t j = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < hi; j += (int64_t)gridDim.x * blockDim.x) {
-    double M = 0.0, c0 = 0.0, c1 = 0.0, c2 = 0.0;
-    double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0, q4 = 0.0, q5 = 0.0;
-    const int nc = nnchild[j];
-    if (nc == 0) continue;  // leaves: leaf_moments_kernel
-    {
-      // an internal node (at most 8 children): the children's masses and
-      // centres requested before the sums start, then their tensors; every
-      // sum runs in child order, the host builder's expressions
-      const int f = nfirst[j];
-      double cm[8], cx[8], cy[8], cz[8];
+// Mass, centre of mass and Q of an internal node from its NC children
+// [f, f + NC): the children's masses and centres requested before the sums
+// start, then their tensors; every sum runs in child order, the host
+// builder's expressions (parallel-axis shift: Q = sum Q_c + 3 S - tr(S) I
+// with S = sum m_c d d^T).
+template <int NC>
+__device__ __forceinline__ void internal_sums(int f, const double *__restrict__ mass, const double *__restrict__ com,
+                                              const double *q, double &M, double (&c)[3], double (&qq)[6]) {
+  double cm[NC], cx[NC], cy[NC], cz[NC];
 #pragma unroll
-      for (int k = 0; k < 8; k++) {
-        const bool in = k < nc;
-        cm[k] = in ? mass[f + k] : 0.0;
-        cx[k] = in ? com[3 * (f + k)] : 0.0;
-        cy[k] = in ? com[3 * (f + k) + 1] : 0.0;
-        cz[k] = in ? com[3 * (f + k) + 2] : 0.0;
-      }
+  for (int k = 0; k < NC; k++) {
+    cm[k] = mass[f + k];
+    cx[k] = com[3 * (f + k)];
+    cy[k] = com[3 * (f + k) + 1];
+    cz[k] = com[3 * (f + k) + 2];
+  }
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+  M = 0.0;
 #pragma unroll
-      for (int k = 0; k < 8; k++)
-        if (k < nc) {
-          M += cm[k];
-          c0 = fma(cm[k], cx[k], c0);
-          c1 = fma(cm[k], cy[k], c1);
-          c2 = fma(cm[k], cz[k], c2);
-        }
-      if (M > 0) {  // one FP64 division, the host builder's expressions
-        const double inv = 1.0 / M;
-        c0 *= inv;
-        c1 *= inv;
-        c2 *= inv;
-      }
-      // parallel-axis shift: Q = sum Q_c + 3 S - tr(S) I with S = sum m_c d d^T
-      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
+  for (int k = 0; k < NC; k++) {
+    M += cm[k];
+    c0 = fma(cm[k], cx[k], c0);
+    c1 = fma(cm[k], cy[k], c1);
+    c2 = fma(cm[k], cz[k], c2);
+  }
+  if (M > 0) {  // one FP64 division, the host builder's expressions
+    const double inv = 1.0 / M;
+    c0 *= inv;
+    c1 *= inv;
+    c2 *= inv;
+  }
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0, s5 = 0.0;
 #pragma unroll
-      for (int k = 0; k < 8; k++)
-        if (k < nc) {
-          const double r0 = cx[k] - c0, r1 = cy[k] - c1, r2c = cz[k] - c2;
-          const double m0 = cm[k] * r0, m1 = cm[k] * r1, m2 = cm[k] * r2c;
-          s0 = fma(m0, r0, s0);
-          s1 = fma(m0, r1, s1);
-          s2 = fma(m0, r2c, s2);
-          s3 = fma(m1, r1, s3);
-          s4 = fma(m1, r2c, s4);
-          s5 = fma(m2, r2c, s5);
-        }
+  for (int k = 0; k < NC; k++) {
+    const double r0 = cx[k] - c0, r1 = cy[k] - c1, r2c = cz[k] - c2;
+    const double m0 = cm[k] * r0, m1 = cm[k] * r1, m2 = cm[k] * r2c;
+    s0 = fma(m0, r0, s0);
+    s1 = fma(m0, r1, s1);
+    s2 = fma(m0, r2c, s2);
+    s3 = fma(m1, r1, s3);
+    s4 = fma(m1, r2c, s4);
+    s5 = fma(m2, r2c, s5);
+  }
+  double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0, q4 = 0.0, q5 = 0.0;
 #pragma unroll
-      for (int k = 0; k < 8; k++)
-        if (k < nc) {
-          const double *qc = q + 6 * (f + k);
-          q0 += qc[0];
-          q1 += qc[1];
-          q2 += qc[2];
-          q3 += qc[3];
-          q4 += qc[4];
-          q5 += qc[5];
-        }
-      const double tr = s0 + s3 + s5;
-      q0 = q0 + (3 * s0 - tr);
-      q1 = q1 + 3 * s1;
-      q2 = q2 + 3 * s2;
-      q3 = q3 + (3 * s3 - tr);
-      q4 = q4 + 3 * s4;
-      q5 = q5 + (3 * s5 - tr);
+  for (int k = 0; k < NC; k++) {
+    const double *qc = q + 6 * (f + k);
+    q0 += qc[0];
+    q1 += qc[1];
+    q2 += qc[2];
+    q3 += qc[3];
+    q4 += qc[4];
+    q5 += qc[5];
+  }
+  const double tr = s0 + s3 + s5;
+  c[0] = c0;
+  c[1] = c1;
+  c[2] = c2;
+  qq[0] = q0 + (3 * s0 - tr);
+  qq[1] = q1 + 3 * s1;
+  qq[2] = q2 + 3 * s2;
+  qq[3] = q3 + (3 * s3 - tr);
+  qq[4] = q4 + 3 * s4;
+  qq[5] = q5 + (3 * s5 - tr);
+}
+
+// Moments (Eq. 2) of the internal nodes of one level from their children's
+// (the level below, done before), bucket by bucket of child count.
+__global__ void internal_moments_kernel(int level, const int *__restrict__ pre, const int32_t *__restrict__ order,
+                                        const int64_t *__restrict__ nbeg, const int64_t *__restrict__ nend,
+                                        const int32_t *__restrict__ nfirst, const int32_t *__restrict__ nnchild,
+                                        double *__restrict__ com, double *__restrict__ mass, double *q,
+                                        double *__restrict__ side, const double *__restrict__ half,
+                                        int64_t *__restrict__ range) {
+  const int64_t lo = pre[kLeafBuckets + 8 * level], hi = pre[kLeafBuckets + 8 * level + 8];
+  for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = order[i];
+    const int f = nfirst[j];
+    double M, c[3], qq[6];
+    switch (nnchild[j]) {
+      case 1: internal_sums<1>(f, mass, com, q, M, c, qq); break;
+      case 2: internal_sums<2>(f, mass, com, q, M, c, qq); break;
+      case 3: internal_sums<3>(f, mass, com, q, M, c, qq); break;
+      case 4: internal_sums<4>(f, mass, com, q, M, c, qq); break;
+      case 5: internal_sums<5>(f, mass, com, q, M, c, qq); break;
+      case 6: internal_sums<6>(f, mass, com, q, M, c, qq); break;
+      case 7: internal_sums<7>(f, mass, com, q, M, c, qq); break;
+      default: internal_sums<8>(f, mass, com, q, M, c, qq);
     }
     mass[j] = M;
-    com[3 * j] = c0;
-    com[3 * j + 1] = c1;
-    com[3 * j + 2] = c2;
-    q[6 * j] = q0;
-    q[6 * j + 1] = q1;
-    q[6 * j + 2] = q2;
-    q[6 * j + 3] = q3;
-    q[6 * j + 4] = q4;
-    q[6 * j + 5] = q5;
+    com[3 * j] = c[0];
+    com[3 * j + 1] = c[1];
+    com[3 * j + 2] = c[2];
+#pragma unroll
+    for (int k = 0; k < 6; k++) q[6 * j + k] = qq[k];
     side[j] = 2.0 * half[j];
     range[2 * j] = nbeg[j];
     range[2 * j + 1] = nend[j];
@@ -1325,7 +1346,7 @@ void qg_gtree_destroy(qg_gtree *t) {
   t->nbeg.release(); t->nend.release(); t->range.release(); t->nlevel.release(); t->nparent.release();
   t->nfirst.release(); t->nnchild.release(); t->nsysid.release(); t->cstart.release(); t->flag.release();
   t->excl.release(); t->centre.release(); t->half.release(); t->side.release(); t->com.release();
-  t->mass.release(); t->q.release(); t->leaves.release(); t->leaf_hist.release(); t->sys_root.release(); t->gflag.release(); t->gnode_at.release();
+  t->mass.release(); t->q.release(); t->morder.release(); t->mbuckets.release(); t->sys_root.release(); t->gflag.release(); t->gnode_at.release();
   t->group_node.release(); t->cnt_p.release(); t->cnt_c.release(); t->gidx.release(); t->group_off.release();
   t->plist_off.release(); t->clist_off.release(); t->plist_idx.release(); t->clist_idx.release();
   for (auto &b : t->scan_tmp) b.release();
@@ -1513,26 +1534,28 @@ static qg_status build_impl(qg_gtree *t, int64_t n, const double *x, const doubl
   GT_CUDA(t->q.reserve(6 * nn));
   GT_CUDA(t->side.reserve(nn));
   GT_CUDA(t->range.reserve(2 * nn));
-  // every leaf at once (their moments come from particles only), grouped by
-  // particle count, then the internal nodes level by level, deepest first
-  GT_CUDA(t->leaves.reserve(std::max<int64_t>(nn, 1)));
-  GT_CUDA(t->leaf_hist.reserve(2 * kLeafBuckets));
-  GT_CUDA(cudaMemsetAsync(t->leaf_hist.p, 0, 2 * kLeafBuckets * sizeof(int), s));
+  // every leaf at once (their moments come from particles only), then the
+  // internal nodes level by level, deepest first; the nodes grouped by
+  // particle or child count first (node_bucket)
+  GT_CUDA(t->morder.reserve(std::max<int64_t>(nn, 1)));
+  GT_CUDA(t->mbuckets.reserve(3 * kNodeBuckets + 1));
+  int *mhist = t->mbuckets.p, *mcursor = mhist + kNodeBuckets, *mpre = mcursor + kNodeBuckets;
+  GT_CUDA(cudaMemsetAsync(mhist, 0, 2 * kNodeBuckets * sizeof(int), s));
   if (nn > 0) {
-    int *hist = t->leaf_hist.p, *cursor = t->leaf_hist.p + kLeafBuckets;
-    leaf_hist_kernel<<<grid1(nn), 256, 0, s>>>((int32_t)nn, t->nnchild.p, t->nbeg.p, t->nend.p, hist);
-    leaf_fill_kernel<<<grid1(nn), 256, 0, s>>>((int32_t)nn, t->nnchild.p, t->nbeg.p, t->nend.p, hist, cursor,
-                                               t->leaves.p);
-    leaf_moments_kernel<<<grid1(nn), 256, 0, s>>>(hist, t->leaves.p, t->nbeg.p, t->nend.p, t->xs.p, t->ms.p,
+    node_hist_kernel<<<grid1(nn), 256, 0, s>>>((int32_t)nn, t->nnchild.p, t->nbeg.p, t->nend.p, t->nlevel.p, mhist);
+    bucket_scan_kernel<<<1, 1, 0, s>>>(mhist, mpre);
+    node_fill_kernel<<<grid1(nn), 256, 0, s>>>((int32_t)nn, t->nnchild.p, t->nbeg.p, t->nend.p, t->nlevel.p, mpre,
+                                               mcursor, t->morder.p);
+    leaf_moments_kernel<<<grid1(nn), 256, 0, s>>>(mpre, t->morder.p, t->nbeg.p, t->nend.p, t->xs.p, t->ms.p,
                                                   t->com.p, t->mass.p, t->q.p, t->side.p, t->half.p, t->range.p);
   }
   GT_CUDA(cudaGetLastError());
   for (int l = (int)t->level_begin.size() - 2; l >= 0; l--) {
     const int64_t a = t->level_begin[l], b = t->level_begin[l + 1];
-    if (b > a && l + 2 < (int)t->level_begin.size())  // the deepest level holds leaves only
-      moments_kernel<<<grid1(b - a), 256, 0, s>>>((int32_t)a, (int32_t)b, t->nbeg.p, t->nend.p, t->nfirst.p,
-                                                  t->nnchild.p, t->xs.p, t->ms.p, t->com.p, t->mass.p, t->q.p,
-                                                  t->side.p, t->half.p, t->range.p);
+    if (b > a && l + 2 < (int)t->level_begin.size() && l < kMaxLevel)  // the deepest level holds leaves only
+      internal_moments_kernel<<<grid1(b - a), 256, 0, s>>>(l, mpre, t->morder.p, t->nbeg.p, t->nend.p, t->nfirst.p,
+                                                           t->nnchild.p, t->com.p, t->mass.p, t->q.p, t->side.p,
+                                                           t->half.p, t->range.p);
     GT_CUDA(cudaGetLastError());
   }
   // ---- compact walk data
