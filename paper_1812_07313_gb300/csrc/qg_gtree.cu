@@ -41,7 +41,7 @@ int blocks_for(int64_t n, int per_block) {
 // [n+1] long: out[n] receives the total when with_total.
 
 __global__ void scan_block_kernel(int64_t n, const int32_t *__restrict__ in, int64_t *__restrict__ out,
-                                  int64_t *__restrict__ sums) {
+                                  int64_t *__restrict__ sums, int64_t *__restrict__ total) {
   __shared__ int64_t s[kScanThreads];
   const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
   int64_t v[kScanItems];
@@ -65,16 +65,26 @@ __global__ void scan_block_kernel(int64_t n, const int32_t *__restrict__ in, int
     if (base + k < n) out[base + k] = run;
     run += v[k];
   }
-  if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = s[threadIdx.x];
+  if (threadIdx.x == kScanThreads - 1) {
+    sums[blockIdx.x] = s[threadIdx.x];
+    if (total && gridDim.x == 1) *total = s[threadIdx.x];  // one block: its sum is the total
+  }
 }
 
-__global__ void scan_add_kernel(int64_t n, int64_t *__restrict__ out, const int64_t *__restrict__ offs) {
+// out[j] += offs[block of j]; with in and total (the last level of a scan of
+// int32 counts over several blocks), also *total = out[n - 1] + in[n - 1].
+__global__ void scan_add_kernel(int64_t n, int64_t *__restrict__ out, const int64_t *__restrict__ offs,
+                                const int32_t *__restrict__ in, int64_t *__restrict__ total) {
   const int64_t i = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
   const int64_t off = offs[blockIdx.x];
 #pragma unroll
   for (int k = 0; k < kScanItems; k++) {
     const int64_t j = i + (int64_t)k * kScanThreads;
-    if (j < n) out[j] += off;
+    if (j < n) {
+      const int64_t o = out[j] + off;
+      out[j] = o;
+      if (total && j == n - 1) *total = o + (int64_t)in[j];
+    }
   }
 }
 
@@ -107,10 +117,6 @@ __global__ void scan_block64_kernel(int64_t n, const int64_t *__restrict__ in, i
   if (threadIdx.x == kScanThreads - 1) sums[blockIdx.x] = s[threadIdx.x];
 }
 
-__global__ void set_total_kernel(int64_t n, const int32_t *in, int64_t *out) {
-  // out[n] = out[n-1] + in[n-1] (or 0 when n == 0)
-  if (threadIdx.x == 0 && blockIdx.x == 0) out[n] = n > 0 ? out[n - 1] + (int64_t)in[n - 1] : 0;
-}
 
 }  // namespace
 
@@ -188,29 +194,29 @@ qg_status scan_inplace64(qg_gtree *t, int64_t m, int64_t *arr, int lvl, cudaStre
   if (mb > 1) {
     const qg_status st = scan_inplace64(t, mb, t->scan_tmp[lvl].p, lvl + 1, s);
     if (st != QG_OK) return st;
-    scan_add_kernel<<<(unsigned)mb, kScanThreads, 0, s>>>(m, arr, t->scan_tmp[lvl].p);
+    scan_add_kernel<<<(unsigned)mb, kScanThreads, 0, s>>>(m, arr, t->scan_tmp[lvl].p, nullptr, nullptr);
     GT_CUDA(cudaGetLastError());
   }
   return QG_OK;
 }
 
-// out[0..n) = exclusive scan of the int32 counts in; out[n] = their total.
-// out must hold n + 1 elements.
+// out[0..n) = exclusive scan of the int32 counts in; out[n] = their total
+// (written by the scan's last kernel).  out must hold n + 1 elements.
 qg_status scan_excl(qg_gtree *t, int64_t n, const int32_t *in, int64_t *out, cudaStream_t s) {
-  if (n > 0) {
-    const int64_t nb = (n + kScanTile - 1) / kScanTile;
-    GT_CUDA(t->scan_tmp[0].reserve(nb));
-    scan_block_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(n, in, out, t->scan_tmp[0].p);
-    GT_CUDA(cudaGetLastError());
-    if (nb > 1) {
-      const qg_status st = scan_inplace64(t, nb, t->scan_tmp[0].p, 1, s);
-      if (st != QG_OK) return st;
-      scan_add_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(n, out, t->scan_tmp[0].p);
-      GT_CUDA(cudaGetLastError());
-    }
+  if (n == 0) {
+    GT_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), s));
+    return QG_OK;
   }
-  set_total_kernel<<<1, 1, 0, s>>>(n, in, out);
+  const int64_t nb = (n + kScanTile - 1) / kScanTile;
+  GT_CUDA(t->scan_tmp[0].reserve(nb));
+  scan_block_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(n, in, out, t->scan_tmp[0].p, out + n);
   GT_CUDA(cudaGetLastError());
+  if (nb > 1) {
+    const qg_status st = scan_inplace64(t, nb, t->scan_tmp[0].p, 1, s);
+    if (st != QG_OK) return st;
+    scan_add_kernel<<<(unsigned)nb, kScanThreads, 0, s>>>(n, out, t->scan_tmp[0].p, in, out + n);
+    GT_CUDA(cudaGetLastError());
+  }
   return QG_OK;
 }
 
